@@ -1,0 +1,322 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these tests compares the oracle with itself: each checks a closed
+form, an invariant, a special case, a printed value of the paper (Table 1),
+an independent implementation (the NumPy micro-oracle) or a brute-force
+library routine (networkx connected components).
+"""
+import math
+import os
+from concurrent.futures import ProcessPoolExecutor
+from fractions import Fraction
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import lbm_inputs
+import oracle
+from oracle import np_oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# P1: D3Q19 lattice identities (exact rationals)
+# --------------------------------------------------------------------------
+
+def test_lattice_isotropy_exact():
+    c, w, opp = oracle.lattice()
+    wf = [Fraction(x).limit_denominator(100) for x in w]
+    for x, q in zip(w, wf):
+        assert abs(x - float(q)) <= 1e-16
+    assert sorted(set(wf)) == [Fraction(1, 36), Fraction(1, 18), Fraction(1, 3)]
+    assert sum(wf) == 1
+    for i in range(3):
+        assert sum(wf[a] * c[a, i] for a in range(19)) == 0
+        for j in range(3):
+            assert sum(wf[a] * c[a, i] * c[a, j] for a in range(19)) == Fraction(int(i == j), 3)
+            for k in range(3):
+                assert sum(wf[a] * c[a, i] * c[a, j] * c[a, k] for a in range(19)) == 0
+                for l in range(3):
+                    d = lambda p, q: int(p == q)
+                    want = Fraction(d(i, j) * d(k, l) + d(i, k) * d(j, l) + d(i, l) * d(j, k), 9)
+                    got = sum(wf[a] * c[a, i] * c[a, j] * c[a, k] * c[a, l] for a in range(19))
+                    assert got == want
+    # weights by speed class, opposite table, canonical order
+    for a in range(19):
+        assert wf[a] == {0: Fraction(1, 3), 1: Fraction(1, 18), 2: Fraction(1, 36)}[
+            int(c[a] @ c[a])]
+        assert (c[opp[a]] == -c[a]).all()
+    assert (c[0] == 0).all()
+    assert [tuple(v) for v in c[1:7]] == [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0),
+                                          (0, 0, 1), (0, 0, -1)]
+    assert len({tuple(v) for v in c}) == 19
+
+
+# --------------------------------------------------------------------------
+# P2: moments of the equilibrium (Eq. 2 with reading R1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rho,u", [(1.0, (0.0, 0.0, 0.0)), (2.7, (0.03, -0.01, 0.02)),
+                                   (0.07, (-0.1, 0.05, 0.08))])
+def test_equilibrium_moments(rho, u):
+    c, w, _ = oracle.lattice()
+    fe = oracle.feq(rho, u)
+    u = np.array(u)
+    assert abs(fe.sum() - rho) <= 1e-15 * rho
+    np.testing.assert_allclose(c.T @ fe, rho * u, atol=1e-15 * rho)
+    pi = np.einsum("ai,aj,a->ij", c, c, fe)
+    np.testing.assert_allclose(pi, rho / 3.0 * np.eye(3) + rho * np.outer(u, u), atol=2e-15 * rho)
+    if not u.any():
+        np.testing.assert_array_equal(fe, w * rho)
+
+
+def test_psi_functional():
+    # psi = rho0 (1 - exp(-rho / rho0)) (text after Eq. 5); psi = rho form for tests
+    assert oracle.psi(0.0) == 0.0
+    assert abs(oracle.psi(math.log(2.0)) - 0.5) < 1e-16
+    assert abs(oracle.psi(50.0) - 1.0) < 1e-16
+    assert abs(oracle.psi(1.0, 0, 2.0) - 2.0 * (1 - math.exp(-0.5))) < 1e-15
+    assert oracle.psi(1.7, 1) == 1.7
+
+
+# --------------------------------------------------------------------------
+# P3: uniform states are fixed points (F = 0 for uniform psi)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("u0", [(0.0, 0.0, 0.0), (0.04, -0.02, 0.01)])
+def test_uniform_fixed_point(u0):
+    rho0 = 0.7
+    fe = oracle.feq(rho0, u0)
+    f = np.broadcast_to(fe[:, None, None, None], (19, 4, 5, 6)).copy()
+    g = oracle.step(f, tau=0.8, G=-6.0, nsteps=50)
+    np.testing.assert_allclose(g, f, rtol=2e-15, atol=0)
+
+
+# --------------------------------------------------------------------------
+# P4: single-phase BGK shear wave (G = 0): decay exp(-nu k^2 t),
+# nu = (tau - 1/2)/3, and advection by a uniform stream (streaming direction)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tau,U", [(0.8, 0.0), (1.2, 0.0), (0.9, 0.05)])
+def test_shear_wave_decay_and_advection(tau, U):
+    nx, ny, nz = 64, 3, 3
+    k = 2 * math.pi / nx
+    A0 = 1e-3
+    x = np.arange(nx)
+    f = np.zeros((19, nz, ny, nx))
+    for i in range(nx):
+        f[:, :, :, i] = oracle.feq(1.0, (U, A0 * math.sin(k * i), 0.0))[:, None, None]
+
+    def amp_phase(g):
+        rho, ux, uy, uz = oracle.moments(g, G=0.0, bare=True)
+        prof = uy[0, 0]
+        z = (prof * np.exp(-1j * k * x)).sum() * 2 / nx
+        return abs(z), np.angle(z)
+
+    t1, t2 = 200, 1200
+    g1 = oracle.step(f, tau, 0.0, t1)
+    g2 = oracle.step(g1, tau, 0.0, t2 - t1)
+    a1, p1 = amp_phase(g1)
+    a2, p2 = amp_phase(g2)
+    nu = (tau - 0.5) / 3.0
+    rate = -math.log(a2 / a1) / (t2 - t1)
+    assert abs(rate / (nu * k * k) - 1.0) < 0.01
+    # a pattern advected by +U: the phase of sin(k(x - U t)) drops by k U t
+    err = ((p2 - p1) + k * U * (t2 - t1) + math.pi) % (2 * math.pi) - math.pi
+    assert abs(err) < 0.02
+
+
+# --------------------------------------------------------------------------
+# P5: conservation — mass, and total momentum (sum_x F = 0 on a periodic box)
+# --------------------------------------------------------------------------
+
+def test_mass_and_momentum_conservation():
+    c, _, _ = oracle.lattice()
+    f = lbm_inputs.random_populations(12, 10, 8, seed=7)
+    M0 = f.sum()
+    J0 = np.einsum("ak,azyx->k", c.astype(float), f)
+    g = oracle.step(f, tau=0.9, G=-5.5, nsteps=300)
+    assert abs(g.sum() - M0) / M0 <= 1e-13
+    J1 = np.einsum("ak,azyx->k", c.astype(float), g)
+    assert np.abs(J1 - J0).max() <= 1e-12 * M0
+    # the force field itself sums to zero
+    F = oracle.force(f, G=-5.5)
+    assert np.abs(F.sum(axis=(1, 2, 3))).max() <= 1e-13 * np.abs(F).sum()
+
+
+# --------------------------------------------------------------------------
+# P6: brute force against the independent NumPy oracle
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape,tau,G,form", [((8, 8, 8), 0.8, -5.5, 0), ((5, 3, 7), 1.0, -6.0, 0),
+                                              ((6, 4, 5), 0.7, -1.0, 1)])
+def test_c_oracle_vs_numpy_oracle(shape, tau, G, form):
+    nx, ny, nz = shape
+    c, _, _ = oracle.lattice()
+    p = np_oracle.perm_to(c)            # numpy index of the oracle's direction a
+    f = lbm_inputs.random_populations(nx, ny, nz, seed=11, smooth=False, rho_lo=0.3, rho_hi=2.0)
+    g_c = oracle.step(f, tau, G, nsteps=20, psi_form=form)
+    fn = np.zeros_like(f)
+    fn[p] = f
+    g_np = np_oracle.run(fn, tau, G, 20, form)[p]
+    assert np.abs(g_c - g_np).max() <= 1e-13 * np.abs(g_np).max()
+
+
+def test_step_nodes_matches_full_step():
+    f = lbm_inputs.random_populations(9, 7, 6, seed=3)
+    full = oracle.step(f, 0.85, -5.8, 1)
+    nodes = np.array([0, 1, 8, 9, 62, 63, 100, 377])
+    got = oracle.step_nodes(f, nodes, 0.85, -5.8)
+    want = full.reshape(19, -1)[:, nodes].T
+    np.testing.assert_allclose(got, want, rtol=1e-15, atol=0)
+
+
+# --------------------------------------------------------------------------
+# P7: Table 1 — flat-interface coexistence densities at G = -5.3
+# --------------------------------------------------------------------------
+
+def _table1():
+    rows = []
+    with open(os.path.join(GOLDEN, "table1.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append([float(v) for v in line.split()])
+    return rows
+
+
+def tau_from_oh(R0, rho_l, sigma, Oh=0.1):
+    """tau from Oh = nu sqrt(rho_l / (sigma R0)), nu = (tau - 1/2)/3 (reading R10)."""
+    nu = Oh * math.sqrt(sigma * R0 / rho_l)
+    return 0.5 + 3.0 * nu
+
+
+def _coex(tau):
+    import oracle as o
+    r = o.coexistence(tau, -5.3, n=64, tol=1e-10, rho_l0=2.1, rho_v0=0.1)
+    return r["rho_l"], r["rho_v"]
+
+
+def test_table1_coexistence_densities():
+    rows = _table1()
+    assert len(rows) == 7
+    taus = [tau_from_oh(R0, rl, s) for R0, rl, rv, s in rows]
+    # the Oh = 0.1 reading gives tau from 0.624 (R0 = 7) to 1.035 (R0 = 84)
+    assert abs(taus[0] - 0.624) < 1e-3 and abs(taus[-1] - 1.035) < 1e-3
+    with ProcessPoolExecutor(max_workers=min(7, os.cpu_count() or 1),
+                             mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_coex, taus))
+    for (R0, rl, rv, s), (ol, ov) in zip(rows, res):
+        assert abs(ol - rl) <= 0.003, (R0, ol, rl)
+        assert abs(ov - rv) <= 0.002, (R0, ov, rv)
+
+
+# --------------------------------------------------------------------------
+# Ligament initial condition (set-up section, readings R9, R11-R13)
+# --------------------------------------------------------------------------
+
+def test_ligament_init_geometry():
+    nx, ny, nz = 32, 25, 25
+    R0, lam, eps, ph, rl, rv, W = 6.0, 32.0, 0.1, 0.4, 2.6, 0.07, 2.0
+    f = oracle.init_ligament(nx, ny, nz, R0, lam, eps, ph, rl, rv, W)
+    c, w, _ = oracle.lattice()
+    rho = f.sum(axis=0)
+    # zero velocity, populations proportional to the weights
+    np.testing.assert_allclose(f / rho[None], np.broadcast_to(w[:, None, None, None], f.shape),
+                               rtol=1e-15)
+    assert np.abs(np.einsum("ak,azyx->kzyx", c.astype(float), f)).max() < 1e-15
+    # axis symmetry about y = z = 12 (the centre node of a 25-wide section)
+    np.testing.assert_allclose(rho, rho[:, ::-1, :], rtol=1e-15)
+    np.testing.assert_allclose(rho, rho[::-1, :, :], rtol=1e-15)
+    np.testing.assert_allclose(rho, np.transpose(rho, (1, 0, 2)), rtol=1e-15)
+    # deep inside / far outside, within the tanh tail exp(-2 * 2 * 5.4 / W)
+    assert abs(rho[12, 12, 0] - rl) < 1e-5 and abs(rho[0, 0, 0] - rv) < 1e-8
+    # half-level radius along +y recovered by inverting the profile at the node
+    # nearest the interface: mean R0, amplitude eps*R0, maximum where the
+    # phase 2 pi x / lam + ph is 0 (mod 2 pi)
+    est = []
+    for x in range(nx):
+        prof = rho[12, 12:, x]
+        r = int(np.argmin(np.abs(prof - 0.5 * (rl + rv))))
+        t = 1.0 - 2.0 * (prof[r] - rv) / (rl - rv)
+        est.append(r - W / 2.0 * math.atanh(t))
+    est = np.array(est)
+    assert abs(est.mean() - R0) < 1e-9
+    assert abs((est.max() - est.min()) / 2 - eps * R0) < 0.02 * eps * R0
+    xs = np.arange(nx)
+    z = (est * np.exp(-2j * math.pi * xs / lam)).sum() * 2 / nx
+    assert abs(abs(z) - eps * R0) < 1e-9 and abs(np.angle(z) - ph) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# Connected components (droplet count) against networkx
+# --------------------------------------------------------------------------
+
+def _nx_components(mask):
+    import networkx as nx_
+    nz, ny, nx = mask.shape
+    g = nx_.Graph()
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                if not mask[z, y, x]:
+                    continue
+                g.add_node((z, y, x))
+                for dz, dy, dx in ((0, 0, 1), (0, 1, 0), (1, 0, 0)):
+                    q = ((z + dz) % nz, (y + dy) % ny, (x + dx) % nx)
+                    if mask[q]:
+                        g.add_edge((z, y, x), q)
+    return sorted(len(cc) for cc in nx_.connected_components(g))
+
+
+@pytest.mark.parametrize("seed,shape,p", [(1, (5, 6, 7), 0.3), (2, (4, 4, 4), 0.45),
+                                          (3, (3, 8, 5), 0.25), (4, (6, 5, 9), 0.35)])
+def test_ccl_vs_networkx(seed, shape, p):
+    mask = lbm_inputs.uniform(seed, int(np.prod(shape))).reshape(shape) < p
+    n, labels, sizes = oracle.ccl(mask)
+    want = _nx_components(mask)
+    assert n == len(want)
+    assert sorted(sizes.tolist()) == want
+    assert ((labels >= 0) == mask).all()
+
+
+def test_ccl_periodic_wrap():
+    mask = np.zeros((5, 5, 8), dtype=bool)
+    mask[2, 2, :] = True                 # a line through the x boundary: one component
+    mask[0, 0, 0] = mask[4, 0, 0] = True  # joined across z
+    n, _, sizes = oracle.ccl(mask)
+    assert n == 2 and sorted(sizes.tolist()) == [2, 8]
+    mask[2, 2, 3] = False                # cut once: the ring is still one piece
+    assert oracle.ccl(mask)[0] == 2
+    mask[2, 2, 6] = False                # cut twice: two pieces
+    assert oracle.ccl(mask)[0] == 3
+
+
+# --------------------------------------------------------------------------
+# Diagnostics against an independent numpy evaluation
+# --------------------------------------------------------------------------
+
+def test_diagnostics_vs_numpy():
+    nx, ny, nz = 20, 16, 16
+    rl, rv = 2.6, 0.07
+    f = oracle.init_ligament(nx, ny, nz, 4.0, 20.0, 0.3, 0.0, rl, rv, 2.0)
+    f = oracle.step(f, 1.0, -6.0, 5)
+    d, sw, sn = oracle.diagnostics(f, rl, rv, slices=True)
+    c, _, _ = oracle.lattice()
+    rho = f.sum(axis=0)
+    j = np.einsum("ak,azyx->kzyx", c.astype(float), f)
+    phi = np.clip((rho - rv) / (rl - rv), 0, 1)
+    liq = rho > 0.5 * (rl + rv)
+    assert abs(d["mass"] - rho.sum()) <= 1e-12 * rho.sum()
+    np.testing.assert_allclose([d["mom_x"], d["mom_y"], d["mom_z"]], j.sum(axis=(1, 2, 3)),
+                               atol=1e-12 * rho.sum())
+    assert abs(d["liquid_volume_w"] - phi.sum()) <= 1e-12 * phi.sum()
+    assert d["liquid_count"] == liq.sum()
+    np.testing.assert_allclose(sw, phi.sum(axis=(0, 1)), rtol=1e-12)
+    np.testing.assert_array_equal(sn, liq.sum(axis=(0, 1)))
+    assert d["min_slice_count"] == liq.sum(axis=(0, 1)).min()
+    assert d["min_slice_x"] == int(np.argmin(liq.sum(axis=(0, 1))))
+    assert abs(d["max_u"] - (np.sqrt((j ** 2).sum(axis=0)) / rho).max()) < 1e-15
+    assert d["numeric_ok"] == 1.0
+    assert abs(d["neck_radius"] - math.sqrt(phi.sum(axis=(0, 1)).min() / math.pi)) < 1e-12
