@@ -1,0 +1,347 @@
+"""Benchmark of the D3Q19 Shan-Chen time step: GLUPS and fraction of the HBM roofline.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: the grid-convergence ligament, periodic 256 x 128 x 128 (4.19 M
+nodes), R0 = 32, lambda = 256, eps = 0.02, tau = 1, G = -6, psi =
+1 - exp(-rho), FP32 storage and arithmetic, A-B streaming; liquid and
+vapour densities from a flat-interface run on the GPU.  One benchmark step
+= 10 lattice time steps (psi pass + fused force/collide/stream each) plus
+the FP64 diagnostics of the state (mass, momentum, liquid volume, neck
+area), the diagnostic interval of this workload.  The populations (637 MB
+for both arrays) exceed the 129 MB L2, so no cache flush is needed between
+steps.
+
+--impl reference times the CPU FP64 oracle on this machine's cores on the
+same box (one lattice step per benchmark step, a bounded sample).
+With N > 1 (torchrun) every rank runs its own replica: the step has no
+data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lbm_inputs  # noqa: E402
+
+WORKLOAD = lbm_inputs.GRID_256
+LBM_PER_STEP = 10
+METRIC = "D3Q19 Shan-Chen GLUPS (giga lattice-node updates per second)"
+UNIT = "GLUPS"
+# algorithmic bytes per lattice update of the collide-stream kernel (FP32):
+# read 19 f + write 19 f + read psi(x) once
+K2_BYTES_PER_LU = {"f64": 19 * 8 * 2 + 8, "f32": 19 * 4 * 2 + 4, "f16dev": 19 * 2 * 2 + 4,
+                   "bf16dev": 19 * 2 * 2 + 4}
+# two-pass model of the whole step (psi pass reads 19 f and writes psi)
+STEP_BYTES_PER_LU = {"f64": 3 * 19 * 8 + 16, "f32": 3 * 19 * 4 + 8, "f16dev": 3 * 19 * 2 + 8,
+                     "bf16dev": 3 * 19 * 2 + 8}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(precision: str):
+    """DRAM bytes per collide-stream launch from the committed ncu summary, if
+    it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "collide_stream_traffic.json")
+    src = os.path.join(ROOT, "paper_1904_11792_gb300", "csrc", "lbm_step.cu")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    with open(src, "rb") as fh:
+        digest = hashlib.sha256(fh.read()).hexdigest()
+    if d.get("kernel_source_sha256") != digest:
+        return None
+    e = d.get("workloads", {}).get(precision)
+    if not e:
+        return None
+    return float(e["dram_bytes_per_launch_full_size"])
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), hw=parts[5],
+                                 hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                            ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["smax"] for r in rows), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def coexistence_densities(G, tau):
+    from paper_1904_11792_gb300.coexistence import coexistence
+    r = coexistence(G, tau, n=64, tol=1e-10)
+    return r["rho_l"], r["rho_v"]
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1904_11792_gb300 import build, lbm as L
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    build.build()
+    L.load()
+    w = WORKLOAD
+    N = w.nodes
+    if args.rho_l and args.rho_v:
+        rho_l, rho_v = args.rho_l, args.rho_v
+    else:
+        rho_l, rho_v = coexistence_densities(w.G, w.tau)
+    lat = L.Lattice(w.nx, w.ny, w.nz, w.tau, w.G, precision=args.precision, pattern=args.pattern,
+                    rho_ref=rho_v if args.precision.endswith("dev") else 0.0)
+    lat.init_ligament(w.R0, w.lam, w.eps, w.phase, rho_l, rho_v, w.width)
+    stream = torch.cuda.current_stream()
+
+    def bench_step():
+        lat.step(LBM_PER_STEP)
+        return lat.diagnostics()
+
+    for _ in range(args.warmup):
+        bench_step()
+    lat.sync()
+    # ---- timed region: device time, kernel events on the library's stream ----
+    lat.set_option("kernel_timing", 1)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            d = bench_step()
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = t0.elapsed_time(t1)
+    n_psi, ms_psi = L.lbm_kernel_time(lat.h, 0)
+    n_k2, ms_k2 = L.lbm_kernel_time(lat.h, 1)
+    lat.set_option("kernel_timing", 0)
+    lat.sync()
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    lbm_steps = args.steps * LBM_PER_STEP
+    value = world * N * lbm_steps / (ms * 1e-3) / 1e9
+    # ---- end to end through the C ABI with pinned host buffers ----
+    e2e = None if args.no_extras else run_e2e(args, lat, L, torch, N)
+    peak, peak_kind = peaks()
+    k2_avg = ms_k2 / max(n_k2, 1)
+    achieved = K2_BYTES_PER_LU[args.precision] * N / (k2_avg * 1e-3) / 1e9
+    traffic = ncu_traffic(args.precision)
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "f32" else args.precision,
+        "data": "synthetic (seeded ligament initial condition, no dataset)",
+        "config": {
+            "workload": "ligament %dx%dx%d R0=%g lambda=%g eps=%g tau=%g G=%g, %s storage, %s "
+                        "streaming" % (w.nx, w.ny, w.nz, w.R0, w.lam, w.eps, w.tau, w.G,
+                                       args.precision, args.pattern.upper()),
+            "nodes": N, "lattice_steps_per_step": LBM_PER_STEP, "diagnostics_every": LBM_PER_STEP,
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "no flush: populations %.0f MB > 129 MB L2" % (
+                2 * 19 * N * (4 if args.precision == "f32" else 8 if args.precision == "f64" else 2)
+                / 1e6),
+            "rho_l": round(rho_l, 6), "rho_v": round(rho_v, 6),
+            "step_model_bytes_per_lu": STEP_BYTES_PER_LU[args.precision],
+            "hbm_frac_step_model": round(value / world * STEP_BYTES_PER_LU[args.precision] / peak, 4),
+        },
+        "roofline": {"bound": "hbm", "kernel": "collide_stream", "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "peak_source": peak_kind,
+                     "traffic": traffic, "bytes_per_lu": K2_BYTES_PER_LU[args.precision],
+                     "avg_launch_ms": round(k2_avg, 5), "launches": n_k2,
+                     "psi_pass_avg_ms": round(ms_psi / max(n_psi, 1), 5)},
+        "e2e": e2e,
+        "gpu_launches": int(args.steps * (2 * LBM_PER_STEP + 2)),
+        "clocks": clocks,
+        "diag_last": {"mass": d["mass"], "neck_radius": d["neck_radius"], "step": d["step"]},
+    }
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["cpu_baseline"] = cpu_baseline(w, rho_l, rho_v)
+    lat.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, lat, L, torch, N):
+    """Same metric through the C ABI with host buffers: the state is loaded
+    from pinned host memory, stepped with a diagnostics read-back every
+    benchmark step, and the final density field is read back."""
+    lib = L.load()
+    nbytes = L.lbm_state_bytes(lat.h)
+    host_state = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    rc = lib.lbm_save_state(lat.h, ctypes.c_void_p(host_state.data_ptr()), nbytes)
+    L.check(rc)
+    host_rho = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    diag = L.lbm_diag()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L.check(lib.lbm_load_state(lat.h, ctypes.c_void_p(host_state.data_ptr()), nbytes))
+    for _ in range(args.steps):
+        L.check(lib.lbm_step(lat.h, LBM_PER_STEP))
+        L.check(lib.lbm_diagnostics(lat.h, ctypes.byref(diag), 0))
+    L.check(lib.lbm_moments(lat.h, ctypes.c_void_p(host_rho.data_ptr()), None, None, None))
+    t1 = time.perf_counter()
+    steps = args.steps * LBM_PER_STEP
+    return {"value": round(N * steps / (t1 - t0) / 1e9, 4), "unit": UNIT,
+            "h2d_bytes_per_step": int(nbytes // args.steps),
+            "d2h_bytes_per_step": int(ctypes.sizeof(diag) + 8 * N // args.steps)}
+
+
+def cpu_baseline(w, rho_l, rho_v, budget_s: float = 12.0):
+    """The oracle, as it stands, on this machine's cores: FP64 A-B steps of the
+    same 256x128x128 ligament, as many as fit in about budget_s seconds."""
+    import oracle
+    f = oracle.init_ligament(w.nx, w.ny, w.nz, w.R0, w.lam, w.eps, w.phase, rho_l, rho_v, w.width)
+    t = time.perf_counter()
+    f = oracle.step(f, w.tau, w.G, 1)
+    one = time.perf_counter() - t
+    n = max(1, min(200, int(budget_s / max(one, 1e-3))))
+    t = time.perf_counter()
+    oracle.step(f, w.tau, w.G, n)
+    el = time.perf_counter() - t
+    return {"value": round(w.nodes * n / el / 1e9, 6), "unit": UNIT,
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d FP64 A-B steps of the %dx%dx%d ligament (%.1f s)" % (
+                n, w.nx, w.ny, w.nz, el)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    w = WORKLOAD
+    rc = oracle.coexistence(w.tau, w.G, n=64, tol=1e-10, rho_l0=2.6, rho_v0=0.07)
+    f = oracle.init_ligament(w.nx, w.ny, w.nz, w.R0, w.lam, w.eps, w.phase, rc["rho_l"],
+                             rc["rho_v"], w.width)
+    for _ in range(args.warmup):
+        f = oracle.step(f, w.tau, w.G, 1)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle.step(f, w.tau, w.G, 1)
+    el = time.perf_counter() - t
+    value = w.nodes * args.steps / el / 1e9
+    sample = "%d FP64 A-B lattice steps of the %dx%dx%d ligament, one per benchmark step" % (
+        args.steps, w.nx, w.ny, w.nz)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(el * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded ligament initial condition, no dataset)",
+        "config": {"workload": "ligament %dx%dx%d R0=%g lambda=%g eps=%g tau=%g G=%g, CPU FP64 "
+                               "oracle" % (w.nx, w.ny, w.nz, w.R0, w.lam, w.eps, w.tau, w.G),
+                   "nodes": w.nodes},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("f32", "f64", "f16dev", "bf16dev"), default="f32")
+    ap.add_argument("--pattern", choices=("ab", "aa"), default="ab")
+    ap.add_argument("--rho-l", type=float, default=None,
+                    help="liquid density (with --rho-v: skip the flat-interface run)")
+    ap.add_argument("--rho-v", type=float, default=None)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the end-to-end and CPU-baseline legs (profiling runs)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

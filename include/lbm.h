@@ -1,0 +1,206 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) D3Q19 pseudo-potential lattice
+ * Boltzmann library, liblbm.so.
+ *
+ * The library advances the single-relaxation-time D3Q19 lattice Boltzmann
+ * equation with single-belt Shan-Chen forcing on a periodic Cartesian
+ * lattice, as defined in Chiappini, Xue, Falcucci, Sbragaglia, "Ligament
+ * break-up simulation through pseudo-potential Lattice Boltzmann Method"
+ * (arXiv:1904.11792), section "Numerical model":
+ *   Eq. 4   rho = sum_a f_a,  rho u = sum_a c_a f_a
+ *   psi(rho) = rho0 (1 - exp(-rho / rho0))   (definition after Eq. 5)
+ *   Eq. 5   F = -G psi(x) sum_a w_a psi(x + c_a) c_a
+ *   Eq. 6   u' = u + tau F / rho
+ *   Eq. 2   f_eq(rho, u') = w_a rho [1 + c.u'/cs2 + (c.u')^2/(2 cs2^2) - u'.u'/(2 cs2)]
+ *           (the leading 1 is missing in the paper's print; cs2 = 1/3)
+ *   Eq. 3   f_a(x + c_a, t + 1) = f_a - (f_a - f_eq_a) / tau   (force only via Eq. 6)
+ * The test case is the perturbed liquid ligament of section "Ligament
+ * set-up" (Plateau-Rayleigh break-up).
+ *
+ * Conventions
+ *  - Every call returns an int status (LBM_OK = 0 on success) except the
+ *    constructors, which return a handle or NULL; after NULL (or any error)
+ *    lbm_last_error() gives a message (per host thread).
+ *  - No C++ exception crosses this interface.
+ *  - Node index i = x + nx * (y + ny * z), x fastest.  N = nx * ny * nz.
+ *  - Canonical population arrays (lbm_get/set_populations) are float64,
+ *    19 * N values, direction-major: f[a * N + i], holding the
+ *    pre-collision populations of the current time step.
+ *  - Canonical direction order (a = 0..18): rest; +x, -x, +y, -y, +z, -z;
+ *    then opposite pairs (+x+y, -x-y), (+x-y, -x+y), (+x+z, -x-z),
+ *    (+x-z, -x+z), (+y+z, -y-z), (+y-z, -y+z).  Weights 1/3, 1/18, 1/36.
+ *  - Host arrays are owned by the caller and must hold the sizes stated.
+ *    The library owns all device memory it allocates; buffers passed in
+ *    lbm_config.ext_* stay owned by the caller and must outlive the handle.
+ *  - A handle is not thread-safe.  All its GPU work goes to one CUDA
+ *    stream (lbm_set_stream); calls that return host data synchronise it.
+ *  - The library runs only on a CUDA device of compute capability 10.3
+ *    (built for sm_103a); there is no CPU fallback.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_Q 19
+
+/* Status codes. */
+enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,      /* invalid argument (sizes, tau <= 1/2, non-finite values ...) */
+    LBM_ERR_CUDA = 2,     /* a CUDA runtime call failed; see lbm_last_error()              */
+    LBM_ERR_OOM = 3,      /* device allocation failed (or exceeded LBM_ALLOC_CAP_BYTES)    */
+    LBM_ERR_NUMERIC = 4,  /* a density became non-positive or non-finite                   */
+    LBM_ERR_TIMEOUT = 5,  /* a bounded device wait gave up                                 */
+    LBM_ERR_STATE = 6     /* call not valid in the current state (e.g. no init yet)        */
+};
+
+/* Pseudo-potential functional psi(rho). */
+enum {
+    LBM_PSI_EXP = 0, /* psi = rho0 (1 - exp(-rho / rho0)), the paper's choice (after Eq. 5) */
+    LBM_PSI_RHO = 1  /* psi = rho (a test functional)                                       */
+};
+
+/* Storage precision of the populations.  Arithmetic is FP64 for LBM_F64
+ * and FP32 otherwise.  The *DEV forms store g_a = f_a - w_a rho_ref. */
+enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16DEV = 2, LBM_BF16DEV = 3 };
+
+/* Streaming pattern: two arrays (A-B, push), or one array updated in place
+ * with alternating even/odd steps (AA). */
+enum { LBM_AB = 0, LBM_AA = 1 };
+
+typedef struct lbm_ctx *lbm_handle;
+
+typedef struct {
+    int nx, ny, nz;        /* lattice size, each >= 3                               */
+    double tau;            /* relaxation time, > 1/2 (Eq. 3)                         */
+    double G;              /* interaction strength of Eq. 5 (signed; < 0 attracts)   */
+    int psi_form;          /* LBM_PSI_EXP or LBM_PSI_RHO                             */
+    double rho0;           /* reference density of psi, > 0 (paper: 1)               */
+    int precision;         /* LBM_F64, LBM_F32, LBM_F16DEV, LBM_BF16DEV              */
+    int pattern;           /* LBM_AB or LBM_AA                                       */
+    double rho_ref;        /* deviation reference density of the *DEV storage forms  */
+    int block_x, block_y, block_z; /* collide-stream block shape, 0 = default        */
+    void *ext_state;       /* optional caller device buffer for the populations      */
+    size_t ext_state_bytes;
+    void *ext_psi;         /* optional caller device buffer for psi                  */
+    size_t ext_psi_bytes;
+    void *stream;          /* cudaStream_t to use (cudaStreamLegacy = (void*)1 for the
+                              legacy default stream); NULL = a new non-blocking stream */
+} lbm_config;
+
+/* Diagnostics of the current state, all sums in FP64 with a fixed
+ * reduction order (bitwise reproducible).  Liquid means
+ * rho > (rho_l + rho_v) / 2 with the densities given at initialisation
+ * (or set by lbm_set_option "rho_l"/"rho_v"); phi = clamp((rho - rho_v) /
+ * (rho_l - rho_v), 0, 1) is the weighted liquid fraction. */
+typedef struct {
+    long long step;            /* time steps done                                  */
+    double mass;               /* sum_i rho_i                                      */
+    double mom[3];             /* sum_i j_i (bare momentum, Eq. 4)                 */
+    double liquid_volume_w;    /* sum_i phi_i                                      */
+    long long liquid_count;    /* number of liquid nodes                           */
+    double min_slice_area_w;   /* min over x of sum_{y,z} phi                      */
+    long long min_slice_count; /* min over x of the liquid nodes of slice x        */
+    int min_slice_x;           /* first x where min_slice_count is reached         */
+    double neck_radius;        /* sqrt(min_slice_area_w / pi)                      */
+    double max_u;              /* max_i |j_i| / rho_i                              */
+    double rho_min, rho_max;
+    int droplets;              /* connected liquid components (6-conn., periodic),
+                                  -1 when not requested                            */
+    int droplets_min8;         /* components with at least 8 nodes, -1 if not run  */
+    long long largest_droplet; /* node count of the largest component, -1 if not run */
+    int numeric_ok;            /* 1 if every rho is finite and positive            */
+} lbm_diag;
+
+/* Fills cfg with defaults: F32, AB, psi form EXP, rho0 = 1, rho_ref = 0,
+ * default block shape, no external buffers, library stream. */
+void lbm_config_default(lbm_config *cfg);
+
+/* Device bytes the populations and psi need for cfg (for ext_* buffers). */
+int lbm_required_bytes(const lbm_config *cfg, size_t *state_bytes, size_t *psi_bytes);
+
+/* Creates a lattice.  lbm_create is lbm_create_ex with the defaults above
+ * (FP32, A-B).  The populations are zero until an init call.  Returns NULL
+ * on error (LBM_ERR_ARG / CUDA / OOM in lbm_last_error()). */
+lbm_handle lbm_create(int nx, int ny, int nz, double tau, double G, int psi_form);
+lbm_handle lbm_create_ex(const lbm_config *cfg);
+void lbm_destroy(lbm_handle h);
+
+const char *lbm_last_error(void);
+const char *lbm_strerror(int status);
+
+/* The canonical direction table: c[a * 3 + k] (k = x, y, z) and w[a]. */
+int lbm_lattice(int *c, double *w);
+
+/* Uses the given cudaStream_t (NULL = the library's own stream;
+ * (void*)1 = cudaStreamLegacy). */
+int lbm_set_stream(lbm_handle h, void *stream);
+
+/* Named options (value as double): "tau", "G", "rho_l", "rho_v",
+ * "graph" (0/1: replay captured CUDA graphs in lbm_step, default 1),
+ * "kernel_timing" (0/1: record CUDA events around every kernel of lbm_step;
+ * disables graphs), "block_x", "block_y", "block_z" (collide-stream block
+ * shape).  lbm_get_option also answers "step", "nx", "ny", "nz",
+ * "precision", "pattern". */
+int lbm_set_option(lbm_handle h, const char *key, double value);
+int lbm_get_option(lbm_handle h, const char *key, double *value);
+
+/* Ligament initial condition (section "Ligament set-up", Fig. 1):
+ * R(x) = R0 (1 + eps cos(2 pi x / lambda + phase)), axis at
+ * ((ny-1)/2, (nz-1)/2), rho = rho_v + (rho_l - rho_v)/2 [1 - tanh(2 (r - R(x)) / width)],
+ * f_a = w_a rho (zero velocity).  Resets the step count to 0.
+ * Requires rho_l > rho_v > 0, width > 0, lambda > 0. */
+int lbm_init_ligament(lbm_handle h, double R0, double lambda, double eps, double phase,
+                      double rho_l, double rho_v, double width);
+
+/* Same geometry, rho = prof(r - R(x)) from n >= 2 samples prof[k] at
+ * d0 + k dd (linear interpolation, clamped).  prof is a host array; rho_l
+ * and rho_v (thresholds of the diagnostics) are set to prof's largest and
+ * smallest value. */
+int lbm_init_profile(lbm_handle h, double R0, double lambda, double eps, double phase,
+                     const double *prof, int n, double d0, double dd);
+
+/* Enqueues n >= 0 time steps (psi pass, then fused force + collision +
+ * streaming) on the handle's stream and returns without waiting. */
+int lbm_step(lbm_handle h, int n);
+
+/* Waits for the handle's stream; LBM_ERR_NUMERIC if any psi pass since
+ * the last check met a non-positive or non-finite density. */
+int lbm_sync(lbm_handle h);
+
+/* Macroscopic fields of the current state into host arrays of N doubles:
+ * rho (Eq. 4) and u = (j + F/2) / rho with F of Eq. 5.  Any pointer may
+ * be NULL.  Synchronises. */
+int lbm_moments(lbm_handle h, double *rho, double *ux, double *uy, double *uz);
+
+/* Diagnostics (see lbm_diag); want_ccl != 0 also labels the liquid
+ * components on the GPU.  Synchronises. */
+int lbm_diagnostics(lbm_handle h, lbm_diag *out, int want_ccl);
+
+/* Canonical populations (see Conventions), host arrays of 19 * N doubles.
+ * set converts to the storage precision (round to nearest even). */
+int lbm_get_populations(lbm_handle h, double *host);
+int lbm_set_populations(lbm_handle h, const double *host);
+
+/* Raw checkpoint: the storage bytes plus a small header (layout, size,
+ * step count).  lbm_load_state restores it bitwise into a handle of the
+ * same size, precision and pattern. */
+int lbm_state_bytes(lbm_handle h, size_t *bytes);
+int lbm_save_state(lbm_handle h, void *host, size_t bytes);
+int lbm_load_state(lbm_handle h, const void *host, size_t bytes);
+
+/* Kernel timing (option "kernel_timing"): launches and summed device time
+ * in ms of kernel class k since the option was set, k = 0 psi pass,
+ * 1 collide-stream.  Synchronises. */
+int lbm_kernel_time(lbm_handle h, int k, long long *launches, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

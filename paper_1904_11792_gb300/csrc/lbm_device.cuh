@@ -1,0 +1,137 @@
+// Device-side definitions shared by the kernels of liblbm.so: the D3Q19
+// lattice, the storage-precision traits and the periodic index helper.
+//
+// D3Q19 (paper, section "Numerical model": 19 velocities, weights
+// normalised to unity): c_0 = 0 with w = 1/3, the six +-e_i with w = 1/18,
+// the twelve +-e_i +- e_j with w = 1/36, cs^2 = 1/3.  Directions are in the
+// library's canonical order (rest, +x,-x,+y,-y,+z,-z, then opposite pairs of
+// diagonals), so opp(a) = a + 1 for odd a and a - 1 for even a > 0.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm.h"
+
+namespace lbm {
+
+constexpr int Q = 19;
+
+// Components of c_a.  Written as constexpr functions so that, inside fully
+// unrolled loops over a, every use folds to an immediate.
+__host__ __device__ constexpr int cx(int a) {
+  return (a == 1 || a == 7 || a == 9 || a == 11 || a == 13) ? 1
+         : (a == 2 || a == 8 || a == 10 || a == 12 || a == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int a) {
+  return (a == 3 || a == 7 || a == 10 || a == 15 || a == 17) ? 1
+         : (a == 4 || a == 8 || a == 9 || a == 16 || a == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz(int a) {
+  return (a == 5 || a == 11 || a == 14 || a == 15 || a == 18) ? 1
+         : (a == 6 || a == 12 || a == 13 || a == 16 || a == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
+__host__ __device__ constexpr double wgt(int a) {
+  return a == 0 ? 1.0 / 3.0 : (a <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// Storage traits.  T = stored type, C = compute type.  The *DEV forms store
+// the deviation g_a = f_a - w_a rho_ref and add it back on load.  load()
+// goes through the read-only data path and is only used on arrays the kernel
+// does not write; load_rw() is a plain load for in-place (AA) updates.
+template <int P> struct Prec;
+template <> struct Prec<LBM_F64> {
+  using T = double;
+  using C = double;
+  static constexpr bool dev = false;
+  __device__ static __forceinline__ C load(const T* p, C) { return __ldg(p); }
+  __device__ static __forceinline__ C load_rw(const T* p, C) { return *p; }
+  __device__ static __forceinline__ void store(T* p, C v, C) { *p = v; }
+};
+template <> struct Prec<LBM_F32> {
+  using T = float;
+  using C = float;
+  static constexpr bool dev = false;
+  __device__ static __forceinline__ C load(const T* p, C) { return __ldg(p); }
+  __device__ static __forceinline__ C load_rw(const T* p, C) { return *p; }
+  __device__ static __forceinline__ void store(T* p, C v, C) { *p = v; }
+};
+template <> struct Prec<LBM_F16DEV> {
+  using T = __half;
+  using C = float;
+  static constexpr bool dev = true;
+  __device__ static __forceinline__ C load(const T* p, C shift) {
+    return __half2float(__ldg(p)) + shift;
+  }
+  __device__ static __forceinline__ C load_rw(const T* p, C shift) {
+    return __half2float(*p) + shift;
+  }
+  __device__ static __forceinline__ void store(T* p, C v, C shift) {
+    *p = __float2half_rn(v - shift);
+  }
+};
+template <> struct Prec<LBM_BF16DEV> {
+  using T = __nv_bfloat16;
+  using C = float;
+  static constexpr bool dev = true;
+  __device__ static __forceinline__ C load(const T* p, C shift) {
+    return __bfloat162float(__ldg(p)) + shift;
+  }
+  __device__ static __forceinline__ C load_rw(const T* p, C shift) {
+    return __bfloat162float(*p) + shift;
+  }
+  __device__ static __forceinline__ void store(T* p, C v, C shift) {
+    *p = __float2bfloat16_rn(v - shift);
+  }
+};
+
+// Per-lattice constants handed to every kernel by value.
+struct Geom {
+  int nx, ny, nz;
+  long long N;  // nx * ny * nz
+};
+
+struct Phys {
+  double tau, G, rho0, rho_ref;
+  int psi_form;
+};
+
+// Neighbour index table of one node: x-1, x, x+1 and the 9 row offsets of
+// (y + dy, z + dz), all periodic.  idx(cxa, cya, cza) is the flat index of
+// the node x + c.
+struct Nbr {
+  long long xs[3];
+  long long rows[3][3];
+  __device__ __forceinline__ void make(const Geom& g, int x, int y, int z) {
+    const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+    xs[0] = xm;
+    xs[1] = x;
+    xs[2] = xp;
+    const int yv[3] = {ym, y, yp}, zv[3] = {zm, z, zp};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) rows[i][k] = (long long)g.nx * ((long long)yv[i] + (long long)g.ny * zv[k]);
+  }
+  __device__ __forceinline__ long long idx(int dx, int dy, int dz) const {
+    return xs[dx + 1] + rows[dy + 1][dz + 1];
+  }
+};
+
+// psi(rho) (definition after Eq. 5).
+template <typename C>
+__device__ __forceinline__ C psi_of(C rho, int form, C rho0) {
+  if (form == LBM_PSI_RHO) return rho;
+  if constexpr (sizeof(C) == 8) {
+    return rho0 * (1.0 - exp(-rho / rho0));
+  } else {
+    return rho0 * (1.0f - expf(-rho / rho0));
+  }
+}
+
+}  // namespace lbm

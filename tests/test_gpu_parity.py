@@ -1,0 +1,362 @@
+"""GPU path (liblbm.so, through its C ABI) against the CPU FP64 oracle.
+
+Tolerances (relative, per node, on rho and on the populations):
+  FP64 storage: 1e-12 after 100 steps (rounding-order differences only);
+  FP32 storage: 1e-5 after 100 steps;
+  layout equivalences (AA vs A-B, graph vs eager, checkpoint resume): bitwise.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import lbm_inputs
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+G6 = -6.0
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1904_11792_gb300 import build, lbm
+    build.build()
+    lbm.load()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return lbm
+
+
+@pytest.fixture(scope="module")
+def coex():
+    r = oracle.coexistence(1.0, G6, n=64, tol=1e-10, rho_l0=2.6, rho_v0=0.07)
+    return r["rho_l"], r["rho_v"]
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+def make(L, shape, tau, G, precision="f64", pattern="ab", **kw):
+    nx, ny, nz = shape
+    return L.Lattice(nx, ny, nz, tau, G, precision=precision, pattern=pattern, **kw)
+
+
+# ---------------------------------------------------------------------------
+# initial condition
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-15), ("f32", 1.2e-7)])
+def test_init_ligament_matches_oracle(L, coex, precision, tol):
+    rl, rv = coex
+    shape = (64, 32, 32)
+    with make(L, shape, 1.0, G6, precision) as lat:
+        lat.init_ligament(8.0, 64.0, 0.05, 0.3, rl, rv, 2.0)
+        got = lat.populations()
+    want = oracle.init_ligament(*shape, 8.0, 64.0, 0.05, 0.3, rl, rv, 2.0)
+    assert rel(got, want) <= tol
+
+
+def test_init_profile_matches_oracle(L):
+    prof = np.linspace(2.6, 0.07, 17)
+    shape = (24, 20, 20)
+    with make(L, shape, 1.0, G6, "f64") as lat:
+        lat.init_profile(5.0, 24.0, 0.1, 1.0, prof, -8.0, 1.0)
+        got = lat.populations()
+    want = oracle.init_profile(*shape, 5.0, 24.0, 0.1, 1.0, prof, -8.0, 1.0)
+    assert rel(got, want) <= 1e-15
+
+
+# ---------------------------------------------------------------------------
+# time-step parity
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(37, 11, 9), (3, 3, 3), (5, 3, 7), (130, 6, 5)])
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_fp64_random_state_parity(L, shape, pattern):
+    f0 = lbm_inputs.random_populations(*shape, seed=21)
+    tau, G = 0.9, -5.5
+    with make(L, shape, tau, G, "f64", pattern) as lat:
+        lat.set_populations(f0)
+        lat.step(100)
+        got = lat.populations()
+        rho = lat.rho()
+    want = oracle.step(f0, tau, G, 100)
+    assert rel(got, want) <= 1e-12
+    assert rel(rho, want.sum(axis=0)) <= 1e-12
+
+
+def test_fp64_ligament_parity_100_steps(L, coex):
+    rl, rv = coex
+    shape = (64, 32, 32)
+    f0 = oracle.init_ligament(*shape, 8.0, 64.0, 0.05, 0.0, rl, rv, 2.0)
+    want = oracle.step(f0, 1.0, G6, 100)
+    with make(L, shape, 1.0, G6, "f64") as lat:
+        lat.init_ligament(8.0, 64.0, 0.05, 0.0, rl, rv, 2.0)
+        lat.step(100)
+        got = lat.populations()
+        rho = lat.rho()
+    assert rel(rho, want.sum(axis=0)) <= 1e-12
+    assert rel(got, want) <= 1e-12
+
+
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_fp32_ligament_parity_100_steps(L, coex, pattern):
+    rl, rv = coex
+    shape = (64, 32, 32)
+    f0 = oracle.init_ligament(*shape, 8.0, 64.0, 0.05, 0.0, rl, rv, 2.0)
+    want = oracle.step(f0, 1.0, G6, 100)
+    with make(L, shape, 1.0, G6, "f32", pattern) as lat:
+        lat.init_ligament(8.0, 64.0, 0.05, 0.0, rl, rv, 2.0)
+        lat.step(100)
+        rho = lat.rho()
+    assert rel(rho, want.sum(axis=0)) <= 1e-5
+
+
+def test_psi_rho_form_parity(L):
+    shape = (12, 9, 7)
+    f0 = lbm_inputs.random_populations(*shape, seed=5, rho_lo=0.5, rho_hi=1.5)
+    with make(L, shape, 0.7, -0.8, "f64", psi_form=L.LBM_PSI_RHO) as lat:
+        lat.set_populations(f0)
+        lat.step(30)
+        got = lat.populations()
+    want = oracle.step(f0, 0.7, -0.8, 30, psi_form=1)
+    assert rel(got, want) <= 1e-12
+
+
+@pytest.mark.parametrize("block", [(32, 1, 1), (64, 2, 2), (128, 4, 1), (32, 4, 4)])
+def test_block_shapes_agree_bitwise(L, block):
+    shape = (70, 13, 11)
+    f0 = lbm_inputs.random_populations(*shape, seed=9)
+    res = []
+    for b in (None, block):
+        with make(L, shape, 0.8, G6, "f32", block=b) as lat:
+            lat.set_populations(f0)
+            lat.step(7)
+            res.append(lat.populations())
+    np.testing.assert_array_equal(res[0], res[1])
+
+
+# ---------------------------------------------------------------------------
+# layout equivalences: AA == A-B, graph == eager, checkpoint resume
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16dev", "bf16dev"])
+@pytest.mark.parametrize("nsteps", [1, 2, 7, 20])
+def test_aa_equals_ab_bitwise(L, precision, nsteps):
+    shape = (33, 10, 9)
+    f0 = lbm_inputs.random_populations(*shape, seed=13)
+    out = []
+    for pattern in ("ab", "aa"):
+        with make(L, shape, 0.85, G6, precision, pattern, rho_ref=0.1) as lat:
+            lat.set_populations(f0)
+            lat.step(nsteps)
+            out.append((lat.populations(), lat.rho()))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_graph_equals_eager_bitwise(L, pattern):
+    shape = (40, 12, 8)
+    f0 = lbm_inputs.random_populations(*shape, seed=17)
+    out = []
+    for graph in (1, 0):
+        with make(L, shape, 0.9, G6, "f32", pattern) as lat:
+            lat.set_option("graph", graph)
+            lat.set_populations(f0)
+            lat.step(3)
+            lat.step(10)
+            out.append(lat.populations())
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_checkpoint_resume_bitwise(L, coex, pattern):
+    rl, rv = coex
+    shape = (48, 24, 24)
+    with make(L, shape, 1.0, G6, "f32", pattern) as lat:
+        lat.init_ligament(6.0, 48.0, 0.05, 0.0, rl, rv, 2.0)
+        lat.step(25)
+        buf = lat.save_state()
+        lat.step(30)
+        full = lat.populations()
+    with make(L, shape, 1.0, G6, "f32", pattern) as lat:
+        lat.load_state(buf)
+        assert lat.step_count == 25
+        lat.step(30)
+        resumed = lat.populations()
+    np.testing.assert_array_equal(full, resumed)
+
+
+# ---------------------------------------------------------------------------
+# moments and diagnostics
+# ---------------------------------------------------------------------------
+
+def test_moments_match_oracle(L, coex):
+    rl, rv = coex
+    shape = (32, 20, 20)
+    f0 = oracle.init_ligament(*shape, 5.0, 32.0, 0.1, 0.0, rl, rv, 2.0)
+    f1 = oracle.step(f0, 1.0, G6, 20)
+    want = oracle.moments(f1, G6)
+    with make(L, shape, 1.0, G6, "f64") as lat:
+        lat.set_populations(f1)
+        m = lat.moments()
+    assert rel(m["rho"], want[0]) <= 1e-14
+    for k, w in zip(("ux", "uy", "uz"), want[1:]):
+        assert np.abs(m[k] - w).max() <= 1e-14 * max(1.0, np.abs(w).max())
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_diagnostics_and_droplets_match_oracle(L, coex, precision):
+    rl, rv = coex
+    shape = (40, 24, 24)
+    # three blobs and a thin ligament piece: several components, wraps in x
+    with make(L, shape, 1.0, G6, precision) as lat:
+        lat.init_ligament(4.5, 20.0, 0.6, 0.0, rl, rv, 2.0)
+        lat.step(40)
+        d = lat.diagnostics(ccl=True)
+        rho = lat.rho()
+        f = lat.populations()
+    o = oracle.diagnostics(f, rl, rv)
+    # FP64: rounding order only; FP32: rho itself is summed in FP32 on the GPU
+    tol = 1e-12 if precision == "f64" else 2e-6
+    assert abs(d["mass"] - o["mass"]) <= tol * o["mass"]
+    for k in range(3):
+        assert abs(d["mom"][k] - (o["mom_x"], o["mom_y"], o["mom_z"])[k]) <= tol * o["mass"]
+    assert abs(d["liquid_volume_w"] - o["liquid_volume_w"]) <= tol * o["liquid_volume_w"]
+    assert abs(d["min_slice_area_w"] - o["min_slice_area_w"]) <= tol * max(1.0, o["min_slice_area_w"])
+    # integer decisions on the GPU's own rho: compare with the oracle on the same field
+    liq = rho > 0.5 * (rl + rv)
+    assert d["liquid_count"] == int(liq.sum())
+    assert d["min_slice_count"] == int(liq.sum(axis=(0, 1)).min())
+    assert d["min_slice_x"] == int(np.argmin(liq.sum(axis=(0, 1))))
+    n, labels, sizes = oracle.ccl(liq)
+    assert d["droplets"] == n
+    assert d["droplets_min8"] == int((sizes >= 8).sum())
+    assert d["largest_droplet"] == (int(sizes.max()) if n else 0)
+    assert d["numeric_ok"] == 1
+    assert abs(d["max_u"] - o["max_u"]) <= 1e-6 * max(o["max_u"], 1e-12) + (1e-12 if precision == "f64" else 1e-6)
+
+
+def test_droplet_count_random_masks(L):
+    # densities built so that the liquid mask is a random pattern with many
+    # components, including ones joined across the periodic boundaries
+    shape = (17, 9, 11)
+    nx, ny, nz = shape
+    u = lbm_inputs.uniform(99, nx * ny * nz).reshape(nz, ny, nx)
+    rho = np.where(u < 0.35, 2.0, 0.1)
+    _, w = L.lbm_lattice()
+    f = w[:, None, None, None] * rho[None]
+    with make(L, shape, 1.0, G6, "f64") as lat:
+        lat.set_populations(f)
+        lat.set_option("rho_l", 2.0)
+        lat.set_option("rho_v", 0.1)
+        d = lat.diagnostics(ccl=True)
+    n, _, sizes = oracle.ccl(rho > 1.05)
+    assert d["droplets"] == n and d["largest_droplet"] == sizes.max()
+
+
+# ---------------------------------------------------------------------------
+# reduced-precision storage (deviation form): bounded error vs FP64
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision,tol", [("f16dev", 5e-3), ("bf16dev", 4e-2)])
+def test_deviation_storage_error(L, coex, precision, tol):
+    rl, rv = coex
+    shape = (64, 32, 32)
+    out = {}
+    for p in ("f64", precision):
+        with make(L, shape, 1.0, G6, p, rho_ref=rv) as lat:
+            lat.init_ligament(8.0, 64.0, 0.05, 0.0, rl, rv, 2.0)
+            lat.step(100)
+            out[p] = (lat.rho(), lat.diagnostics())
+    err = np.abs(out[precision][0] - out["f64"][0]) / out["f64"][0]
+    assert err.max() <= tol
+    drift = abs(out[precision][1]["mass"] - out["f64"][1]["mass"]) / out["f64"][1]["mass"]
+    assert drift <= tol
+
+
+# ---------------------------------------------------------------------------
+# full-size grid-convergence box 256x128x128 (FP32, the benchmark's launch
+# configuration): one step checked node by node on a sample
+# ---------------------------------------------------------------------------
+
+def test_full_size_sampled_one_step(L, coex):
+    rl, rv = coex
+    w = lbm_inputs.GRID_256
+    shape = (w.nx, w.ny, w.nz)
+    with make(L, shape, w.tau, w.G, "f32") as lat:
+        lat.init_ligament(w.R0, w.lam, w.eps, w.phase, rl, rv, w.width)
+        lat.step(50)
+        f = lat.populations()
+        lat.step(1)
+        g = lat.populations()
+        d = lat.diagnostics()
+    N = w.nx * w.ny * w.nz
+    u = lbm_inputs.uniform(4242, 400)
+    nodes = np.unique((u * N).astype(np.int64))
+    # nodes on the interface and on the periodic faces as well
+    nodes = np.concatenate([nodes, [0, N - 1, w.nx - 1, w.nx * w.ny - 1,
+                                    (w.ny // 2) * w.nx + (w.nz // 2) * w.nx * w.ny + 24]])
+    want = oracle.step_nodes(f, nodes, w.tau, w.G)
+    got = g.reshape(19, -1)[:, nodes].T
+    assert rel(got, want) <= 1e-5
+    assert abs(d["mass"] - f.sum()) <= 1e-6 * f.sum()
+
+
+# ---------------------------------------------------------------------------
+# failure handling without faulting the GPU
+# ---------------------------------------------------------------------------
+
+def test_numeric_flag_on_negative_density(L):
+    shape = (8, 6, 5)
+    f = lbm_inputs.random_populations(*shape, seed=2)
+    f[:, 2, 3, 4] = -0.01
+    with make(L, shape, 1.0, G6, "f32") as lat:
+        lat.set_populations(f)
+        assert lat.diagnostics()["numeric_ok"] == 0
+        lat.step(1)
+        with pytest.raises(L.LbmError) as ei:
+            lat.sync()
+        assert ei.value.status == L.LBM_ERR_NUMERIC
+        lat.sync()  # the flag is cleared once reported
+
+
+def test_alloc_cap_gives_oom(L, monkeypatch):
+    monkeypatch.setenv("LBM_ALLOC_CAP_BYTES", "1024")
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_create(64, 64, 64, 1.0, G6)
+    assert "LBM_ALLOC_CAP_BYTES" in str(ei.value)
+    monkeypatch.delenv("LBM_ALLOC_CAP_BYTES")
+    h = L.lbm_create(8, 8, 8, 1.0, G6)
+    L.lbm_destroy(h)
+
+
+def test_step_before_init_is_a_state_error(L):
+    h = L.lbm_create(8, 8, 8, 1.0, G6)
+    try:
+        with pytest.raises(L.LbmError) as ei:
+            L.lbm_step(h, 1)
+        assert ei.value.status == L.LBM_ERR_STATE
+    finally:
+        L.lbm_destroy(h)
+
+
+def test_kernel_timing_counts_launches(L):
+    with make(L, (64, 16, 16), 1.0, G6, "f32") as lat:
+        lat.set_populations(lbm_inputs.random_populations(64, 16, 16, seed=1))
+        lat.set_option("kernel_timing", 1)
+        lat.step(6)
+        n0, ms0 = L.lbm_kernel_time(lat.h, 0)
+        n1, ms1 = L.lbm_kernel_time(lat.h, 1)
+    assert n0 == 6 and n1 == 6 and ms0 > 0 and ms1 > 0
+
+
+def test_gpu_coexistence_matches_oracle(L):
+    from paper_1904_11792_gb300.coexistence import coexistence
+    got = coexistence(G6, 1.0, n=64, tol=1e-10)
+    want = oracle.coexistence(1.0, G6, n=64, tol=1e-10, rho_l0=2.6, rho_v0=0.07)
+    assert abs(got["rho_l"] - want["rho_l"]) <= 1e-8
+    assert abs(got["rho_v"] - want["rho_v"]) <= 1e-8
