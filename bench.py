@@ -63,17 +63,24 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def kernel_digest() -> str:
+    """sha256 over the sources of the time-step kernels."""
+    h = hashlib.sha256()
+    for name in ("lbm_node.cuh", "lbm_step.cu", "lbm_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1904_11792_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def ncu_traffic(precision: str):
     """DRAM bytes per collide-stream launch from the committed ncu summary, if
     it was taken on the current kernel source; else None."""
     p = os.path.join(ROOT, "profiles", "collide_stream_traffic.json")
-    src = os.path.join(ROOT, "paper_1904_11792_gb300", "csrc", "lbm_step.cu")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    with open(src, "rb") as fh:
-        digest = hashlib.sha256(fh.read()).hexdigest()
+    digest = kernel_digest()
     if d.get("kernel_source_sha256") != digest:
         return None
     e = d.get("workloads", {}).get(precision)
@@ -160,18 +167,35 @@ def run_ours(args):
         rho_l, rho_v = args.rho_l, args.rho_v
     else:
         rho_l, rho_v = coexistence_densities(w.G, w.tau)
-    lat = L.Lattice(w.nx, w.ny, w.nz, w.tau, w.G, precision=args.precision, pattern=args.pattern,
+    # streaming pattern, block shape and register budget from the autotuner
+    # (timed on this GPU before the measured region)
+    from paper_1904_11792_gb300 import autotune
+    patterns = ("ab", "aa") if args.pattern == "auto" else (args.pattern,)
+    if args.no_tune:
+        choice = dict(pattern=patterns[-1], block=(128, 2, 1), occupancy=0)
+    else:
+        choice = autotune.tune_lattice(w.nx, w.ny, w.nz, precision=args.precision,
+                                       patterns=patterns,
+                                       blocks=((128, 2, 1), (64, 4, 1), (32, 8, 1)),
+                                       occupancies=(2, 3), tau=w.tau, G=w.G, steps=10,
+                                       use_cache=False)
+    pattern = choice["pattern"]
+    lat = L.Lattice(w.nx, w.ny, w.nz, w.tau, w.G, precision=args.precision, pattern=pattern,
                     rho_ref=rho_v if args.precision.endswith("dev") else 0.0)
+    autotune.apply(lat, choice)
     lat.init_ligament(w.R0, w.lam, w.eps, w.phase, rho_l, rho_v, w.width)
+    # diagnostics inside the time loop: the psi pass of every 10th step also
+    # reduces mass, momentum, liquid volume and the neck area (FP64)
+    lat.set_option("diag_interval", LBM_PER_STEP)
     stream = torch.cuda.current_stream()
 
     def bench_step():
         lat.step(LBM_PER_STEP)
-        return lat.diagnostics()
 
     for _ in range(args.warmup):
         bench_step()
     lat.sync()
+    lat.diag_history()
     # ---- timed region: device time, kernel events on the library's stream ----
     lat.set_option("kernel_timing", 1)
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -181,7 +205,7 @@ def run_ours(args):
     with Clocks(local) as clk:
         t0.record(stream)
         for _ in range(args.steps):
-            d = bench_step()
+            bench_step()
         t1.record(stream)
         torch.cuda.synchronize()
     if world > 1:
@@ -191,6 +215,8 @@ def run_ours(args):
     n_k2, ms_k2 = L.lbm_kernel_time(lat.h, 1)
     lat.set_option("kernel_timing", 0)
     lat.sync()
+    hist = lat.diag_history()
+    d = hist[-1]
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -213,12 +239,14 @@ def run_ours(args):
         "config": {
             "workload": "ligament %dx%dx%d R0=%g lambda=%g eps=%g tau=%g G=%g, %s storage, %s "
                         "streaming" % (w.nx, w.ny, w.nz, w.R0, w.lam, w.eps, w.tau, w.G,
-                                       args.precision, args.pattern.upper()),
+                                       args.precision, pattern.upper()),
+            "tuned": {"pattern": pattern, "block": choice["block"],
+                      "occupancy": choice["occupancy"], "vector": True},
             "nodes": N, "lattice_steps_per_step": LBM_PER_STEP, "diagnostics_every": LBM_PER_STEP,
             "parallelism": "replicas" if world > 1 else "single GPU",
             "l2": "no flush: populations %.0f MB > 129 MB L2" % (
-                2 * 19 * N * (4 if args.precision == "f32" else 8 if args.precision == "f64" else 2)
-                / 1e6),
+                (2 if pattern == "ab" else 1) * 19 * N
+                * (4 if args.precision == "f32" else 8 if args.precision == "f64" else 2) / 1e6),
             "rho_l": round(rho_l, 6), "rho_v": round(rho_v, 6),
             "step_model_bytes_per_lu": STEP_BYTES_PER_LU[args.precision],
             "hbm_frac_step_model": round(value / world * STEP_BYTES_PER_LU[args.precision] / peak, 4),
@@ -230,9 +258,10 @@ def run_ours(args):
                      "avg_launch_ms": round(k2_avg, 5), "launches": n_k2,
                      "psi_pass_avg_ms": round(ms_psi / max(n_psi, 1), 5)},
         "e2e": e2e,
-        "gpu_launches": int(args.steps * (2 * LBM_PER_STEP + 2)),
+        "gpu_launches": int(args.steps * (2 * LBM_PER_STEP + 1)),
         "clocks": clocks,
-        "diag_last": {"mass": d["mass"], "neck_radius": d["neck_radius"], "step": d["step"]},
+        "diag_last": {"mass": d["mass"], "neck_radius": round(d["neck_radius"], 4),
+                      "step": d["step"], "records_in_timed_region": len(hist)},
     }
     if rank == 0 and world == 1 and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline(w, rho_l, rho_v)
@@ -253,19 +282,21 @@ def run_e2e(args, lat, L, torch, N):
     rc = lib.lbm_save_state(lat.h, ctypes.c_void_p(host_state.data_ptr()), nbytes)
     L.check(rc)
     host_rho = torch.empty(N, dtype=torch.float64, pin_memory=True)
-    diag = L.lbm_diag()
+    diag = (L.lbm_diag * 4)()
+    got = ctypes.c_int()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     L.check(lib.lbm_load_state(lat.h, ctypes.c_void_p(host_state.data_ptr()), nbytes))
     for _ in range(args.steps):
         L.check(lib.lbm_step(lat.h, LBM_PER_STEP))
-        L.check(lib.lbm_diagnostics(lat.h, ctypes.byref(diag), 0))
+        # this step's diagnostics record, read back to the host
+        L.check(lib.lbm_diag_history(lat.h, diag, 4, ctypes.byref(got)))
     L.check(lib.lbm_moments(lat.h, ctypes.c_void_p(host_rho.data_ptr()), None, None, None))
     t1 = time.perf_counter()
     steps = args.steps * LBM_PER_STEP
     return {"value": round(N * steps / (t1 - t0) / 1e9, 4), "unit": UNIT,
             "h2d_bytes_per_step": int(nbytes // args.steps),
-            "d2h_bytes_per_step": int(ctypes.sizeof(diag) + 8 * N // args.steps)}
+            "d2h_bytes_per_step": int(ctypes.sizeof(L.lbm_diag) + 8 * N // args.steps)}
 
 
 def cpu_baseline(w, rho_l, rho_v, budget_s: float = 12.0):
@@ -321,17 +352,92 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """The batched sweep: 48 periodic ligaments of uneven size (R0 in
+    {8..24}, box lambda x 4R0 x 4R0, tau in [0.6, 1]), FP32, stepped as one
+    graph-replayed pair of launches per step for the whole batch (block shape
+    from the autotuner), against the same steps as 48 x 2 launches per step."""
+    import torch
+    from paper_1904_11792_gb300 import autotune, build, lbm as L
+    torch.cuda.set_device(dist_env()[2])
+    build.build()
+    L.load()
+    rho_l, rho_v = (args.rho_l, args.rho_v) if (args.rho_l and args.rho_v) else \
+        coexistence_densities(-6.0, 1.0)
+    sweep = lbm_inputs.batched_sweep(48)
+    insts = [dict(nx=i.nx, ny=i.ny, nz=i.nz, tau=i.tau, G=i.G, R0=i.R0, lam=i.lam, eps=i.eps,
+                  phase=i.phase, rho_l=rho_l, rho_v=rho_v, width=i.width) for i in sweep]
+    total = sum(d["nx"] * d["ny"] * d["nz"] for d in insts)
+    stream = torch.cuda.current_stream()
+    with L.Batch(insts, precision=args.precision) as b:
+        b.init()
+        tuned = autotune.tune_batch(b, blocks=((128, 2, 1), (64, 4, 1), (32, 8, 1), (64, 2, 2)),
+                                    occupancies=(2, 3), steps=10)
+        b.init()
+
+        def timed(fn, nsteps):
+            for _ in range(args.warmup):
+                fn(LBM_PER_STEP)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(nsteps):
+                fn(LBM_PER_STEP)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        with Clocks(dist_env()[2]) as clk:
+            ms_b = timed(b.step, args.steps)
+        ms_s = timed(b.step_sequential, args.steps)
+        unstable = [k for k in range(len(insts)) if b.diagnostics(k)["numeric_ok"] != 1]
+        try:
+            b.sync()
+        except L.LbmError:
+            pass
+    steps = args.steps * LBM_PER_STEP
+    value = total * steps / (ms_b * 1e-3) / 1e9
+    seq = total * steps / (ms_s * 1e-3) / 1e9
+    peak, _ = peaks()
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_b / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+        "data": "synthetic (seeded ligament sweep, no dataset)",
+        "config": {"workload": "batched sweep: 48 periodic ligaments, R0 in {8,12,16,20,24}, "
+                               "lambda/R0 in [4.5,12], tau in [0.6,1.0], G=-6, eps=0.05, box "
+                               "lambda x 4R0 x 4R0, %s A-B" % args.precision,
+                   "total_nodes": total, "lattice_steps_per_step": LBM_PER_STEP,
+                   "mode": "one psi + one collide launch per step for all instances, graph",
+                   "tuned": tuned,
+                   "sequential_glups": round(seq, 4),
+                   "speedup_vs_sequential": round(value / seq, 3),
+                   "hbm_frac_step_model": round(value * STEP_BYTES_PER_LU[args.precision] / peak, 4),
+                   "unstable_instances": unstable,
+                   "note": "instances with tau < ~0.75 go non-finite from the tanh start "
+                           "(G=-6 SRT stability limit); their launches still run in full"},
+        "clocks": clk.summary(),
+        "gpu_launches": int(args.steps * LBM_PER_STEP * 2),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=("grid256", "batch48"), default="grid256",
+                    help="grid256: the headline ligament; batch48: the batched sweep")
     ap.add_argument("--precision", choices=("f32", "f64", "f16dev", "bf16dev"), default="f32")
-    ap.add_argument("--pattern", choices=("ab", "aa"), default="ab")
+    ap.add_argument("--pattern", choices=("auto", "ab", "aa"), default="auto",
+                    help="streaming pattern; auto = the autotuner's choice")
     ap.add_argument("--rho-l", type=float, default=None,
                     help="liquid density (with --rho-v: skip the flat-interface run)")
     ap.add_argument("--rho-v", type=float, default=None)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner (default launch configuration; profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the end-to-end and CPU-baseline legs (profiling runs)")
     args = ap.parse_args()
@@ -339,6 +445,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch48":
+        run_batch(args)
     else:
         run_ours(args)
 

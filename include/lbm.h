@@ -84,7 +84,7 @@ typedef struct {
     int precision;         /* LBM_F64, LBM_F32, LBM_F16DEV, LBM_BF16DEV              */
     int pattern;           /* LBM_AB or LBM_AA                                       */
     double rho_ref;        /* deviation reference density of the *DEV storage forms  */
-    int block_x, block_y, block_z; /* collide-stream block shape, 0 = default        */
+    int block_x, block_y, block_z; /* collide-stream block shape (<= 256 threads), 0 = default */
     void *ext_state;       /* optional caller device buffer for the populations      */
     size_t ext_state_bytes;
     void *ext_psi;         /* optional caller device buffer for psi                  */
@@ -143,9 +143,17 @@ int lbm_set_stream(lbm_handle h, void *stream);
 
 /* Named options (value as double): "tau", "G", "rho_l", "rho_v",
  * "graph" (0/1: replay captured CUDA graphs in lbm_step, default 1),
+ * "diag_interval" (k >= 0: every step t with t % k == 0 the psi pass also
+ * reduces the diagnostics of the state at t into a device ring, read with
+ * lbm_diag_history; 0 = off, the default),
  * "kernel_timing" (0/1: record CUDA events around every kernel of lbm_step;
  * disables graphs), "block_x", "block_y", "block_z" (collide-stream block
- * shape).  lbm_get_option also answers "step", "nx", "ny", "nz",
+ * shape, at most 256 threads), "occupancy" (2, 3 or 4: 256-thread blocks
+ * per SM the collide-stream kernel's register budget allows; 0 = auto,
+ * the default: 2 for the two-node kernel, 3 for the one-node kernel),
+ * "vector" (0/1, default 1: when nx is even each thread updates two
+ * neighbouring nodes with 2-element vector loads and stores; block_x then
+ * counts node pairs).  lbm_get_option also answers "step", "nx", "ny", "nz",
  * "precision", "pattern". */
 int lbm_set_option(lbm_handle h, const char *key, double value);
 int lbm_get_option(lbm_handle h, const char *key, double *value);
@@ -168,6 +176,12 @@ int lbm_init_profile(lbm_handle h, double R0, double lambda, double eps, double 
 /* Enqueues n >= 0 time steps (psi pass, then fused force + collision +
  * streaming) on the handle's stream and returns without waiting. */
 int lbm_step(lbm_handle h, int n);
+
+/* Diagnostics recorded inside lbm_step (option "diag_interval"), oldest
+ * first: up to max_records of the records not returned before (the device
+ * ring keeps the last 1024).  droplets* are -1 (no labelling in the loop).
+ * *count receives the number written.  Synchronises. */
+int lbm_diag_history(lbm_handle h, lbm_diag *out, int max_records, int *count);
 
 /* Waits for the handle's stream; LBM_ERR_NUMERIC if any psi pass since
  * the last check met a non-positive or non-finite density. */
@@ -198,6 +212,52 @@ int lbm_load_state(lbm_handle h, const void *host, size_t bytes);
  * in ms of kernel class k since the option was set, k = 0 psi pass,
  * 1 collide-stream.  Synchronises. */
 int lbm_kernel_time(lbm_handle h, int k, long long *launches, double *ms);
+
+/* ---- batched form ---------------------------------------------------------
+ * A batch advances many independent periodic lattices of uneven size (e.g.
+ * a sweep of ligaments) together: every time step is one psi-pass launch and
+ * one collide-stream launch for the whole batch (blocks find their lattice
+ * in a tile table), replayed from a captured CUDA graph.  The per-node
+ * arithmetic is that of a single lattice, so each instance evolves bitwise
+ * as it would alone.  A-B streaming; all instances share the precision. */
+typedef struct lbm_batch_ctx *lbm_batch;
+
+typedef struct {
+    int nx, ny, nz;                   /* lattice size, each >= 3                  */
+    double tau, G;                    /* as in lbm_config                        */
+    double R0, lambda, eps, phase;    /* ligament of lbm_init_ligament            */
+    double rho_l, rho_v, width;       /* densities and interface width            */
+} lbm_instance;
+
+/* Creates a batch of count instances (host array, copied).  The *DEV
+ * precisions use rho_ref = rho_v of each instance.  NULL on error, message
+ * in lbm_batch_last_error(). */
+lbm_batch lbm_batch_create(const lbm_instance *inst, int count, int precision, int psi_form,
+                           double rho0, void *stream);
+void lbm_batch_destroy(lbm_batch b);
+const char *lbm_batch_last_error(void);
+int lbm_batch_set_stream(lbm_batch b, void *stream);
+/* "graph" (0/1), "occupancy" (2, 3, 4; default 2), "vector" (0/1, default 1:
+ * instances with even nx update two nodes per thread), "block_x",
+ * "block_y", "block_z" (collide-stream block shape of the batched kernel,
+ * <= 256 threads; block_x counts node pairs on instances with even nx). */
+int lbm_batch_set_option(lbm_batch b, const char *key, double value);
+/* Total nodes, collide-stream tiles of one launch, block shape (int[3]);
+ * any pointer may be NULL. */
+int lbm_batch_info(lbm_batch b, long long *total_nodes, int *collide_tiles, int *block3);
+/* Ligament initial condition of every instance; resets the step count. */
+int lbm_batch_init(lbm_batch b);
+/* n steps of every instance: two launches per step for the whole batch. */
+int lbm_batch_step(lbm_batch b, int n);
+/* n steps, each instance with its own two launches per step (the plain
+ * per-lattice path, for comparison). */
+int lbm_batch_step_sequential(lbm_batch b, int n);
+/* Waits; LBM_ERR_NUMERIC if a density of any instance went bad. */
+int lbm_batch_sync(lbm_batch b);
+/* Canonical FP64 populations of instance k (19 * N_k doubles). */
+int lbm_batch_get_populations(lbm_batch b, int k, double *host);
+/* Diagnostics of instance k (as lbm_diagnostics). */
+int lbm_batch_diagnostics(lbm_batch b, int k, lbm_diag *out, int want_ccl);
 
 #ifdef __cplusplus
 }

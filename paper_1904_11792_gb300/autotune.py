@@ -1,0 +1,155 @@
+"""Autotuner of the time-step launch configuration.
+
+For a lattice size and storage precision it times, on the GPU, the streaming
+pattern (A-B or AA), the collide-stream block shape and the register budget
+variant (blocks per SM), picks the fastest whole step, and caches the choice in
+a JSON file keyed by device, size and precision.  For a batch it tunes the
+batched kernel's block shape.  All timing is CUDA events around real steps of
+the library (kernel_timing for per-kernel times).
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+from . import lbm as L
+
+DEFAULT_BLOCKS = ((256, 1, 1), (128, 2, 1), (64, 4, 1), (32, 8, 1), (64, 2, 2), (32, 4, 2),
+                  (128, 1, 2), (32, 2, 4))
+DEFAULT_OCC = (2, 3, 4)
+
+
+def cache_path() -> str:
+    p = os.environ.get("LBM_TUNE_CACHE")
+    if p:
+        return p
+    base = os.environ.get("XDG_CACHE_HOME") or os.path.join(os.path.expanduser("~"), ".cache")
+    return os.path.join(base, "lbm_gb300_tune.json")
+
+
+def _load_cache() -> dict:
+    try:
+        with open(cache_path()) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save_cache(c: dict) -> None:
+    p = cache_path()
+    try:
+        os.makedirs(os.path.dirname(p), exist_ok=True)
+        tmp = p + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as fh:
+            json.dump(c, fh, indent=1, sort_keys=True)
+        os.replace(tmp, p)
+    except OSError:
+        pass
+
+
+def _device_key() -> str:
+    import torch
+    return torch.cuda.get_device_name()
+
+
+def _key(kind, dims, precision, extra="") -> str:
+    return "%s|%s|%s|%s|%s" % (_device_key(), kind, "x".join(map(str, dims)), precision, extra)
+
+
+def _fits(block, nx):
+    return block[0] <= max(32, nx) * 2
+
+
+def tune_lattice(nx, ny, nz, precision="f32", patterns=("ab", "aa"), blocks=DEFAULT_BLOCKS,
+                 occupancies=DEFAULT_OCC, tau=1.0, G=-6.0, steps=20, use_cache=True,
+                 verbose=False) -> dict:
+    """Best (pattern, block, occupancy) for one lattice; returns a dict with the
+    choice and the measured per-step time and GLUPS."""
+    import torch
+    key = _key("lattice", (nx, ny, nz), precision, ",".join(patterns))
+    cache = _load_cache() if use_cache else {}
+    if use_cache and key in cache:
+        return cache[key]
+    rl, rv = 2.6489, 0.0732
+    N = nx * ny * nz
+    best = None
+    trials = []
+    for pattern in patterns:
+        with L.Lattice(nx, ny, nz, tau, G, precision=precision, pattern=pattern,
+                       rho_ref=rv if precision.endswith("dev") else 0.0) as lat:
+            lat.init_ligament(min(ny, nz) / 4.0, float(nx), 0.02, 0.0, rl, rv, 2.0)
+            for occ in occupancies:
+                for b in blocks:
+                    if not _fits(b, nx):
+                        continue
+                    for k, v in zip(("block_x", "block_y", "block_z"), (1, 1, 1)):
+                        lat.set_option(k, v)
+                    for k, v in zip(("block_x", "block_y", "block_z"), b):
+                        lat.set_option(k, v)
+                    lat.set_option("occupancy", occ)
+                    lat.step(4)
+                    torch.cuda.synchronize()
+                    lat.set_option("kernel_timing", 1)
+                    lat.step(steps)
+                    n0, ms0 = L.lbm_kernel_time(lat.h, 0)
+                    n1, ms1 = L.lbm_kernel_time(lat.h, 1)
+                    lat.set_option("kernel_timing", 0)
+                    step_ms = ms0 / max(n0, 1) + ms1 / max(n1, 1)
+                    t = dict(pattern=pattern, block=list(b), occupancy=occ, step_ms=step_ms,
+                             glups=N / (step_ms * 1e-3) / 1e9)
+                    trials.append(t)
+                    if verbose:
+                        print(json.dumps(t))
+                    if best is None or step_ms < best["step_ms"]:
+                        best = t
+    best = dict(best, trials=len(trials), tuned_at=time.strftime("%Y-%m-%dT%H:%M:%S"))
+    if use_cache:
+        cache = _load_cache()
+        cache[key] = best
+        _save_cache(cache)
+    return best
+
+
+def apply(lat: "L.Lattice", choice: dict) -> None:
+    """Applies a tuned block shape and occupancy to a lattice (the pattern is
+    fixed at creation: create the lattice with choice['pattern'])."""
+    for k, v in zip(("block_x", "block_y", "block_z"), (1, 1, 1)):
+        lat.set_option(k, v)
+    for k, v in zip(("block_x", "block_y", "block_z"), choice["block"]):
+        lat.set_option(k, v)
+    lat.set_option("occupancy", choice["occupancy"])
+
+
+def tune_batch(batch: "L.Batch", blocks=DEFAULT_BLOCKS, occupancies=(3, 4), steps=20,
+               verbose=False) -> dict:
+    """Times the batched step for each block shape / occupancy and leaves the
+    batch configured with the fastest; returns the choice."""
+    import torch
+    best = None
+    for occ in occupancies:
+        for b in blocks:
+            for k, v in zip(("block_x", "block_y", "block_z"), (1, 1, 1)):
+                batch.set_option(k, v)
+            for k, v in zip(("block_x", "block_y", "block_z"), b):
+                batch.set_option(k, v)
+            batch.set_option("occupancy", occ)
+            batch.step(2)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            batch.step(steps)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            t = dict(block=list(b), occupancy=occ, step_ms=ms)
+            if verbose:
+                print(json.dumps(t))
+            if best is None or ms < best["step_ms"]:
+                best = t
+    for k, v in zip(("block_x", "block_y", "block_z"), (1, 1, 1)):
+        batch.set_option(k, v)
+    for k, v in zip(("block_x", "block_y", "block_z"), best["block"]):
+        batch.set_option(k, v)
+    batch.set_option("occupancy", best["occupancy"])
+    return best

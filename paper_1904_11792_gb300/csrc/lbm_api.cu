@@ -74,8 +74,8 @@ int validate(const lbm_config* c) {
   if (!std::isfinite(c->rho_ref)) return fail(LBM_ERR_ARG, "rho_ref must be finite");
   const int bx = c->block_x, by = c->block_y, bz = c->block_z;
   if (bx < 0 || by < 0 || bz < 0) return fail(LBM_ERR_ARG, "negative block size");
-  if ((bx || by || bz) && (bx == 0 || by == 0 || bz == 0 || (long long)bx * by * bz > 512 || bz > 64))
-    return fail(LBM_ERR_ARG, "block shape must be all zero or have 1..512 threads (bz <= 64)");
+  if ((bx || by || bz) && (bx == 0 || by == 0 || bz == 0 || (long long)bx * by * bz > 256 || bz > 64))
+    return fail(LBM_ERR_ARG, "block shape must be all zero or have 1..256 threads (bz <= 64)");
   return LBM_OK;
 }
 
@@ -87,10 +87,13 @@ void sizes_for(const lbm_config* c, size_t* state, size_t* psi) {
   *psi = N * (c->precision == LBM_F64 ? 8 : 4);
 }
 
+// Default collide-stream block: 256 threads, as long along x (the
+// contiguous axis) as the lattice allows; with two nodes per thread (nx
+// even) block.x counts node pairs.
 dim3 default_block(const Geom& g) {
-  const unsigned bx = g.nx >= 128 ? 128 : (g.nx >= 64 ? 64 : 32);
-  const unsigned by = 256 / bx >= 2 ? 2 : 1;
-  return dim3(bx, by, 1);
+  const int ux = g.nx % 2 == 0 ? g.nx / 2 : g.nx;
+  const unsigned bx = ux >= 256 ? 256 : (ux >= 128 ? 128 : (ux >= 64 ? 64 : 32));
+  return dim3(bx, 256 / bx, 1);
 }
 
 // ---- per-handle helpers -----------------------------------------------------
@@ -142,9 +145,18 @@ int enqueue_step(lbm_ctx* h, cudaStream_t s, long long step, int cur, bool timed
     e2 = take_event(h);
     CK(cudaEventRecord(e0, s));
   }
-  CK(launch_psi(prec, layout, h->g, h->ph, src, h->psi, h->d_flag, s));
+  if (h->diag_interval > 0 && step % h->diag_interval == 0) {
+    CK(launch_diagnostics(prec, layout, h->g, h->ph, src, h->rho_l, h->rho_v, h->d_scratch, h->d_ring,
+                          h->psi, h->d_flag, h->d_ring_count, lbm_ctx::kRing, s));
+  } else {
+    CK(launch_psi(prec, layout, h->vec, h->g, h->ph, src, h->psi, h->d_flag, s));
+  }
   if (timed) CK(cudaEventRecord(e1, s));
-  CK(launch_collide(prec, mode, h->g, h->ph, src, dst, h->psi, h->block, s));
+  // default register budget: 2 blocks/SM for the two-node kernel (no
+  // spills at <= 128 registers), 3 for the one-node kernel
+  const bool vec = h->vec && (h->g.nx % 2 == 0);
+  const int minb = h->minb ? h->minb : (vec ? 2 : 3);
+  CK(launch_collide(prec, mode, minb, vec, h->g, h->ph, src, dst, h->psi, h->block, s));
   if (timed) {
     CK(cudaEventRecord(e2, s));
     h->pending.push_back({0, e0, e1});
@@ -176,11 +188,22 @@ int settle_timing(lbm_ctx* h) {
   return LBM_OK;
 }
 
-// Captures two consecutive steps starting at parity/array `phase` into an
-// executable graph.  Capture runs on a private stream (capture is not
-// allowed on the legacy default stream); the graph is launched on the
-// handle's stream.
-int capture_pair(lbm_ctx* h, int phase) {
+// Steps per captured graph: 2 without in-loop diagnostics; with them, the
+// diagnostic interval k (2k for AA when k is odd, so every chunk starts on
+// an even step).  Chunks are replayed only from steps that are multiples of
+// the chunk length, so the diagnostic steps inside a chunk are fixed.
+int chunk_len(const lbm_ctx* h) {
+  const int k = h->diag_interval;
+  if (k <= 0) return 2;
+  if (h->cfg.pattern == LBM_AA && (k & 1)) return 2 * k;
+  return k;
+}
+
+// Captures chunk_len() consecutive steps starting at array `phase` (A-B; 0
+// for AA) into an executable graph.  Capture runs on a private stream
+// (capture is not allowed on the legacy default stream); the graph is
+// launched on the handle's stream.
+int capture_chunk(lbm_ctx* h, int phase) {
   cudaStream_t cs;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;
@@ -190,11 +213,11 @@ int capture_pair(lbm_ctx* h, int phase) {
     cudaStreamDestroy(cs);
     return cuda_fail(e, "cudaStreamBeginCapture");
   }
-  const bool aa = h->cfg.pattern == LBM_AA;
-  for (int k = 0; k < 2 && rc == LBM_OK; ++k) {
-    const long long step = aa ? (phase + k) : 0;
-    const int cur = aa ? 0 : (phase ^ k);
-    rc = enqueue_step(h, cs, step, cur, false);
+  const int C = chunk_len(h);
+  for (int k = 0; k < C && rc == LBM_OK; ++k) {
+    // step numbers relative to a chunk start (a multiple of C): the same
+    // parity and the same diagnostic steps as every replay
+    rc = enqueue_step(h, cs, k, phase ^ (k & 1), false);
   }
   e = cudaStreamEndCapture(cs, &graph);
   cudaStreamDestroy(cs);
@@ -216,6 +239,37 @@ int ensure_scratch(lbm_ctx* h) {
   if (h->d_scratch) return LBM_OK;
   h->scratch_doubles = diag_scratch_doubles(h->g);
   return dev_alloc((void**)&h->d_scratch, h->scratch_doubles * sizeof(double), "diagnostics scratch");
+}
+
+int ensure_ring(lbm_ctx* h) {
+  if (h->d_ring) return LBM_OK;
+  int rc = dev_alloc((void**)&h->d_ring, sizeof(double) * DIAG_STRIDE * lbm_ctx::kRing, "diagnostics ring");
+  if (rc) return rc;
+  rc = dev_alloc((void**)&h->d_ring_count, sizeof(unsigned long long), "ring counter");
+  if (rc) return rc;
+  CK(cudaMemsetAsync(h->d_ring_count, 0, sizeof(unsigned long long), h->stream));
+  return LBM_OK;
+}
+
+void fill_diag(lbm_diag* out, const double* r, long long step) {
+  out->step = step;
+  out->mass = r[0];
+  out->mom[0] = r[1];
+  out->mom[1] = r[2];
+  out->mom[2] = r[3];
+  out->liquid_volume_w = r[4];
+  out->liquid_count = (long long)r[5];
+  out->min_slice_area_w = r[6];
+  out->min_slice_count = (long long)r[7];
+  out->min_slice_x = (int)r[8];
+  out->neck_radius = std::sqrt(r[6] / 3.14159265358979323846);
+  out->max_u = r[9];
+  out->rho_min = r[10];
+  out->rho_max = r[11];
+  out->numeric_ok = (int)r[12];
+  out->droplets = -1;
+  out->droplets_min8 = -1;
+  out->largest_droplet = -1;
 }
 
 // One FP64 plane of N doubles for host transfers (moments, populations).
@@ -305,6 +359,8 @@ void lbm_destroy(lbm_handle h) {
   dev_free(h->d_small, sizeof(double) * 64);
   dev_free(h->d_scratch, h->scratch_doubles * sizeof(double));
   dev_free(h->d_labels, (size_t)h->g.N * 2 * sizeof(int));
+  dev_free(h->d_ring, sizeof(double) * DIAG_STRIDE * lbm_ctx::kRing);
+  dev_free(h->d_ring_count, sizeof(unsigned long long));
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;
 }
@@ -425,6 +481,23 @@ int lbm_set_option(lbm_handle h, const char* key, double v) {
     h->rho_v = v;
   } else if (k == "graph") {
     h->use_graph = v != 0.0;
+  } else if (k == "vector") {
+    h->vec = v != 0.0;
+    drop_graphs(h);
+  } else if (k == "occupancy") {
+    if (v != 0.0 && v != 2.0 && v != 3.0 && v != 4.0) return fail(LBM_ERR_ARG, "occupancy must be 0 (auto), 2, 3 or 4");
+    h->minb = (int)v;
+    drop_graphs(h);
+  } else if (k == "diag_interval") {
+    const long long d = (long long)v;
+    if (d < 0 || d > 1000000 || (double)d != v) return fail(LBM_ERR_ARG, "diag_interval must be an integer in 0..1e6");
+    if (d > 0) {
+      int rc = ensure_scratch(h);
+      if (rc == LBM_OK) rc = ensure_ring(h);
+      if (rc) return rc;
+    }
+    h->diag_interval = (int)d;
+    drop_graphs(h);
   } else if (k == "kernel_timing") {
     if (v != 0.0 && !h->kernel_timing) {
       int rc = settle_timing(h);
@@ -435,13 +508,13 @@ int lbm_set_option(lbm_handle h, const char* key, double v) {
     h->kernel_timing = v != 0.0;
   } else if (k == "block_x" || k == "block_y" || k == "block_z") {
     const long long b = (long long)v;
-    if (b < 1 || b > 512 || (double)b != v) return fail(LBM_ERR_ARG, "block size must be an integer in 1..512");
+    if (b < 1 || b > 256 || (double)b != v) return fail(LBM_ERR_ARG, "block size must be an integer in 1..256");
     dim3 nb = h->block;
     if (k == "block_x") nb.x = (unsigned)b;
     if (k == "block_y") nb.y = (unsigned)b;
     if (k == "block_z") nb.z = (unsigned)b;
-    if ((long long)nb.x * nb.y * nb.z > 512 || nb.z > 64)
-      return fail(LBM_ERR_ARG, "block shape has more than 512 threads");
+    if ((long long)nb.x * nb.y * nb.z > 256 || nb.z > 64)
+      return fail(LBM_ERR_ARG, "block shape has more than 256 threads");
     h->block = nb;
     drop_graphs(h);
   } else {
@@ -458,6 +531,9 @@ int lbm_get_option(lbm_handle h, const char* key, double* v) {
   else if (k == "rho_l") *v = h->rho_l;
   else if (k == "rho_v") *v = h->rho_v;
   else if (k == "graph") *v = h->use_graph;
+  else if (k == "diag_interval") *v = h->diag_interval;
+  else if (k == "occupancy") *v = h->minb ? h->minb : ((h->vec && h->g.nx % 2 == 0) ? 2 : 3);
+  else if (k == "vector") *v = h->vec && (h->g.nx % 2 == 0);
   else if (k == "kernel_timing") *v = h->kernel_timing;
   else if (k == "block_x") *v = h->block.x;
   else if (k == "block_y") *v = h->block.y;
@@ -527,24 +603,62 @@ int lbm_step(lbm_handle h, int n) {
   if (n < 0) return fail(LBM_ERR_ARG, "negative step count");
   if (!h->initialized) return fail(LBM_ERR_STATE, "lattice not initialised");
   const bool aa = h->cfg.pattern == LBM_AA;
+  const int C = chunk_len(h);
+  const int k = h->diag_interval;
+  if (h->graph_chunk != C) {
+    drop_graphs(h);
+    h->graph_chunk = C;
+  }
   while (n > 0) {
-    if (h->use_graph && !h->kernel_timing && n >= 2) {
-      const int phase = aa ? (int)(h->step & 1) : h->cur;
+    if (h->use_graph && !h->kernel_timing && n >= C && h->step % C == 0) {
+      const int phase = aa ? 0 : h->cur;
       if (!h->graph[phase]) {
-        int rc = capture_pair(h, phase);
+        int rc = capture_chunk(h, phase);
         if (rc) return rc;
       }
       CK(cudaGraphLaunch(h->graph[phase], h->stream));
-      h->step += 2;
-      n -= 2;
+      if (k > 0)
+        for (long long t = h->step; t < h->step + C; t += k) h->diag_steps.push_back(t);
+      if (!aa && (C & 1)) h->cur ^= 1;
+      h->step += C;
+      n -= C;
     } else {
       int rc = enqueue_step(h, h->stream, h->step, h->cur, h->kernel_timing);
       if (rc) return rc;
+      if (k > 0 && h->step % k == 0) h->diag_steps.push_back(h->step);
       if (!aa) h->cur ^= 1;
       h->step += 1;
       n -= 1;
     }
   }
+  return LBM_OK;
+}
+
+int lbm_diag_history(lbm_handle h, lbm_diag* out, int max_records, int* count) {
+  if (!h || !count || max_records < 0 || (max_records > 0 && !out)) return fail(LBM_ERR_ARG, "bad argument");
+  *count = 0;
+  const long long total = (long long)h->diag_steps.size();
+  if (!h->d_ring || total == h->diag_fetched) {
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+  }
+  unsigned long long dev_total = 0;
+  CK(cudaMemcpyAsync(&dev_total, h->d_ring_count, sizeof(dev_total), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if ((long long)dev_total != total) return fail(LBM_ERR_STATE, "diagnostics ring out of step with the host log");
+  long long first = h->diag_fetched;
+  if (total - first > lbm_ctx::kRing) first = total - lbm_ctx::kRing;  // older records were overwritten
+  if (total - first > max_records) first = total - max_records;
+  std::vector<double> rec(DIAG_STRIDE);
+  int n = 0;
+  for (long long r = first; r < total; ++r) {
+    const long long slot = r % lbm_ctx::kRing;
+    CK(cudaMemcpy(rec.data(), h->d_ring + slot * DIAG_STRIDE, sizeof(double) * DIAG_STRIDE,
+                  cudaMemcpyDeviceToHost));
+    fill_diag(&out[n++], rec.data(), h->diag_steps[(size_t)r]);
+  }
+  h->diag_fetched = total;
+  *count = n;
   return LBM_OK;
 }
 
@@ -566,7 +680,7 @@ int lbm_moments(lbm_handle h, double* rho, double* ux, double* uy, double* uz) {
   if (!h->initialized) return fail(LBM_ERR_STATE, "lattice not initialised");
   const int layout = cur_layout(h);
   const void* f = cur_array(h);
-  CK(launch_psi(h->cfg.precision, layout, h->g, h->ph, f, h->psi, h->d_flag, h->stream));
+  CK(launch_psi(h->cfg.precision, layout, h->vec, h->g, h->ph, f, h->psi, h->d_flag, h->stream));
   double* plane = nullptr;
   int rc = with_plane(h, &plane);
   if (rc) return rc;
@@ -594,7 +708,7 @@ int lbm_diagnostics(lbm_handle h, lbm_diag* out, int want_ccl) {
   const int layout = cur_layout(h);
   const void* f = cur_array(h);
   CK(launch_diagnostics(h->cfg.precision, layout, h->g, h->ph, f, h->rho_l, h->rho_v, h->d_scratch,
-                        h->d_small, h->stream));
+                        h->d_small, nullptr, nullptr, nullptr, 0, h->stream));
   double r[DIAG_OUT];
   long long c4[4] = {-1, -1, -1, 0};
   if (want_ccl) {
@@ -610,21 +724,7 @@ int lbm_diagnostics(lbm_handle h, lbm_diag* out, int want_ccl) {
   CK(cudaMemcpyAsync(r, h->d_small, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (want_ccl && c4[3]) return fail(LBM_ERR_TIMEOUT, "connected-component labelling guard tripped");
-  out->step = h->step;
-  out->mass = r[0];
-  out->mom[0] = r[1];
-  out->mom[1] = r[2];
-  out->mom[2] = r[3];
-  out->liquid_volume_w = r[4];
-  out->liquid_count = (long long)r[5];
-  out->min_slice_area_w = r[6];
-  out->min_slice_count = (long long)r[7];
-  out->min_slice_x = (int)r[8];
-  out->neck_radius = std::sqrt(r[6] / 3.14159265358979323846);
-  out->max_u = r[9];
-  out->rho_min = r[10];
-  out->rho_max = r[11];
-  out->numeric_ok = (int)r[12];
+  fill_diag(out, r, h->step);
   out->droplets = (int)c4[0];
   out->droplets_min8 = (int)c4[1];
   out->largest_droplet = c4[2];

@@ -146,69 +146,127 @@ __global__ void moments_kernel(Geom g, Phys ph, int layout, const typename Prec<
 // Block (32, 8): threadIdx.x walks x, threadIdx.y and blockIdx.y walk rows
 // (y, z).  Per-thread accumulation in a fixed order, then fixed-order
 // block reductions; the final kernel combines block partials in index order.
+// With WRITE_PSI the partial kernel is also the psi pass of the step: it
+// writes psi(rho) of every node and raises the numeric flag, so diagnostics
+// on a time step cost no extra pass over the populations.
 // ---------------------------------------------------------------------------
 constexpr int DX = 32, DY = 8;
 constexpr int NG = 12;  // global partial slots per block
 // slots: 0 mass, 1-3 momentum, 4 volume_w, 5 count, 6 max_u, 7 rho_min,
 // 8 rho_max, 9 bad, 10-11 unused
 
+// Row-blocks of the partial kernel: enough blocks to fill the GPU (about 16
+// per SM) while the per-slice partials (row-blocks x nx x 2 doubles) stay
+// small; each thread then walks rows / (8 row-blocks) rows.
 int diag_row_blocks(const Geom& g) {
   const long long rows = (long long)g.ny * g.nz;
+  const long long gx = (g.nx + DX - 1) / DX;
+  long long want = (16 * 152 + gx - 1) / gx;
+  const long long cap = (2ll << 20) / (2ll * g.nx);  // slices <= 2 Mi doubles
+  if (want > cap) want = cap;
   long long rb = (rows + DY - 1) / DY;
-  if (rb > 64) rb = 64;
+  if (rb > want) rb = want;
+  if (rb < 1) rb = 1;
   return (int)rb;
 }
 
-template <int P>
-__global__ void __launch_bounds__(DX* DY) diag_partial_kernel(Geom g, Phys ph, int layout,
+// Per-thread sums run in the compute precision (FP32 except in FP64 mode:
+// GB300's FP64 units are slow) over the thread's rows, then every block
+// reduces them in FP64 in a fixed order.
+template <int P, bool WRITE_PSI, int LAYOUT>
+__global__ void __launch_bounds__(DX* DY) diag_partial_kernel(Geom g, Phys ph,
                                                               const typename Prec<P>::T* f,
                                                               double rho_l, double rho_v,
-                                                              double* slices, double* blocks) {
+                                                              double* slices, double* blocks,
+                                                              typename Prec<P>::C* psi, int* flag) {
   using C = typename Prec<P>::C;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int x = blockIdx.x * DX + tx;
   const long long rows = (long long)g.ny * g.nz;
-  const double thr = 0.5 * (rho_l + rho_v), inv = 1.0 / (rho_l - rho_v);
-  double acc[NG];
-#pragma unroll
-  for (int k = 0; k < NG; ++k) acc[k] = 0.0;
-  acc[7] = 1e300;
-  acc[8] = -1e300;
-  double sw = 0.0, sn = 0.0;
+  const C thr = (C)(0.5 * (rho_l + rho_v)), inv = (C)(1.0 / (rho_l - rho_v)), rv = (C)rho_v;
+  C s_mass = 0, s_jx = 0, s_jy = 0, s_jz = 0, s_vol = 0, umax = 0;
+  C rmin = (C)3.0e38, rmax = (C)-3.0e38;
+  int cnt = 0;
+  bool bad = false;
+  const C s0 = (C)(Prec<P>::dev ? wgt(0) * ph.rho_ref : 0.0);
+  const C s1 = (C)(Prec<P>::dev ? wgt(1) * ph.rho_ref : 0.0);
+  const C s2 = (C)(Prec<P>::dev ? wgt(7) * ph.rho_ref : 0.0);
   if (x < g.nx) {
+#pragma unroll 2
     for (long long r = (long long)blockIdx.y * DY + ty; r < rows; r += (long long)DY * gridDim.y) {
-      const int y = (int)(r % g.ny), z = (int)(r / g.ny);
-      Nbr nb;
-      nb.make(g, x, y, z);
-      C rho_c, j[3];
-      node_rho_j<P>(g, ph, layout, f, nb, rho_c, j);
-      const double rho = (double)rho_c;
-      acc[0] += rho;
-      acc[1] += (double)j[0];
-      acc[2] += (double)j[1];
-      acc[3] += (double)j[2];
-      double phi = (rho - rho_v) * inv;
-      phi = phi < 0.0 ? 0.0 : (phi > 1.0 ? 1.0 : phi);
-      acc[4] += phi;
-      sw += phi;
-      if (rho > thr) {
-        acc[5] += 1.0;
-        sn += 1.0;
+      const int i = x + g.nx * (int)r;
+      C fv[Q];
+      if constexpr (LAYOUT == LAYOUT_LOCAL) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a)
+          fv[a] = Prec<P>::load(f + (long long)a * g.N + i, a == 0 ? s0 : (a <= 6 ? s1 : s2));
+      } else {
+        Nbr nb;
+        nb.make(g, x, (int)(r % g.ny), (int)(r / g.ny));
+#pragma unroll
+        for (int a = 0; a < Q; ++a)
+          fv[a] = Prec<P>::load(f + (long long)opp(a) * g.N + nb.idx(-cx(a), -cy(a), -cz(a)),
+                                a == 0 ? s0 : (a <= 6 ? s1 : s2));
       }
-      const double u = sqrt((double)j[0] * j[0] + (double)j[1] * j[1] + (double)j[2] * j[2]) / rho;
-      if (u > acc[6]) acc[6] = u;
-      if (rho < acc[7]) acc[7] = rho;
-      if (rho > acc[8]) acc[8] = rho;
-      if (!(rho > 0.0) || !(rho <= 1e300)) acc[9] = 1.0;
+      C rho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        rho += fv[a];
+        if (cx(a)) jx += cx(a) > 0 ? fv[a] : -fv[a];
+        if (cy(a)) jy += cy(a) > 0 ? fv[a] : -fv[a];
+        if (cz(a)) jz += cz(a) > 0 ? fv[a] : -fv[a];
+      }
+      if constexpr (WRITE_PSI) psi[i] = psi_of<C>(rho, ph.psi_form, (C)ph.rho0);
+      s_mass += rho;
+      s_jx += jx;
+      s_jy += jy;
+      s_jz += jz;
+      C phi = (rho - rv) * inv;
+      phi = phi < (C)0 ? (C)0 : (phi > (C)1 ? (C)1 : phi);
+      s_vol += phi;
+      cnt += rho > thr;
+      const C u = sqrt(jx * jx + jy * jy + jz * jz) / rho;
+      umax = u > umax ? u : umax;
+      rmin = rho < rmin ? rho : rmin;
+      rmax = rho > rmax ? rho : rmax;
+      bad |= !(rho > (C)0) || !(rho <= (C)3.0e38);
     }
   }
+  if constexpr (WRITE_PSI) raise_flag(bad, flag);
+  // per-slice sums over the block's 8 row groups (FP64, fixed order)
   __shared__ double sh_s[2][DY][DX];
-  __shared__ double sh_g[NG][DY * DX];
-  sh_s[0][ty][tx] = sw;
-  sh_s[1][ty][tx] = sn;
-  const int t = ty * DX + tx;
+  sh_s[0][ty][tx] = (double)s_vol;
+  sh_s[1][ty][tx] = (double)cnt;
+  // block totals: a fixed shuffle tree within each warp (in the compute
+  // precision), then the 8 warp results in FP64 in warp order
+  C v[6] = {s_mass, s_jx, s_jy, s_jz, s_vol, (C)0};
+  float c_f = (float)cnt;  // exact below 2^24 nodes per warp
 #pragma unroll
-  for (int k = 0; k < NG; ++k) sh_g[k][t] = acc[k];
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    c_f += __shfl_down_sync(0xffffffffu, c_f, o);
+    const C um = __shfl_down_sync(0xffffffffu, umax, o);
+    const C mn = __shfl_down_sync(0xffffffffu, rmin, o);
+    const C mx = __shfl_down_sync(0xffffffffu, rmax, o);
+    umax = um > umax ? um : umax;
+    rmin = mn < rmin ? mn : rmin;
+    rmax = mx > rmax ? mx : rmax;
+  }
+  const int anybad = __any_sync(0xffffffffu, bad);
+  __shared__ double sh_w[NG][DY];
+  if (tx == 0) {
+    sh_w[0][ty] = (double)v[0];
+    sh_w[1][ty] = (double)v[1];
+    sh_w[2][ty] = (double)v[2];
+    sh_w[3][ty] = (double)v[3];
+    sh_w[4][ty] = (double)v[4];
+    sh_w[5][ty] = (double)c_f;
+    sh_w[6][ty] = (double)umax;
+    sh_w[7][ty] = (double)rmin;
+    sh_w[8][ty] = (double)rmax;
+    sh_w[9][ty] = anybad ? 1.0 : 0.0;
+  }
   __syncthreads();
   if (ty == 0 && x < g.nx) {
     double a = 0.0, b = 0.0;
@@ -219,29 +277,66 @@ __global__ void __launch_bounds__(DX* DY) diag_partial_kernel(Geom g, Phys ph, i
     slices[((long long)blockIdx.y * g.nx + x) * 2 + 0] = a;
     slices[((long long)blockIdx.y * g.nx + x) * 2 + 1] = b;
   }
-  for (int s = DX * DY / 2; s > 0; s >>= 1) {
-    if (t < s) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) sh_g[k][t] += sh_g[k][t + s];
-      sh_g[6][t] = fmax(sh_g[6][t], sh_g[6][t + s]);
-      sh_g[7][t] = fmin(sh_g[7][t], sh_g[7][t + s]);
-      sh_g[8][t] = fmax(sh_g[8][t], sh_g[8][t + s]);
-      sh_g[9][t] = fmax(sh_g[9][t], sh_g[9][t + s]);
+  if (ty == 0 && tx < NG) {
+    double r;
+    if (tx < 6) {
+      r = 0.0;
+      for (int k = 0; k < DY; ++k) r += sh_w[tx][k];
+    } else if (tx == 7) {
+      r = 1e300;
+      for (int k = 0; k < DY; ++k) r = fmin(r, sh_w[tx][k]);
+    } else if (tx < 10) {
+      r = -1e300;
+      for (int k = 0; k < DY; ++k) r = fmax(r, sh_w[tx][k]);
+    } else {
+      r = 0.0;
     }
-    __syncthreads();
-  }
-  if (t == 0) {
-    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-#pragma unroll
-    for (int k = 0; k < NG; ++k) blocks[b * NG + k] = sh_g[k][0];
+    blocks[((long long)blockIdx.y * gridDim.x + blockIdx.x) * NG + tx] = r;
   }
 }
 
 constexpr int FT = 256;
 
-__global__ void __launch_bounds__(FT) diag_final_kernel(Geom g, int nblocks, int row_blocks,
-                                                       const double* slices, const double* blocks,
-                                                       double* out) {
+// Per-slice totals: one warp per slice x; lane l sums row-blocks l, l + 32,
+// ... with four independent accumulators (loads in flight), then a fixed
+// shuffle tree.  tot[2x] = liquid area A_w(x), tot[2x + 1] = liquid nodes.
+__global__ void __launch_bounds__(256) diag_slices_kernel(Geom g, int row_blocks,
+                                                         const double* __restrict__ slices,
+                                                         double* __restrict__ tot) {
+  const int lane = threadIdx.x & 31;
+  const int x = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (x >= g.nx) return;
+  double a[4] = {0.0, 0.0, 0.0, 0.0}, c[4] = {0.0, 0.0, 0.0, 0.0};
+  int rb = lane;
+  for (; rb + 96 < row_blocks; rb += 128) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      a[k] += slices[((long long)(rb + 32 * k) * g.nx + x) * 2 + 0];
+      c[k] += slices[((long long)(rb + 32 * k) * g.nx + x) * 2 + 1];
+    }
+  }
+  for (; rb < row_blocks; rb += 32) {
+    a[0] += slices[((long long)rb * g.nx + x) * 2 + 0];
+    c[0] += slices[((long long)rb * g.nx + x) * 2 + 1];
+  }
+  double sa = (a[0] + a[1]) + (a[2] + a[3]), sc = (c[0] + c[1]) + (c[2] + c[3]);
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_down_sync(0xffffffffu, sa, o);
+    sc += __shfl_down_sync(0xffffffffu, sc, o);
+  }
+  if (lane == 0) {
+    tot[2 * x] = sa;
+    tot[2 * x + 1] = sc;
+  }
+}
+
+// Writes the DIAG_OUT results to out, or, with a ring counter, to record
+// slot (counter++ mod ring_cap) of the ring at out (DIAG_STRIDE doubles per
+// record).
+__global__ void __launch_bounds__(FT) diag_final_kernel(Geom g, int nblocks,
+                                                       const double* slice_tot, const double* blocks,
+                                                       double* out, unsigned long long* ring_count,
+                                                       int ring_cap) {
   __shared__ double sg[NG][FT];
   __shared__ double smin_w[FT], smin_n[FT];
   __shared__ int smin_x[FT];
@@ -251,6 +346,7 @@ __global__ void __launch_bounds__(FT) diag_final_kernel(Geom g, int nblocks, int
   for (int k = 0; k < NG; ++k) acc[k] = 0.0;
   acc[7] = 1e300;
   acc[8] = -1e300;
+#pragma unroll 4
   for (int b = t; b < nblocks; b += FT) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) acc[k] += blocks[(long long)b * NG + k];
@@ -259,15 +355,11 @@ __global__ void __launch_bounds__(FT) diag_final_kernel(Geom g, int nblocks, int
     acc[8] = fmax(acc[8], blocks[(long long)b * NG + 8]);
     acc[9] = fmax(acc[9], blocks[(long long)b * NG + 9]);
   }
-  // per-slice totals and their minima (first x on ties)
+  // minima over the slice totals (first x on ties)
   double mw = 1e300, mn = 1e300;
   int mx = 0x7fffffff;
   for (int x = t; x < g.nx; x += FT) {
-    double a = 0.0, c = 0.0;
-    for (int rb = 0; rb < row_blocks; ++rb) {
-      a += slices[((long long)rb * g.nx + x) * 2 + 0];
-      c += slices[((long long)rb * g.nx + x) * 2 + 1];
-    }
+    const double a = slice_tot[2 * x], c = slice_tot[2 * x + 1];
     if (a < mw) mw = a;
     if (c < mn) {
       mn = c;
@@ -299,6 +391,12 @@ __global__ void __launch_bounds__(FT) diag_final_kernel(Geom g, int nblocks, int
     __syncthreads();
   }
   if (t == 0) {
+    if (ring_count) {
+      const unsigned long long n = *ring_count;
+      *ring_count = n + 1;
+      out += (n % (unsigned long long)ring_cap) * DIAG_STRIDE;
+      out[DIAG_OUT] = (double)n;
+    }
     out[0] = sg[0][0];
     out[1] = sg[1][0];
     out[2] = sg[2][0];
@@ -429,16 +527,37 @@ cudaError_t moments_t(int layout, const Geom& g, const Phys& ph, const void* f, 
 }
 template <int P>
 cudaError_t diag_t(int layout, const Geom& g, const Phys& ph, const void* f, double rho_l,
-                   double rho_v, double* scratch, double* out, cudaStream_t s) {
+                   double rho_v, double* scratch, double* out, void* psi, int* flag,
+                   unsigned long long* ring_count, int ring_cap, cudaStream_t s) {
   const int rb = diag_row_blocks(g);
   const int gx = (g.nx + DX - 1) / DX;
   double* slices = scratch;
   double* blocks = scratch + (size_t)rb * g.nx * 2;
-  diag_partial_kernel<P><<<dim3(gx, rb), dim3(DX, DY), 0, s>>>(
-      g, ph, layout, (const typename Prec<P>::T*)f, rho_l, rho_v, slices, blocks);
+  double* slice_tot = blocks + (size_t)gx * rb * NG;
+  using T = typename Prec<P>::T;
+  using C = typename Prec<P>::C;
+  const dim3 grid(gx, rb), block(DX, DY);
+  if (psi) {
+    if (layout == LAYOUT_LOCAL)
+      diag_partial_kernel<P, true, LAYOUT_LOCAL><<<grid, block, 0, s>>>(
+          g, ph, (const T*)f, rho_l, rho_v, slices, blocks, (C*)psi, flag);
+    else
+      diag_partial_kernel<P, true, LAYOUT_GATHER><<<grid, block, 0, s>>>(
+          g, ph, (const T*)f, rho_l, rho_v, slices, blocks, (C*)psi, flag);
+  } else {
+    if (layout == LAYOUT_LOCAL)
+      diag_partial_kernel<P, false, LAYOUT_LOCAL><<<grid, block, 0, s>>>(
+          g, ph, (const T*)f, rho_l, rho_v, slices, blocks, nullptr, nullptr);
+    else
+      diag_partial_kernel<P, false, LAYOUT_GATHER><<<grid, block, 0, s>>>(
+          g, ph, (const T*)f, rho_l, rho_v, slices, blocks, nullptr, nullptr);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  diag_final_kernel<<<1, FT, 0, s>>>(g, gx * rb, rb, slices, blocks, out);
+  diag_slices_kernel<<<(g.nx + 7) / 8, 256, 0, s>>>(g, rb, slices, slice_tot);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  diag_final_kernel<<<1, FT, 0, s>>>(g, gx * rb, slice_tot, blocks, out, ring_count, ring_cap);
   return cudaGetLastError();
 }
 template <int P>
@@ -505,17 +624,22 @@ cudaError_t launch_moments(int precision, int layout, const Geom& g, const Phys&
 size_t diag_scratch_doubles(const Geom& g) {
   const int rb = diag_row_blocks(g);
   const int gx = (g.nx + DX - 1) / DX;
-  return (size_t)rb * g.nx * 2 + (size_t)gx * rb * NG;
+  return (size_t)rb * g.nx * 2 + (size_t)gx * rb * NG + (size_t)g.nx * 2;
 }
 
 cudaError_t launch_diagnostics(int precision, int layout, const Geom& g, const Phys& ph, const void* f,
-                               double rho_l, double rho_v, double* scratch, double* out,
+                               double rho_l, double rho_v, double* scratch, double* out, void* psi,
+                               int* flag, unsigned long long* ring_count, int ring_cap,
                                cudaStream_t s) {
   switch (precision) {
-    case LBM_F64: return diag_t<LBM_F64>(layout, g, ph, f, rho_l, rho_v, scratch, out, s);
-    case LBM_F32: return diag_t<LBM_F32>(layout, g, ph, f, rho_l, rho_v, scratch, out, s);
-    case LBM_F16DEV: return diag_t<LBM_F16DEV>(layout, g, ph, f, rho_l, rho_v, scratch, out, s);
-    case LBM_BF16DEV: return diag_t<LBM_BF16DEV>(layout, g, ph, f, rho_l, rho_v, scratch, out, s);
+    case LBM_F64:
+      return diag_t<LBM_F64>(layout, g, ph, f, rho_l, rho_v, scratch, out, psi, flag, ring_count, ring_cap, s);
+    case LBM_F32:
+      return diag_t<LBM_F32>(layout, g, ph, f, rho_l, rho_v, scratch, out, psi, flag, ring_count, ring_cap, s);
+    case LBM_F16DEV:
+      return diag_t<LBM_F16DEV>(layout, g, ph, f, rho_l, rho_v, scratch, out, psi, flag, ring_count, ring_cap, s);
+    case LBM_BF16DEV:
+      return diag_t<LBM_BF16DEV>(layout, g, ph, f, rho_l, rho_v, scratch, out, psi, flag, ring_count, ring_cap, s);
   }
   return cudaErrorInvalidValue;
 }

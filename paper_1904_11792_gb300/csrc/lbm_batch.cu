@@ -1,0 +1,550 @@
+// Batched form: many independent periodic lattices of uneven size (a sweep of
+// ligaments) advanced together.  Every time step is two launches for the
+// whole batch - one psi pass and one collide-stream kernel - whose blocks
+// find their lattice in a tile table, and lbm_batch_step replays those
+// launches from a captured CUDA graph.  The per-node code is the one the
+// single-lattice kernels run (lbm_node.cuh), so each instance evolves
+// bitwise as it would alone.  lbm_batch_step_sequential is the plain
+// alternative: per instance, its own two launches per step.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_node.cuh"
+
+namespace lbm {
+
+// One lattice of a batch, as the kernels see it.
+struct BatchInst {
+  Geom g;
+  Phys ph;
+  long long off_f;    // element offset of the instance's first array in the pool
+  long long off_psi;  // element offset of its psi
+  int tile0;          // first collide tile of the instance
+  int tx, ty;         // collide tiles along x and y
+  int psi_block0;     // first psi-pass block of the instance
+  int vec;            // two nodes per thread (nx even and the batch allows it)
+};
+
+namespace {
+
+// Instance of a block: largest k with start[k] <= b (binary search over the
+// batch's cumulative tile starts, kept in the descriptors).
+__device__ __forceinline__ int find_inst(const BatchInst* __restrict__ inst, int count, int b,
+                                         bool psi_blocks) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int start = psi_blocks ? inst[mid].psi_block0 : inst[mid].tile0;
+    if (start <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) batch_psi_kernel(const BatchInst* __restrict__ inst, int count,
+                                                        const typename Prec<P>::T* pool_f, int cur,
+                                                        typename Prec<P>::C* pool_psi, int* flag) {
+  const int k = find_inst(inst, count, blockIdx.x, true);
+  const BatchInst I = inst[k];
+  const long long t = (long long)(blockIdx.x - I.psi_block0) * blockDim.x + threadIdx.x;
+  const typename Prec<P>::T* f = pool_f + I.off_f + (long long)cur * Q * I.g.N;
+  if (I.vec) {
+    if (2 * t >= I.g.N) return;
+    psi_pair<P, LAYOUT_LOCAL>(I.g, I.ph, f, pool_psi + I.off_psi, flag, 2 * t);
+  } else {
+    if (t >= I.g.N) return;
+    psi_node<P, LAYOUT_LOCAL>(I.g, I.ph, f, pool_psi + I.off_psi, flag, t);
+  }
+}
+
+template <int P, int MINB>
+__global__ void __launch_bounds__(256, MINB) batch_collide_kernel(const BatchInst* __restrict__ inst,
+                                                                  int count,
+                                                                  typename Prec<P>::T* pool_f, int cur,
+                                                                  const typename Prec<P>::C* pool_psi) {
+  const int k = find_inst(inst, count, blockIdx.x, false);
+  const BatchInst I = inst[k];
+  const int t = blockIdx.x - I.tile0;
+  const int bx = t % I.tx, r = t / I.tx;
+  const int by = r % I.ty, bz = r / I.ty;
+  const int xt = bx * blockDim.x + threadIdx.x;
+  const int y = by * blockDim.y + threadIdx.y;
+  const int z = bz * blockDim.z + threadIdx.z;
+  const int x = I.vec ? 2 * xt : xt;
+  if (x >= I.g.nx || y >= I.g.ny || z >= I.g.nz) return;
+  const long long plane = (long long)Q * I.g.N;
+  const typename Prec<P>::T* src = pool_f + I.off_f + (long long)cur * plane;
+  typename Prec<P>::T* dst = pool_f + I.off_f + (long long)(cur ^ 1) * plane;
+  // the branch is uniform over a block (one instance per block)
+  if (I.vec)
+    collide_pair<P, MODE_AB>(I.g, I.ph, src, dst, pool_psi + I.off_psi, x, y, z);
+  else
+    collide_node<P, MODE_AB>(I.g, I.ph, src, dst, pool_psi + I.off_psi, x, y, z);
+}
+
+template <int P>
+cudaError_t batch_launch_t(const BatchInst* d_inst, int count, int psi_blocks, int tiles, void* pool_f,
+                           int cur, void* pool_psi, int* flag, dim3 block, int minb, cudaStream_t s) {
+  using T = typename Prec<P>::T;
+  using C = typename Prec<P>::C;
+  batch_psi_kernel<P><<<psi_blocks, 256, 0, s>>>(d_inst, count, (const T*)pool_f, cur, (C*)pool_psi, flag);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  switch (minb) {
+    case 2:
+      batch_collide_kernel<P, 2><<<tiles, block, 0, s>>>(d_inst, count, (T*)pool_f, cur, (const C*)pool_psi);
+      break;
+    case 3:
+      batch_collide_kernel<P, 3><<<tiles, block, 0, s>>>(d_inst, count, (T*)pool_f, cur, (const C*)pool_psi);
+      break;
+    default:
+      batch_collide_kernel<P, 4><<<tiles, block, 0, s>>>(d_inst, count, (T*)pool_f, cur, (const C*)pool_psi);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t batch_launch(int precision, const BatchInst* d_inst, int count, int psi_blocks, int tiles,
+                         void* pool_f, int cur, void* pool_psi, int* flag, dim3 block, int minb,
+                         cudaStream_t s) {
+  switch (precision) {
+    case LBM_F64:
+      return batch_launch_t<LBM_F64>(d_inst, count, psi_blocks, tiles, pool_f, cur, pool_psi, flag, block, minb, s);
+    case LBM_F32:
+      return batch_launch_t<LBM_F32>(d_inst, count, psi_blocks, tiles, pool_f, cur, pool_psi, flag, block, minb, s);
+    case LBM_F16DEV:
+      return batch_launch_t<LBM_F16DEV>(d_inst, count, psi_blocks, tiles, pool_f, cur, pool_psi, flag, block, minb, s);
+    case LBM_BF16DEV:
+      return batch_launch_t<LBM_BF16DEV>(d_inst, count, psi_blocks, tiles, pool_f, cur, pool_psi, flag, block, minb, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_batch_ctx {
+  int count = 0;
+  int precision = LBM_F32;
+  std::vector<lbm_instance> spec;
+  std::vector<BatchInst> inst;
+  BatchInst* d_inst = nullptr;
+  void* pool_f = nullptr;
+  size_t pool_f_bytes = 0;
+  void* pool_psi = nullptr;
+  size_t pool_psi_bytes = 0;
+  int* d_flag = nullptr;
+  double* d_small = nullptr;
+  double* d_scratch = nullptr;
+  size_t scratch_doubles = 0;
+  int* d_labels = nullptr;
+  size_t labels_ints = 0;
+  double* d_plane = nullptr;
+  long long max_nodes = 0, total_nodes = 0;
+  int tiles = 0, psi_blocks = 0;
+  dim3 block{32, 8, 1};
+  int minb = 2;
+  bool vec = true;
+  int cur = 0;
+  long long step = 0;
+  bool initialized = false;
+  bool use_graph = true;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaStream_t stream = nullptr, own_stream = nullptr;
+};
+
+namespace {
+
+thread_local std::string b_err;
+
+int bfail(int status, const std::string& m);
+int bcuda(cudaError_t e, const char* where);
+
+#define BCK(call)                                    \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return bcuda(e_, #call);  \
+  } while (0)
+
+void drop_graphs(lbm_batch_ctx* b) {
+  for (auto& g : b->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+// Recomputes the tile table for the current block shape and uploads it.
+int layout_tiles(lbm_batch_ctx* b) {
+  int tiles = 0, psi_blocks = 0;
+  for (auto& I : b->inst) {
+    I.vec = (b->vec && I.g.nx % 2 == 0) ? 1 : 0;
+    const int ux = I.vec ? I.g.nx / 2 : I.g.nx;
+    I.tile0 = tiles;
+    I.tx = (ux + b->block.x - 1) / b->block.x;
+    I.ty = (I.g.ny + b->block.y - 1) / b->block.y;
+    const int tz = (I.g.nz + b->block.z - 1) / b->block.z;
+    tiles += I.tx * I.ty * tz;
+    I.psi_block0 = psi_blocks;
+    psi_blocks += (int)(((I.vec ? I.g.N / 2 : I.g.N) + 255) / 256);
+  }
+  b->tiles = tiles;
+  b->psi_blocks = psi_blocks;
+  BCK(cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(BatchInst) * b->count, cudaMemcpyHostToDevice,
+                      b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  drop_graphs(b);
+  return LBM_OK;
+}
+
+int enqueue_batch_step(lbm_batch_ctx* b, cudaStream_t s, int cur) {
+  BCK(batch_launch(b->precision, b->d_inst, b->count, b->psi_blocks, b->tiles, b->pool_f, cur, b->pool_psi,
+                   b->d_flag, b->block, b->minb, s));
+  return LBM_OK;
+}
+
+int capture_pair(lbm_batch_ctx* b, int phase) {
+  cudaStream_t cs;
+  BCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  int rc = LBM_OK;
+  if (e == cudaSuccess) {
+    rc = enqueue_batch_step(b, cs, phase);
+    if (rc == LBM_OK) rc = enqueue_batch_step(b, cs, phase ^ 1);
+    e = cudaStreamEndCapture(cs, &g);
+  }
+  cudaStreamDestroy(cs);
+  if (rc != LBM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return bcuda(e, "batch graph capture");
+  e = cudaGraphInstantiate(&b->graph[phase], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b->graph[phase] = nullptr;
+    return bcuda(e, "cudaGraphInstantiate");
+  }
+  return LBM_OK;
+}
+
+// A single-lattice view (geometry, physics, current array) of instance k.
+struct View {
+  Geom g;
+  Phys ph;
+  void* f;
+  void* psi;
+};
+
+View view_of(lbm_batch_ctx* b, int k) {
+  const BatchInst& I = b->inst[k];
+  const size_t e = elem_size(b->precision);
+  const size_t pe = b->precision == LBM_F64 ? 8 : 4;
+  View v;
+  v.g = I.g;
+  v.ph = I.ph;
+  v.f = (char*)b->pool_f + (I.off_f + (long long)b->cur * Q * I.g.N) * e;
+  v.psi = (char*)b->pool_psi + I.off_psi * pe;
+  return v;
+}
+
+int bfail(int status, const std::string& m) {
+  b_err = m;
+  // surface through the single-lattice error channel as well
+  return status;
+}
+
+int bcuda(cudaError_t e, const char* where) {
+  b_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_batch_last_error(void) { return b_err.c_str(); }
+
+void lbm_batch_destroy(lbm_batch b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  drop_graphs(b);
+  cudaFree(b->d_inst);
+  cudaFree(b->pool_f);
+  cudaFree(b->pool_psi);
+  cudaFree(b->d_flag);
+  cudaFree(b->d_small);
+  cudaFree(b->d_scratch);
+  cudaFree(b->d_labels);
+  cudaFree(b->d_plane);
+  if (b->own_stream) cudaStreamDestroy(b->own_stream);
+  delete b;
+}
+
+lbm_batch lbm_batch_create(const lbm_instance* inst, int count, int precision, int psi_form, double rho0,
+                           void* stream) {
+  if (!inst || count < 1 || count > 1 << 20) {
+    bfail(LBM_ERR_ARG, "need 1 <= count <= 2^20 instances");
+    return nullptr;
+  }
+  if (precision < LBM_F64 || precision > LBM_BF16DEV || (psi_form != LBM_PSI_EXP && psi_form != LBM_PSI_RHO) ||
+      !(rho0 > 0.0) || !std::isfinite(rho0)) {
+    bfail(LBM_ERR_ARG, "bad precision, psi_form or rho0");
+    return nullptr;
+  }
+  lbm_batch_ctx* b = new (std::nothrow) lbm_batch_ctx();
+  if (!b) {
+    bfail(LBM_ERR_OOM, "host allocation failed");
+    return nullptr;
+  }
+  b->count = count;
+  b->precision = precision;
+  b->spec.assign(inst, inst + count);
+  long long off_f = 0, off_psi = 0;
+  for (int k = 0; k < count; ++k) {
+    const lbm_instance& s = inst[k];
+    const long long N = (long long)s.nx * s.ny * s.nz;
+    if (s.nx < 3 || s.ny < 3 || s.nz < 3 || N > 0x7fffffffLL || !(s.tau > 0.5) || !std::isfinite(s.tau) ||
+        !std::isfinite(s.G) || !(s.rho_l > s.rho_v) || !(s.rho_v > 0.0) || !(s.width > 0.0) || !(s.lambda > 0.0)) {
+      bfail(LBM_ERR_ARG, "instance " + std::to_string(k) + ": bad size or parameters");
+      delete b;
+      return nullptr;
+    }
+    BatchInst I;
+    std::memset(&I, 0, sizeof(I));
+    I.g = Geom{s.nx, s.ny, s.nz, N};
+    I.ph = Phys{s.tau, s.G, rho0, precision >= LBM_F16DEV ? s.rho_v : 0.0, psi_form};
+    I.off_f = off_f;
+    I.off_psi = off_psi;
+    off_f += 2 * (long long)Q * N;
+    off_psi += N;
+    b->inst.push_back(I);
+    b->max_nodes = N > b->max_nodes ? N : b->max_nodes;
+    b->total_nodes += N;
+  }
+  const size_t e = elem_size(precision);
+  b->pool_f_bytes = (size_t)off_f * e;
+  b->pool_psi_bytes = (size_t)off_psi * (precision == LBM_F64 ? 8 : 4);
+  cudaError_t err = cudaSuccess;
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    err = cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking);
+    b->stream = b->own_stream;
+  }
+  if (err == cudaSuccess) err = cudaMalloc(&b->d_inst, sizeof(BatchInst) * count);
+  if (err == cudaSuccess) err = cudaMalloc(&b->pool_f, b->pool_f_bytes);
+  if (err == cudaSuccess) err = cudaMalloc(&b->pool_psi, b->pool_psi_bytes);
+  if (err == cudaSuccess) err = cudaMalloc(&b->d_flag, sizeof(int) * 4);
+  if (err == cudaSuccess) err = cudaMalloc(&b->d_small, sizeof(double) * 64);
+  if (err == cudaSuccess) err = cudaMemsetAsync(b->d_flag, 0, sizeof(int) * 4, b->stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(b->pool_f, 0, b->pool_f_bytes, b->stream);
+  if (err != cudaSuccess) {
+    bcuda(err, "lbm_batch_create");
+    lbm_batch_destroy(b);
+    return nullptr;
+  }
+  if (layout_tiles(b) != LBM_OK) {
+    lbm_batch_destroy(b);
+    return nullptr;
+  }
+  return b;
+}
+
+int lbm_batch_set_stream(lbm_batch b, void* stream) {
+  if (!b) return bfail(LBM_ERR_ARG, "null batch");
+  BCK(cudaStreamSynchronize(b->stream));
+  b->stream = stream ? (cudaStream_t)stream : b->own_stream;
+  if (!b->stream) {
+    BCK(cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking));
+    b->stream = b->own_stream;
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_set_option(lbm_batch b, const char* key, double v) {
+  if (!b || !key) return bfail(LBM_ERR_ARG, "null argument");
+  const std::string k(key);
+  if (k == "graph") {
+    b->use_graph = v != 0.0;
+    return LBM_OK;
+  }
+  if (k == "vector") {
+    b->vec = v != 0.0;
+    return layout_tiles(b);
+  }
+  if (k == "occupancy") {
+    if (v != 2.0 && v != 3.0 && v != 4.0) return bfail(LBM_ERR_ARG, "occupancy must be 2, 3 or 4");
+    b->minb = (int)v;
+    drop_graphs(b);
+    return LBM_OK;
+  }
+  if (k == "block_x" || k == "block_y" || k == "block_z") {
+    const long long n = (long long)v;
+    if (n < 1 || n > 256 || (double)n != v) return bfail(LBM_ERR_ARG, "block size must be an integer in 1..256");
+    dim3 nb = b->block;
+    if (k == "block_x") nb.x = (unsigned)n;
+    if (k == "block_y") nb.y = (unsigned)n;
+    if (k == "block_z") nb.z = (unsigned)n;
+    if ((long long)nb.x * nb.y * nb.z > 256 || nb.z > 64) return bfail(LBM_ERR_ARG, "block shape has more than 256 threads");
+    b->block = nb;
+    return layout_tiles(b);
+  }
+  return bfail(LBM_ERR_ARG, "unknown option " + k);
+}
+
+int lbm_batch_info(lbm_batch b, long long* total_nodes, int* collide_tiles, int* block3) {
+  if (!b) return bfail(LBM_ERR_ARG, "null batch");
+  if (total_nodes) *total_nodes = b->total_nodes;
+  if (collide_tiles) *collide_tiles = b->tiles;
+  if (block3) {
+    block3[0] = (int)b->block.x;
+    block3[1] = (int)b->block.y;
+    block3[2] = (int)b->block.z;
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_init(lbm_batch b) {
+  if (!b) return bfail(LBM_ERR_ARG, "null batch");
+  b->cur = 0;
+  b->step = 0;
+  for (int k = 0; k < b->count; ++k) {
+    const lbm_instance& s = b->spec[k];
+    View v = view_of(b, k);
+    InitSpec sp{s.R0, s.lambda, s.eps, s.phase, s.rho_l, s.rho_v, s.width, nullptr, 0, 0.0, 1.0};
+    BCK(launch_init(b->precision, v.g, v.ph, sp, v.f, b->stream));
+  }
+  BCK(cudaStreamSynchronize(b->stream));
+  b->initialized = true;
+  return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch b, int n) {
+  if (!b || n < 0) return bfail(LBM_ERR_ARG, "null batch or negative step count");
+  if (!b->initialized) return bfail(LBM_ERR_STATE, "batch not initialised");
+  while (n > 0) {
+    if (b->use_graph && n >= 2) {
+      if (!b->graph[b->cur]) {
+        int rc = capture_pair(b, b->cur);
+        if (rc) return rc;
+      }
+      BCK(cudaGraphLaunch(b->graph[b->cur], b->stream));
+      n -= 2;
+      b->step += 2;
+    } else {
+      int rc = enqueue_batch_step(b, b->stream, b->cur);
+      if (rc) return rc;
+      b->cur ^= 1;
+      n -= 1;
+      b->step += 1;
+    }
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_step_sequential(lbm_batch b, int n) {
+  if (!b || n < 0) return bfail(LBM_ERR_ARG, "null batch or negative step count");
+  if (!b->initialized) return bfail(LBM_ERR_STATE, "batch not initialised");
+  const size_t e = elem_size(b->precision);
+  for (int s = 0; s < n; ++s) {
+    for (int k = 0; k < b->count; ++k) {
+      View v = view_of(b, k);
+      void* dst = (char*)v.f + (b->cur ? -1 : 1) * (long long)Q * v.g.N * (long long)e;
+      const bool vec = b->inst[k].vec != 0;
+      BCK(launch_psi(b->precision, LAYOUT_LOCAL, vec, v.g, v.ph, v.f, v.psi, b->d_flag, b->stream));
+      BCK(launch_collide(b->precision, MODE_AB, b->minb, vec, v.g, v.ph, v.f, dst, v.psi, b->block,
+                         b->stream));
+    }
+    b->cur ^= 1;
+    b->step += 1;
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_sync(lbm_batch b) {
+  if (!b) return bfail(LBM_ERR_ARG, "null batch");
+  int flag = 0;
+  BCK(cudaMemcpyAsync(&flag, b->d_flag, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  if (flag) {
+    BCK(cudaMemsetAsync(b->d_flag, 0, sizeof(int), b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    return bfail(LBM_ERR_NUMERIC, "a density became non-positive or non-finite");
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_get_populations(lbm_batch b, int k, double* host) {
+  if (!b || !host || k < 0 || k >= b->count) return bfail(LBM_ERR_ARG, "bad batch, instance or buffer");
+  if (!b->d_plane) BCK(cudaMalloc(&b->d_plane, sizeof(double) * b->max_nodes));
+  View v = view_of(b, k);
+  for (int a = 0; a < Q; ++a) {
+    BCK(launch_get_plane(b->precision, LAYOUT_LOCAL, v.g, v.ph, v.f, a, b->d_plane, b->stream));
+    BCK(cudaMemcpyAsync(host + (size_t)a * v.g.N, b->d_plane, sizeof(double) * v.g.N, cudaMemcpyDeviceToHost,
+                        b->stream));
+  }
+  BCK(cudaStreamSynchronize(b->stream));
+  return LBM_OK;
+}
+
+int lbm_batch_diagnostics(lbm_batch b, int k, lbm_diag* out, int want_ccl) {
+  if (!b || !out || k < 0 || k >= b->count) return bfail(LBM_ERR_ARG, "bad batch, instance or output");
+  View v = view_of(b, k);
+  const size_t need = diag_scratch_doubles(v.g);
+  if (need > b->scratch_doubles) {
+    cudaFree(b->d_scratch);
+    b->d_scratch = nullptr;
+    BCK(cudaMalloc(&b->d_scratch, sizeof(double) * need));
+    b->scratch_doubles = need;
+  }
+  const lbm_instance& s = b->spec[k];
+  BCK(launch_diagnostics(b->precision, LAYOUT_LOCAL, v.g, v.ph, v.f, s.rho_l, s.rho_v, b->d_scratch, b->d_small,
+                         nullptr, nullptr, nullptr, 0, b->stream));
+  double r[DIAG_OUT];
+  long long c4[4] = {-1, -1, -1, 0};
+  if (want_ccl) {
+    if ((size_t)(2 * v.g.N) > b->labels_ints) {
+      cudaFree(b->d_labels);
+      b->d_labels = nullptr;
+      BCK(cudaMalloc(&b->d_labels, sizeof(int) * 2 * b->max_nodes));
+      b->labels_ints = 2 * b->max_nodes;
+    }
+    long long* d4 = (long long*)(b->d_small + 32);
+    BCK(launch_ccl(b->precision, LAYOUT_LOCAL, v.g, v.ph, v.f, 0.5 * (s.rho_l + s.rho_v), b->d_labels,
+                   b->d_labels + v.g.N, d4, b->stream));
+    BCK(cudaMemcpyAsync(c4, d4, sizeof(c4), cudaMemcpyDeviceToHost, b->stream));
+  }
+  BCK(cudaMemcpyAsync(r, b->d_small, sizeof(r), cudaMemcpyDeviceToHost, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  if (want_ccl && c4[3]) return bfail(LBM_ERR_TIMEOUT, "connected-component labelling guard tripped");
+  std::memset(out, 0, sizeof(*out));
+  out->step = b->step;
+  out->mass = r[0];
+  out->mom[0] = r[1];
+  out->mom[1] = r[2];
+  out->mom[2] = r[3];
+  out->liquid_volume_w = r[4];
+  out->liquid_count = (long long)r[5];
+  out->min_slice_area_w = r[6];
+  out->min_slice_count = (long long)r[7];
+  out->min_slice_x = (int)r[8];
+  out->neck_radius = std::sqrt(r[6] / 3.14159265358979323846);
+  out->max_u = r[9];
+  out->rho_min = r[10];
+  out->rho_max = r[11];
+  out->numeric_ok = (int)r[12];
+  out->droplets = (int)c4[0];
+  out->droplets_min8 = (int)c4[1];
+  out->largest_droplet = c4[2];
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -101,10 +101,11 @@ struct Phys {
 
 // Neighbour index table of one node: x-1, x, x+1 and the 9 row offsets of
 // (y + dy, z + dz), all periodic.  idx(cxa, cya, cza) is the flat index of
-// the node x + c.
+// the node x + c.  Indices within one plane are 32-bit (N < 2^31 is checked
+// at creation); plane offsets a * N are formed in 64 bits by the caller.
 struct Nbr {
-  long long xs[3];
-  long long rows[3][3];
+  int xs[3];
+  int rows[3][3];
   __device__ __forceinline__ void make(const Geom& g, int x, int y, int z) {
     const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
     const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
@@ -116,12 +117,25 @@ struct Nbr {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) rows[i][k] = (long long)g.nx * ((long long)yv[i] + (long long)g.ny * zv[k]);
+      for (int k = 0; k < 3; ++k) rows[i][k] = g.nx * (yv[i] + g.ny * zv[k]);
   }
-  __device__ __forceinline__ long long idx(int dx, int dy, int dz) const {
+  __device__ __forceinline__ int idx(int dx, int dy, int dz) const {
     return xs[dx + 1] + rows[dy + 1][dz + 1];
   }
 };
+
+// Raises *flag when any active lane of the warp has bad != 0, with at most
+// one atomic per warp (a lattice that has gone non-finite everywhere must not
+// serialise on the flag).
+__device__ __forceinline__ void raise_flag(bool bad, int* flag) {
+  const unsigned m = __ballot_sync(__activemask(), bad);
+  if (m) {
+    unsigned lane;
+    asm("mov.u32 %0, %%laneid;" : "=r"(lane));
+    // once set, later warps only read the flag
+    if (lane == (unsigned)(__ffs(m) - 1) && *(volatile int*)flag == 0) atomicOr(flag, 1);
+  }
+}
 
 // psi(rho) (definition after Eq. 5).
 template <typename C>

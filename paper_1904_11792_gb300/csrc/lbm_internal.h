@@ -29,11 +29,15 @@ size_t elem_size(int precision);
 // ---- launchers (lbm_step.cu) ---------------------------------------------
 // psi pass: psi[i] = psi(rho_i) for all nodes; flag |= 1 on a non-positive
 // or non-finite density.
-cudaError_t launch_psi(int precision, int layout, const Geom& g, const Phys& ph, const void* f,
-                       void* psi, int* flag, cudaStream_t s);
-// fused force + collision + streaming of one step.
-cudaError_t launch_collide(int precision, int mode, const Geom& g, const Phys& ph, const void* src,
-                           void* dst, const void* psi, dim3 block, cudaStream_t s);
+// vec: two nodes per thread with vector accesses (used when nx is even).
+cudaError_t launch_psi(int precision, int layout, bool vec, const Geom& g, const Phys& ph,
+                       const void* f, void* psi, int* flag, cudaStream_t s);
+// fused force + collision + streaming of one step; block has at most 256
+// threads (with vec, block.x counts node pairs); minb (2, 3, 4) = blocks per
+// SM the register budget must allow.
+cudaError_t launch_collide(int precision, int mode, int minb, bool vec, const Geom& g,
+                           const Phys& ph, const void* src, void* dst, const void* psi, dim3 block,
+                           cudaStream_t s);
 
 // ---- auxiliary kernels (lbm_aux.cu) ---------------------------------------
 struct InitSpec {
@@ -56,12 +60,19 @@ cudaError_t launch_moments(int precision, int layout, const Geom& g, const Phys&
 
 // Diagnostics reduction.  scratch must hold diag_scratch_doubles(g) doubles.
 size_t diag_scratch_doubles(const Geom& g);
-// out (device) receives DIAG_OUT doubles in the order of the oracle's
-// diagnostics; see lbm_aux.cu.
+// Results: DIAG_OUT doubles, 0 mass, 1-3 momentum, 4 liquid volume (phi),
+// 5 liquid count, 6 min slice area (phi), 7 min slice count, 8 its x,
+// 9 max |j|/rho, 10 min rho, 11 max rho, 12 numeric ok (1/0).  A ring
+// record holds them plus, at DIAG_OUT, its sequence number.
 constexpr int DIAG_OUT = 13;
+constexpr int DIAG_STRIDE = 16;
+// psi (nullable): also write psi of every node and raise flag on a bad
+// density (the psi pass of a diagnostic step).  ring_count (nullable):
+// append the record to the ring at out instead of writing out[0..12].
 cudaError_t launch_diagnostics(int precision, int layout, const Geom& g, const Phys& ph,
                                const void* f, double rho_l, double rho_v, double* scratch,
-                               double* out, cudaStream_t s);
+                               double* out, void* psi, int* flag,
+                               unsigned long long* ring_count, int ring_cap, cudaStream_t s);
 
 // Connected components of the liquid mask.  labels: N ints; sizes: N ints;
 // out3 (device, 4 long long): components, components with >= 8 nodes,
@@ -98,10 +109,23 @@ struct lbm_ctx {
   size_t scratch_doubles = 0;
   int* d_labels = nullptr;        // CCL labels and sizes (2 N ints)
 
-  // CUDA graphs of one A-B/AA step pair, keyed by the phase they start on
+  // CUDA graphs of one chunk of steps, keyed by the A-B array they start on
+  // (AA chunks always start on an even step)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_chunk = 0;            // steps per captured chunk
   bool use_graph = true;
   dim3 block{0, 0, 0};
+  int minb = 0;                   // collide kernel register budget variant (0 = auto)
+  bool vec = true;                // two nodes per thread (when nx is even)
+
+  // diagnostics inside the time loop: every diag_interval steps the psi
+  // pass also reduces the diagnostics into a device ring of records
+  int diag_interval = 0;
+  static constexpr int kRing = 1024;
+  double* d_ring = nullptr;                 // kRing * DIAG_STRIDE doubles
+  unsigned long long* d_ring_count = nullptr;
+  std::vector<long long> diag_steps;        // step of every record launched
+  long long diag_fetched = 0;               // records already returned
 
   // kernel timing
   bool kernel_timing = false;

@@ -1,0 +1,415 @@
+// Per-node bodies of the two time-step kernels, shared by the single-lattice
+// kernels (lbm_step.cu) and the batched kernels (lbm_batch.cu) so that a
+// batched instance computes bitwise what a standalone lattice computes.
+//
+//   psi pass      rho = sum_a f_a (Eq. 4) and psi(rho) of a node.  The force
+//                 of Eq. 5 needs psi of all 18 neighbours at the same time
+//                 level, so psi exists for the whole lattice before any
+//                 collision starts.
+//   collide       moments (Eq. 4), Shan-Chen force from the neighbour psi
+//                 (Eq. 5), velocity shift u' = (j + tau F)/rho (Eq. 6),
+//                 second-order equilibrium (Eq. 2, with the leading 1), BGK
+//                 relaxation (Eq. 3) and streaming to x + c_a.
+//
+// Each comes in a one-node form and a two-node form (x and x + 1, x even)
+// that loads and stores pairs of populations as one 2-element vector where
+// the addresses allow it.  Both forms call the same arithmetic
+// (collide_math, psi_math), so their results are identical.
+#pragma once
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+template <int P>
+__device__ __forceinline__ typename Prec<P>::C shift_of(int a, double rho_ref) {
+  using C = typename Prec<P>::C;
+  if constexpr (Prec<P>::dev) {
+    return (C)(wgt(a) * rho_ref);
+  } else {
+    return (C)0;
+  }
+}
+
+// Two adjacent stored populations (x, x + 1) as one vector access.
+template <int P> struct Pair;
+template <> struct Pair<LBM_F64> {
+  using V = double2;
+  __device__ static __forceinline__ void unpack(V v, double& a, double& b) { a = v.x; b = v.y; }
+  __device__ static __forceinline__ V pack(double a, double b) { return make_double2(a, b); }
+};
+template <> struct Pair<LBM_F32> {
+  using V = float2;
+  __device__ static __forceinline__ void unpack(V v, float& a, float& b) { a = v.x; b = v.y; }
+  __device__ static __forceinline__ V pack(float a, float b) { return make_float2(a, b); }
+};
+template <> struct Pair<LBM_F16DEV> {
+  using V = __half2;
+  __device__ static __forceinline__ void unpack(V v, float& a, float& b) {
+    a = __low2float(v);
+    b = __high2float(v);
+  }
+  __device__ static __forceinline__ V pack(float a, float b) {
+    return __halves2half2(__float2half_rn(a), __float2half_rn(b));
+  }
+};
+template <> struct Pair<LBM_BF16DEV> {
+  using V = __nv_bfloat162;
+  __device__ static __forceinline__ void unpack(V v, float& a, float& b) {
+    a = __low2float(v);
+    b = __high2float(v);
+  }
+  __device__ static __forceinline__ V pack(float a, float b) {
+    return __halves2bfloat162(__float2bfloat16_rn(a), __float2bfloat16_rn(b));
+  }
+};
+
+// Loads populations x and x + 1 (RO: read-only path; else a plain load for
+// in-place updates) and adds the deviation shift.
+template <int P, bool RO>
+__device__ __forceinline__ void load_pair(const typename Prec<P>::T* p, typename Prec<P>::C sh,
+                                          typename Prec<P>::C& a, typename Prec<P>::C& b) {
+  using V = typename Pair<P>::V;
+  V v;
+  if constexpr (RO)
+    v = __ldg(reinterpret_cast<const V*>(p));
+  else
+    v = *reinterpret_cast<const V*>(p);
+  Pair<P>::unpack(v, a, b);
+  a += sh;
+  b += sh;
+}
+
+template <int P>
+__device__ __forceinline__ void store_pair(typename Prec<P>::T* p, typename Prec<P>::C a,
+                                           typename Prec<P>::C b, typename Prec<P>::C sh) {
+  using V = typename Pair<P>::V;
+  *reinterpret_cast<V*>(p) = Pair<P>::pack(a - sh, b - sh);
+}
+
+// ---------------------------------------------------------------------------
+// arithmetic of one node
+// ---------------------------------------------------------------------------
+
+template <typename C>
+__device__ __forceinline__ C rho_of(const C f[Q]) {
+  C rho = 0;
+#pragma unroll
+  for (int a = 0; a < Q; ++a) rho += f[a];
+  return rho;
+}
+
+// Post-collision populations fs of a node with populations f, psi(x) = pc
+// and neighbour values pn[a] = psi(x + c_a) (a = 1..18).
+template <typename C>
+__device__ __forceinline__ void collide_math(const Phys& ph, const C f[Q], C pc, const C pn[Q],
+                                             C fs[Q]) {
+  // Eq. 4
+  C rho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    rho += f[a];
+    if (cx(a) > 0) jx += f[a];
+    if (cx(a) < 0) jx -= f[a];
+    if (cy(a) > 0) jy += f[a];
+    if (cy(a) < 0) jy -= f[a];
+    if (cz(a) > 0) jz += f[a];
+    if (cz(a) < 0) jz -= f[a];
+  }
+  // Eq. 5: sum_a w_a psi(x + c_a) c_a, split by weight class
+  C ax = 0, ay = 0, az = 0, dx = 0, dy = 0, dz = 0;
+#pragma unroll
+  for (int a = 1; a < Q; ++a) {
+    const C p = pn[a];
+    if (a <= 6) {
+      if (cx(a)) ax += cx(a) > 0 ? p : -p;
+      if (cy(a)) ay += cy(a) > 0 ? p : -p;
+      if (cz(a)) az += cz(a) > 0 ? p : -p;
+    } else {
+      if (cx(a)) dx += cx(a) > 0 ? p : -p;
+      if (cy(a)) dy += cy(a) > 0 ? p : -p;
+      if (cz(a)) dz += cz(a) > 0 ? p : -p;
+    }
+  }
+  const C w1 = (C)(1.0 / 18.0), w2 = (C)(1.0 / 36.0);
+  const C gp = -(C)ph.G * pc;
+  const C Fx = gp * (w1 * ax + w2 * dx);
+  const C Fy = gp * (w1 * ay + w2 * dy);
+  const C Fz = gp * (w1 * az + w2 * dz);
+  // Eq. 6
+  const C tau = (C)ph.tau;
+  const C inv_rho = (C)1 / rho;
+  const C ux = (jx + tau * Fx) * inv_rho;
+  const C uy = (jy + tau * Fy) * inv_rho;
+  const C uz = (jz + tau * Fz) * inv_rho;
+  const C usq = (C)1.5 * (ux * ux + uy * uy + uz * uz);
+  const C omega = (C)1 / tau;
+  // Eq. 2 and Eq. 3.  The moving populations a = 1..18 take f_eq from Eq. 2
+  // directly; the rest population takes f_eq_0 = rho - sum_{a>=1} f_eq_a,
+  // which equals Eq. 2's w_0 rho (1 - 3/2 u.u) for the exact weights
+  // (sum_{a>=1} w_a = 2/3, sum_{a>=1} w_a (c_a.u)^2 = u.u/3).  With weights
+  // rounded to the arithmetic's precision the direct form makes every
+  // collision create mass of relative order 1e-8 (FP32) in one direction;
+  // this form conserves mass up to unbiased rounding.
+  C feq_sum = 0;
+#pragma unroll
+  for (int a = 1; a < Q; a += 2) {
+    const int b = a + 1;  // opp(a)
+    const C cu = cx(a) * ux + cy(a) * uy + cz(a) * uz;
+    const C wr = (C)wgt(a) * rho;
+    const C even = (C)1 + (C)4.5 * cu * cu - usq;
+    const C feq_a = wr * (even + (C)3 * cu);
+    const C feq_b = wr * (even - (C)3 * cu);
+    feq_sum += feq_a + feq_b;
+    fs[a] = f[a] - omega * (f[a] - feq_a);
+    fs[b] = f[b] - omega * (f[b] - feq_b);
+  }
+  const C feq_0 = rho - feq_sum;
+  fs[0] = f[0] - omega * (f[0] - feq_0);
+}
+
+template <typename C>
+__device__ __forceinline__ void psi_math(const Phys& ph, C rho, C* out, int* flag) {
+  *out = psi_of<C>(rho, ph.psi_form, (C)ph.rho0);
+  // non-positive, NaN or infinite density
+  raise_flag(!(rho > (C)0) || !(rho <= (C)3.0e38), flag);
+}
+
+// ---------------------------------------------------------------------------
+// psi pass
+// ---------------------------------------------------------------------------
+
+// LAYOUT_LOCAL reads slot a at x; LAYOUT_GATHER (AA before an odd step)
+// reads slot opp(a) at x - c_a.
+template <int P, int LAYOUT>
+__device__ __forceinline__ void psi_node(const Geom& g, const Phys& ph,
+                                         const typename Prec<P>::T* f,
+                                         typename Prec<P>::C* __restrict__ psi,
+                                         int* __restrict__ flag, long long i) {
+  using C = typename Prec<P>::C;
+  const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
+          s2 = shift_of<P>(7, ph.rho_ref);
+  C fv[Q];
+  if constexpr (LAYOUT == LAYOUT_LOCAL) {
+#pragma unroll
+    for (int a = 0; a < Q; ++a)
+      fv[a] = Prec<P>::load(f + (long long)a * g.N + i, a == 0 ? s0 : (a <= 6 ? s1 : s2));
+  } else {
+    const int x = (int)(i % g.nx);
+    const long long r = i / g.nx;
+    const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+    Nbr nb;
+    nb.make(g, x, y, z);
+#pragma unroll
+    for (int a = 0; a < Q; ++a)
+      fv[a] = Prec<P>::load(f + (long long)opp(a) * g.N + nb.idx(-cx(a), -cy(a), -cz(a)),
+                            a == 0 ? s0 : (a <= 6 ? s1 : s2));
+  }
+  psi_math<C>(ph, rho_of<C>(fv), psi + i, flag);
+}
+
+// Two nodes i, i + 1 (i even, nx even), vector loads where the addresses
+// allow (all of LAYOUT_LOCAL; the c_x = 0 slots of LAYOUT_GATHER) and a
+// vector store of the two psi values.
+template <int P, int LAYOUT>
+__device__ __forceinline__ void psi_pair(const Geom& g, const Phys& ph, const typename Prec<P>::T* f,
+                                         typename Prec<P>::C* __restrict__ psi,
+                                         int* __restrict__ flag, long long i) {
+  using C = typename Prec<P>::C;
+  const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
+          s2 = shift_of<P>(7, ph.rho_ref);
+  C f0[Q], f1[Q];
+  if constexpr (LAYOUT == LAYOUT_LOCAL) {
+#pragma unroll
+    for (int a = 0; a < Q; ++a)
+      load_pair<P, true>(f + (long long)a * g.N + i, a == 0 ? s0 : (a <= 6 ? s1 : s2), f0[a], f1[a]);
+  } else {
+    const int x0 = (int)(i % g.nx);
+    const long long r = i / g.nx;
+    const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+    const int xm = x0 == 0 ? g.nx - 1 : x0 - 1, xp = x0 + 2 == g.nx ? 0 : x0 + 2;
+    const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+    const int yv[3] = {ym, y, yp}, zv[3] = {zm, z, zp};
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      // slot opp(a) at x - c_a
+      const int row = g.nx * (yv[1 - cy(a)] + g.ny * zv[1 - cz(a)]);
+      const typename Prec<P>::T* base = f + (long long)opp(a) * g.N + row;
+      const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
+      if (cx(a) == 0) {
+        load_pair<P, true>(base + x0, sh, f0[a], f1[a]);
+      } else if (cx(a) > 0) {  // from x0 - 1 and x0
+        f0[a] = Prec<P>::load(base + xm, sh);
+        f1[a] = Prec<P>::load(base + x0, sh);
+      } else {                 // from x0 + 1 and x0 + 2
+        f0[a] = Prec<P>::load(base + x0 + 1, sh);
+        f1[a] = Prec<P>::load(base + xp, sh);
+      }
+    }
+  }
+  C p0, p1;
+  psi_math<C>(ph, rho_of<C>(f0), &p0, flag);
+  psi_math<C>(ph, rho_of<C>(f1), &p1, flag);
+  if constexpr (sizeof(C) == 4) {
+    *reinterpret_cast<float2*>(psi + i) = make_float2(p0, p1);
+  } else {
+    *reinterpret_cast<double2*>(psi + i) = make_double2(p0, p1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// collide + stream
+// ---------------------------------------------------------------------------
+
+// One node.
+template <int P, int MODE>
+__device__ __forceinline__ void collide_node(const Geom& g, const Phys& ph,
+                                             const typename Prec<P>::T* src,
+                                             typename Prec<P>::T* dst,
+                                             const typename Prec<P>::C* __restrict__ psi, int x,
+                                             int y, int z) {
+  using C = typename Prec<P>::C;
+  Nbr nb;
+  nb.make(g, x, y, z);
+  const int i = nb.idx(0, 0, 0);
+  const long long N = g.N;
+  const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
+          s2 = shift_of<P>(7, ph.rho_ref);
+  C f[Q];
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
+    if constexpr (MODE == MODE_AB)
+      f[a] = Prec<P>::load(src + (long long)a * N + i, sh);
+    else if constexpr (MODE == MODE_AA_EVEN)
+      f[a] = Prec<P>::load_rw(src + (long long)a * N + i, sh);
+    else
+      f[a] = Prec<P>::load_rw(src + (long long)opp(a) * N + nb.idx(-cx(a), -cy(a), -cz(a)), sh);
+  }
+  C pn[Q];
+  pn[0] = 0;
+#pragma unroll
+  for (int a = 1; a < Q; ++a) pn[a] = __ldg(psi + nb.idx(cx(a), cy(a), cz(a)));
+  C fs[Q];
+  collide_math<C>(ph, f, __ldg(psi + i), pn, fs);
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
+    long long d;  // 64-bit: plane offset a * N plus the in-plane index
+    if constexpr (MODE == MODE_AA_EVEN)
+      d = (long long)opp(a) * N + i;
+    else
+      d = (long long)a * N + nb.idx(cx(a), cy(a), cz(a));
+    Prec<P>::store(dst + d, fs[a], sh);
+  }
+}
+
+// Two nodes x0, x0 + 1 of one row (x0 even, nx even).  Populations whose
+// address pair is contiguous and aligned (x unchanged) move as one vector;
+// those shifted along x (c_x != 0 on a gather or scatter) move one by one.
+template <int P, int MODE>
+__device__ __forceinline__ void collide_pair(const Geom& g, const Phys& ph,
+                                             const typename Prec<P>::T* src,
+                                             typename Prec<P>::T* dst,
+                                             const typename Prec<P>::C* __restrict__ psi, int x0,
+                                             int y, int z) {
+  using C = typename Prec<P>::C;
+  const int xm = x0 == 0 ? g.nx - 1 : x0 - 1;      // left of node 0
+  const int xp = x0 + 2 == g.nx ? 0 : x0 + 2;      // right of node 1
+  const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+  const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+  const int yv[3] = {ym, y, yp}, zv[3] = {zm, z, zp};
+  int rows[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) rows[i][k] = g.nx * (yv[i] + g.ny * zv[k]);
+  // x of node k (0, 1) moved by d (-1, 0, 1)
+  auto xof = [&](int k, int d) -> int {
+    return k == 0 ? (d < 0 ? xm : (d > 0 ? x0 + 1 : x0)) : (d < 0 ? x0 : (d > 0 ? xp : x0 + 1));
+  };
+  const int i0 = x0 + rows[1][1];
+  const long long N = g.N;
+  const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
+          s2 = shift_of<P>(7, ph.rho_ref);
+
+  C f0[Q], f1[Q];
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
+    if constexpr (MODE == MODE_AB) {
+      load_pair<P, true>(src + (long long)a * N + i0, sh, f0[a], f1[a]);
+    } else if constexpr (MODE == MODE_AA_EVEN) {
+      load_pair<P, false>(src + (long long)a * N + i0, sh, f0[a], f1[a]);
+    } else {
+      const int r = rows[1 - cy(a)][1 - cz(a)];
+      const typename Prec<P>::T* base = src + (long long)opp(a) * N + r;
+      if (cx(a) == 0) {
+        load_pair<P, false>(base + x0, sh, f0[a], f1[a]);
+      } else {
+        f0[a] = Prec<P>::load_rw(base + xof(0, -cx(a)), sh);
+        f1[a] = Prec<P>::load_rw(base + xof(1, -cx(a)), sh);
+      }
+    }
+  }
+
+  // psi along the 9 rows (y + dy, z + dz): q[..][0] = x0 - 1, [1] = x0,
+  // [2] = x0 + 1, [3] = x0 + 2 (periodic); only the elements some direction
+  // of that row needs are loaded.
+  C q[3][3][4];
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+      const C* row = psi + rows[dy + 1][dz + 1];
+      C c0, c1;
+      if constexpr (sizeof(C) == 4) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(row + x0));
+        c0 = v.x;
+        c1 = v.y;
+      } else {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(row + x0));
+        c0 = v.x;
+        c1 = v.y;
+      }
+      q[dy + 1][dz + 1][1] = c0;
+      q[dy + 1][dz + 1][2] = c1;
+      // rows holding a direction with c_x != 0: (0,0), (+-1,0), (0,+-1)
+      if (dy == 0 || dz == 0) {
+        q[dy + 1][dz + 1][0] = __ldg(row + xm);
+        q[dy + 1][dz + 1][3] = __ldg(row + xp);
+      } else {
+        q[dy + 1][dz + 1][0] = 0;
+        q[dy + 1][dz + 1][3] = 0;
+      }
+    }
+  C pn0[Q], pn1[Q];
+  pn0[0] = pn1[0] = 0;
+#pragma unroll
+  for (int a = 1; a < Q; ++a) {
+    pn0[a] = q[cy(a) + 1][cz(a) + 1][1 + cx(a)];
+    pn1[a] = q[cy(a) + 1][cz(a) + 1][2 + cx(a)];
+  }
+  C fs0[Q], fs1[Q];
+  collide_math<C>(ph, f0, q[1][1][1], pn0, fs0);
+  collide_math<C>(ph, f1, q[1][1][2], pn1, fs1);
+
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
+    if constexpr (MODE == MODE_AA_EVEN) {
+      store_pair<P>(dst + (long long)opp(a) * N + i0, fs0[a], fs1[a], sh);
+    } else {
+      typename Prec<P>::T* base = dst + (long long)a * N + rows[1 + cy(a)][1 + cz(a)];
+      if (cx(a) == 0) {
+        store_pair<P>(base + x0, fs0[a], fs1[a], sh);
+      } else {
+        Prec<P>::store(base + xof(0, cx(a)), fs0[a], sh);
+        Prec<P>::store(base + xof(1, cx(a)), fs1[a], sh);
+      }
+    }
+  }
+}
+
+}  // namespace lbm

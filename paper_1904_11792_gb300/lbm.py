@@ -32,9 +32,14 @@ PATTERNS = {"ab": LBM_AB, "aa": LBM_AA}
 EXPORTS = (
     "lbm_config_default", "lbm_required_bytes", "lbm_create", "lbm_create_ex", "lbm_destroy",
     "lbm_last_error", "lbm_strerror", "lbm_lattice", "lbm_set_stream", "lbm_set_option",
-    "lbm_get_option", "lbm_init_ligament", "lbm_init_profile", "lbm_step", "lbm_sync",
+    "lbm_get_option", "lbm_init_ligament", "lbm_init_profile", "lbm_step", "lbm_diag_history",
+    "lbm_sync",
     "lbm_moments", "lbm_diagnostics", "lbm_get_populations", "lbm_set_populations",
     "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_kernel_time",
+    "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_set_stream",
+    "lbm_batch_set_option", "lbm_batch_info", "lbm_batch_init", "lbm_batch_step",
+    "lbm_batch_step_sequential", "lbm_batch_sync", "lbm_batch_get_populations",
+    "lbm_batch_diagnostics",
 )
 
 
@@ -106,6 +111,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "lbm_init_profile": (I, [H, D, D, D, D, P, I, D, D]),
         "lbm_step": (I, [H, I]),
         "lbm_sync": (I, [H]),
+        "lbm_diag_history": (I, [H, P, I, P]),
         "lbm_moments": (I, [H, P, P, P, P]),
         "lbm_diagnostics": (I, [H, P, I]),
         "lbm_get_populations": (I, [H, P]),
@@ -116,13 +122,16 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "lbm_kernel_time": (I, [H, I, P, P]),
         "lbm_batch_create": (H, [P, I, I, I, D, P]),
         "lbm_batch_destroy": (None, [H]),
+        "lbm_batch_last_error": (ctypes.c_char_p, []),
+        "lbm_batch_set_stream": (I, [H, P]),
+        "lbm_batch_set_option": (I, [H, ctypes.c_char_p, D]),
+        "lbm_batch_info": (I, [H, P, P, P]),
         "lbm_batch_init": (I, [H]),
         "lbm_batch_step": (I, [H, I]),
         "lbm_batch_step_sequential": (I, [H, I]),
-        "lbm_batch_set_stream": (I, [H, P]),
+        "lbm_batch_sync": (I, [H]),
         "lbm_batch_get_populations": (I, [H, I, P]),
-        "lbm_batch_diagnostics": (I, [H, I, P]),
-        "lbm_batch_info": (I, [H, P, P, P]),
+        "lbm_batch_diagnostics": (I, [H, I, P, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name, None)
@@ -219,6 +228,13 @@ def lbm_step(h, n: int) -> None:
     check(load().lbm_step(h, int(n)))
 
 
+def lbm_diag_history(h, max_records: int = 1024) -> list:
+    arr = (lbm_diag * max(max_records, 1))()
+    n = ctypes.c_int()
+    check(load().lbm_diag_history(h, arr, int(max_records), ctypes.byref(n)))
+    return [arr[i].as_dict() for i in range(n.value)]
+
+
 def lbm_sync(h) -> None:
     check(load().lbm_sync(h))
 
@@ -269,6 +285,84 @@ def lbm_kernel_time(h, k: int):
     n, ms = ctypes.c_longlong(), ctypes.c_double()
     check(load().lbm_kernel_time(h, int(k), ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
+
+
+# ---- batched form -------------------------------------------------------------
+
+def _bcheck(status: int) -> None:
+    if status != LBM_OK:
+        raise LbmError(status, load().lbm_batch_last_error().decode())
+
+
+class Batch:
+    """Many independent ligaments of uneven size stepped together.
+
+    ``instances``: sequence of dicts (or objects) with nx, ny, nz, tau, G,
+    R0, lam, eps, phase, rho_l, rho_v, width."""
+
+    def __init__(self, instances, precision="f32", psi_form=LBM_PSI_EXP, rho0=1.0):
+        import torch
+        arr = (lbm_instance * len(instances))()
+        self.shapes = []
+        for k, d in enumerate(instances):
+            g = (lambda key: d[key]) if isinstance(d, dict) else (lambda key: getattr(d, key))
+            arr[k] = lbm_instance(g("nx"), g("ny"), g("nz"), g("tau"), g("G"), g("R0"), g("lam"),
+                                  g("eps"), g("phase"), g("rho_l"), g("rho_v"), g("width"))
+            self.shapes.append((g("nz"), g("ny"), g("nx")))
+        prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+        stream = torch.cuda.current_stream().cuda_stream or 1
+        self.b = load().lbm_batch_create(arr, len(instances), prec, psi_form, float(rho0),
+                                         ctypes.c_void_p(stream))
+        if not self.b:
+            raise LbmError(-1, load().lbm_batch_last_error().decode())
+
+    def close(self):
+        if getattr(self, "b", None):
+            load().lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_option(self, key, value):
+        _bcheck(load().lbm_batch_set_option(self.b, key.encode(), float(value)))
+
+    def info(self):
+        n, t = ctypes.c_longlong(), ctypes.c_int()
+        blk = (ctypes.c_int * 3)()
+        _bcheck(load().lbm_batch_info(self.b, ctypes.byref(n), ctypes.byref(t), blk))
+        return dict(total_nodes=n.value, tiles=t.value, block=tuple(blk))
+
+    def init(self):
+        _bcheck(load().lbm_batch_init(self.b))
+
+    def step(self, n=1):
+        _bcheck(load().lbm_batch_step(self.b, int(n)))
+
+    def step_sequential(self, n=1):
+        _bcheck(load().lbm_batch_step_sequential(self.b, int(n)))
+
+    def sync(self):
+        _bcheck(load().lbm_batch_sync(self.b))
+
+    def populations(self, k) -> np.ndarray:
+        out = np.zeros((Q,) + self.shapes[k])
+        _bcheck(load().lbm_batch_get_populations(self.b, int(k), _ptr(out)))
+        return out
+
+    def diagnostics(self, k, ccl=False) -> dict:
+        d = lbm_diag()
+        _bcheck(load().lbm_batch_diagnostics(self.b, int(k), ctypes.byref(d), int(bool(ccl))))
+        return d.as_dict()
 
 
 # ---- convenience wrapper --------------------------------------------------
@@ -357,6 +451,9 @@ class Lattice:
 
     def rho(self) -> np.ndarray:
         return lbm_moments(self.h, self.shape, ("rho",))["rho"]
+
+    def diag_history(self, max_records: int = 1024) -> list:
+        return lbm_diag_history(self.h, max_records)
 
     def diagnostics(self, ccl=False) -> dict:
         return lbm_diagnostics(self.h, ccl).as_dict()

