@@ -259,6 +259,44 @@ int lbm_batch_get_populations(lbm_batch b, int k, double *host);
 /* Diagnostics of instance k (as lbm_diagnostics). */
 int lbm_batch_diagnostics(lbm_batch b, int k, lbm_diag *out, int want_ccl);
 
+/* ---- diagnostics without device allocation ------------------------------
+ * The paper has no counterpart of this entry point.  It serves callers that
+ * cannot allocate device memory at the moment they need the diagnostics:
+ * code running while another stream of the process is capturing a CUDA
+ * graph (an allocation there can synchronise the device or break the
+ * capture), code inside an allocator or memory-pool callback (re-entering
+ * the allocator), and hosts that forbid the library to grow its device
+ * memory after start-up.  It computes what lbm_diagnostics computes (not the
+ * droplet count) from a population array the caller owns, with the same
+ * kernels, but keeps the reduction's partial sums in one static device array
+ * of lbm_diagnostics_noalloc_max_scratch() doubles (4 MiB) that every GPU
+ * loading the library holds until the process exits.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   f:       device populations of an nx x ny x nz lattice in the library's
+ *            storage layout with slot a of node i at f[a * N + i] (the current
+ *            array of an A-B lattice, or an AA lattice after an even number of
+ *            steps); for the *DEV precisions the stored deviations from
+ *            w_a * rho_ref.
+ *   out:     device array of 13 doubles: mass, momentum x, y, z, liquid volume
+ *            (sum of phi), liquid node count, minimum slice area (phi), minimum
+ *            slice node count, its x, max |j|/rho, min rho, max rho, 1 if every
+ *            density is finite and positive else 0 (definitions as lbm_diag).
+ *   stream:  cudaStream_t the kernels run on (NULL = the legacy default stream).
+ * Asynchronous: out holds the results once the stream reaches them.  The
+ * first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the array and leaves its last
+ * contents there (nothing in it needs to start at zero: the kernels write
+ * every partial before reading it); calls that overlap on the GPU (streams
+ * without an ordering between them) race and give wrong results.  A lattice
+ * whose reduction needs more partial sums than the array holds (very large
+ * nx) is rejected with LBM_ERR_ARG; the message is in
+ * lbm_noalloc_last_error(). */
+int lbm_diagnostics_noalloc(const void *f, int nx, int ny, int nz, int precision, double rho_ref,
+                            double rho_l, double rho_v, double *out, void *stream);
+size_t lbm_diagnostics_noalloc_max_scratch(void);
+const char *lbm_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,7 +39,8 @@ EXPORTS = (
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_set_stream",
     "lbm_batch_set_option", "lbm_batch_info", "lbm_batch_init", "lbm_batch_step",
     "lbm_batch_step_sequential", "lbm_batch_sync", "lbm_batch_get_populations",
-    "lbm_batch_diagnostics",
+    "lbm_batch_diagnostics", "lbm_diagnostics_noalloc", "lbm_diagnostics_noalloc_max_scratch",
+    "lbm_noalloc_last_error",
 )
 
 
@@ -132,6 +133,9 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "lbm_batch_sync": (I, [H]),
         "lbm_batch_get_populations": (I, [H, I, P]),
         "lbm_batch_diagnostics": (I, [H, I, P, I]),
+        "lbm_diagnostics_noalloc": (I, [P, I, I, I, I, D, D, D, P, P]),
+        "lbm_diagnostics_noalloc_max_scratch": (ctypes.c_size_t, []),
+        "lbm_noalloc_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name, None)
