@@ -72,7 +72,7 @@ def kernel_digest() -> str:
     return h.hexdigest()
 
 
-def ncu_traffic(precision: str):
+def ncu_traffic(precision: str, pattern: str):
     """DRAM bytes per collide-stream launch from the committed ncu summary, if
     it was taken on the current kernel source; else None."""
     p = os.path.join(ROOT, "profiles", "collide_stream_traffic.json")
@@ -83,7 +83,7 @@ def ncu_traffic(precision: str):
     digest = kernel_digest()
     if d.get("kernel_source_sha256") != digest:
         return None
-    e = d.get("workloads", {}).get(precision)
+    e = d.get("workloads", {}).get("%s/%s" % (precision, pattern))
     if not e:
         return None
     return float(e["dram_bytes_per_launch_full_size"])
@@ -228,7 +228,7 @@ def run_ours(args):
     peak, peak_kind = peaks()
     k2_avg = ms_k2 / max(n_k2, 1)
     achieved = K2_BYTES_PER_LU[args.precision] * N / (k2_avg * 1e-3) / 1e9
-    traffic = ncu_traffic(args.precision)
+    traffic = ncu_traffic(args.precision, pattern)
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
