@@ -54,6 +54,23 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Max of x over all ranks (the job's time is its slowest replica)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(nodes_per_rank: int, lattice_steps: int, ms: float, world: int) -> float:
+    """Whole-job GLUPS: every rank advances its own replica of nodes_per_rank
+    nodes by lattice_steps in the (max-over-ranks) time ms."""
+    return world * nodes_per_rank * lattice_steps / (ms * 1e-3) / 1e9
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -183,6 +200,8 @@ def run_ours(args):
     lat = L.Lattice(w.nx, w.ny, w.nz, w.tau, w.G, precision=args.precision, pattern=pattern,
                     rho_ref=rho_v if args.precision.endswith("dev") else 0.0)
     autotune.apply(lat, choice)
+    if args.fused:
+        lat.set_option("fused", 1)
     lat.init_ligament(w.R0, w.lam, w.eps, w.phase, rho_l, rho_v, w.width)
     # diagnostics inside the time loop: the psi pass of every 10th step also
     # reduces mass, momentum, liquid volume and the neck area (FP64)
@@ -217,12 +236,9 @@ def run_ours(args):
     lat.sync()
     hist = lat.diag_history()
     d = hist[-1]
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, device="cuda")
     lbm_steps = args.steps * LBM_PER_STEP
-    value = world * N * lbm_steps / (ms * 1e-3) / 1e9
+    value = job_value(N, lbm_steps, ms, world)
     # ---- end to end through the C ABI with pinned host buffers ----
     e2e = None if args.no_extras else run_e2e(args, lat, L, torch, N)
     peak, peak_kind = peaks()
@@ -436,6 +452,8 @@ def main():
     ap.add_argument("--rho-l", type=float, default=None,
                     help="liquid density (with --rho-v: skip the flat-interface run)")
     ap.add_argument("--rho-v", type=float, default=None)
+    ap.add_argument("--fused", action="store_true",
+                    help="single-pass fused step kernel on non-diagnostic A-B steps")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (default launch configuration; profiling runs)")
     ap.add_argument("--no-extras", action="store_true",

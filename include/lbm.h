@@ -153,7 +153,15 @@ int lbm_set_stream(lbm_handle h, void *stream);
  * the default: 2 for the two-node kernel, 3 for the one-node kernel),
  * "vector" (0/1, default 1: when nx is even each thread updates two
  * neighbouring nodes with 2-element vector loads and stores; block_x then
- * counts node pairs).  lbm_get_option also answers "step", "nx", "ny", "nz",
+ * counts node pairs), "fused" (0/1, default 0: A-B steps without in-loop
+ * diagnostics run as one single-pass kernel that recomputes psi per tile in
+ * shared memory, reading the populations once per step; applies when
+ * nx % 32 == 0 and ny % 8 == 0; results equal the two-kernel step bitwise),
+ * "stochastic_rounding" (0/1, default 1 for LBM_F16DEV / LBM_BF16DEV: the
+ * stored deviations are rounded up or down with probability given by the
+ * discarded fraction, from a hash of the node index and its post-collision
+ * rest population, instead of to nearest; removes the mass bias of
+ * round-to-nearest in uniform regions; deterministic).  lbm_get_option also answers "step", "nx", "ny", "nz",
  * "precision", "pattern". */
 int lbm_set_option(lbm_handle h, const char *key, double value);
 int lbm_get_option(lbm_handle h, const char *key, double *value);
@@ -184,7 +192,8 @@ int lbm_step(lbm_handle h, int n);
 int lbm_diag_history(lbm_handle h, lbm_diag *out, int max_records, int *count);
 
 /* Waits for the handle's stream; LBM_ERR_NUMERIC if any psi pass since
- * the last check met a non-positive or non-finite density. */
+ * the last check met a non-positive or non-finite density, LBM_ERR_TIMEOUT
+ * if a bounded device wait of the fused step gave up. */
 int lbm_sync(lbm_handle h);
 
 /* Macroscopic fields of the current state into host arrays of N doubles:
@@ -210,7 +219,7 @@ int lbm_load_state(lbm_handle h, const void *host, size_t bytes);
 
 /* Kernel timing (option "kernel_timing"): launches and summed device time
  * in ms of kernel class k since the option was set, k = 0 psi pass,
- * 1 collide-stream.  Synchronises. */
+ * 1 collide-stream, 2 fused single-pass step.  Synchronises. */
 int lbm_kernel_time(lbm_handle h, int k, long long *launches, double *ms);
 
 /* ---- batched form ---------------------------------------------------------
@@ -237,7 +246,8 @@ lbm_batch lbm_batch_create(const lbm_instance *inst, int count, int precision, i
 void lbm_batch_destroy(lbm_batch b);
 const char *lbm_batch_last_error(void);
 int lbm_batch_set_stream(lbm_batch b, void *stream);
-/* "graph" (0/1), "occupancy" (2, 3, 4; default 2), "vector" (0/1, default 1:
+/* "graph" (0/1), "stochastic_rounding" (0/1, as lbm_set_option),
+ * "occupancy" (2, 3, 4; default 2), "vector" (0/1, default 1:
  * instances with even nx update two nodes per thread), "block_x",
  * "block_y", "block_z" (collide-stream block shape of the batched kernel,
  * <= 256 threads; block_x counts node pairs on instances with even nx). */

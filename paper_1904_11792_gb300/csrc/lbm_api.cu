@@ -139,13 +139,28 @@ int enqueue_step(lbm_ctx* h, cudaStream_t s, long long step, int cur, bool timed
   void* dst = aa ? h->state : array_ptr(h, cur ^ 1);
   const int mode = aa ? ((step & 1) ? MODE_AA_ODD : MODE_AA_EVEN) : MODE_AB;
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  const bool diag_step = h->diag_interval > 0 && step % h->diag_interval == 0;
+  if (h->fused && !aa && !diag_step && fused_applicable(h->g)) {
+    // single pass: psi of each tile is recomputed from the staged populations
+    if (timed) {
+      e0 = take_event(h);
+      e1 = take_event(h);
+      CK(cudaEventRecord(e0, s));
+    }
+    CK(launch_fused(prec, h->g, h->ph, src, dst, h->d_flag, s));
+    if (timed) {
+      CK(cudaEventRecord(e1, s));
+      h->pending.push_back({2, e0, e1});
+    }
+    return LBM_OK;
+  }
   if (timed) {
     e0 = take_event(h);
     e1 = take_event(h);
     e2 = take_event(h);
     CK(cudaEventRecord(e0, s));
   }
-  if (h->diag_interval > 0 && step % h->diag_interval == 0) {
+  if (diag_step) {
     CK(launch_diagnostics(prec, layout, h->g, h->ph, src, h->rho_l, h->rho_v, h->d_scratch, h->d_ring,
                           h->psi, h->d_flag, h->d_ring_count, lbm_ctx::kRing, s));
   } else {
@@ -374,7 +389,9 @@ lbm_handle lbm_create_ex(const lbm_config* cfg) {
   }
   h->cfg = *cfg;
   h->g = Geom{cfg->nx, cfg->ny, cfg->nz, (long long)cfg->nx * cfg->ny * cfg->nz};
-  h->ph = Phys{cfg->tau, cfg->G, cfg->rho0, cfg->rho_ref, cfg->psi_form};
+  // stochastic rounding is on by default for the reduced-precision forms
+  h->ph = Phys{cfg->tau, cfg->G, cfg->rho0, cfg->rho_ref, cfg->psi_form,
+               cfg->precision >= LBM_F16DEV ? 1 : 0};
   h->block = (cfg->block_x && cfg->block_y && cfg->block_z)
                  ? dim3(cfg->block_x, cfg->block_y, cfg->block_z)
                  : default_block(h->g);
@@ -481,6 +498,12 @@ int lbm_set_option(lbm_handle h, const char* key, double v) {
     h->rho_v = v;
   } else if (k == "graph") {
     h->use_graph = v != 0.0;
+  } else if (k == "stochastic_rounding") {
+    h->ph.sr = v != 0.0 ? 1 : 0;
+    drop_graphs(h);
+  } else if (k == "fused") {
+    h->fused = v != 0.0;
+    drop_graphs(h);
   } else if (k == "vector") {
     h->vec = v != 0.0;
     drop_graphs(h);
@@ -502,8 +525,10 @@ int lbm_set_option(lbm_handle h, const char* key, double v) {
     if (v != 0.0 && !h->kernel_timing) {
       int rc = settle_timing(h);
       if (rc) return rc;
-      h->t_launches[0] = h->t_launches[1] = 0;
-      h->t_ms[0] = h->t_ms[1] = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        h->t_launches[c] = 0;
+        h->t_ms[c] = 0.0;
+      }
     }
     h->kernel_timing = v != 0.0;
   } else if (k == "block_x" || k == "block_y" || k == "block_z") {
@@ -534,6 +559,8 @@ int lbm_get_option(lbm_handle h, const char* key, double* v) {
   else if (k == "diag_interval") *v = h->diag_interval;
   else if (k == "occupancy") *v = h->minb ? h->minb : ((h->vec && h->g.nx % 2 == 0) ? 2 : 3);
   else if (k == "vector") *v = h->vec && (h->g.nx % 2 == 0);
+  else if (k == "stochastic_rounding") *v = h->ph.sr;
+  else if (k == "fused") *v = h->fused && h->cfg.pattern == LBM_AB && fused_applicable(h->g);
   else if (k == "kernel_timing") *v = h->kernel_timing;
   else if (k == "block_x") *v = h->block.x;
   else if (k == "block_y") *v = h->block.y;
@@ -670,6 +697,7 @@ int lbm_sync(lbm_handle h) {
   if (flag) {
     CK(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (flag & 2) return fail(LBM_ERR_TIMEOUT, "a staged copy of the fused step did not complete in time");
     return fail(LBM_ERR_NUMERIC, "a density became non-positive or non-finite");
   }
   return LBM_OK;
@@ -825,7 +853,7 @@ int lbm_load_state(lbm_handle h, const void* host, size_t bytes) {
 }
 
 int lbm_kernel_time(lbm_handle h, int k, long long* launches, double* ms) {
-  if (!h || k < 0 || k > 1) return fail(LBM_ERR_ARG, "bad handle or kernel class");
+  if (!h || k < 0 || k > 2) return fail(LBM_ERR_ARG, "bad handle or kernel class");
   int rc = settle_timing(h);
   if (rc) return rc;
   if (launches) *launches = h->t_launches[k];

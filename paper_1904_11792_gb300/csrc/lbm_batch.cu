@@ -320,7 +320,8 @@ lbm_batch lbm_batch_create(const lbm_instance* inst, int count, int precision, i
     BatchInst I;
     std::memset(&I, 0, sizeof(I));
     I.g = Geom{s.nx, s.ny, s.nz, N};
-    I.ph = Phys{s.tau, s.G, rho0, precision >= LBM_F16DEV ? s.rho_v : 0.0, psi_form};
+    I.ph = Phys{s.tau, s.G, rho0, precision >= LBM_F16DEV ? s.rho_v : 0.0, psi_form,
+                precision >= LBM_F16DEV ? 1 : 0};
     I.off_f = off_f;
     I.off_psi = off_psi;
     off_f += 2 * (long long)Q * N;
@@ -375,6 +376,10 @@ int lbm_batch_set_option(lbm_batch b, const char* key, double v) {
   if (k == "graph") {
     b->use_graph = v != 0.0;
     return LBM_OK;
+  }
+  if (k == "stochastic_rounding") {
+    for (auto& I : b->inst) I.ph.sr = v != 0.0 ? 1 : 0;
+    return layout_tiles(b);
   }
   if (k == "vector") {
     b->vec = v != 0.0;

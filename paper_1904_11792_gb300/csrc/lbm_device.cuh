@@ -38,6 +38,46 @@ __host__ __device__ constexpr double wgt(int a) {
   return a == 0 ? 1.0 / 3.0 : (a <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
 }
 
+// Stochastic rounding of the reduced-precision stores.  Round-to-nearest of
+// the same value at every node of a uniform region, step after step, biases
+// the stored mass in one direction; rounding up with probability equal to
+// the discarded fraction removes the bias.  The random bits come from a
+// counter-free hash of the node index and the bits of the node's
+// post-collision rest population (which changes from step to step wherever
+// the flow changes), so results stay deterministic and independent of the
+// kernel variant, the streaming pattern and batching.
+__device__ __forceinline__ unsigned mix32(unsigned h) {
+  // integer finaliser with full avalanche (multiply-xorshift, two rounds)
+  h ^= h >> 16;
+  h *= 0x7feb352dU;
+  h ^= h >> 15;
+  h *= 0x846ca68bU;
+  h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ unsigned sr_seed(long long node, float rest) {
+  return mix32((unsigned)node * 0x9E3779B9u ^ (unsigned)(node >> 32) ^ __float_as_uint(rest));
+}
+__device__ __forceinline__ unsigned sr_seed(long long node, double rest) {
+  return sr_seed(node, (float)rest);
+}
+// 16 random bits for direction a of a node with (well mixed) seed s: the
+// top half of s times a distinct odd constant per direction (one multiply).
+__device__ __forceinline__ unsigned sr_bits(unsigned s, int a) {
+  return (s * (0x9E3779B1u + 0x6A09E668u * (unsigned)a)) >> 16;
+}
+__device__ __forceinline__ __half half_sr(float x, unsigned r16) {
+  // FP16 normal range: add 13 random bits below the kept mantissa, truncate
+  if (fabsf(x) >= 6.103515625e-05f && fabsf(x) < 65504.0f)
+    return __float2half_rz(__uint_as_float(__float_as_uint(x) + (r16 & 0x1FFFu)));
+  return __float2half_rn(x);  // subnormal results (and overflow): nearest
+}
+__device__ __forceinline__ __nv_bfloat16 bf16_sr(float x, unsigned r16) {
+  const unsigned b = __float_as_uint(x);
+  if ((b & 0x7f800000u) == 0x7f800000u) return __float2bfloat16_rn(x);  // inf / nan
+  return __ushort_as_bfloat16((unsigned short)((b + r16) >> 16));
+}
+
 // Storage traits.  T = stored type, C = compute type.  The *DEV forms store
 // the deviation g_a = f_a - w_a rho_ref and add it back on load.  load()
 // goes through the read-only data path and is only used on arrays the kernel
@@ -50,6 +90,7 @@ template <> struct Prec<LBM_F64> {
   __device__ static __forceinline__ C load(const T* p, C) { return __ldg(p); }
   __device__ static __forceinline__ C load_rw(const T* p, C) { return *p; }
   __device__ static __forceinline__ void store(T* p, C v, C) { *p = v; }
+  __device__ static __forceinline__ void store_sr(T* p, C v, C, unsigned) { *p = v; }
 };
 template <> struct Prec<LBM_F32> {
   using T = float;
@@ -58,6 +99,7 @@ template <> struct Prec<LBM_F32> {
   __device__ static __forceinline__ C load(const T* p, C) { return __ldg(p); }
   __device__ static __forceinline__ C load_rw(const T* p, C) { return *p; }
   __device__ static __forceinline__ void store(T* p, C v, C) { *p = v; }
+  __device__ static __forceinline__ void store_sr(T* p, C v, C, unsigned) { *p = v; }
 };
 template <> struct Prec<LBM_F16DEV> {
   using T = __half;
@@ -71,6 +113,9 @@ template <> struct Prec<LBM_F16DEV> {
   }
   __device__ static __forceinline__ void store(T* p, C v, C shift) {
     *p = __float2half_rn(v - shift);
+  }
+  __device__ static __forceinline__ void store_sr(T* p, C v, C shift, unsigned r16) {
+    *p = half_sr(v - shift, r16);
   }
 };
 template <> struct Prec<LBM_BF16DEV> {
@@ -86,6 +131,9 @@ template <> struct Prec<LBM_BF16DEV> {
   __device__ static __forceinline__ void store(T* p, C v, C shift) {
     *p = __float2bfloat16_rn(v - shift);
   }
+  __device__ static __forceinline__ void store_sr(T* p, C v, C shift, unsigned r16) {
+    *p = bf16_sr(v - shift, r16);
+  }
 };
 
 // Per-lattice constants handed to every kernel by value.
@@ -97,6 +145,7 @@ struct Geom {
 struct Phys {
   double tau, G, rho0, rho_ref;
   int psi_form;
+  int sr;  // stochastic rounding of reduced-precision stores (deviation forms)
 };
 
 // Neighbour index table of one node: x-1, x, x+1 and the 9 row offsets of

@@ -39,6 +39,13 @@ cudaError_t launch_collide(int precision, int mode, int minb, bool vec, const Ge
                            const Phys& ph, const void* src, void* dst, const void* psi, dim3 block,
                            cudaStream_t s);
 
+// ---- fused single-pass step (lbm_fused.cu) ----------------------------------
+// One kernel per A-B step (psi recomputed per tile in shared memory); needs
+// nx % 32 == 0 and ny % 8 == 0.
+bool fused_applicable(const Geom& g);
+cudaError_t launch_fused(int precision, const Geom& g, const Phys& ph, const void* src, void* dst,
+                         int* flag, cudaStream_t s);
+
 // ---- auxiliary kernels (lbm_aux.cu) ---------------------------------------
 struct InitSpec {
   double R0, lambda, eps, phase, rho_l, rho_v, width;
@@ -117,6 +124,7 @@ struct lbm_ctx {
   dim3 block{0, 0, 0};
   int minb = 0;                   // collide kernel register budget variant (0 = auto)
   bool vec = true;                // two nodes per thread (when nx is even)
+  bool fused = false;             // single-pass fused step on non-diagnostic A-B steps
 
   // diagnostics inside the time loop: every diag_interval steps the psi
   // pass also reduces the diagnostics into a device ring of records
@@ -135,6 +143,6 @@ struct lbm_ctx {
     cudaEvent_t a, b;
   };
   std::vector<Pending> pending;
-  long long t_launches[2] = {0, 0};
-  double t_ms[2] = {0.0, 0.0};
+  long long t_launches[3] = {0, 0, 0};
+  double t_ms[3] = {0.0, 0.0, 0.0};
 };

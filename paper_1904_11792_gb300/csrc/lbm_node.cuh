@@ -37,11 +37,13 @@ template <> struct Pair<LBM_F64> {
   using V = double2;
   __device__ static __forceinline__ void unpack(V v, double& a, double& b) { a = v.x; b = v.y; }
   __device__ static __forceinline__ V pack(double a, double b) { return make_double2(a, b); }
+  __device__ static __forceinline__ V pack_sr(double a, double b, unsigned, unsigned) { return make_double2(a, b); }
 };
 template <> struct Pair<LBM_F32> {
   using V = float2;
   __device__ static __forceinline__ void unpack(V v, float& a, float& b) { a = v.x; b = v.y; }
   __device__ static __forceinline__ V pack(float a, float b) { return make_float2(a, b); }
+  __device__ static __forceinline__ V pack_sr(float a, float b, unsigned, unsigned) { return make_float2(a, b); }
 };
 template <> struct Pair<LBM_F16DEV> {
   using V = __half2;
@@ -52,6 +54,9 @@ template <> struct Pair<LBM_F16DEV> {
   __device__ static __forceinline__ V pack(float a, float b) {
     return __halves2half2(__float2half_rn(a), __float2half_rn(b));
   }
+  __device__ static __forceinline__ V pack_sr(float a, float b, unsigned ra, unsigned rb) {
+    return __halves2half2(half_sr(a, ra), half_sr(b, rb));
+  }
 };
 template <> struct Pair<LBM_BF16DEV> {
   using V = __nv_bfloat162;
@@ -61,6 +66,9 @@ template <> struct Pair<LBM_BF16DEV> {
   }
   __device__ static __forceinline__ V pack(float a, float b) {
     return __halves2bfloat162(__float2bfloat16_rn(a), __float2bfloat16_rn(b));
+  }
+  __device__ static __forceinline__ V pack_sr(float a, float b, unsigned ra, unsigned rb) {
+    return __halves2bfloat162(bf16_sr(a, ra), bf16_sr(b, rb));
   }
 };
 
@@ -85,6 +93,26 @@ __device__ __forceinline__ void store_pair(typename Prec<P>::T* p, typename Prec
                                            typename Prec<P>::C b, typename Prec<P>::C sh) {
   using V = typename Pair<P>::V;
   *reinterpret_cast<V*>(p) = Pair<P>::pack(a - sh, b - sh);
+}
+
+template <int P>
+__device__ __forceinline__ void store_pair_sr(typename Prec<P>::T* p, typename Prec<P>::C a,
+                                              typename Prec<P>::C b, typename Prec<P>::C sh,
+                                              unsigned ra, unsigned rb) {
+  using V = typename Pair<P>::V;
+  *reinterpret_cast<V*>(p) = Pair<P>::pack_sr(a - sh, b - sh, ra, rb);
+}
+
+// Store of population a of a node with seed s: nearest, or stochastic when
+// the lattice asks for it (reduced-precision storage only).
+template <int P>
+__device__ __forceinline__ void store_pop(const Phys& ph, typename Prec<P>::T* p,
+                                          typename Prec<P>::C v, typename Prec<P>::C sh, unsigned s,
+                                          int a) {
+  if (Prec<P>::dev && ph.sr)
+    Prec<P>::store_sr(p, v, sh, sr_bits(s, a));
+  else
+    Prec<P>::store(p, v, sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -293,6 +321,7 @@ __device__ __forceinline__ void collide_node(const Geom& g, const Phys& ph,
   for (int a = 1; a < Q; ++a) pn[a] = __ldg(psi + nb.idx(cx(a), cy(a), cz(a)));
   C fs[Q];
   collide_math<C>(ph, f, __ldg(psi + i), pn, fs);
+  const unsigned seed = (Prec<P>::dev && ph.sr) ? sr_seed(i, fs[0]) : 0u;
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
     const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
@@ -301,7 +330,7 @@ __device__ __forceinline__ void collide_node(const Geom& g, const Phys& ph,
       d = (long long)opp(a) * N + i;
     else
       d = (long long)a * N + nb.idx(cx(a), cy(a), cz(a));
-    Prec<P>::store(dst + d, fs[a], sh);
+    store_pop<P>(ph, dst + d, fs[a], sh, seed, a);
   }
 }
 
@@ -394,19 +423,28 @@ __device__ __forceinline__ void collide_pair(const Geom& g, const Phys& ph,
   C fs0[Q], fs1[Q];
   collide_math<C>(ph, f0, q[1][1][1], pn0, fs0);
   collide_math<C>(ph, f1, q[1][1][2], pn1, fs1);
+  const bool sr = Prec<P>::dev && ph.sr;
+  const unsigned seed0 = sr ? sr_seed(i0, fs0[0]) : 0u, seed1 = sr ? sr_seed(i0 + 1, fs1[0]) : 0u;
 
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
     const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
     if constexpr (MODE == MODE_AA_EVEN) {
-      store_pair<P>(dst + (long long)opp(a) * N + i0, fs0[a], fs1[a], sh);
+      if (sr)
+        store_pair_sr<P>(dst + (long long)opp(a) * N + i0, fs0[a], fs1[a], sh, sr_bits(seed0, a),
+                         sr_bits(seed1, a));
+      else
+        store_pair<P>(dst + (long long)opp(a) * N + i0, fs0[a], fs1[a], sh);
     } else {
       typename Prec<P>::T* base = dst + (long long)a * N + rows[1 + cy(a)][1 + cz(a)];
       if (cx(a) == 0) {
-        store_pair<P>(base + x0, fs0[a], fs1[a], sh);
+        if (sr)
+          store_pair_sr<P>(base + x0, fs0[a], fs1[a], sh, sr_bits(seed0, a), sr_bits(seed1, a));
+        else
+          store_pair<P>(base + x0, fs0[a], fs1[a], sh);
       } else {
-        Prec<P>::store(base + xof(0, cx(a)), fs0[a], sh);
-        Prec<P>::store(base + xof(1, cx(a)), fs1[a], sh);
+        store_pop<P>(ph, base + xof(0, cx(a)), fs0[a], sh, seed0, a);
+        store_pop<P>(ph, base + xof(1, cx(a)), fs1[a], sh, seed1, a);
       }
     }
   }

@@ -438,3 +438,81 @@ def test_fp64_vector_path_parity(L, shape):
     want = oracle.step(f0, 0.95, -5.0, 41)
     assert np.isfinite(want).all()
     assert rel(got, want) <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# fused single-pass step equals the two-kernel step bitwise
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16dev", "bf16dev"])
+@pytest.mark.parametrize("shape", [(64, 16, 12), (32, 8, 5), (96, 24, 17)])
+def test_fused_equals_two_pass_bitwise(L, precision, shape):
+    f0 = lbm_inputs.random_populations(*shape, seed=51)
+    out = []
+    for fused in (1, 0):
+        with make(L, shape, 0.9, -5.5, precision, "ab", rho_ref=0.1) as lat:
+            lat.set_option("fused", fused)
+            assert lat.get_option("fused") == fused
+            lat.set_populations(f0)
+            lat.step(1)
+            lat.step(6)
+            out.append((lat.populations(), lat.rho()))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+def test_fused_with_in_loop_diagnostics_and_oracle(L, coex):
+    rl, rv = coex
+    shape = (64, 32, 32)
+    f0 = oracle.init_ligament(*shape, 8.0, 64.0, 0.05, 0.0, rl, rv, 2.0)
+    want = oracle.step(f0, 1.0, G6, 100)
+    with make(L, shape, 1.0, G6, "f64") as lat:
+        lat.set_option("fused", 1)
+        lat.set_option("diag_interval", 7)
+        lat.init_ligament(8.0, 64.0, 0.05, 0.0, rl, rv, 2.0)
+        lat.step(100)
+        got = lat.populations()
+        hist = lat.diag_history()
+    assert rel(got, want) <= 1e-12
+    assert [h["step"] for h in hist] == list(range(0, 100, 7))
+
+
+def test_fused_numeric_flag(L):
+    shape = (32, 8, 8)
+    f = lbm_inputs.random_populations(*shape, seed=2)
+    f[:, 3, 4, 5] = -0.01
+    with make(L, shape, 1.0, G6, "f32") as lat:
+        lat.set_option("fused", 1)
+        lat.set_populations(f)
+        lat.step(1)
+        with pytest.raises(L.LbmError) as ei:
+            lat.sync()
+        assert ei.value.status == L.LBM_ERR_NUMERIC
+
+
+# ---------------------------------------------------------------------------
+# stochastic rounding of the deviation storage: deterministic, and far less
+# mass drift than round-to-nearest through a break-up (the 64x32x32 ligament
+# pinches off near step 1400)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["f16dev", "bf16dev"])
+def test_stochastic_rounding_mass_drift(L, coex, precision):
+    rl, rv = coex
+    shape = (64, 32, 32)
+    drift = {}
+    for sr in (0, 1):
+        runs = []
+        for _ in range(2 if sr else 1):
+            with make(L, shape, 1.0, G6, precision, rho_ref=rv) as lat:
+                lat.set_option("stochastic_rounding", sr)
+                lat.init_ligament(8.0, 64.0, 0.05, 0.0, rl, rv, 2.0)
+                m0 = lat.diagnostics()["mass"]
+                lat.step(1600)
+                m1 = lat.diagnostics()["mass"]
+                runs.append((m1, lat.rho()))
+        if sr:
+            np.testing.assert_array_equal(runs[0][1], runs[1][1])   # deterministic
+        drift[sr] = abs(runs[0][0] - m0) / m0
+    assert drift[1] < drift[0] / 3.0, drift
+    assert drift[1] < (2e-3 if precision == "f16dev" else 1e-2), drift
