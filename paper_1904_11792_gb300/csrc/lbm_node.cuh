@@ -286,6 +286,45 @@ __device__ __forceinline__ void psi_pair(const Geom& g, const Phys& ph, const ty
   }
 }
 
+// Four nodes i .. i + 3 (i % 4 == 0, nx % 4 == 0, LAYOUT_LOCAL): one 16-byte
+// (FP32) or 8-byte (FP16/BF16) load per population, one 16-byte psi store.
+template <int P>
+__device__ __forceinline__ void psi_quad(const Geom& g, const Phys& ph, const typename Prec<P>::T* f,
+                                         typename Prec<P>::C* __restrict__ psi,
+                                         int* __restrict__ flag, long long i) {
+  static_assert(P != LBM_F64, "four-node psi pass is for 4- and 2-byte storage");
+  const float s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
+              s2 = shift_of<P>(7, ph.rho_ref);
+  float fv[4][Q];
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const float sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
+    const typename Prec<P>::T* p = f + (long long)a * g.N + i;
+    if constexpr (P == LBM_F32) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+      fv[0][a] = v.x + sh;
+      fv[1][a] = v.y + sh;
+      fv[2][a] = v.z + sh;
+      fv[3][a] = v.w + sh;
+    } else {
+      const uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
+      typename Pair<P>::V lo, hi;
+      memcpy(&lo, &raw.x, 4);
+      memcpy(&hi, &raw.y, 4);
+      Pair<P>::unpack(lo, fv[0][a], fv[1][a]);
+      Pair<P>::unpack(hi, fv[2][a], fv[3][a]);
+      fv[0][a] += sh;
+      fv[1][a] += sh;
+      fv[2][a] += sh;
+      fv[3][a] += sh;
+    }
+  }
+  float ps[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) psi_math<float>(ph, rho_of<float>(fv[k]), &ps[k], flag);
+  *reinterpret_cast<float4*>(psi + i) = make_float4(ps[0], ps[1], ps[2], ps[3]);
+}
+
 // ---------------------------------------------------------------------------
 // collide + stream
 // ---------------------------------------------------------------------------

@@ -46,6 +46,15 @@ __global__ void __launch_bounds__(256) psi_pair_kernel(Geom g, Phys ph, const ty
   psi_pair<P, LAYOUT>(g, ph, f, psi, flag, i);
 }
 
+template <int P>
+__global__ void __launch_bounds__(256) psi_quad_kernel(Geom g, Phys ph, const typename Prec<P>::T* f,
+                                                       typename Prec<P>::C* __restrict__ psi,
+                                                       int* __restrict__ flag) {
+  const long long i = 4 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= g.N) return;
+  psi_quad<P>(g, ph, f, psi, flag, i);
+}
+
 template <int P, int MODE, int MINB>
 __global__ void __launch_bounds__(256, MINB) collide_pair_kernel(Geom g, Phys ph,
                                                                  const typename Prec<P>::T* src,
@@ -64,6 +73,13 @@ cudaError_t psi_dispatch(int layout, bool vec, const Geom& g, const Phys& ph, co
   using T = typename Prec<P>::T;
   using C = typename Prec<P>::C;
   const int threads = 256;
+  if constexpr (P != LBM_F64) {
+    if (vec && layout == LAYOUT_LOCAL && g.nx % 4 == 0) {
+      const long long blocks = (g.N / 4 + threads - 1) / threads;
+      psi_quad_kernel<P><<<(unsigned)blocks, threads, 0, s>>>(g, ph, (const T*)f, (C*)psi, flag);
+      return cudaGetLastError();
+    }
+  }
   if (vec) {
     const long long blocks = (g.N / 2 + threads - 1) / threads;
     if (layout == LAYOUT_LOCAL)

@@ -114,9 +114,75 @@ def precision_study(nx, ny, nz, R0, lam, eps, tau, G=-6.0,
     return out
 
 
+# Table 1 of the paper (section "Results"): R0, rho_l, rho_v, sigma at G0 = 5.3
+# (G = -5.3) and Oh = 0.1.
+TABLE1 = ((7, 2.112, 0.081, 0.05159), (14, 2.117, 0.084, 0.05345), (28, 2.125, 0.090, 0.05775),
+          (42, 2.135, 0.097, 0.06277), (56, 2.145, 0.106, 0.06848), (70, 2.156, 0.116, 0.07491),
+          (84, 2.167, 0.126, 0.08206))
+
+
+def tau_from_oh(R0: float, rho_l: float, sigma: float, Oh: float = 0.1) -> float:
+    """tau with Oh = nu sqrt(rho_l / (sigma R0)), nu = (tau - 1/2)/3 (the
+    dimensionally consistent reading of Eq. 8)."""
+    return 0.5 + 3.0 * Oh * math.sqrt(sigma * R0 / rho_l)
+
+
+def table1(G: float = -5.3, radii=(8.0, 10.0, 12.0, 16.0)) -> list:
+    """Reproduces Table 1 on the GPU: for each column, tau from Oh = 0.1,
+    flat-interface rho_l, rho_v and sigma from static cylinders."""
+    rows = []
+    for R0, rl_p, rv_p, sg_p in TABLE1:
+        tau = tau_from_oh(R0, rl_p, sg_p)
+        c = coexistence(G, tau, rho_l0=2.1, rho_v0=0.1)
+        sg = surface_tension(G, tau, radii=radii, rho_l=c["rho_l"], rho_v=c["rho_v"])
+        rows.append(dict(R0=R0, tau=tau, rho_l=c["rho_l"], rho_v=c["rho_v"], sigma=sg["sigma"],
+                         paper=dict(rho_l=rl_p, rho_v=rv_p, sigma=sg_p)))
+    return rows
+
+
+def breakup_vs_radius(radii=(7, 14, 28, 42, 56, 70, 84), G: float = -5.3, eps: float = 0.1,
+                      kR0: float = 0.7, precision: str = "f32", check: int = 100,
+                      max_steps: int = 80000, table=None) -> list:
+    """The paper's study (Fig. 2): dimensionless break-up time t_bu / t_cap
+    against R0 at G = -5.3, Oh = 0.1, all radii in one batch (box
+    lambda x 4 R0 x 4 R0, lambda = 2 pi R0 / kR0, perturbation eps R0)."""
+    if table is None:
+        table = {r["R0"]: r for r in table1(G)}
+    insts = []
+    for R0 in radii:
+        t = table[R0]
+        lam = int(round(2 * math.pi * R0 / kR0))
+        insts.append(dict(nx=lam, ny=4 * R0, nz=4 * R0, tau=t["tau"], G=G, R0=float(R0),
+                          lam=float(lam), eps=eps, phase=0.0, rho_l=t["rho_l"], rho_v=t["rho_v"],
+                          width=2.0))
+    t_bu = [None] * len(insts)
+    steps = 0
+    with L.Batch(insts, precision=precision) as b:
+        b.init()
+        while steps < max_steps and any(t is None for t in t_bu):
+            b.step(check)
+            steps += check
+            for k in range(len(insts)):
+                if t_bu[k] is None:
+                    d = b.diagnostics(k)
+                    if not d["numeric_ok"]:
+                        raise FloatingPointError("R0=%d went non-finite" % radii[k])
+                    if d["min_slice_count"] == 0:
+                        t_bu[k] = steps
+        b.sync()
+    out = []
+    for k, R0 in enumerate(radii):
+        t = table[R0]
+        t_cap = math.sqrt(t["rho_l"] * R0 ** 3 / t["sigma"])
+        out.append(dict(R0=R0, tau=t["tau"], lam=insts[k]["nx"], nodes=insts[k]["nx"] * 16 * R0 * R0,
+                        breakup_step=t_bu[k], t_cap=t_cap,
+                        breakup_over_tcap=(t_bu[k] / t_cap) if t_bu[k] else None))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=("precision", "sigma"))
+    ap.add_argument("study", choices=("precision", "sigma", "table1", "radius"))
     ap.add_argument("--nx", type=int, default=256)
     ap.add_argument("--ny", type=int, default=128)
     ap.add_argument("--nz", type=int, default=128)
@@ -130,6 +196,14 @@ def main():
     a = ap.parse_args()
     if a.study == "sigma":
         print(json.dumps(surface_tension(a.G, a.tau)))
+        return
+    if a.study == "table1":
+        print(json.dumps(table1()))
+        return
+    if a.study == "radius":
+        t = table1()
+        print(json.dumps({"table1": t, "breakup": breakup_vs_radius(table={r["R0"]: r for r in t},
+                                                                     max_steps=a.max_steps)}))
         return
     res = precision_study(a.nx, a.ny, a.nz, a.R0, a.lam, a.eps, a.tau, a.G,
                           precisions=tuple(a.precisions.split(",")), max_steps=a.max_steps)

@@ -412,8 +412,9 @@ def test_diag_interval_does_not_change_the_state(L):
 
 @pytest.mark.parametrize("precision", ["f64", "f32", "f16dev", "bf16dev"])
 @pytest.mark.parametrize("pattern", ["ab", "aa"])
-def test_vector_kernels_equal_scalar_bitwise(L, precision, pattern):
-    shape = (34, 10, 7)          # even nx: the two-node kernels apply
+@pytest.mark.parametrize("shape", [(34, 10, 7), (36, 10, 7)])
+def test_vector_kernels_equal_scalar_bitwise(L, precision, pattern, shape):
+    # even nx: two-node kernels; nx % 4 == 0: also the four-node psi pass
     f0 = lbm_inputs.random_populations(*shape, seed=41)
     out = []
     for vec in (1, 0):
