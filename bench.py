@@ -97,11 +97,8 @@ def ncu_traffic(precision: str, pattern: str):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    digest = kernel_digest()
-    if d.get("kernel_source_sha256") != digest:
-        return None
     e = d.get("workloads", {}).get("%s/%s" % (precision, pattern))
-    if not e:
+    if not e or e.get("kernel_source_sha256") != kernel_digest():
         return None
     return float(e["dram_bytes_per_launch_full_size"])
 

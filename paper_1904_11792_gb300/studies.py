@@ -156,26 +156,34 @@ def breakup_vs_radius(radii=(7, 14, 28, 42, 56, 70, 84), G: float = -5.3, eps: f
                           lam=float(lam), eps=eps, phase=0.0, rho_l=t["rho_l"], rho_v=t["rho_v"],
                           width=2.0))
     t_bu = [None] * len(insts)
+    nonfinite = [None] * len(insts)     # step at which an instance lost finiteness
     steps = 0
     with L.Batch(insts, precision=precision) as b:
         b.init()
-        while steps < max_steps and any(t is None for t in t_bu):
+        while steps < max_steps and any(t is None and n is None for t, n in zip(t_bu, nonfinite)):
             b.step(check)
             steps += check
             for k in range(len(insts)):
-                if t_bu[k] is None:
+                if t_bu[k] is None and nonfinite[k] is None:
                     d = b.diagnostics(k)
                     if not d["numeric_ok"]:
-                        raise FloatingPointError("R0=%d went non-finite" % radii[k])
-                    if d["min_slice_count"] == 0:
+                        nonfinite[k] = steps
+                    elif d["min_slice_count"] == 0:
                         t_bu[k] = steps
-        b.sync()
+        try:
+            b.sync()
+        except L.LbmError as e:
+            # an instance past its break-up step (or already reported above)
+            # lost finiteness; the instances are independent, so the recorded
+            # break-up steps of the others stand
+            if e.status != L.LBM_ERR_NUMERIC:
+                raise
     out = []
     for k, R0 in enumerate(radii):
         t = table[R0]
         t_cap = math.sqrt(t["rho_l"] * R0 ** 3 / t["sigma"])
         out.append(dict(R0=R0, tau=t["tau"], lam=insts[k]["nx"], nodes=insts[k]["nx"] * 16 * R0 * R0,
-                        breakup_step=t_bu[k], t_cap=t_cap,
+                        breakup_step=t_bu[k], nonfinite_step=nonfinite[k], t_cap=t_cap,
                         breakup_over_tcap=(t_bu[k] / t_cap) if t_bu[k] else None))
     return out
 
@@ -202,7 +210,8 @@ def main():
         return
     if a.study == "radius":
         t = table1()
-        print(json.dumps({"table1": t, "breakup": breakup_vs_radius(table={r["R0"]: r for r in t},
+        print(json.dumps({"table1": t}), flush=True)
+        print(json.dumps({"breakup": breakup_vs_radius(table={r["R0"]: r for r in t},
                                                                      max_steps=a.max_steps)}))
         return
     res = precision_study(a.nx, a.ny, a.nz, a.R0, a.lam, a.eps, a.tau, a.G,
