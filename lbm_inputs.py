@@ -126,3 +126,23 @@ def batched_sweep(count: int = 48, seed: int = BASE_SEED) -> list[Ligament]:
         out.append(Ligament("batch[%d] R0=%d lam=%d" % (k, R0, lam), lam, 4 * R0, 4 * R0,
                             float(R0), float(lam), 0.05, tau, phase=phase))
     return out
+
+
+def droplet_populations(nx: int, ny: int, nz: int, seed: int = BASE_SEED, p: float = 0.3,
+                        rho_l: float = 2.65, rho_v: float = 0.073, mask=None) -> np.ndarray:
+    """A state f[19, nz, ny, nx] (float64) whose liquid forms many droplets.
+
+    Liquid nodes (a uniform draw below p, or the given boolean mask) get a
+    density in [0.9, 1.1] rho_l, the others one in [0.5, 1.5] rho_v, far from
+    the threshold (rho_l + rho_v)/2 in any storage precision.  The density is
+    spread over the 19 populations by positive random shares."""
+    N = nx * ny * nz
+    u = uniform(seed, 2 * N)
+    if mask is None:
+        mask = (u[:N] < p).reshape(nz, ny, nx)
+    mask = np.asarray(mask, dtype=bool)
+    v = u[N:].reshape(nz, ny, nx)
+    rho = np.where(mask, rho_l * (0.9 + 0.2 * v), rho_v * (0.5 + v))
+    share = 0.5 + uniform(seed ^ 0x2545F491, 19 * N).reshape(19, nz, ny, nx)
+    share /= share.sum(axis=0, keepdims=True)
+    return share * rho[None]

@@ -69,6 +69,8 @@ def _load():
             lib.orc_ccl.argtypes = [I, I, I, P, P, P]
             lib.orc_ccl.restype = I
             lib.orc_diagnostics.argtypes = [I, I, I, P, D, D, P, P, P]
+            lib.orc_droplets.argtypes = [I, I, I, P, D, D, P, I]
+            lib.orc_droplets.restype = I
             lib.orc_step_nodes.argtypes = [I, I, I, D, D, I, D, P, P, I, P]
             lib.orc_coexistence.argtypes = [I, D, D, I, D, D, D, I, D, I, LL, P, P, P]
             lib.orc_coexistence.restype = I
@@ -200,6 +202,25 @@ def diagnostics(f: np.ndarray, rho_l: float, rho_v: float, slices: bool = False)
     if slices:
         return d, sw, sn
     return d
+
+
+DROPLET_KEYS = ("first", "nodes", "volume_w", "mass", "cx", "cy", "cz", "rx", "ry", "rz", "x_slices")
+
+
+def droplets(f: np.ndarray, rho_l: float, rho_v: float, max_out: int | None = None):
+    """Per-droplet statistics (connected liquid components), largest first.
+
+    Returns (count, records): records is a (min(count, max_out), 11) array
+    with the columns of DROPLET_KEYS."""
+    g = _f64(f)
+    _, nz, ny, nx = g.shape
+    if max_out is None:
+        max_out = g[0].size
+    out = np.zeros((max(max_out, 1), len(DROPLET_KEYS)))
+    n = _load().orc_droplets(nx, ny, nz, _ptr(g), float(rho_l), float(rho_v), _ptr(out), int(max_out))
+    if n < 0:
+        raise MemoryError("oracle droplets: allocation failed")
+    return n, out[:min(n, max_out)].copy()
 
 
 def step_nodes(f: np.ndarray, nodes, tau: float, G: float, psi_form: int = 0,

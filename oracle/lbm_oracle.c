@@ -449,6 +449,111 @@ void orc_diagnostics(int nx, int ny, int nz, const double *f, double rho_l, doub
 }
 
 /*
+ * Droplet statistics (the droplets of the break-up study, reading R16/R17):
+ * the liquid components of orc_ccl, each with
+ *   first  smallest linear node index in the droplet,
+ *   nodes  node count,
+ *   vol    sum of phi = clamp((rho - rho_v)/(rho_l - rho_v), 0, 1),
+ *   mass   sum of rho,
+ *   c[3]   centroid of its nodes on the periodic box: per axis the circular
+ *          mean, i.e. the direction of sum(cos t, sin t) with t = 2 pi x / n,
+ *          mapped back to a coordinate in [0, n),
+ *   r[3]   length of that mean vector divided by the node count (1 for a
+ *          droplet in one plane, near 0 when the droplet fills the axis, in
+ *          which case the centroid along it is not defined),
+ *   xs     number of x slices holding a node of the droplet (nx: it wraps).
+ * Records of ORC_DROPLET_REC doubles [first, nodes, vol, mass, c0, c1, c2,
+ * r0, r1, r2, xs], sorted by node count (largest first), ties by first index.
+ * Writes min(count, max_out) records; returns the droplet count, or -1 when
+ * memory runs out.  Sums run in node-index order.
+ */
+#define ORC_DROPLET_REC 11
+static int cmp_droplet(const void *pa, const void *pb) {
+    const double *a = (const double *)pa, *b = (const double *)pb;
+    if (a[1] != b[1]) return a[1] > b[1] ? -1 : 1;
+    return a[0] < b[0] ? -1 : (a[0] > b[0] ? 1 : 0);
+}
+
+int orc_droplets(int nx, int ny, int nz, const double *f, double rho_l, double rho_v,
+                 double *out, int max_out) {
+    const double TWO_PI = 6.283185307179586476925286766559;
+    size_t N = (size_t)nx * ny * nz;
+    double thr = 0.5 * (rho_l + rho_v);
+    double *rho = (double *)malloc(N * sizeof(double));
+    unsigned char *mask = (unsigned char *)malloc(N);
+    int *labels = (int *)malloc(N * sizeof(int));
+    if (!rho || !mask || !labels) {
+        free(rho); free(mask); free(labels);
+        return -1;
+    }
+    for (size_t i = 0; i < N; ++i) {
+        double j[3];
+        node_moments(f, N, i, &rho[i], j);
+        mask[i] = rho[i] > thr;
+    }
+    int count = orc_ccl(nx, ny, nz, mask, labels, NULL);
+    /* per droplet: first, nodes, vol, mass, (cos, sin) x 3 */
+    double *acc = count > 0 ? (double *)calloc((size_t)count * 10, sizeof(double)) : NULL;
+    unsigned char *occ = count > 0 ? (unsigned char *)calloc((size_t)count * nx, 1) : NULL;
+    if (count < 0 || (count > 0 && (!acc || !occ))) {
+        free(rho); free(mask); free(labels); free(acc); free(occ);
+        return -1;
+    }
+    for (int k = 0; k < count; ++k) acc[10 * k] = -1.0;
+    const int dims[3] = {nx, ny, nz};
+    for (size_t i = 0; i < N; ++i) {
+        int k = labels[i];
+        if (k < 0) continue;
+        double *a = acc + 10 * (size_t)k;
+        if (a[0] < 0.0) a[0] = (double)i;   /* the first node met in index order */
+        int crd[3] = {(int)(i % (size_t)nx), (int)((i / (size_t)nx) % (size_t)ny),
+                      (int)(i / ((size_t)nx * ny))};
+        double phi = (rho[i] - rho_v) / (rho_l - rho_v);
+        if (phi < 0.0) phi = 0.0;
+        if (phi > 1.0) phi = 1.0;
+        a[1] += 1.0;
+        a[2] += phi;
+        a[3] += rho[i];
+        for (int d = 0; d < 3; ++d) {
+            double t = TWO_PI * (double)crd[d] / (double)dims[d];
+            a[4 + 2 * d] += cos(t);
+            a[5 + 2 * d] += sin(t);
+        }
+        occ[(size_t)k * nx + crd[0]] = 1;
+    }
+    double *rec = count > 0 ? (double *)malloc((size_t)count * ORC_DROPLET_REC * sizeof(double)) : NULL;
+    if (count > 0 && !rec) {
+        free(rho); free(mask); free(labels); free(acc); free(occ);
+        return -1;
+    }
+    for (int k = 0; k < count; ++k) {
+        const double *a = acc + 10 * (size_t)k;
+        double *r = rec + (size_t)k * ORC_DROPLET_REC;
+        r[0] = a[0];
+        r[1] = a[1];
+        r[2] = a[2];
+        r[3] = a[3];
+        for (int d = 0; d < 3; ++d) {
+            double c = a[4 + 2 * d], sn = a[5 + 2 * d];
+            double t = atan2(sn, c);
+            if (t < 0.0) t += TWO_PI;
+            double pos = t / TWO_PI * (double)dims[d];
+            if (pos >= (double)dims[d]) pos -= (double)dims[d];
+            r[4 + d] = pos;
+            r[7 + d] = sqrt(c * c + sn * sn) / a[1];
+        }
+        int xs = 0;
+        for (int x = 0; x < nx; ++x) xs += occ[(size_t)k * nx + x];
+        r[10] = (double)xs;
+    }
+    if (count > 1) qsort(rec, (size_t)count, ORC_DROPLET_REC * sizeof(double), cmp_droplet);
+    int n = count < max_out ? count : max_out;
+    if (n > 0) memcpy(out, rec, (size_t)n * ORC_DROPLET_REC * sizeof(double));
+    free(rho); free(mask); free(labels); free(acc); free(occ); free(rec);
+    return count;
+}
+
+/*
  * One time step evaluated only at selected nodes: out[k*19 + a] is the
  * population a at node nodes[k] after the step, i.e. the post-collision
  * value of the upstream node nodes[k] - c_a.  psi is evaluated on demand,

@@ -429,3 +429,80 @@ def test_flat_interface_meets_mechanical_stability_at_tau_one(G):
     r = oracle.coexistence(1.0, G, n=64, tol=1e-10, rho_l0=2.4, rho_v0=0.1)
     assert abs(r["rho_l"] / rl_th - 1.0) < 1e-3, (r["rho_l"], rl_th)
     assert abs(r["rho_v"] / rv_th - 1.0) < 1e-2, (r["rho_v"], rv_th)
+
+
+# --------------------------------------------------------------------------
+# Droplet statistics (reading R16/R17) against networkx components and
+# closed-form geometry
+# --------------------------------------------------------------------------
+
+def _nx_component_nodes(mask):
+    import networkx as nx_
+    nz, ny, nx = mask.shape
+    g = nx_.Graph()
+    idx = lambda z, y, x: x + nx * (y + ny * z)
+    for z, y, x in zip(*np.nonzero(mask)):
+        g.add_node(idx(z, y, x))
+        for dz, dy, dx in ((0, 0, 1), (0, 1, 0), (1, 0, 0)):
+            q = ((z + dz) % nz, (y + dy) % ny, (x + dx) % nx)
+            if mask[q]:
+                g.add_edge(idx(z, y, x), idx(*q))
+    return [sorted(cc) for cc in nx_.connected_components(g)]
+
+
+@pytest.mark.parametrize("seed,shape,p", [(11, (6, 7, 9), 0.3), (12, (5, 5, 5), 0.4), (13, (4, 9, 6), 0.25)])
+def test_droplets_vs_networkx(seed, shape, p):
+    rl, rv = 2.65, 0.073
+    nz, ny, nx = shape
+    f = lbm_inputs.droplet_populations(nx, ny, nz, seed=seed, p=p, rho_l=rl, rho_v=rv)
+    rho = f.sum(axis=0).ravel()
+    comps = _nx_component_nodes(rho.reshape(shape) > 0.5 * (rl + rv))
+    n, rec = oracle.droplets(f, rl, rv)
+    assert n == len(comps) and rec.shape[0] == n
+    want = sorted(((len(c), c[0]) for c in comps), key=lambda t: (-t[0], t[1]))
+    assert [(int(r[1]), int(r[0])) for r in rec] == want
+    by_first = {c[0]: np.array(c) for c in comps}
+    for r in rec:
+        nodes = by_first[int(r[0])]
+        phi = np.clip((rho[nodes] - rv) / (rl - rv), 0.0, 1.0)
+        assert r[2] == pytest.approx(phi.sum(), rel=1e-13)
+        assert r[3] == pytest.approx(rho[nodes].sum(), rel=1e-13)
+        assert int(r[10]) == len(set((nodes % nx).tolist()))
+
+
+def test_droplet_centroid_on_periodic_box():
+    # two balls of radius 2 (33 lattice points each: 1 + 6 + 12 + 8 + 6 at
+    # squared distance 0..4), one centred on a corner of the periodic box so
+    # that it is cut by the x and y boundaries; each centroid is its centre
+    nx, ny, nz = 14, 11, 12
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+
+    def ball(c):
+        d = [np.minimum(np.abs(a - ca), n - np.abs(a - ca)) for a, ca, n in
+             ((xx, c[0], nx), (yy, c[1], ny), (zz, c[2], nz))]
+        return d[0] ** 2 + d[1] ** 2 + d[2] ** 2 <= 4
+    centres = [(0, ny - 1, 3), (7, 5, 8)]
+    mask = ball(centres[0]) | ball(centres[1])
+    # a ring along x through y = 5, z = 0: wraps, every x slice, no x centroid
+    mask[0, 5, :] = True
+    f = lbm_inputs.droplet_populations(nx, ny, nz, seed=5, mask=mask)
+    n, rec = oracle.droplets(f, 2.65, 0.073)
+    assert n == 3
+    ring = rec[2]                        # largest first: the balls (33 nodes) lead
+    assert int(ring[1]) == nx and int(ring[10]) == nx and ring[7] < 1e-12
+    assert ring[5] == pytest.approx(5.0, abs=1e-12) and ring[6] == pytest.approx(0.0, abs=1e-12)
+    assert rec[0][0] < rec[1][0]         # equal sizes: ordered by first node index
+    got = sorted((tuple(r[4:7]), int(r[1]), int(r[10])) for r in rec[:2])
+    for (c, nodes, xs), want in zip(got, sorted(centres)):
+        assert nodes == 33 and xs == 5
+        for d, n_ in enumerate((nx, ny, nz)):
+            err = abs(c[d] - want[d])
+            assert min(err, n_ - err) < 1e-9, (c, want)
+
+
+def test_droplets_empty_and_full():
+    f = lbm_inputs.droplet_populations(6, 5, 4, seed=3, mask=np.zeros((4, 5, 6), bool))
+    assert oracle.droplets(f, 2.65, 0.073)[0] == 0
+    f = lbm_inputs.droplet_populations(6, 5, 4, seed=3, mask=np.ones((4, 5, 6), bool))
+    n, rec = oracle.droplets(f, 2.65, 0.073)
+    assert n == 1 and int(rec[0][1]) == 120 and int(rec[0][0]) == 0 and int(rec[0][10]) == 6
