@@ -73,6 +73,11 @@ def _load():
             lib.orc_droplets.restype = I
             lib.orc_step_nodes.argtypes = [I, I, I, D, D, I, D, P, P, I, P]
             lib.orc_coexistence.argtypes = [I, D, D, I, D, D, D, I, D, I, LL, P, P, P]
+            lib.orc_coexistence_ex.argtypes = [I, D, P, D, I, D, D, D, I, D, I, LL, P, P, P]
+            lib.orc_coexistence_ex.restype = I
+            lib.orc_mrt_matrix.argtypes = [P]
+            lib.orc_step_forcing.argtypes = [I, I, I, D, P, D, I, D, P, I]
+            lib.orc_step_forcing.restype = I
             lib.orc_coexistence.restype = I
             _lib = lib
     return _lib
@@ -223,6 +228,41 @@ def droplets(f: np.ndarray, rho_l: float, rho_v: float, max_out: int | None = No
     return n, out[:min(n, max_out)].copy()
 
 
+def mrt_matrix() -> np.ndarray:
+    """The 19 x 19 D3Q19 moment matrix M of the MRT collision."""
+    M = np.zeros((Q, Q))
+    _load().orc_mrt_matrix(_ptr(M))
+    return M
+
+
+def mrt_rates(tau: float, s_e: float = 1.19, s_eps: float = 1.4, s_q: float = 1.2,
+              s_pi: float = 1.4, s_m: float = 1.98) -> np.ndarray:
+    """The 19 diagonal relaxation rates: shear moments (9, 11, 13, 14, 15)
+    relax at 1/tau (nu = (tau - 1/2)/3); the conserved moments (0, 3, 5, 7)
+    take 0 (their value does not matter); the others the given rates."""
+    s = np.zeros(Q)
+    s[1], s[2] = s_e, s_eps
+    s[[4, 6, 8]] = s_q
+    s[[9, 11, 13, 14, 15]] = 1.0 / tau
+    s[[10, 12]] = s_pi
+    s[[16, 17, 18]] = s_m
+    return s
+
+
+def step_forcing(f: np.ndarray, G: float, nsteps: int = 1, rates=None, tau: float = 1.0,
+                 psi_form: int = 0, rho0: float = 1.0) -> np.ndarray:
+    """nsteps MRT steps with Guo forcing (rates: 19 values), or, with rates
+    None, SRT steps of relaxation time tau with the same Guo forcing."""
+    g = _f64(f).copy()
+    _, nz, ny, nx = g.shape
+    r = None if rates is None else _f64(rates)
+    rc = _load().orc_step_forcing(nx, ny, nz, float(tau), None if r is None else _ptr(r), float(G),
+                                  int(psi_form), float(rho0), _ptr(g), int(nsteps))
+    if rc != 0:
+        raise MemoryError("oracle step_forcing: allocation failed")
+    return g
+
+
 def step_nodes(f: np.ndarray, nodes, tau: float, G: float, psi_form: int = 0,
                rho0: float = 1.0) -> np.ndarray:
     """Populations after one step at the given flat node indices, shape (k, 19)."""
@@ -237,17 +277,22 @@ def step_nodes(f: np.ndarray, nodes, tau: float, G: float, psi_form: int = 0,
 
 def coexistence(tau: float, G: float, n: int = 128, rho_l0: float = 2.5, rho_v0: float = 0.1,
                 tol: float = 1e-12, check: int = 1000, max_steps: int = 400000,
-                psi_form: int = 0, rho0: float = 1.0, f_init: np.ndarray | None = None):
+                psi_form: int = 0, rho0: float = 1.0, f_init: np.ndarray | None = None,
+                mrt_rates=None):
     """Flat-interface coexistence run (reading R14).
 
-    Returns dict(rho_l, rho_v, steps, dmax, profile, f) with f the final
-    (19, 3, 3, n) state, which can seed a run at another tau."""
+    mrt_rates (19 values) runs the MRT collision with Guo forcing instead of
+    the paper's SRT step.  Returns dict(rho_l, rho_v, steps, dmax, profile,
+    f) with f the final (19, 3, 3, n) state, which can seed a run at another
+    tau."""
     f = np.zeros((Q, 3, 3, n)) if f_init is None else _f64(f_init).copy()
     out = np.zeros(4)
     prof = np.zeros(n)
-    rc = _load().orc_coexistence(int(n), float(tau), float(G), int(psi_form), float(rho0),
-                                 float(rho_l0), float(rho_v0), int(f_init is None), float(tol),
-                                 int(check), int(max_steps), _ptr(f), _ptr(out), _ptr(prof))
+    rates = None if mrt_rates is None else _f64(mrt_rates)
+    rc = _load().orc_coexistence_ex(int(n), float(tau), None if rates is None else _ptr(rates),
+                                    float(G), int(psi_form), float(rho0),
+                                    float(rho_l0), float(rho_v0), int(f_init is None), float(tol),
+                                    int(check), int(max_steps), _ptr(f), _ptr(out), _ptr(prof))
     if rc != 0:
         raise MemoryError("oracle coexistence: allocation failed")
     return dict(rho_l=out[0], rho_v=out[1], steps=int(out[2]), dmax=out[3], profile=prof, f=f)

@@ -229,6 +229,169 @@ int orc_step(int nx, int ny, int nz, double tau, double G, int psi_form, double 
     return 0;
 }
 
+/*
+ * Multiple-relaxation-time collision: the operator the paper names as its
+ * next step (section "Conclusions": MRT keeps the density ratio fixed while
+ * the viscosity changes).  It is not specified in the paper; this follows the
+ * standard D3Q19 MRT of d'Humieres, Ginzburg, Krafczyk, Lallemand and Luo
+ * (Phil. Trans. R. Soc. A 360, 2002) with the forcing of Guo, Zheng and Shi
+ * (Phys. Rev. E 65, 046308, 2002) written in moment space:
+ *   m = M f,  m_eq = M f_eq(rho, u),  s_F = M F_guo,  u = (j + F/2) / rho,
+ *   F_guo_a = w_a [ (c_a - u).F / cs2 + (c_a.u)(c_a.F) / cs2^2 ],
+ *   m* = m - S (m - m_eq) + (I - S/2) s_F,   f* = M^-1 m*,
+ * with F the Shan-Chen force of Eq. 5 and f_eq the equilibrium of Eq. 2
+ * (reading R1).  S = diag(rates[0..18]).
+ *
+ * Rows of M: polynomials of the velocity c (c2 = c.c) evaluated on the 19
+ * lattice velocities, in this order:
+ *   0 1 (density)   1 19 c2 - 30 (energy)   2 (21 c2^2 - 53 c2 + 24)/2
+ *   3 cx   4 (5 c2 - 9) cx   5 cy   6 (5 c2 - 9) cy   7 cz   8 (5 c2 - 9) cz
+ *   9 3 cx^2 - c2   10 (3 c2 - 5)(3 cx^2 - c2)   11 cy^2 - cz^2
+ *   12 (3 c2 - 5)(cy^2 - cz^2)   13 cx cy   14 cy cz   15 cx cz
+ *   16 (cy^2 - cz^2) cx   17 (cz^2 - cx^2) cy   18 (cx^2 - cy^2) cz
+ * The rows are mutually orthogonal, so M^-1 = M^T diag(1 / |row|^2).
+ */
+static double mrt_row(int k, const int c[3]) {
+    double x = c[0], y = c[1], z = c[2], c2 = x * x + y * y + z * z;
+    switch (k) {
+        case 0: return 1.0;
+        case 1: return 19.0 * c2 - 30.0;
+        case 2: return (21.0 * c2 * c2 - 53.0 * c2 + 24.0) / 2.0;
+        case 3: return x;
+        case 4: return (5.0 * c2 - 9.0) * x;
+        case 5: return y;
+        case 6: return (5.0 * c2 - 9.0) * y;
+        case 7: return z;
+        case 8: return (5.0 * c2 - 9.0) * z;
+        case 9: return 3.0 * x * x - c2;
+        case 10: return (3.0 * c2 - 5.0) * (3.0 * x * x - c2);
+        case 11: return y * y - z * z;
+        case 12: return (3.0 * c2 - 5.0) * (y * y - z * z);
+        case 13: return x * y;
+        case 14: return y * z;
+        case 15: return x * z;
+        case 16: return (y * y - z * z) * x;
+        case 17: return (z * z - x * x) * y;
+        default: return (x * x - y * y) * z;
+    }
+}
+
+/* M (19 x 19, row-major, M[k*19 + a] = row k at velocity a). */
+void orc_mrt_matrix(double *M) {
+    for (int k = 0; k < Q; ++k)
+        for (int a = 0; a < Q; ++a) M[k * Q + a] = mrt_row(k, CV[a]);
+}
+
+/* Guo forcing populations F_guo_a for velocity u and force F. */
+static void guo_source(const double u[3], const double F[3], double src[Q]) {
+    for (int a = 0; a < Q; ++a) {
+        double cu = CV[a][0] * u[0] + CV[a][1] * u[1] + CV[a][2] * u[2];
+        double cF = CV[a][0] * F[0] + CV[a][1] * F[1] + CV[a][2] * F[2];
+        double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+        src[a] = WT[a] * ((cF - uF) / CS2 + cu * cF / (CS2 * CS2));
+    }
+}
+
+/* Collision of one node with the MRT operator above (rates = diag S). */
+static void node_collide_mrt(int nx, int ny, int nz, const double *rates, double G,
+                             const double *M, const double *Minv, const double *f,
+                             const double *psi, int x, int y, int z, double fstar[Q]) {
+    size_t N = (size_t)nx * ny * nz;
+    size_t i = node_index(x, y, z, nx, ny);
+    double rho, j[3], F[3], u[3], feq[Q], src[Q], fl[Q];
+    node_moments(f, N, i, &rho, j);
+    node_force(nx, ny, nz, psi, x, y, z, G, F);
+    for (int k = 0; k < 3; ++k) u[k] = (j[k] + 0.5 * F[k]) / rho;
+    orc_feq(rho, u, feq);
+    guo_source(u, F, src);
+    for (int a = 0; a < Q; ++a) fl[a] = f[(size_t)a * N + i];
+    double mstar[Q];
+    for (int k = 0; k < Q; ++k) {
+        double m = 0.0, meq = 0.0, sF = 0.0;
+        for (int a = 0; a < Q; ++a) {
+            m += M[k * Q + a] * fl[a];
+            meq += M[k * Q + a] * feq[a];
+            sF += M[k * Q + a] * src[a];
+        }
+        mstar[k] = m - rates[k] * (m - meq) + (1.0 - 0.5 * rates[k]) * sF;
+    }
+    for (int a = 0; a < Q; ++a) {
+        double v = 0.0;
+        for (int k = 0; k < Q; ++k) v += Minv[a * Q + k] * mstar[k];
+        fstar[a] = v;
+    }
+}
+
+/* SRT collision with the same Guo forcing, written in velocity space:
+ * f* = f - (f - f_eq(rho, u)) / tau + (1 - 1/(2 tau)) F_guo, u = (j + F/2)/rho. */
+static void node_collide_bgk_guo(int nx, int ny, int nz, double tau, double G, const double *f,
+                                 const double *psi, int x, int y, int z, double fstar[Q]) {
+    size_t N = (size_t)nx * ny * nz;
+    size_t i = node_index(x, y, z, nx, ny);
+    double rho, j[3], F[3], u[3], feq[Q], src[Q];
+    node_moments(f, N, i, &rho, j);
+    node_force(nx, ny, nz, psi, x, y, z, G, F);
+    for (int k = 0; k < 3; ++k) u[k] = (j[k] + 0.5 * F[k]) / rho;
+    orc_feq(rho, u, feq);
+    guo_source(u, F, src);
+    for (int a = 0; a < Q; ++a) {
+        double fa = f[(size_t)a * N + i];
+        fstar[a] = fa - (fa - feq[a]) / tau + (1.0 - 0.5 / tau) * src[a];
+    }
+}
+
+/*
+ * nsteps A-B steps with the MRT collision (rates: the 19 diagonal entries
+ * of S) or, when rates is NULL, with the velocity-space SRT-Guo collision of
+ * relaxation time tau.  Same psi pass and streaming as orc_step.
+ */
+int orc_step_forcing(int nx, int ny, int nz, double tau, const double *rates, double G, int psi_form,
+                     double rho0, double *f, int nsteps) {
+    size_t N = (size_t)nx * ny * nz;
+    double *psi = (double *)malloc(N * sizeof(double));
+    double *g = (double *)malloc((size_t)Q * N * sizeof(double));
+    double M[Q * Q], Minv[Q * Q];
+    if (!psi || !g) {
+        free(psi);
+        free(g);
+        return -1;
+    }
+    orc_mrt_matrix(M);
+    for (int k = 0; k < Q; ++k) {
+        double n2 = 0.0;
+        for (int a = 0; a < Q; ++a) n2 += M[k * Q + a] * M[k * Q + a];
+        for (int a = 0; a < Q; ++a) Minv[a * Q + k] = M[k * Q + a] / n2;
+    }
+    double *cur = f, *nxt = g;
+    for (int s = 0; s < nsteps; ++s) {
+        psi_field(nx, ny, nz, psi_form, rho0, cur, psi);
+        long long rows = (long long)ny * nz;
+#pragma omp parallel for if (N > PAR_MIN_NODES) schedule(static)
+        for (long long r = 0; r < rows; ++r) {
+            int y = (int)(r % ny), z = (int)(r / ny);
+            for (int x = 0; x < nx; ++x) {
+                double fstar[Q];
+                if (rates)
+                    node_collide_mrt(nx, ny, nz, rates, G, M, Minv, cur, psi, x, y, z, fstar);
+                else
+                    node_collide_bgk_guo(nx, ny, nz, tau, G, cur, psi, x, y, z, fstar);
+                for (int a = 0; a < Q; ++a) {
+                    size_t d = node_index(wrap(x + CV[a][0], nx), wrap(y + CV[a][1], ny),
+                                          wrap(z + CV[a][2], nz), nx, ny);
+                    nxt[(size_t)a * N + d] = fstar[a];
+                }
+            }
+        }
+        double *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    if (cur != f) memcpy(f, cur, (size_t)Q * N * sizeof(double));
+    free(psi);
+    free(g);
+    return 0;
+}
+
 /* Force field F (3*N, component-major) of the current state (Eq. 5). */
 int orc_force(int nx, int ny, int nz, double G, int psi_form, double rho0, const double *f,
               double *F) {
@@ -602,11 +765,12 @@ void orc_step_nodes(int nx, int ny, int nz, double tau, double G, int psi_form, 
  * out[0] = rho at the slab centre x = n/2, out[1] = rho at x = 0,
  * out[2] = steps run, out[3] = last max |drho|.  prof (may be NULL): the
  * n densities along x of the final state.  f (19 * n * 9) holds the final
- * state.
+ * state.  rates != NULL runs the MRT collision with those 19 rates instead
+ * of the paper's SRT step (tau is then unused).
  */
-int orc_coexistence(int n, double tau, double G, int psi_form, double rho0, double rho_l0,
-                    double rho_v0, int init, double tol, int check, long long max_steps,
-                    double *f, double *out, double *prof) {
+int orc_coexistence_ex(int n, double tau, const double *rates, double G, int psi_form, double rho0,
+                       double rho_l0, double rho_v0, int init, double tol, int check,
+                       long long max_steps, double *f, double *out, double *prof) {
     const int ny = 3, nz = 3;
     size_t N = (size_t)n * ny * nz;
     double *rprev = (double *)malloc(N * sizeof(double));
@@ -629,7 +793,9 @@ int orc_coexistence(int n, double tau, double G, int psi_form, double rho0, doub
         node_moments(f, N, i, &rprev[i], j);
     }
     while (steps < max_steps) {
-        if (orc_step(n, ny, nz, tau, G, psi_form, rho0, f, check) != 0) {
+        int rc = rates ? orc_step_forcing(n, ny, nz, tau, rates, G, psi_form, rho0, f, check)
+                       : orc_step(n, ny, nz, tau, G, psi_form, rho0, f, check);
+        if (rc != 0) {
             free(rprev);
             return -1;
         }
@@ -658,4 +824,13 @@ int orc_coexistence(int n, double tau, double G, int psi_form, double rho0, doub
         for (int x = 0; x < n; ++x) prof[x] = rprev[node_index(x, 1, 1, n, ny)];
     free(rprev);
     return 0;
+}
+
+/* Flat-interface run of the paper's SRT model (orc_coexistence_ex with no
+ * MRT rates). */
+int orc_coexistence(int n, double tau, double G, int psi_form, double rho0, double rho_l0,
+                    double rho_v0, int init, double tol, int check, long long max_steps,
+                    double *f, double *out, double *prof) {
+    return orc_coexistence_ex(n, tau, NULL, G, psi_form, rho0, rho_l0, rho_v0, init, tol, check,
+                              max_steps, f, out, prof);
 }

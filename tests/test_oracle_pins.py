@@ -506,3 +506,107 @@ def test_droplets_empty_and_full():
     f = lbm_inputs.droplet_populations(6, 5, 4, seed=3, mask=np.ones((4, 5, 6), bool))
     n, rec = oracle.droplets(f, 2.65, 0.073)
     assert n == 1 and int(rec[0][1]) == 120 and int(rec[0][0]) == 0 and int(rec[0][10]) == 6
+
+
+# --------------------------------------------------------------------------
+# MRT collision with Guo forcing (the operator the conclusions name as the
+# next step: moments of d'Humieres et al. 2002, forcing of Guo et al. 2002)
+# --------------------------------------------------------------------------
+
+def test_mrt_matrix_orthogonal_with_the_published_norms():
+    M = oracle.mrt_matrix()
+    c, w, _ = oracle.lattice()
+    D = M @ M.T
+    assert np.array_equal(D, np.diag(np.diag(D)))
+    assert np.diag(D).tolist() == [19, 2394, 252, 10, 40, 10, 40, 10, 40, 36, 72, 12, 24,
+                                   4, 4, 4, 8, 8, 8]
+    # conserved rows: density and the three momentum components
+    assert (M[0] == 1).all()
+    assert np.array_equal(M[[3, 5, 7]], c.T)
+    # the equilibrium moments of energy and of its square are those of the
+    # standard basis: m_eq(e) = rho (-11 + 19 u.u), m_eq(eps) = rho (3 - 11/2 u.u)
+    u = np.array([0.03, -0.02, 0.05])
+    meq = M @ oracle.feq(1.7, u)
+    assert meq[1] == pytest.approx(1.7 * (-11 + 19 * u @ u), abs=1e-13)
+    assert meq[2] == pytest.approx(1.7 * (3 - 5.5 * u @ u), abs=1e-13)
+
+
+def _post_collision(g):
+    """f*_a(x) from the state after one streaming step: g_a(x + c_a)."""
+    c, _, _ = oracle.lattice()
+    return np.stack([np.roll(g[a], shift=(-c[a][2], -c[a][1], -c[a][0]), axis=(0, 1, 2))
+                     for a in range(19)])
+
+
+@pytest.mark.parametrize("rates", ["srt", "mrt", "random"])
+def test_guo_forcing_adds_the_force_to_the_momentum(rates):
+    # any collision with Guo's forcing keeps rho and moves j to j + F at
+    # every node, whatever the rates of the non-conserved moments
+    f = lbm_inputs.random_populations(9, 7, 6, seed=81, rho_lo=0.3, rho_hi=2.2)
+    G, tau = -5.3, 0.85
+    if rates == "srt":
+        g = oracle.step_forcing(f, G, 1, rates=None, tau=tau)
+    else:
+        r = oracle.mrt_rates(tau) if rates == "mrt" else 0.2 + 1.6 * lbm_inputs.uniform(5, 19)
+        g = oracle.step_forcing(f, G, 1, rates=r)
+    fs = _post_collision(g)
+    c, _, _ = oracle.lattice()
+    F = oracle.force(f, G)
+    assert np.abs(fs.sum(0) - f.sum(0)).max() < 1e-14
+    for k in range(3):
+        dj = np.tensordot(c[:, k], fs - f, axes=1)
+        assert np.abs(dj - F[k]).max() < 1e-14
+
+
+def test_mrt_with_one_rate_is_srt_guo():
+    f = lbm_inputs.random_populations(7, 6, 5, seed=71, rho_lo=0.3, rho_hi=2.2)
+    tau = 0.9
+    a = oracle.step_forcing(f, -5.3, 3, rates=np.full(19, 1.0 / tau))
+    b = oracle.step_forcing(f, -5.3, 3, rates=None, tau=tau)
+    assert np.abs(a - b).max() < 1e-13
+
+
+@pytest.mark.parametrize("tau,others", [(0.8, (1.19, 1.4, 1.2, 1.4, 1.98)), (0.8, (1.6, 1.0, 1.0, 1.0, 1.0)),
+                                        (1.3, (1.19, 1.4, 1.2, 1.4, 1.98))])
+def test_mrt_shear_wave_decays_at_the_shear_rate(tau, others):
+    # nu = (1/s_nu - 1/2)/3 with s_nu = 1/tau, whatever the other rates
+    nx, k, A0 = 64, 2 * math.pi / 64, 1e-3
+    x = np.arange(nx)
+    f = np.zeros((19, 3, 3, nx))
+    for i in range(nx):
+        f[:, :, :, i] = oracle.feq(1.0, (0.0, A0 * math.sin(k * i), 0.0))[:, None, None]
+    rates = oracle.mrt_rates(tau, *others)
+
+    def amp(g):
+        uy = oracle.moments(g, G=0.0, bare=True)[2][0, 0]
+        return abs((uy * np.exp(-1j * k * x)).sum() * 2 / nx)
+    g1 = oracle.step_forcing(f, 0.0, 200, rates=rates)
+    g2 = oracle.step_forcing(g1, 0.0, 1000, rates=rates)
+    rate = -math.log(amp(g2) / amp(g1)) / 1000
+    assert abs(rate / ((tau - 0.5) / 3 * k * k) - 1.0) < 0.01
+
+
+def test_mrt_flat_interface_is_independent_of_viscosity_and_meets_guo_stability():
+    # with Guo forcing the flat interface satisfies the pseudo-potential
+    # equal-area condition with weight psi'/psi (the tau = 1 velocity-shift
+    # case of P8 has psi'/psi^2), so the densities do not change with the
+    # shear rate: the density ratio stays fixed as the viscosity varies
+    from scipy.integrate import quad
+    from scipy.optimize import fsolve
+    G = -5.3
+    psi = lambda r: 1.0 - math.exp(-r)
+    P = lambda r: r / 3.0 + G / 6.0 * psi(r) ** 2
+
+    def eqs(v):
+        rl, rv = v
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore")
+            I = quad(lambda r: (P(rl) - P(r)) * math.exp(-r) / psi(r), rv, rl, limit=200)[0]
+        return [P(rl) - P(rv), I]
+    rl_th, rv_th = fsolve(eqs, [2.1, 0.08], xtol=1e-13)
+    got = [oracle.coexistence(1.0, G, n=64, tol=1e-10, rho_l0=2.2, rho_v0=0.15,
+                              mrt_rates=oracle.mrt_rates(t), max_steps=200000) for t in (1.0, 1.5)]
+    for r in got:
+        assert abs(r["rho_l"] / rl_th - 1) < 1e-4 and abs(r["rho_v"] / rv_th - 1) < 1e-3
+    assert abs(got[0]["rho_l"] - got[1]["rho_l"]) < 1e-8
+    assert abs(got[0]["rho_v"] - got[1]["rho_v"]) < 1e-8
