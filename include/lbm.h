@@ -161,7 +161,10 @@ int lbm_set_stream(lbm_handle h, void *stream);
  * stored deviations are rounded up or down with probability given by the
  * discarded fraction, from a hash of the node index and its post-collision
  * rest population, instead of to nearest; removes the mass bias of
- * round-to-nearest in uniform regions; deterministic).  lbm_get_option also answers "step", "nx", "ny", "nz",
+ * round-to-nearest in uniform regions; deterministic), "diag_ccl" (0/1,
+ * default 0: every in-loop diagnostic step also labels the liquid
+ * components on the GPU, so the records of lbm_diag_history carry the
+ * droplet counts; needs 8 N bytes of labels).  lbm_get_option also answers "step", "nx", "ny", "nz",
  * "precision", "pattern". */
 int lbm_set_option(lbm_handle h, const char *key, double value);
 int lbm_get_option(lbm_handle h, const char *key, double *value);
@@ -187,7 +190,8 @@ int lbm_step(lbm_handle h, int n);
 
 /* Diagnostics recorded inside lbm_step (option "diag_interval"), oldest
  * first: up to max_records of the records not returned before (the device
- * ring keeps the last 1024).  droplets* are -1 (no labelling in the loop).
+ * ring keeps the last 1024).  droplets* are -1 unless option "diag_ccl"
+ * was on when the record's step ran.
  * *count receives the number written.  Synchronises. */
 int lbm_diag_history(lbm_handle h, lbm_diag *out, int max_records, int *count);
 
@@ -204,6 +208,33 @@ int lbm_moments(lbm_handle h, double *rho, double *ux, double *uy, double *uz);
 /* Diagnostics (see lbm_diag); want_ccl != 0 also labels the liquid
  * components on the GPU.  Synchronises. */
 int lbm_diagnostics(lbm_handle h, lbm_diag *out, int want_ccl);
+
+/* One droplet: a connected liquid component (6-connectivity, periodic;
+ * liquid as in lbm_diag), the droplets and satellites of the break-up
+ * study (section "Results": the main drop and the satellite droplets left
+ * after the ligament pinches off). */
+typedef struct {
+    long long first_node;   /* smallest linear index x + nx (y + ny z) in it          */
+    long long nodes;        /* node count                                             */
+    double volume_w;        /* sum of phi over its nodes                              */
+    double mass;            /* sum of rho over its nodes                              */
+    double centroid[3];     /* circular mean of its node coordinates on the periodic
+                               box, each in [0, n)                                   */
+    double resultant[3];    /* length of the mean unit vector per axis, in [0, 1];
+                               near 0 the centroid along that axis is undefined
+                               (the droplet fills the axis)                          */
+    int x_slices;           /* x slices holding one of its nodes (nx: it wraps)       */
+    int reserved;
+} lbm_droplet;
+
+/* Labels the liquid of the current state on the GPU and returns per-droplet
+ * statistics, largest first (ties: smaller first_node first): *count
+ * receives the number of droplets, out the first min(*count, max_droplets)
+ * of them (out may be NULL when max_droplets is 0).  The FP64 sums are
+ * accumulated with atomics, so their last bits may differ between calls.
+ * Device scratch: 8 N bytes of labels plus (80 + 4 ceil(nx/32)) bytes per
+ * droplet.  Synchronises.  LBM_ERR_TIMEOUT if the labelling guard tripped. */
+int lbm_droplets(lbm_handle h, lbm_droplet *out, int max_droplets, int *count);
 
 /* Canonical populations (see Conventions), host arrays of 19 * N doubles.
  * set converts to the storage precision (round to nearest even). */

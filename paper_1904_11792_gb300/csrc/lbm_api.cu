@@ -1,6 +1,7 @@
 // Host runtime and C ABI of liblbm.so (declared in include/lbm.h): handle
 // life cycle, device memory, the stream, CUDA-graph replay of the time step,
 // kernel timing, checkpoints and the host side of diagnostics.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -140,7 +141,7 @@ int enqueue_step(lbm_ctx* h, cudaStream_t s, long long step, int cur, bool timed
   const int mode = aa ? ((step & 1) ? MODE_AA_ODD : MODE_AA_EVEN) : MODE_AB;
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   const bool diag_step = h->diag_interval > 0 && step % h->diag_interval == 0;
-  if (h->fused && !aa && !diag_step && fused_applicable(h->g)) {
+  if (h->fused && !aa && !diag_step && fused_applicable(h->g, prec)) {
     // single pass: psi of each tile is recomputed from the staged populations
     if (timed) {
       e0 = take_event(h);
@@ -163,6 +164,12 @@ int enqueue_step(lbm_ctx* h, cudaStream_t s, long long step, int cur, bool timed
   if (diag_step) {
     CK(launch_diagnostics(prec, layout, h->g, h->ph, src, h->rho_l, h->rho_v, h->d_scratch, h->d_ring,
                           h->psi, h->d_flag, h->d_ring_count, lbm_ctx::kRing, s));
+    if (h->diag_ccl) {
+      long long* d4 = (long long*)(h->d_small + 32);
+      CK(launch_ccl(prec, layout, h->g, h->ph, src, 0.5 * (h->rho_l + h->rho_v), h->d_labels,
+                    h->d_labels + h->g.N, d4, s));
+      CK(launch_ccl_ring(d4, h->d_ring, h->d_ring_count, lbm_ctx::kRing, s));
+    }
   } else {
     CK(launch_psi(prec, layout, h->vec, h->g, h->ph, src, h->psi, h->d_flag, s));
   }
@@ -254,6 +261,11 @@ int ensure_scratch(lbm_ctx* h) {
   if (h->d_scratch) return LBM_OK;
   h->scratch_doubles = diag_scratch_doubles(h->g);
   return dev_alloc((void**)&h->d_scratch, h->scratch_doubles * sizeof(double), "diagnostics scratch");
+}
+
+int ensure_labels(lbm_ctx* h) {
+  if (h->d_labels) return LBM_OK;
+  return dev_alloc((void**)&h->d_labels, (size_t)h->g.N * 2 * sizeof(int), "labels");
 }
 
 int ensure_ring(lbm_ctx* h) {
@@ -374,6 +386,7 @@ void lbm_destroy(lbm_handle h) {
   dev_free(h->d_small, sizeof(double) * 64);
   dev_free(h->d_scratch, h->scratch_doubles * sizeof(double));
   dev_free(h->d_labels, (size_t)h->g.N * 2 * sizeof(int));
+  dev_free(h->d_drop, h->drop_bytes);
   dev_free(h->d_ring, sizeof(double) * DIAG_STRIDE * lbm_ctx::kRing);
   dev_free(h->d_ring_count, sizeof(unsigned long long));
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
@@ -494,8 +507,10 @@ int lbm_set_option(lbm_handle h, const char* key, double v) {
     drop_graphs(h);
   } else if (k == "rho_l") {
     h->rho_l = v;
+    drop_graphs(h);   // the in-loop diagnostics capture the densities
   } else if (k == "rho_v") {
     h->rho_v = v;
+    drop_graphs(h);
   } else if (k == "graph") {
     h->use_graph = v != 0.0;
   } else if (k == "stochastic_rounding") {
@@ -520,6 +535,13 @@ int lbm_set_option(lbm_handle h, const char* key, double v) {
       if (rc) return rc;
     }
     h->diag_interval = (int)d;
+    drop_graphs(h);
+  } else if (k == "diag_ccl") {
+    if (v != 0.0) {
+      int rc = ensure_labels(h);
+      if (rc) return rc;
+    }
+    h->diag_ccl = v != 0.0;
     drop_graphs(h);
   } else if (k == "kernel_timing") {
     if (v != 0.0 && !h->kernel_timing) {
@@ -557,10 +579,11 @@ int lbm_get_option(lbm_handle h, const char* key, double* v) {
   else if (k == "rho_v") *v = h->rho_v;
   else if (k == "graph") *v = h->use_graph;
   else if (k == "diag_interval") *v = h->diag_interval;
+  else if (k == "diag_ccl") *v = h->diag_ccl;
   else if (k == "occupancy") *v = h->minb ? h->minb : ((h->vec && h->g.nx % 2 == 0) ? 2 : 3);
   else if (k == "vector") *v = h->vec && (h->g.nx % 2 == 0);
   else if (k == "stochastic_rounding") *v = h->ph.sr;
-  else if (k == "fused") *v = h->fused && h->cfg.pattern == LBM_AB && fused_applicable(h->g);
+  else if (k == "fused") *v = h->fused && h->cfg.pattern == LBM_AB && fused_applicable(h->g, h->cfg.precision);
   else if (k == "kernel_timing") *v = h->kernel_timing;
   else if (k == "block_x") *v = h->block.x;
   else if (k == "block_y") *v = h->block.y;
@@ -578,6 +601,7 @@ int lbm_get_option(lbm_handle h, const char* key, double* v) {
 static int init_common(lbm_handle h, const InitSpec& sp) {
   h->step = 0;
   h->cur = 0;
+  drop_graphs(h);   // the in-loop diagnostics capture the densities
   CK(launch_init(h->cfg.precision, h->g, h->ph, sp, array_ptr(h, 0), h->stream));
   h->initialized = true;
   return LBM_OK;
@@ -682,7 +706,12 @@ int lbm_diag_history(lbm_handle h, lbm_diag* out, int max_records, int* count) {
     const long long slot = r % lbm_ctx::kRing;
     CK(cudaMemcpy(rec.data(), h->d_ring + slot * DIAG_STRIDE, sizeof(double) * DIAG_STRIDE,
                   cudaMemcpyDeviceToHost));
-    fill_diag(&out[n++], rec.data(), h->diag_steps[(size_t)r]);
+    fill_diag(&out[n], rec.data(), h->diag_steps[(size_t)r]);
+    if (rec[DIAG_CCL + 3] != 0.0) return fail(LBM_ERR_TIMEOUT, "connected-component labelling guard tripped");
+    out[n].droplets = (int)rec[DIAG_CCL];
+    out[n].droplets_min8 = (int)rec[DIAG_CCL + 1];
+    out[n].largest_droplet = (long long)rec[DIAG_CCL + 2];
+    ++n;
   }
   h->diag_fetched = total;
   *count = n;
@@ -740,10 +769,8 @@ int lbm_diagnostics(lbm_handle h, lbm_diag* out, int want_ccl) {
   double r[DIAG_OUT];
   long long c4[4] = {-1, -1, -1, 0};
   if (want_ccl) {
-    if (!h->d_labels) {
-      rc = dev_alloc((void**)&h->d_labels, (size_t)h->g.N * 2 * sizeof(int), "labels");
-      if (rc) return rc;
-    }
+    rc = ensure_labels(h);
+    if (rc) return rc;
     long long* d4 = (long long*)(h->d_small + 32);
     CK(launch_ccl(h->cfg.precision, layout, h->g, h->ph, f, 0.5 * (h->rho_l + h->rho_v), h->d_labels,
                   h->d_labels + h->g.N, d4, h->stream));
@@ -756,6 +783,81 @@ int lbm_diagnostics(lbm_handle h, lbm_diag* out, int want_ccl) {
   out->droplets = (int)c4[0];
   out->droplets_min8 = (int)c4[1];
   out->largest_droplet = c4[2];
+  return LBM_OK;
+}
+
+int lbm_droplets(lbm_handle h, lbm_droplet* out, int max_droplets, int* count) {
+  if (!h || !count || max_droplets < 0 || (max_droplets > 0 && !out)) return fail(LBM_ERR_ARG, "bad argument");
+  if (!h->initialized) return fail(LBM_ERR_STATE, "lattice not initialised");
+  *count = 0;
+  int rc = ensure_labels(h);
+  if (rc) return rc;
+  const int layout = cur_layout(h);
+  const void* f = cur_array(h);
+  long long* d4 = (long long*)(h->d_small + 32);
+  int* L = h->d_labels;
+  int* sizes = h->d_labels + h->g.N;
+  CK(launch_ccl(h->cfg.precision, layout, h->g, h->ph, f, 0.5 * (h->rho_l + h->rho_v), L, sizes, d4, h->stream));
+  long long c4[4];
+  CK(cudaMemcpyAsync(c4, d4, sizeof(c4), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (c4[3]) return fail(LBM_ERR_TIMEOUT, "connected-component labelling guard tripped");
+  const long long nd = c4[0];
+  *count = (int)nd;
+  if (nd == 0) return LBM_OK;
+  const int words = (h->g.nx + 31) / 32;
+  const size_t rec_bytes = sizeof(double) * DROP_REC * (size_t)nd;
+  const size_t need = rec_bytes + sizeof(unsigned) * ((size_t)words * nd + 1);
+  if (need > h->drop_bytes) {
+    dev_free(h->d_drop, h->drop_bytes);
+    h->d_drop = nullptr;
+    h->drop_bytes = 0;
+    rc = dev_alloc((void**)&h->d_drop, need, "droplet records");
+    if (rc) return rc;
+    h->drop_bytes = need;
+  }
+  double* rec = h->d_drop;
+  unsigned* xbits = (unsigned*)((char*)h->d_drop + rec_bytes);
+  unsigned* nslot = xbits + (size_t)words * nd;
+  CK(launch_droplets(h->cfg.precision, layout, h->g, h->ph, f, h->rho_l, h->rho_v, L, sizes, rec, xbits, nslot,
+                     (int)nd, h->stream));
+  std::vector<double> hr((size_t)DROP_REC * nd);
+  std::vector<unsigned> hb((size_t)words * nd);
+  unsigned ns = 0;
+  CK(cudaMemcpyAsync(hr.data(), rec, rec_bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(hb.data(), xbits, sizeof(unsigned) * hb.size(), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&ns, nslot, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if ((long long)ns != nd) return fail(LBM_ERR_STATE, "droplet roots differ from the component count");
+  std::vector<lbm_droplet> d((size_t)nd);
+  const double two_pi = 6.283185307179586476925286766559;
+  const int dims[3] = {h->g.nx, h->g.ny, h->g.nz};
+  for (long long k = 0; k < nd; ++k) {
+    const double* r = &hr[(size_t)k * DROP_REC];
+    lbm_droplet& o = d[(size_t)k];
+    o.first_node = (long long)r[0];
+    o.nodes = (long long)r[1];
+    o.volume_w = r[2];
+    o.mass = r[3];
+    for (int a = 0; a < 3; ++a) {
+      const double c = r[4 + 2 * a], sn = r[5 + 2 * a];
+      double t = std::atan2(sn, c);
+      if (t < 0.0) t += two_pi;
+      double pos = t / two_pi * dims[a];
+      if (pos >= dims[a]) pos -= dims[a];
+      o.centroid[a] = pos;
+      o.resultant[a] = std::sqrt(c * c + sn * sn) / r[1];
+    }
+    int xs = 0;
+    for (int w = 0; w < words; ++w) xs += __builtin_popcount(hb[(size_t)k * words + w]);
+    o.x_slices = xs;
+    o.reserved = 0;
+  }
+  std::sort(d.begin(), d.end(), [](const lbm_droplet& a, const lbm_droplet& b) {
+    return a.nodes != b.nodes ? a.nodes > b.nodes : a.first_node < b.first_node;
+  });
+  const long long n = std::min<long long>(nd, max_droplets);
+  for (long long k = 0; k < n; ++k) out[k] = d[(size_t)k];
   return LBM_OK;
 }
 

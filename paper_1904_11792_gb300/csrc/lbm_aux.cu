@@ -396,6 +396,8 @@ __global__ void __launch_bounds__(FT) diag_final_kernel(Geom g, int nblocks,
       *ring_count = n + 1;
       out += (n % (unsigned long long)ring_cap) * DIAG_STRIDE;
       out[DIAG_OUT] = (double)n;
+      out[DIAG_CCL + 0] = out[DIAG_CCL + 1] = out[DIAG_CCL + 2] = -1.0;
+      out[DIAG_CCL + 3] = 0.0;
     }
     out[0] = sg[0][0];
     out[1] = sg[1][0];
@@ -480,12 +482,16 @@ __global__ void ccl_union_kernel(Geom g, int* L, unsigned long long* err) {
     if (L[n[k]] >= 0) unite(L, (int)i, (int)n[k], err);
 }
 
+// After the unions every tree is final, so pointing a node straight at its
+// root (the smallest index of its component) leaves every concurrent root
+// search valid.
 __global__ void ccl_compress_kernel(Geom g, int* L, int* sizes, unsigned long long* err) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.N || L[i] < 0) return;
   long long hops = 0;
   const int r = find_root(L, (int)i, hops);
   if (hops >= kMaxHops) atomicOr(err, 1ull);
+  L[i] = r;
   atomicAdd(&sizes[r], 1);
 }
 
@@ -495,6 +501,88 @@ __global__ void ccl_count_kernel(Geom g, const int* L, const int* sizes, unsigne
   atomicAdd(&out[0], 1ull);
   if (sizes[i] >= 8) atomicAdd(&out[1], 1ull);
   atomicMax(&out[2], (unsigned long long)sizes[i]);
+}
+
+// Copies the droplet counts of the CCL just run into the ring record the
+// diagnostics of the same step appended (slot counter - 1).
+__global__ void ccl_ring_kernel(const long long* out4, double* ring, const unsigned long long* ring_count,
+                                int ring_cap) {
+  const unsigned long long n = *ring_count - 1;
+  double* rec = ring + (n % (unsigned long long)ring_cap) * DIAG_STRIDE;
+  rec[DIAG_CCL + 0] = (double)out4[0];
+  rec[DIAG_CCL + 1] = (double)out4[1];
+  rec[DIAG_CCL + 2] = (double)out4[2];
+  rec[DIAG_CCL + 3] = (double)out4[3];
+}
+
+// ---------------------------------------------------------------------------
+// Per-droplet statistics (after launch_ccl): every root takes a record slot;
+// every liquid node adds to its droplet's record
+//   [root, nodes, sum phi, sum rho, cos/sin sums of 2 pi x/nx, y, z]
+// and sets the bit of its x slice in the droplet's x-occupancy mask.  The
+// FP64 sums are atomic (their order, and so the last bits, vary run to run).
+// ---------------------------------------------------------------------------
+__global__ void droplet_slot_kernel(Geom g, const int* L, int* slot_of, double* rec, unsigned* nslot,
+                                    int cap) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.N || L[i] != (int)i) return;
+  const unsigned k = atomicAdd(nslot, 1u);
+  slot_of[i] = k < (unsigned)cap ? (int)k : -1;
+  if (k < (unsigned)cap) rec[(size_t)k * DROP_REC] = (double)i;
+}
+
+template <int P>
+__global__ void droplet_stats_kernel(Geom g, Phys ph, int layout, const typename Prec<P>::T* f, double rho_l,
+                                     double rho_v, const int* L, const int* slot_of, double* rec, unsigned* xbits,
+                                     int words) {
+  using C = typename Prec<P>::C;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int k = -1, x = 0;
+  double v[DROP_REC - 1];
+#pragma unroll
+  for (int m = 0; m < DROP_REC - 1; ++m) v[m] = 0.0;
+  if (i < g.N && L[i] >= 0) {
+    k = slot_of[L[i]];
+    if (k >= 0) {
+      int y, z;
+      coords(g, i, x, y, z);
+      Nbr nb;
+      nb.make(g, x, y, z);
+      C rc, j[3];
+      node_rho_j<P>(g, ph, layout, f, nb, rc, j);
+      const double rho = (double)rc;
+      v[0] = 1.0;
+      v[1] = fmin(fmax((rho - rho_v) / (rho_l - rho_v), 0.0), 1.0);
+      v[2] = rho;
+      sincospi(2.0 * x / g.nx, &v[4], &v[3]);
+      sincospi(2.0 * y / g.ny, &v[6], &v[5]);
+      sincospi(2.0 * z / g.nz, &v[8], &v[7]);
+    }
+  }
+  // one set of atomics per warp when all its liquid lanes share a droplet
+  // (the common case: the warp covers 32 consecutive nodes of a row)
+  const int kmax = __reduce_max_sync(0xffffffffu, k);
+  const bool uniform = __all_sync(0xffffffffu, k < 0 || k == kmax);
+  if (uniform) {
+    if (kmax < 0) return;
+#pragma unroll
+    for (int m = 0; m < DROP_REC - 1; ++m)
+      for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_xor_sync(0xffffffffu, v[m], o);
+    if ((threadIdx.x & 31) == 0) {
+      double* r = rec + (size_t)kmax * DROP_REC + 1;
+#pragma unroll
+      for (int m = 0; m < DROP_REC - 1; ++m) atomicAdd(r + m, v[m]);
+    }
+  } else if (k >= 0) {
+    double* r = rec + (size_t)k * DROP_REC + 1;
+#pragma unroll
+    for (int m = 0; m < DROP_REC - 1; ++m) atomicAdd(r + m, v[m]);
+  }
+  if (k >= 0) {
+    unsigned* w = xbits + (size_t)k * words + (x >> 5);
+    const unsigned bit = 1u << (x & 31);
+    if (!(*(volatile unsigned*)w & bit)) atomicOr(w, bit);
+  }
 }
 
 inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
@@ -574,7 +662,43 @@ cudaError_t ccl_t(int layout, const Geom& g, const Phys& ph, const void* f, doub
   return cudaGetLastError();
 }
 
+template <int P>
+cudaError_t droplets_t(int layout, const Geom& g, const Phys& ph, const void* f, double rho_l, double rho_v,
+                       const int* L, int* slot_of, double* rec, unsigned* xbits, unsigned* nslot, int cap,
+                       cudaStream_t s) {
+  const unsigned nb = blocks_for(g.N, 256);
+  const int words = (g.nx + 31) / 32;
+  cudaError_t e = cudaMemsetAsync(rec, 0, sizeof(double) * DROP_REC * (size_t)cap, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(xbits, 0, sizeof(unsigned) * words * (size_t)cap, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(nslot, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  droplet_slot_kernel<<<nb, 256, 0, s>>>(g, L, slot_of, rec, nslot, cap);
+  droplet_stats_kernel<P><<<nb, 256, 0, s>>>(g, ph, layout, (const typename Prec<P>::T*)f, rho_l, rho_v, L,
+                                             slot_of, rec, xbits, words);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_ccl_ring(const long long* out4, double* ring, const unsigned long long* ring_count,
+                            int ring_cap, cudaStream_t s) {
+  ccl_ring_kernel<<<1, 1, 0, s>>>(out4, ring, ring_count, ring_cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_droplets(int precision, int layout, const Geom& g, const Phys& ph, const void* f,
+                            double rho_l, double rho_v, const int* labels, int* sizes, double* rec,
+                            unsigned* xbits, unsigned* nslot, int cap, cudaStream_t s) {
+  switch (precision) {
+    case LBM_F64: return droplets_t<LBM_F64>(layout, g, ph, f, rho_l, rho_v, labels, sizes, rec, xbits, nslot, cap, s);
+    case LBM_F32: return droplets_t<LBM_F32>(layout, g, ph, f, rho_l, rho_v, labels, sizes, rec, xbits, nslot, cap, s);
+    case LBM_F16DEV:
+      return droplets_t<LBM_F16DEV>(layout, g, ph, f, rho_l, rho_v, labels, sizes, rec, xbits, nslot, cap, s);
+    case LBM_BF16DEV:
+      return droplets_t<LBM_BF16DEV>(layout, g, ph, f, rho_l, rho_v, labels, sizes, rec, xbits, nslot, cap, s);
+  }
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_init(int precision, const Geom& g, const Phys& ph, const InitSpec& spec, void* f,
                         cudaStream_t s) {

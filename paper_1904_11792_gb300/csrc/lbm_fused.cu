@@ -2,26 +2,33 @@
 //
 // The two-kernel step reads every population twice (the psi pass needs rho of
 // every node before any collision, because the force of Eq. 5 at x needs psi
-// at all 18 neighbours).  Here each block owns a 32 x 8 tile of (x, y) and a
-// run of z planes.  For every plane of its tile plus a one-node halo it
-// stages the 19 populations in shared memory, computes psi of that footprint,
-// and collides and streams the interior of the plane below once psi of the
-// plane above is known:
+// at all 18 neighbours).  Here a block owns a 64 x TY tile of (x, y) (32
+// lanes x two nodes per row, one warp per row) and a run of z planes, and
+// marches through the run:
 //
-//   plane p = z0 - 1, z0, ..., z1 (periodic):  stage f(p)            (TMA)
-//                                              psi(p) of the footprint -> ring
-//                                              collide + stream plane p - 1
+//   iteration k, plane p = z0 - 1 + k (periodic):
+//     psi of plane p over the tile and its one-node ring  -> psi ring slot
+//     barrier
+//     collide + stream plane p - 1 (psi of planes p - 2 .. p now known)
 //
-// Staging is Blackwell TMA: one thread issues three cp.async.bulk.tensor
-// copies per plane (the 32 x 8 x 19 interior box and the two halo rows, from
-// a 4-D tensor map [19][nz][ny][nx]) that complete on an mbarrier; only the
-// two halo columns (periodic in x) use per-thread cp.async.  Four plane
-// buffers keep two planes in flight while one is collided.  Populations leave
-// DRAM once per step (halo rows and the boundary planes of a z run are read
-// by neighbouring blocks at about the same time and hit L2) and psi never
-// goes to DRAM.  The arithmetic is psi_math and collide_math of lbm_node.cuh,
-// so the results equal the two-kernel step bitwise.  A-B streaming; lattices
-// with nx % 32 == 0 and ny % 8 == 0.
+// Populations reach shared memory by Blackwell TMA: per plane nine
+// cp.async.bulk.tensor copies from 4-D tensor maps [19][nz][ny][nx] (the
+// 64 x TY interior, the two halo rows, the two halo columns and the four
+// corners as 16-byte wide boxes, every box at in-range coordinates so the
+// periodic wrap needs no fill), completing on the buffer's mbarrier.  Two
+// plane buffers: the copies of plane p + 2 start as soon as psi of plane p
+// has been read out of its buffer, a full iteration ahead.  A thread keeps
+// the stored populations of its two nodes in registers from the psi step of
+// plane p to their collision in the next iteration, so a buffer is free
+// after the psi step.  The psi values of four planes sit in a ring (the
+// collision of plane p - 1 reads slots p - 2 .. p while faster warps already
+// write p + 1), so one block barrier per plane suffices.  Populations leave
+// DRAM once per step (halo boxes and the two boundary planes of a run are
+// read by neighbouring blocks at about the same time and mostly hit L2),
+// psi never goes to DRAM.  The arithmetic is psi_math and collide_math of
+// lbm_node.cuh and the stores are those of collide_pair, so the results
+// equal the two-kernel step bitwise.  A-B streaming, 4- and 2-byte storage,
+// lattices with nx % 64 == 0 and ny % 4 == 0.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -35,51 +42,46 @@ namespace lbm {
 
 namespace {
 
-constexpr int FX = 32;   // tile along x (one warp per row)
-constexpr int FY = 8;    // tile along y (eight warps)
-constexpr int FZ = 16;   // z planes per block
-constexpr int FT = FX * FY;
-constexpr int NB = 4;    // staged planes: psi, collide, two in flight
-constexpr int FH = FY + 2;
-constexpr int PW = FX + 2;
+constexpr int TX = 64;   // tile along x: 32 lanes x 2 nodes
+constexpr int TY = 4;    // tile along y: one warp per row
+constexpr int NT = 32 * TY;
+constexpr int NB = 2;    // plane buffers
+constexpr int NR = 4;    // psi ring slots
+constexpr int RW = TX + 4;   // ring row: position x - x0 + 2 (pairs start 8-byte aligned)
+constexpr int RH = TY + 2;
+constexpr int HC = 2 * (TX + 2) + 2 * TY;   // halo cells of a plane
+constexpr int HPT = (HC + NT - 1) / NT;     // halo cells per thread
 constexpr long long kWaitLimit = 1ll << 22;  // bounded mbarrier polls (seconds)
 
 __host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) & ~size_t(127); }
 
 template <int P> struct FusedShape {
   using T = typename Prec<P>::T;
+  using C = typename Prec<P>::C;
   static constexpr int E = sizeof(T);
-  static constexpr int U = E == 2 ? 2 : 1;               // elements per halo-column copy
-  static constexpr int UNIT = U * E;                      // bytes per halo-column copy
-  static constexpr size_t int_bytes = (size_t)Q * FY * FX * E;   // TMA box (32, 8, 1, 19)
-  static constexpr size_t row_bytes = (size_t)Q * FX * E;        // TMA box (32, 1, 1, 19)
-  static constexpr size_t col_bytes = (size_t)Q * FH * U * E;
+  static constexpr int CW = 16 / E;                               // one 16-byte TMA unit along x
+  static constexpr size_t int_bytes = (size_t)Q * TY * TX * E;    // box (64, TY, 1, 19)
+  static constexpr size_t row_bytes = (size_t)Q * TX * E;         // box (64, 1, 1, 19)
+  static constexpr size_t col_bytes = (size_t)Q * TY * CW * E;    // box (CW, TY, 1, 19)
+  static constexpr size_t cor_bytes = (size_t)Q * CW * E;         // box (CW, 1, 1, 19)
   static constexpr size_t off_int = 0;
   static constexpr size_t off_top = align128(off_int + int_bytes);
   static constexpr size_t off_bot = align128(off_top + row_bytes);
-  static constexpr size_t off_xl = align128(off_bot + row_bytes);
-  static constexpr size_t off_xr = align128(off_xl + col_bytes);
-  static constexpr size_t plane = align128(off_xr + col_bytes);
+  static constexpr size_t off_lft = align128(off_bot + row_bytes);
+  static constexpr size_t off_rgt = align128(off_lft + col_bytes);
+  static constexpr size_t off_cor = align128(off_rgt + col_bytes);  // 4 corners, cor_stride apart
+  static constexpr size_t cor_stride = align128(cor_bytes);
+  static constexpr size_t plane = align128(off_cor + 4 * cor_stride);
   static constexpr size_t off_ring = NB * plane;
-  static constexpr size_t ring_bytes = align128(3ull * FH * PW * sizeof(typename Prec<P>::C));
+  static constexpr size_t ring_bytes = align128((size_t)NR * RH * RW * sizeof(C));
   static constexpr size_t off_bar = off_ring + ring_bytes;
   static constexpr size_t smem = off_bar + NB * sizeof(unsigned long long);
-  static constexpr unsigned tx_bytes = (unsigned)(int_bytes + 2 * row_bytes);
+  static constexpr unsigned tx_bytes = (unsigned)(int_bytes + 2 * row_bytes + 2 * col_bytes + 4 * cor_bytes);
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
-
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_addr(smem_dst)), "l"(gmem_src),
-               "n"(BYTES)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
@@ -103,180 +105,230 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2,
                                             unsigned long long* bar) {
   asm volatile(
       "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
       "%5}], [%6];\n" ::"r"(smem_addr(dst)),
-      "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+      "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(0), "r"(smem_addr(bar))
       : "memory");
 }
 
+struct Maps {
+  CUtensorMap interior, row, col, cor;
+};
+
+// Issues the nine copies of plane zz into buffer b (one thread).
 template <int P>
-__global__ void __launch_bounds__(FT, 2) fused_kernel(const __grid_constant__ CUtensorMap tm_int,
-                                                      const __grid_constant__ CUtensorMap tm_row, Geom g,
-                                                      Phys ph, const typename Prec<P>::T* src,
-                                                      typename Prec<P>::T* dst, int* flag, int ntx,
-                                                      int nchunks) {
+__device__ __forceinline__ void issue_plane(unsigned char* smem, const Maps& m, int b, int x0, int y0, int xl,
+                                            int xr, int ym, int yp, int zz, unsigned long long* bar) {
+  using S = FusedShape<P>;
+  unsigned char* base = smem + (size_t)b * S::plane;
+  // order earlier generic-proxy reads of this buffer before the async writes
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  mbar_expect_tx(bar, S::tx_bytes);
+  tma_load_4d(base + S::off_int, &m.interior, x0, y0, zz, bar);
+  tma_load_4d(base + S::off_top, &m.row, x0, ym, zz, bar);
+  tma_load_4d(base + S::off_bot, &m.row, x0, yp, zz, bar);
+  tma_load_4d(base + S::off_lft, &m.col, xl, y0, zz, bar);
+  tma_load_4d(base + S::off_rgt, &m.col, xr, y0, zz, bar);
+  tma_load_4d(base + S::off_cor + 0 * S::cor_stride, &m.cor, xl, ym, zz, bar);
+  tma_load_4d(base + S::off_cor + 1 * S::cor_stride, &m.cor, xr, ym, zz, bar);
+  tma_load_4d(base + S::off_cor + 2 * S::cor_stride, &m.cor, xl, yp, zz, bar);
+  tma_load_4d(base + S::off_cor + 3 * S::cor_stride, &m.cor, xr, yp, zz, bar);
+}
+
+template <int P>
+__global__ void __launch_bounds__(NT, 3) fused_kernel(const __grid_constant__ Maps maps, Geom g, Phys ph,
+                                                      typename Prec<P>::T* dst, int* flag, int ntx, int nchunks,
+                                                      int fz) {
   using T = typename Prec<P>::T;
   using C = typename Prec<P>::C;
+  using V = typename Pair<P>::V;
   using S = FusedShape<P>;
   extern __shared__ __align__(128) unsigned char smem[];
-  C* ring = reinterpret_cast<C*>(smem + S::off_ring);  // [3][FH][PW]
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + S::off_bar);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + S::off_bar);
+  C* ring = reinterpret_cast<C*>(smem + S::off_ring);
 
   const int u = blockIdx.x;
   const int chunk = u % nchunks, xy = u / nchunks;
-  const int x0 = (xy % ntx) * FX, y0 = (xy / ntx) * FY;
-  const int z0 = chunk * FZ, z1 = min(z0 + FZ, g.nz);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int x0 = (xy % ntx) * TX, y0 = (xy / ntx) * TY;
+  const int z0 = chunk * fz, z1 = min(z0 + fz, g.nz);
+  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+  const int np = (z1 - z0) + 2;        // planes z0 - 1 .. z1; plane z0 - 1 + k in buffer k % NB
   const long long N = g.N;
-  const int ym = y0 == 0 ? g.ny - 1 : y0 - 1, yp = y0 + FY == g.ny ? 0 : y0 + FY;
+  const int ym = y0 == 0 ? g.ny - 1 : y0 - 1, yp = y0 + TY == g.ny ? 0 : y0 + TY;
+  const int xl = x0 == 0 ? g.nx - S::CW : x0 - S::CW, xr = x0 + TX == g.nx ? 0 : x0 + TX;
   const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
           s2 = shift_of<P>(7, ph.rho_ref);
+  auto zwrap = [&](int p) { return p < 0 ? p + g.nz : (p >= g.nz ? p - g.nz : p); };
 
-  auto part = [&](int b, size_t off) { return reinterpret_cast<T*>(smem + b * S::plane + off); };
+  // this thread's halo cells: element offset in a plane buffer, stride
+  // between directions, and ring position
+  int h_off[HPT], h_str[HPT], h_ring[HPT];
+#pragma unroll
+  for (int j = 0; j < HPT; ++j) {
+    const int h = tid + j * NT;
+    int off = 0, str = 0, rr = 0, c = 0;
+    if (h < 2 * (TX + 2)) {
+      const int side = h >= TX + 2;             // 0: row y0 - 1, 1: row y0 + TY
+      const int i = h - side * (TX + 2);        // 0 .. TX + 1 <-> x0 - 1 .. x0 + TX
+      rr = side ? TY + 1 : 0;
+      c = i;
+      if (i == 0 || i == TX + 1) {
+        const int corner = 2 * side + (i == 0 ? 0 : 1);
+        off = (int)((S::off_cor + corner * S::cor_stride) / S::E) + (i == 0 ? S::CW - 1 : 0);
+        str = S::CW;
+      } else {
+        off = (int)((side ? S::off_bot : S::off_top) / S::E) + (i - 1);
+        str = TX;
+      }
+    } else if (h < HC) {
+      const int i = h - 2 * (TX + 2);
+      const int side = i >= TY;                 // 0: column x0 - 1, 1: column x0 + TX
+      const int r = i - side * TY;
+      rr = r + 1;
+      c = side ? TX + 1 : 0;
+      off = (int)((side ? S::off_rgt : S::off_lft) / S::E) + r * S::CW + (side ? 0 : S::CW - 1);
+      str = TY * S::CW;
+    } else {
+      off = -1;
+    }
+    h_off[j] = off;
+    h_str[j] = str;
+    h_ring[j] = rr * RW + c + 1;
+  }
 
+  __shared__ int s_abort;
   if (tid == 0) {
-    for (int b = 0; b < NB; ++b) mbar_init(bar + b, 1);
+    // bit 2 of the flag: a block (of this launch or an earlier one) gave up
+    // on a wait, the result is void; skip the work
+    s_abort = (*(volatile int*)flag & 2) != 0;
+    for (int b = 0; b < NB; ++b) mbar_init(full + b, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
+  if (s_abort) return;
+  if (tid == 0)
+    for (int k = 0; k < NB && k < np; ++k)
+      issue_plane<P>(smem, maps, k, x0, y0, xl, xr, ym, yp, zwrap(z0 - 1 + k), full + k);
 
-  // Stage plane p (periodic) of the footprint into buffer b.
-  auto issue = [&](int p, int b) {
-    const int zz = p < 0 ? p + g.nz : (p >= g.nz ? p - g.nz : p);
-    if (tid == 0) {
-      // order earlier generic-proxy reads of this buffer before the TMA writes
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      mbar_expect_tx(bar + b, S::tx_bytes);
-      tma_load_4d(part(b, S::off_int), &tm_int, x0, y0, zz, 0, bar + b);
-      tma_load_4d(part(b, S::off_top), &tm_row, x0, ym, zz, 0, bar + b);
-      tma_load_4d(part(b, S::off_bot), &tm_row, x0, yp, zz, 0, bar + b);
-    }
-    // the two halo columns x0 - 1 and x0 + 32 (periodic), rows y0 - 1 .. y0 + 8
-    for (int job = tid; job < 2 * Q * FH; job += FT) {
-      const int side = job >= Q * FH;
-      const int rem = job - side * Q * FH;
-      const int a = rem / FH, r = rem - a * FH;
-      int yy = y0 - 1 + r;
-      yy = yy < 0 ? yy + g.ny : (yy >= g.ny ? yy - g.ny : yy);
-      int xx = side ? x0 + FX : x0 - S::U;
-      xx = xx < 0 ? xx + g.nx : (xx >= g.nx ? xx - g.nx : xx);
-      T* d = part(b, side ? S::off_xr : S::off_xl) + (a * FH + r) * S::U;
-      cp_async<S::UNIT>(d, src + (long long)a * N + (long long)g.nx * (yy + (long long)g.ny * zz) + xx);
-    }
-    cp_async_commit();
-  };
-
-  // population a of footprint cell (r, c), r in [0, FH), c in [0, PW)
-  auto fp = [&](int b, int a, int r, int c) -> C {
-    const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
-    const T* q;
-    if (c == 0)
-      q = part(b, S::off_xl) + (a * FH + r) * S::U + (S::U - 1);
-    else if (c == PW - 1)
-      q = part(b, S::off_xr) + (a * FH + r) * S::U;
-    else if (r == 0)
-      q = part(b, S::off_top) + a * FX + c - 1;
-    else if (r == FH - 1)
-      q = part(b, S::off_bot) + a * FX + c - 1;
-    else
-      q = part(b, S::off_int) + (a * FY + r - 1) * FX + c - 1;
-    return Prec<P>::load_rw(q, sh);
-  };
-
-  // psi of the footprint of the plane in buffer b into ring slot rs: the
-  // interior (one cell per thread) and the 84 halo cells
-  auto psi_plane = [&](int b, int rs) {
-    {
-      const T* q = part(b, S::off_int) + warp * FX + lane;
-      C fv[Q];
-#pragma unroll
-      for (int a = 0; a < Q; ++a)
-        fv[a] = Prec<P>::load_rw(q + a * FY * FX, a == 0 ? s0 : (a <= 6 ? s1 : s2));
-      psi_math<C>(ph, rho_of<C>(fv), ring + (rs * FH + warp + 1) * PW + lane + 1, flag);
-    }
-    // halo cell h = warp * 11 + lane (lane < 11): every warp takes the same
-    // share of the 84 cells
-    const int h = warp * 11 + lane;
-    if (lane < 11 && h < 2 * FX + 2 * FH) {
-      int r, c;
-      if (h < FX) {
-        r = 0;
-        c = h + 1;
-      } else if (h < 2 * FX) {
-        r = FH - 1;
-        c = h - FX + 1;
-      } else if (h < 2 * FX + FH) {
-        r = h - 2 * FX;
-        c = 0;
-      } else {
-        r = h - 2 * FX - FH;
-        c = PW - 1;
-      }
-      C fv[Q];
-#pragma unroll
-      for (int a = 0; a < Q; ++a) fv[a] = fp(b, a, r, c);
-      psi_math<C>(ph, rho_of<C>(fv), ring + (rs * FH + r) * PW + c, flag);
-    }
-  };
-
-  // collide + stream this thread's interior node on plane z (populations in
-  // buffer fb; psi of planes z - 1, z, z + 1 in ring slots bm, bz, bp)
-  auto collide_plane = [&](int z, int fb, int bm, int bz, int bp) {
-    const int tx = lane, ty = warp;
-    const int x = x0 + tx, y = y0 + ty;
-    const T* q = part(fb, S::off_int) + ty * FX + tx;
-    C f[Q];
-#pragma unroll
-    for (int a = 0; a < Q; ++a) f[a] = Prec<P>::load_rw(q + a * FY * FX, a == 0 ? s0 : (a <= 6 ? s1 : s2));
-    const int slot[3] = {bm, bz, bp};
-    C pn[Q];
-    pn[0] = 0;
-#pragma unroll
-    for (int a = 1; a < Q; ++a)
-      pn[a] = ring[(slot[cz(a) + 1] * FH + ty + 1 + cy(a)) * PW + tx + 1 + cx(a)];
-    const C pc = ring[(bz * FH + ty + 1) * PW + tx + 1];
-    C fs[Q];
-    collide_math<C>(ph, f, pc, pn, fs);
-    Nbr nb;
-    nb.make(g, x, y, z);
-    const unsigned seed = (Prec<P>::dev && ph.sr) ? sr_seed(nb.idx(0, 0, 0), fs[0]) : 0u;
-#pragma unroll
-    for (int a = 0; a < Q; ++a)
-      store_pop<P>(ph, dst + (long long)a * N + nb.idx(cx(a), cy(a), cz(a)), fs[a],
-                   a == 0 ? s0 : (a <= 6 ? s1 : s2), seed, a);
-  };
-
-  // planes P0 .. z1; plane P0 + k sits in buffer k % NB (barrier phase
-  // k / NB) and its psi in ring slot k % 3.
-  const int P0 = z0 - 1;
-  const int np = (z1 - z0) + 2;
-  for (int k = 0; k < NB - 1 && k < np; ++k) issue(P0 + k, k);
-  for (int k = 0; k < np; ++k) {
+  V prev[Q];   // stored populations of this thread's two nodes, previous plane
+  int k = 0;
+  for (; k < np; ++k) {
     const int b = k % NB;
-    const int ahead = np - 1 - k;
-    if (ahead >= 2) cp_async_wait<2>();
-    else if (ahead == 1) cp_async_wait<1>();
-    else cp_async_wait<0>();
-    const bool ok = mbar_wait_bounded(bar + b, (unsigned)((k / NB) & 1));
-    if (__syncthreads_or(!ok)) {
-      // a staged plane never arrived: report and leave after the copies
-      // still in flight have had a bounded chance to land
-      if (tid == 0) {
-        atomicOr(flag, 2);
-        for (int j = 0; j < NB; ++j) mbar_wait_bounded(bar + j, 0u);
-      }
-      cp_async_wait<0>();
-      __syncthreads();
-      return;
+    const bool ok = mbar_wait_bounded(full + b, (unsigned)((k / NB) & 1));
+    const T* buf = reinterpret_cast<const T*>(smem + (size_t)b * S::plane);
+    C* slot = ring + (k % NR) * RH * RW;
+    // psi of this thread's two nodes of plane z0 - 1 + k
+    V cur[Q];
+    C f0[Q], f1[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      cur[a] = *reinterpret_cast<const V*>(buf + (a * TY + ty) * TX + 2 * lane);
+      Pair<P>::unpack(cur[a], f0[a], f1[a]);
+      const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
+      f0[a] += sh;
+      f1[a] += sh;
     }
-    psi_plane(b, k % 3);
-    __syncthreads();
-    if (k >= 2) collide_plane(P0 + k - 1, (k - 1) % NB, (k - 2) % 3, (k - 1) % 3, k % 3);
-    __syncthreads();
-    if (k + NB - 1 < np) issue(P0 + k + NB - 1, (k + NB - 1) % NB);
+    C p0, p1;
+    psi_math<C>(ph, rho_of<C>(f0), &p0, flag);
+    psi_math<C>(ph, rho_of<C>(f1), &p1, flag);
+    if constexpr (sizeof(C) == 4)
+      *reinterpret_cast<float2*>(slot + (ty + 1) * RW + 2 * lane + 2) = make_float2(p0, p1);
+    else
+      *reinterpret_cast<double2*>(slot + (ty + 1) * RW + 2 * lane + 2) = make_double2(p0, p1);
+    // psi of this thread's halo cells
+#pragma unroll
+    for (int j = 0; j < HPT; ++j) {
+      if (h_off[j] >= 0) {
+        C fv[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a)
+          fv[a] = Prec<P>::load_rw(buf + h_off[j] + a * h_str[j], a == 0 ? s0 : (a <= 6 ? s1 : s2));
+        psi_math<C>(ph, rho_of<C>(fv), slot + h_ring[j], flag);
+      }
+    }
+    // every psi of plane z0 - 1 + k is in the ring and buffer b is read out
+    if (__syncthreads_or(!ok)) break;
+    if (tid == 0 && k + NB < np)
+      issue_plane<P>(smem, maps, b, x0, y0, xl, xr, ym, yp, zwrap(z0 - 1 + k + NB), full + b);
+
+    if (k >= 2) {
+      // collide + stream the two nodes (x0 + 2 lane, y0 + ty) of plane z
+      const int z = zwrap(z0 + k - 2);
+      const int x = x0 + 2 * lane, y = y0 + ty;
+      const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x + 2 == g.nx ? 0 : x + 2;
+      const int yv[3] = {y == 0 ? g.ny - 1 : y - 1, y, y == g.ny - 1 ? 0 : y + 1};
+      const int zv[3] = {z == 0 ? g.nz - 1 : z - 1, z, z == g.nz - 1 ? 0 : z + 1};
+      C q[3][3][4];
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+          const C* row = ring + ((k - 1 + dz) % NR) * RH * RW + (ty + 1 + dy) * RW + 2 * lane + 2;
+          if constexpr (sizeof(C) == 4) {
+            const float2 v = *reinterpret_cast<const float2*>(row);
+            q[dy + 1][dz + 1][1] = v.x;
+            q[dy + 1][dz + 1][2] = v.y;
+          } else {
+            const double2 v = *reinterpret_cast<const double2*>(row);
+            q[dy + 1][dz + 1][1] = v.x;
+            q[dy + 1][dz + 1][2] = v.y;
+          }
+          if (dy == 0 || dz == 0) {
+            q[dy + 1][dz + 1][0] = row[-1];
+            q[dy + 1][dz + 1][3] = row[2];
+          } else {
+            q[dy + 1][dz + 1][0] = 0;
+            q[dy + 1][dz + 1][3] = 0;
+          }
+        }
+      C g0[Q], g1[Q], pn0[Q], pn1[Q];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        Pair<P>::unpack(prev[a], g0[a], g1[a]);
+        const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
+        g0[a] += sh;
+        g1[a] += sh;
+      }
+      pn0[0] = pn1[0] = 0;
+#pragma unroll
+      for (int a = 1; a < Q; ++a) {
+        pn0[a] = q[cy(a) + 1][cz(a) + 1][1 + cx(a)];
+        pn1[a] = q[cy(a) + 1][cz(a) + 1][2 + cx(a)];
+      }
+      C fs0[Q], fs1[Q];
+      collide_math<C>(ph, g0, q[1][1][1], pn0, fs0);
+      collide_math<C>(ph, g1, q[1][1][2], pn1, fs1);
+      const int i0 = x + g.nx * (y + g.ny * z);
+      const bool sr = Prec<P>::dev && ph.sr;
+      const unsigned seed0 = sr ? sr_seed(i0, fs0[0]) : 0u, seed1 = sr ? sr_seed(i0 + 1, fs1[0]) : 0u;
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
+        T* base = dst + (long long)a * N + g.nx * (yv[1 + cy(a)] + g.ny * zv[1 + cz(a)]);
+        if (cx(a) == 0) {
+          if (sr)
+            store_pair_sr<P>(base + x, fs0[a], fs1[a], sh, sr_bits(seed0, a), sr_bits(seed1, a));
+          else
+            store_pair<P>(base + x, fs0[a], fs1[a], sh);
+        } else {
+          store_pop<P>(ph, base + (cx(a) > 0 ? x + 1 : xm), fs0[a], sh, seed0, a);
+          store_pop<P>(ph, base + (cx(a) > 0 ? xp : x), fs1[a], sh, seed1, a);
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < Q; ++a) prev[a] = cur[a];
+  }
+  if (k < np) {
+    // a wait gave up: record it, and let the copies already issued land
+    // before the block's shared memory is released
+    if (tid == 0) {
+      atomicOr(flag, 2);
+      for (int j = k; j < k + NB && j < np; ++j) mbar_wait_bounded(full + j % NB, (unsigned)((j / NB) & 1));
+    }
   }
 }
 
@@ -305,14 +357,14 @@ CUtensorMapDataType tma_type(int precision) {
   }
 }
 
-// The 4-D view [19][nz][ny][nx] of a population array with box (32, rows, 1, 19).
-cudaError_t make_map(CUtensorMap* tm, int precision, const Geom& g, const void* base, int rows) {
+// The 4-D view [19][nz][ny][nx] of a population array with box (bx, by, 1, 19).
+cudaError_t make_map(CUtensorMap* tm, int precision, const Geom& g, const void* base, int bx, int by) {
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   const size_t e = elem_size(precision);
   const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)Q};
   const cuuint64_t strides[3] = {(cuuint64_t)g.nx * e, (cuuint64_t)g.nx * g.ny * e, (cuuint64_t)g.N * e};
-  const cuuint32_t box[4] = {(cuuint32_t)FX, (cuuint32_t)rows, 1u, (cuuint32_t)Q};
+  const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1u, (cuuint32_t)Q};
   const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
   const CUresult r = fn(tm, tma_type(precision), 4, const_cast<void*>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -320,21 +372,20 @@ cudaError_t make_map(CUtensorMap* tm, int precision, const Geom& g, const void* 
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-struct MapPair {
-  CUtensorMap interior, row;
-};
-
 // Tensor maps are pure host-side descriptors; they are cached per array.
-cudaError_t maps_for(int precision, const Geom& g, const void* base, MapPair* out) {
+cudaError_t maps_for(int precision, const Geom& g, const void* base, Maps* out) {
   static std::mutex mu;
-  static std::map<std::tuple<const void*, int, int, int, int>, MapPair> cache;
+  static std::map<std::tuple<const void*, int, int, int, int>, Maps> cache;
   const auto key = std::make_tuple(base, precision, g.nx, g.ny, g.nz);
   std::lock_guard<std::mutex> lock(mu);
   auto it = cache.find(key);
   if (it == cache.end()) {
-    MapPair m;
-    cudaError_t e = make_map(&m.interior, precision, g, base, FY);
-    if (e == cudaSuccess) e = make_map(&m.row, precision, g, base, 1);
+    const int cw = 16 / (int)elem_size(precision);
+    Maps m;
+    cudaError_t e = make_map(&m.interior, precision, g, base, TX, TY);
+    if (e == cudaSuccess) e = make_map(&m.row, precision, g, base, TX, 1);
+    if (e == cudaSuccess) e = make_map(&m.col, precision, g, base, cw, TY);
+    if (e == cudaSuccess) e = make_map(&m.cor, precision, g, base, cw, 1);
     if (e != cudaSuccess) return e;
     it = cache.emplace(key, m).first;
   }
@@ -342,36 +393,63 @@ cudaError_t maps_for(int precision, const Geom& g, const void* base, MapPair* ou
   return cudaSuccess;
 }
 
+// z planes per block.  Each block also loads the two planes around its run,
+// and a grid that leaves SMs idle in its last wave wastes their bandwidth;
+// take the run length with the least (waves x planes loaded per block).
+int choose_fz(const Geom& g, long long tiles, long long slots) {
+  int best = g.nz;
+  long long best_cost = -1;
+  for (int fz = 4; fz <= g.nz; ++fz) {
+    const long long chunks = (g.nz + fz - 1) / fz;
+    const long long waves = (tiles * chunks + slots - 1) / slots;
+    const long long cost = waves * (fz + 2);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = fz;
+    }
+  }
+  return best;
+}
+
 template <int P>
 cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, int* flag, cudaStream_t s) {
-  using T = typename Prec<P>::T;
   using S = FusedShape<P>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static int slots_per_sm = 0, sms = 0;
+  if (!slots_per_sm) {
     cudaError_t e = cudaFuncSetAttribute(fused_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::smem);
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&slots_per_sm, fused_kernel<P>, NT, S::smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    if (slots_per_sm < 1) return cudaErrorInvalidConfiguration;
   }
-  MapPair m;
+  Maps m;
   cudaError_t e = maps_for(P, g, src, &m);
   if (e != cudaSuccess) return e;
-  const int ntx = g.nx / FX, nty = g.ny / FY, nchunks = (g.nz + FZ - 1) / FZ;
-  const long long blocks = (long long)ntx * nty * nchunks;
-  fused_kernel<P><<<(unsigned)blocks, FT, S::smem, s>>>(m.interior, m.row, g, ph, (const T*)src, (T*)dst, flag,
-                                                        ntx, nchunks);
+  const int ntx = g.nx / TX, nty = g.ny / TY;
+  const long long tiles = (long long)ntx * nty;
+  const int fz = choose_fz(g, tiles, (long long)slots_per_sm * sms);
+  const int nchunks = (g.nz + fz - 1) / fz;
+  const long long blocks = tiles * nchunks;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  fused_kernel<P><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (typename Prec<P>::T*)dst, flag, ntx, nchunks,
+                                                        fz);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool fused_applicable(const Geom& g) { return g.nx % FX == 0 && g.ny % FY == 0 && g.nz >= 3; }
+bool fused_applicable(const Geom& g, int precision) {
+  return precision != LBM_F64 && g.nx % TX == 0 && g.ny % TY == 0 && g.nz >= 3;
+}
 
 cudaError_t launch_fused(int precision, const Geom& g, const Phys& ph, const void* src, void* dst, int* flag,
                          cudaStream_t s) {
-  if (!fused_applicable(g)) return cudaErrorInvalidValue;
+  if (!fused_applicable(g, precision)) return cudaErrorInvalidValue;
   switch (precision) {
-    case LBM_F64: return fused_t<LBM_F64>(g, ph, src, dst, flag, s);
     case LBM_F32: return fused_t<LBM_F32>(g, ph, src, dst, flag, s);
     case LBM_F16DEV: return fused_t<LBM_F16DEV>(g, ph, src, dst, flag, s);
     case LBM_BF16DEV: return fused_t<LBM_BF16DEV>(g, ph, src, dst, flag, s);

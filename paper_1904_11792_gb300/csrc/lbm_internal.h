@@ -40,9 +40,9 @@ cudaError_t launch_collide(int precision, int mode, int minb, bool vec, const Ge
                            cudaStream_t s);
 
 // ---- fused single-pass step (lbm_fused.cu) ----------------------------------
-// One kernel per A-B step (psi recomputed per tile in shared memory); needs
-// nx % 32 == 0 and ny % 8 == 0.
-bool fused_applicable(const Geom& g);
+// One kernel per A-B step (psi of each tile and its ring computed in shared
+// memory); 4- and 2-byte storage, nx % 64 == 0, ny % 4 == 0, nz >= 3.
+bool fused_applicable(const Geom& g, int precision);
 cudaError_t launch_fused(int precision, const Geom& g, const Phys& ph, const void* src, void* dst,
                          int* flag, cudaStream_t s);
 
@@ -70,9 +70,12 @@ size_t diag_scratch_doubles(const Geom& g);
 // Results: DIAG_OUT doubles, 0 mass, 1-3 momentum, 4 liquid volume (phi),
 // 5 liquid count, 6 min slice area (phi), 7 min slice count, 8 its x,
 // 9 max |j|/rho, 10 min rho, 11 max rho, 12 numeric ok (1/0).  A ring
-// record holds them plus, at DIAG_OUT, its sequence number.
+// record holds them plus, at DIAG_OUT, its sequence number and, from
+// DIAG_CCL, the droplet counts of a step that also ran the labelling
+// (components, components >= 8 nodes, largest, guard error; -1 if it did not).
 constexpr int DIAG_OUT = 13;
-constexpr int DIAG_STRIDE = 16;
+constexpr int DIAG_CCL = 14;
+constexpr int DIAG_STRIDE = 20;
 // psi (nullable): also write psi of every node and raise flag on a bad
 // density (the psi pass of a diagnostic step).  ring_count (nullable):
 // append the record to the ring at out instead of writing out[0..12].
@@ -87,6 +90,22 @@ cudaError_t launch_diagnostics(int precision, int layout, const Geom& g, const P
 cudaError_t launch_ccl(int precision, int layout, const Geom& g, const Phys& ph, const void* f,
                        double threshold, int* labels, int* sizes, long long* out3,
                        cudaStream_t s);
+
+// Appends the counts of the last launch_ccl (out4, device) to the newest
+// ring record (fields DIAG_CCL ..).
+cudaError_t launch_ccl_ring(const long long* out4, double* ring, const unsigned long long* ring_count,
+                            int ring_cap, cudaStream_t s);
+
+// Per-droplet statistics after launch_ccl on the same state: records of
+// DROP_REC doubles [root, nodes, sum phi, sum rho, cos/sin sums of the
+// angles 2 pi x/nx, 2 pi y/ny, 2 pi z/nz] for the first cap roots met, and
+// x-occupancy bit masks of (nx + 31)/32 words per record.  sizes is the CCL
+// sizes array (overwritten with record slots); nslot receives the number of
+// roots.
+constexpr int DROP_REC = 10;
+cudaError_t launch_droplets(int precision, int layout, const Geom& g, const Phys& ph, const void* f,
+                            double rho_l, double rho_v, const int* labels, int* sizes, double* rec,
+                            unsigned* xbits, unsigned* nslot, int cap, cudaStream_t s);
 
 }  // namespace lbm
 
@@ -115,6 +134,9 @@ struct lbm_ctx {
   double* d_scratch = nullptr;    // diagnostics partials
   size_t scratch_doubles = 0;
   int* d_labels = nullptr;        // CCL labels and sizes (2 N ints)
+  bool diag_ccl = false;          // label droplets at every in-loop diagnostic step
+  double* d_drop = nullptr;       // droplet records and x masks (lbm_droplets)
+  size_t drop_bytes = 0;
 
   // CUDA graphs of one chunk of steps, keyed by the A-B array they start on
   // (AA chunks always start on an even step)

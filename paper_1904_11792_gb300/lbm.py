@@ -34,7 +34,7 @@ EXPORTS = (
     "lbm_last_error", "lbm_strerror", "lbm_lattice", "lbm_set_stream", "lbm_set_option",
     "lbm_get_option", "lbm_init_ligament", "lbm_init_profile", "lbm_step", "lbm_diag_history",
     "lbm_sync",
-    "lbm_moments", "lbm_diagnostics", "lbm_get_populations", "lbm_set_populations",
+    "lbm_moments", "lbm_diagnostics", "lbm_droplets", "lbm_get_populations", "lbm_set_populations",
     "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_kernel_time",
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_set_stream",
     "lbm_batch_set_option", "lbm_batch_info", "lbm_batch_init", "lbm_batch_step",
@@ -76,6 +76,18 @@ class lbm_diag(ctypes.Structure):
         return d
 
 
+class lbm_droplet(ctypes.Structure):
+    _fields_ = [("first_node", ctypes.c_longlong), ("nodes", ctypes.c_longlong),
+                ("volume_w", ctypes.c_double), ("mass", ctypes.c_double),
+                ("centroid", ctypes.c_double * 3), ("resultant", ctypes.c_double * 3),
+                ("x_slices", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return dict(first_node=self.first_node, nodes=self.nodes, volume_w=self.volume_w,
+                    mass=self.mass, centroid=tuple(self.centroid), resultant=tuple(self.resultant),
+                    x_slices=self.x_slices)
+
+
 class lbm_instance(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("tau", ctypes.c_double), ("G", ctypes.c_double), ("R0", ctypes.c_double),
@@ -115,6 +127,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "lbm_diag_history": (I, [H, P, I, P]),
         "lbm_moments": (I, [H, P, P, P, P]),
         "lbm_diagnostics": (I, [H, P, I]),
+        "lbm_droplets": (I, [H, P, I, P]),
         "lbm_get_populations": (I, [H, P]),
         "lbm_set_populations": (I, [H, P]),
         "lbm_state_bytes": (I, [H, P]),
@@ -254,6 +267,14 @@ def lbm_diagnostics(h, want_ccl: bool = False) -> lbm_diag:
     d = lbm_diag()
     check(load().lbm_diagnostics(h, ctypes.byref(d), int(bool(want_ccl))))
     return d
+
+
+def lbm_droplets(h, max_droplets: int = 1 << 20) -> tuple:
+    """(count, [lbm_droplet, ...] largest first, at most max_droplets)."""
+    n = ctypes.c_int(0)
+    buf = (lbm_droplet * max(int(max_droplets), 1))()
+    check(load().lbm_droplets(h, buf, int(max_droplets), ctypes.byref(n)))
+    return n.value, [buf[k] for k in range(min(n.value, int(max_droplets)))]
 
 
 def lbm_get_populations(h, shape) -> np.ndarray:
@@ -461,6 +482,11 @@ class Lattice:
 
     def diagnostics(self, ccl=False) -> dict:
         return lbm_diagnostics(self.h, ccl).as_dict()
+
+    def droplets(self, max_droplets: int = 1 << 20) -> tuple:
+        """(count, list of droplet dicts, largest first)."""
+        n, d = lbm_droplets(self.h, max_droplets)
+        return n, [x.as_dict() for x in d]
 
     def save_state(self) -> np.ndarray:
         return lbm_save_state(self.h)
