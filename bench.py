@@ -6,9 +6,12 @@ Workload: the grid-convergence ligament, periodic 256 x 128 x 128 (4.19 M
 nodes), R0 = 32, lambda = 256, eps = 0.02, tau = 1, G = -6, psi =
 1 - exp(-rho), FP32 storage and arithmetic, A-B streaming; liquid and
 vapour densities from a flat-interface run on the GPU.  One benchmark step
-= 10 lattice time steps (psi pass + fused force/collide/stream each) plus
-the FP64 diagnostics of the state (mass, momentum, liquid volume, neck
-area), the diagnostic interval of this workload.  The populations (637 MB
+= 10 lattice time steps plus the FP64 diagnostics of the state (mass,
+momentum, liquid volume, neck area), the diagnostic interval of this
+workload: the diagnostic step runs the psi pass (with the diagnostics) and
+the force/collide/stream kernel, the other nine run as the single-pass fused
+step or as the two kernels, whichever the autotuner (run before the timed
+region) finds faster on this GPU.  The populations (637 MB
 for both arrays) exceed the 129 MB L2, so no cache flush is needed between
 steps.
 
@@ -45,6 +48,8 @@ K2_BYTES_PER_LU = {"f64": 19 * 8 * 2 + 8, "f32": 19 * 4 * 2 + 4, "f16dev": 19 * 
 # two-pass model of the whole step (psi pass reads 19 f and writes psi)
 STEP_BYTES_PER_LU = {"f64": 3 * 19 * 8 + 16, "f32": 3 * 19 * 4 + 8, "f16dev": 3 * 19 * 2 + 8,
                      "bf16dev": 3 * 19 * 2 + 8}
+# single-pass fused step: read 19 f and write 19 f (psi stays on chip)
+FUSED_BYTES_PER_LU = {"f32": 19 * 4 * 2, "f16dev": 19 * 2 * 2, "bf16dev": 19 * 2 * 2}
 
 
 def dist_env():
@@ -80,25 +85,29 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_digest() -> str:
-    """sha256 over the sources of the time-step kernels."""
+def kernel_digest(fused: bool = False) -> str:
+    """sha256 over the sources of the time-step kernels (two-kernel step, or
+    the single-pass fused step)."""
     h = hashlib.sha256()
-    for name in ("lbm_node.cuh", "lbm_step.cu", "lbm_device.cuh"):
+    names = ("lbm_node.cuh", "lbm_fused.cu", "lbm_device.cuh") if fused else (
+        "lbm_node.cuh", "lbm_step.cu", "lbm_device.cuh")
+    for name in names:
         with open(os.path.join(ROOT, "paper_1904_11792_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def ncu_traffic(precision: str, pattern: str):
-    """DRAM bytes per collide-stream launch from the committed ncu summary, if
-    it was taken on the current kernel source; else None."""
+def ncu_traffic(precision: str, pattern: str, fused: bool = False):
+    """DRAM bytes per launch of the dominant kernel (collide-stream, or the
+    fused step) from the committed ncu summary, if it was taken on the
+    current kernel source; else None."""
     p = os.path.join(ROOT, "profiles", "collide_stream_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    e = d.get("workloads", {}).get("%s/%s" % (precision, pattern))
-    if not e or e.get("kernel_source_sha256") != kernel_digest():
+    e = d.get("workloads", {}).get("%s/%s%s" % (precision, pattern, "/fused" if fused else ""))
+    if not e or e.get("kernel_source_sha256") != kernel_digest(fused):
         return None
     return float(e["dram_bytes_per_launch_full_size"])
 
@@ -186,7 +195,7 @@ def run_ours(args):
     from paper_1904_11792_gb300 import autotune
     patterns = ("ab", "aa") if args.pattern == "auto" else (args.pattern,)
     if args.no_tune:
-        choice = dict(pattern=patterns[-1], block=(128, 2, 1), occupancy=0)
+        choice = dict(pattern=patterns[-1], block=(128, 2, 1), occupancy=0, fused=int(args.fused))
     else:
         choice = autotune.tune_lattice(w.nx, w.ny, w.nz, precision=args.precision,
                                        patterns=patterns,
@@ -197,8 +206,7 @@ def run_ours(args):
     lat = L.Lattice(w.nx, w.ny, w.nz, w.tau, w.G, precision=args.precision, pattern=pattern,
                     rho_ref=rho_v if args.precision.endswith("dev") else 0.0)
     autotune.apply(lat, choice)
-    if args.fused:
-        lat.set_option("fused", 1)
+    fused = bool(lat.get_option("fused"))
     lat.init_ligament(w.R0, w.lam, w.eps, w.phase, rho_l, rho_v, w.width)
     # diagnostics inside the time loop: the psi pass of every 10th step also
     # reduces mass, momentum, liquid volume and the neck area (FP64)
@@ -229,6 +237,7 @@ def run_ours(args):
     ms = t0.elapsed_time(t1)
     n_psi, ms_psi = L.lbm_kernel_time(lat.h, 0)
     n_k2, ms_k2 = L.lbm_kernel_time(lat.h, 1)
+    n_fu, ms_fu = L.lbm_kernel_time(lat.h, 2)
     lat.set_option("kernel_timing", 0)
     lat.sync()
     hist = lat.diag_history()
@@ -240,8 +249,19 @@ def run_ours(args):
     e2e = None if args.no_extras else run_e2e(args, lat, L, torch, N)
     peak, peak_kind = peaks()
     k2_avg = ms_k2 / max(n_k2, 1)
-    achieved = K2_BYTES_PER_LU[args.precision] * N / (k2_avg * 1e-3) / 1e9
-    traffic = ncu_traffic(args.precision, pattern)
+    fu_avg = ms_fu / max(n_fu, 1)
+    # the dominant kernel: the fused step when it runs, else collide-stream
+    if fused:
+        kname, bpl, avg, launches = "fused_step", FUSED_BYTES_PER_LU[args.precision], fu_avg, n_fu
+        # 9 of every 10 steps fused, the diagnostic step two-kernel
+        step_model = ((LBM_PER_STEP - 1) * bpl + STEP_BYTES_PER_LU[args.precision]) / LBM_PER_STEP
+        launches_per_step = (LBM_PER_STEP - 1) + 4
+    else:
+        kname, bpl, avg, launches = "collide_stream", K2_BYTES_PER_LU[args.precision], k2_avg, n_k2
+        step_model = STEP_BYTES_PER_LU[args.precision]
+        launches_per_step = 2 * (LBM_PER_STEP - 1) + 4
+    achieved = bpl * N / (avg * 1e-3) / 1e9
+    traffic = ncu_traffic(args.precision, pattern, fused)
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
@@ -253,7 +273,7 @@ def run_ours(args):
             "workload": "ligament %dx%dx%d R0=%g lambda=%g eps=%g tau=%g G=%g, %s storage, %s "
                         "streaming" % (w.nx, w.ny, w.nz, w.R0, w.lam, w.eps, w.tau, w.G,
                                        args.precision, pattern.upper()),
-            "tuned": {"pattern": pattern, "block": choice["block"],
+            "tuned": {"pattern": pattern, "fused": fused, "block": choice["block"],
                       "occupancy": choice["occupancy"], "vector": True},
             "nodes": N, "lattice_steps_per_step": LBM_PER_STEP, "diagnostics_every": LBM_PER_STEP,
             "parallelism": "replicas" if world > 1 else "single GPU",
@@ -261,17 +281,18 @@ def run_ours(args):
                 (2 if pattern == "ab" else 1) * 19 * N
                 * (4 if args.precision == "f32" else 8 if args.precision == "f64" else 2) / 1e6),
             "rho_l": round(rho_l, 6), "rho_v": round(rho_v, 6),
-            "step_model_bytes_per_lu": STEP_BYTES_PER_LU[args.precision],
-            "hbm_frac_step_model": round(value / world * STEP_BYTES_PER_LU[args.precision] / peak, 4),
+            "step_model_bytes_per_lu": round(step_model, 1),
+            "hbm_frac_step_model": round(value / world * step_model / peak, 4),
         },
-        "roofline": {"bound": "hbm", "kernel": "collide_stream", "achieved": round(achieved, 1),
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "peak_source": peak_kind,
-                     "traffic": traffic, "bytes_per_lu": K2_BYTES_PER_LU[args.precision],
-                     "avg_launch_ms": round(k2_avg, 5), "launches": n_k2,
+                     "traffic": traffic, "bytes_per_lu": bpl,
+                     "avg_launch_ms": round(avg, 5), "launches": launches,
+                     "collide_stream_avg_ms": round(k2_avg, 5), "collide_stream_launches": n_k2,
                      "psi_pass_avg_ms": round(ms_psi / max(n_psi, 1), 5)},
         "e2e": e2e,
-        "gpu_launches": int(args.steps * (2 * LBM_PER_STEP + 1)),
+        "gpu_launches": int(args.steps * launches_per_step),
         "clocks": clocks,
         "diag_last": {"mass": d["mass"], "neck_radius": round(d["neck_radius"], 4),
                       "step": d["step"], "records_in_timed_region": len(hist)},
@@ -450,7 +471,8 @@ def main():
                     help="liquid density (with --rho-v: skip the flat-interface run)")
     ap.add_argument("--rho-v", type=float, default=None)
     ap.add_argument("--fused", action="store_true",
-                    help="single-pass fused step kernel on non-diagnostic A-B steps")
+                    help="with --no-tune: the single-pass fused step on non-diagnostic A-B steps "
+                         "(the autotuner otherwise chooses)")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (default launch configuration; profiling runs)")
     ap.add_argument("--no-extras", action="store_true",

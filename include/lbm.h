@@ -153,10 +153,12 @@ int lbm_set_stream(lbm_handle h, void *stream);
  * the default: 2 for the two-node kernel, 3 for the one-node kernel),
  * "vector" (0/1, default 1: when nx is even each thread updates two
  * neighbouring nodes with 2-element vector loads and stores; block_x then
- * counts node pairs), "fused" (0/1, default 0: A-B steps without in-loop
- * diagnostics run as one single-pass kernel that recomputes psi per tile in
- * shared memory, reading the populations once per step; applies when
- * nx % 32 == 0 and ny % 8 == 0; results equal the two-kernel step bitwise),
+ * counts node pairs), "fused" (0/1, default 1: A-B steps without in-loop
+ * diagnostics run as one single-pass kernel that computes psi per tile in
+ * shared memory, reading the populations once per step; applies to FP32,
+ * FP16-dev and BF16-dev storage when nx % 64 == 0 and ny % 4 == 0, other
+ * lattices take the two-kernel step; results equal the two-kernel step
+ * bitwise; lbm_get_option answers whether it applies),
  * "stochastic_rounding" (0/1, default 1 for LBM_F16DEV / LBM_BF16DEV: the
  * stored deviations are rounded up or down with probability given by the
  * discarded fraction, from a hash of the node index and its post-collision
@@ -164,7 +166,15 @@ int lbm_set_stream(lbm_handle h, void *stream);
  * round-to-nearest in uniform regions; deterministic), "diag_ccl" (0/1,
  * default 0: every in-loop diagnostic step also labels the liquid
  * components on the GPU, so the records of lbm_diag_history carry the
- * droplet counts; needs 8 N bytes of labels).  lbm_get_option also answers "step", "nx", "ny", "nz",
+ * droplet counts; needs 8 N bytes of labels), "collision" (0 = the paper's
+ * single-relaxation-time collision with the velocity shift of Eq. 6, the
+ * default; 1 = multiple-relaxation-time collision, the operator the
+ * paper's conclusions name as its next step: D3Q19 moments of d'Humieres et
+ * al. 2002, the Shan-Chen force of Eq. 5 entered by Guo's forcing with
+ * u = (j + F/2)/rho; shear moments relax at 1/tau, so nu = (tau - 1/2)/3;
+ * the fused step does not apply), "mrt_s_e", "mrt_s_eps", "mrt_s_q",
+ * "mrt_s_pi", "mrt_s_m" (its other rates, each in (0, 2); defaults 1.19,
+ * 1.4, 1.2, 1.4, 1.98).  lbm_get_option also answers "step", "nx", "ny", "nz",
  * "precision", "pattern". */
 int lbm_set_option(lbm_handle h, const char *key, double value);
 int lbm_get_option(lbm_handle h, const char *key, double *value);

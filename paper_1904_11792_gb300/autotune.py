@@ -2,8 +2,9 @@
 
 For a lattice size and storage precision it times, on the GPU, the streaming
 pattern (A-B or AA), the collide-stream block shape and the register budget
-variant (blocks per SM), picks the fastest whole step, and caches the choice in
-a JSON file keyed by device, size and precision.  For a batch it tunes the
+variant (blocks per SM) of the two-kernel step, and the single-pass fused step
+where it applies, picks the fastest whole step, and caches the choice in a
+JSON file keyed by device, size and precision.  For a batch it tunes the
 batched kernel's block shape.  All timing is CUDA events around real steps of
 the library (kernel_timing for per-kernel times).
 """
@@ -64,8 +65,8 @@ def _fits(block, nx):
 def tune_lattice(nx, ny, nz, precision="f32", patterns=("ab", "aa"), blocks=DEFAULT_BLOCKS,
                  occupancies=DEFAULT_OCC, tau=1.0, G=-6.0, steps=20, use_cache=True,
                  verbose=False) -> dict:
-    """Best (pattern, block, occupancy) for one lattice; returns a dict with the
-    choice and the measured per-step time and GLUPS."""
+    """Best (pattern, fused, block, occupancy) for one lattice; returns a dict
+    with the choice and the measured per-step time and GLUPS."""
     import torch
     key = _key("lattice", (nx, ny, nz), precision, ",".join(patterns))
     cache = _load_cache() if use_cache else {}
@@ -79,6 +80,23 @@ def tune_lattice(nx, ny, nz, precision="f32", patterns=("ab", "aa"), blocks=DEFA
         with L.Lattice(nx, ny, nz, tau, G, precision=precision, pattern=pattern,
                        rho_ref=rv if precision.endswith("dev") else 0.0) as lat:
             lat.init_ligament(min(ny, nz) / 4.0, float(nx), 0.02, 0.0, rl, rv, 2.0)
+            lat.set_option("fused", 1)
+            if lat.get_option("fused"):
+                lat.step(4)
+                torch.cuda.synchronize()
+                lat.set_option("kernel_timing", 1)
+                lat.step(steps)
+                n2, ms2 = L.lbm_kernel_time(lat.h, 2)
+                lat.set_option("kernel_timing", 0)
+                step_ms = ms2 / max(n2, 1)
+                t = dict(pattern=pattern, fused=1, block=[0, 0, 0], occupancy=0, step_ms=step_ms,
+                         glups=N / (step_ms * 1e-3) / 1e9)
+                trials.append(t)
+                if verbose:
+                    print(json.dumps(t))
+                if best is None or step_ms < best["step_ms"]:
+                    best = t
+            lat.set_option("fused", 0)
             for occ in occupancies:
                 for b in blocks:
                     if not _fits(b, nx):
@@ -96,7 +114,7 @@ def tune_lattice(nx, ny, nz, precision="f32", patterns=("ab", "aa"), blocks=DEFA
                     n1, ms1 = L.lbm_kernel_time(lat.h, 1)
                     lat.set_option("kernel_timing", 0)
                     step_ms = ms0 / max(n0, 1) + ms1 / max(n1, 1)
-                    t = dict(pattern=pattern, block=list(b), occupancy=occ, step_ms=step_ms,
+                    t = dict(pattern=pattern, fused=0, block=list(b), occupancy=occ, step_ms=step_ms,
                              glups=N / (step_ms * 1e-3) / 1e9)
                     trials.append(t)
                     if verbose:
@@ -112,8 +130,12 @@ def tune_lattice(nx, ny, nz, precision="f32", patterns=("ab", "aa"), blocks=DEFA
 
 
 def apply(lat: "L.Lattice", choice: dict) -> None:
-    """Applies a tuned block shape and occupancy to a lattice (the pattern is
-    fixed at creation: create the lattice with choice['pattern'])."""
+    """Applies a tuned choice to a lattice: the fused step, or the two-kernel
+    step with its block shape and occupancy (the pattern is fixed at
+    creation: create the lattice with choice['pattern'])."""
+    lat.set_option("fused", int(choice.get("fused", 0)))
+    if choice.get("fused"):
+        return
     for k, v in zip(("block_x", "block_y", "block_z"), (1, 1, 1)):
         lat.set_option(k, v)
     for k, v in zip(("block_x", "block_y", "block_z"), choice["block"]):

@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbm.so")
 
-SOURCES = ["lbm_step.cu", "lbm_fused.cu", "lbm_aux.cu", "lbm_api.cu", "lbm_batch.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_step.cu", "lbm_mrt.cu", "lbm_fused.cu", "lbm_aux.cu", "lbm_api.cu", "lbm_batch.cu",
+           "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

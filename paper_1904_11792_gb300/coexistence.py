@@ -32,14 +32,16 @@ def _slab(n: int, rho_l: float, rho_v: float) -> np.ndarray:
 
 def coexistence(G: float, tau: float, n: int = 64, tol: float = 1e-10, check: int = 1000,
                 max_steps: int = 400000, rho_l0: float | None = None, rho_v0: float | None = None,
-                tau_start: float | None = None, psi_form: int = L.LBM_PSI_EXP, rho0: float = 1.0):
+                tau_start: float | None = None, psi_form: int = L.LBM_PSI_EXP, rho0: float = 1.0,
+                options: dict | None = None):
     """Relax a flat slab at (G, tau); returns dict(rho_l, rho_v, steps, dmax,
     profile, d0, dd) with profile = rho along the outward normal of one
     interface, sampled at d0 + k dd.
 
     Below tau = 0.8 the slab is first relaxed at tau_start (default 1.0) and
     then continued at tau, since the sharp tanh start can drive the density
-    negative at small tau with strong attraction."""
+    negative at small tau with strong attraction.  options: lattice options
+    to set first (e.g. {"collision": 1} for the MRT collision)."""
     if rho_l0 is None:
         rho_l0 = 2.6 if G <= -5.8 else 2.1
     if rho_v0 is None:
@@ -49,6 +51,8 @@ def coexistence(G: float, tau: float, n: int = 64, tol: float = 1e-10, check: in
     lat = L.Lattice(n, 3, 3, tau_start, G, precision="f64", pattern="ab", psi_form=psi_form,
                     rho0=rho0)
     try:
+        for k, v in (options or {}).items():
+            lat.set_option(k, v)
         lat.set_populations(_slab(n, rho_l0, rho_v0))
         taus = [tau_start] if tau_start == tau else [tau_start, tau]
         steps = 0

@@ -141,7 +141,7 @@ int enqueue_step(lbm_ctx* h, cudaStream_t s, long long step, int cur, bool timed
   const int mode = aa ? ((step & 1) ? MODE_AA_ODD : MODE_AA_EVEN) : MODE_AB;
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   const bool diag_step = h->diag_interval > 0 && step % h->diag_interval == 0;
-  if (h->fused && !aa && !diag_step && fused_applicable(h->g, prec)) {
+  if (h->fused && !aa && !diag_step && h->ph.coll == COLL_SRT && fused_applicable(h->g, prec)) {
     // single pass: psi of each tile is recomputed from the staged populations
     if (timed) {
       e0 = take_event(h);
@@ -178,7 +178,10 @@ int enqueue_step(lbm_ctx* h, cudaStream_t s, long long step, int cur, bool timed
   // spills at <= 128 registers), 3 for the one-node kernel
   const bool vec = h->vec && (h->g.nx % 2 == 0);
   const int minb = h->minb ? h->minb : (vec ? 2 : 3);
-  CK(launch_collide(prec, mode, minb, vec, h->g, h->ph, src, dst, h->psi, h->block, s));
+  if (h->ph.coll == COLL_MRT)
+    CK(launch_collide_mrt(prec, mode, vec, h->g, h->ph, src, dst, h->psi, h->block, s));
+  else
+    CK(launch_collide(prec, mode, minb, vec, h->g, h->ph, src, dst, h->psi, h->block, s));
   if (timed) {
     CK(cudaEventRecord(e2, s));
     h->pending.push_back({0, e0, e1});
@@ -404,7 +407,7 @@ lbm_handle lbm_create_ex(const lbm_config* cfg) {
   h->g = Geom{cfg->nx, cfg->ny, cfg->nz, (long long)cfg->nx * cfg->ny * cfg->nz};
   // stochastic rounding is on by default for the reduced-precision forms
   h->ph = Phys{cfg->tau, cfg->G, cfg->rho0, cfg->rho_ref, cfg->psi_form,
-               cfg->precision >= LBM_F16DEV ? 1 : 0};
+               cfg->precision >= LBM_F16DEV ? 1 : 0, COLL_SRT, 1.19, 1.4, 1.2, 1.4, 1.98};
   h->block = (cfg->block_x && cfg->block_y && cfg->block_z)
                  ? dim3(cfg->block_x, cfg->block_y, cfg->block_z)
                  : default_block(h->g);
@@ -516,6 +519,18 @@ int lbm_set_option(lbm_handle h, const char* key, double v) {
   } else if (k == "stochastic_rounding") {
     h->ph.sr = v != 0.0 ? 1 : 0;
     drop_graphs(h);
+  } else if (k == "collision") {
+    if (v != 0.0 && v != 1.0) return fail(LBM_ERR_ARG, "collision must be 0 (SRT) or 1 (MRT)");
+    h->ph.coll = v != 0.0 ? COLL_MRT : COLL_SRT;
+    drop_graphs(h);
+  } else if (k == "mrt_s_e" || k == "mrt_s_eps" || k == "mrt_s_q" || k == "mrt_s_pi" || k == "mrt_s_m") {
+    if (!(v > 0.0 && v < 2.0)) return fail(LBM_ERR_ARG, "MRT relaxation rates must lie in (0, 2)");
+    if (k == "mrt_s_e") h->ph.s_e = v;
+    if (k == "mrt_s_eps") h->ph.s_eps = v;
+    if (k == "mrt_s_q") h->ph.s_q = v;
+    if (k == "mrt_s_pi") h->ph.s_pi = v;
+    if (k == "mrt_s_m") h->ph.s_m = v;
+    drop_graphs(h);
   } else if (k == "fused") {
     h->fused = v != 0.0;
     drop_graphs(h);
@@ -583,7 +598,14 @@ int lbm_get_option(lbm_handle h, const char* key, double* v) {
   else if (k == "occupancy") *v = h->minb ? h->minb : ((h->vec && h->g.nx % 2 == 0) ? 2 : 3);
   else if (k == "vector") *v = h->vec && (h->g.nx % 2 == 0);
   else if (k == "stochastic_rounding") *v = h->ph.sr;
-  else if (k == "fused") *v = h->fused && h->cfg.pattern == LBM_AB && fused_applicable(h->g, h->cfg.precision);
+  else if (k == "fused")
+    *v = h->fused && h->cfg.pattern == LBM_AB && h->ph.coll == COLL_SRT && fused_applicable(h->g, h->cfg.precision);
+  else if (k == "collision") *v = h->ph.coll;
+  else if (k == "mrt_s_e") *v = h->ph.s_e;
+  else if (k == "mrt_s_eps") *v = h->ph.s_eps;
+  else if (k == "mrt_s_q") *v = h->ph.s_q;
+  else if (k == "mrt_s_pi") *v = h->ph.s_pi;
+  else if (k == "mrt_s_m") *v = h->ph.s_m;
   else if (k == "kernel_timing") *v = h->kernel_timing;
   else if (k == "block_x") *v = h->block.x;
   else if (k == "block_y") *v = h->block.y;

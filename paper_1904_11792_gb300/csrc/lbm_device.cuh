@@ -145,8 +145,14 @@ struct Geom {
 struct Phys {
   double tau, G, rho0, rho_ref;
   int psi_form;
-  int sr;  // stochastic rounding of reduced-precision stores (deviation forms)
+  int sr;    // stochastic rounding of reduced-precision stores (deviation forms)
+  int coll;  // collision operator: COLL_SRT (the paper's) or COLL_MRT
+  // MRT relaxation rates of the energy, energy-square, heat-flux, the two
+  // fourth-order stress and the third-order moments (shear moments relax
+  // at 1/tau)
+  double s_e, s_eps, s_q, s_pi, s_m;
 };
+enum Collision { COLL_SRT = 0, COLL_MRT = 1 };
 
 // Neighbour index table of one node: x-1, x, x+1 and the 9 row offsets of
 // (y + dy, z + dz), all periodic.  idx(cxa, cya, cza) is the flat index of

@@ -6,7 +6,7 @@
 // lanes x two nodes per row, one warp per row) and a run of z planes, and
 // marches through the run:
 //
-//   iteration k, plane p = z0 - 1 + k (periodic):
+//   iteration k, plane p = z0 - 1 + k (periodic; odd runs march downwards):
 //     psi of plane p over the tile and its one-node ring  -> psi ring slot
 //     barrier
 //     collide + stream plane p - 1 (psi of planes p - 2 .. p now known)
@@ -155,13 +155,18 @@ __global__ void __launch_bounds__(NT, 3) fused_kernel(const __grid_constant__ Ma
   const int x0 = (xy % ntx) * TX, y0 = (xy / ntx) * TY;
   const int z0 = chunk * fz, z1 = min(z0 + fz, g.nz);
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
-  const int np = (z1 - z0) + 2;        // planes z0 - 1 .. z1; plane z0 - 1 + k in buffer k % NB
+  const int np = (z1 - z0) + 2;        // planes z0 - 1 .. z1, march index k in buffer k % NB
+  // Even runs march up (z0 - 1 first), odd runs down (z1 first), so the plane
+  // two neighbouring runs share is read by both near the same time (at the
+  // start of both, or at the end of both) and the second read hits L2.
+  const int dir = (chunk & 1) ? -1 : 1;
   const long long N = g.N;
   const int ym = y0 == 0 ? g.ny - 1 : y0 - 1, yp = y0 + TY == g.ny ? 0 : y0 + TY;
   const int xl = x0 == 0 ? g.nx - S::CW : x0 - S::CW, xr = x0 + TX == g.nx ? 0 : x0 + TX;
   const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
           s2 = shift_of<P>(7, ph.rho_ref);
   auto zwrap = [&](int p) { return p < 0 ? p + g.nz : (p >= g.nz ? p - g.nz : p); };
+  auto zplane = [&](int k) { return zwrap(dir > 0 ? z0 - 1 + k : z1 - k); };   // plane of march index k
 
   // this thread's halo cells: element offset in a plane buffer, stride
   // between directions, and ring position
@@ -211,7 +216,7 @@ __global__ void __launch_bounds__(NT, 3) fused_kernel(const __grid_constant__ Ma
   if (s_abort) return;
   if (tid == 0)
     for (int k = 0; k < NB && k < np; ++k)
-      issue_plane<P>(smem, maps, k, x0, y0, xl, xr, ym, yp, zwrap(z0 - 1 + k), full + k);
+      issue_plane<P>(smem, maps, k, x0, y0, xl, xr, ym, yp, zplane(k), full + k);
 
   V prev[Q];   // stored populations of this thread's two nodes, previous plane
   int k = 0;
@@ -220,7 +225,7 @@ __global__ void __launch_bounds__(NT, 3) fused_kernel(const __grid_constant__ Ma
     const bool ok = mbar_wait_bounded(full + b, (unsigned)((k / NB) & 1));
     const T* buf = reinterpret_cast<const T*>(smem + (size_t)b * S::plane);
     C* slot = ring + (k % NR) * RH * RW;
-    // psi of this thread's two nodes of plane z0 - 1 + k
+    // psi of this thread's two nodes of plane zplane(k)
     V cur[Q];
     C f0[Q], f1[Q];
 #pragma unroll
@@ -249,14 +254,15 @@ __global__ void __launch_bounds__(NT, 3) fused_kernel(const __grid_constant__ Ma
         psi_math<C>(ph, rho_of<C>(fv), slot + h_ring[j], flag);
       }
     }
-    // every psi of plane z0 - 1 + k is in the ring and buffer b is read out
+    // every psi of plane zplane(k) is in the ring and buffer b is read out
     if (__syncthreads_or(!ok)) break;
     if (tid == 0 && k + NB < np)
-      issue_plane<P>(smem, maps, b, x0, y0, xl, xr, ym, yp, zwrap(z0 - 1 + k + NB), full + b);
+      issue_plane<P>(smem, maps, b, x0, y0, xl, xr, ym, yp, zplane(k + NB), full + b);
 
     if (k >= 2) {
-      // collide + stream the two nodes (x0 + 2 lane, y0 + ty) of plane z
-      const int z = zwrap(z0 + k - 2);
+      // collide + stream the two nodes (x0 + 2 lane, y0 + ty) of plane z =
+      // zplane(k - 1); plane z + dz has march index k - 1 + dir dz
+      const int z = zplane(k - 1);
       const int x = x0 + 2 * lane, y = y0 + ty;
       const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x + 2 == g.nx ? 0 : x + 2;
       const int yv[3] = {y == 0 ? g.ny - 1 : y - 1, y, y == g.ny - 1 ? 0 : y + 1};
@@ -266,7 +272,7 @@ __global__ void __launch_bounds__(NT, 3) fused_kernel(const __grid_constant__ Ma
       for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
         for (int dz = -1; dz <= 1; ++dz) {
-          const C* row = ring + ((k - 1 + dz) % NR) * RH * RW + (ty + 1 + dy) * RW + 2 * lane + 2;
+          const C* row = ring + ((k - 1 + dir * dz) % NR) * RH * RW + (ty + 1 + dy) * RW + 2 * lane + 2;
           if constexpr (sizeof(C) == 4) {
             const float2 v = *reinterpret_cast<const float2*>(row);
             q[dy + 1][dz + 1][1] = v.x;

@@ -39,6 +39,11 @@ cudaError_t launch_collide(int precision, int mode, int minb, bool vec, const Ge
                            const Phys& ph, const void* src, void* dst, const void* psi, dim3 block,
                            cudaStream_t s);
 
+// force + collision + streaming with the MRT collision (lbm_mrt.cu); the
+// same modes and layouts as launch_collide
+cudaError_t launch_collide_mrt(int precision, int mode, bool vec, const Geom& g, const Phys& ph,
+                               const void* src, void* dst, const void* psi, dim3 block, cudaStream_t s);
+
 // ---- fused single-pass step (lbm_fused.cu) ----------------------------------
 // One kernel per A-B step (psi of each tile and its ring computed in shared
 // memory); 4- and 2-byte storage, nx % 64 == 0, ny % 4 == 0, nz >= 3.
@@ -146,7 +151,7 @@ struct lbm_ctx {
   dim3 block{0, 0, 0};
   int minb = 0;                   // collide kernel register budget variant (0 = auto)
   bool vec = true;                // two nodes per thread (when nx is even)
-  bool fused = false;             // single-pass fused step on non-diagnostic A-B steps
+  bool fused = true;              // single-pass fused step on non-diagnostic A-B steps (where it applies)
 
   // diagnostics inside the time loop: every diag_interval steps the psi
   // pass also reduces the diagnostics into a device ring of records

@@ -348,11 +348,21 @@ def test_step_before_init_is_a_state_error(L):
 def test_kernel_timing_counts_launches(L):
     with make(L, (64, 16, 16), 1.0, G6, "f32") as lat:
         lat.set_populations(lbm_inputs.random_populations(64, 16, 16, seed=1))
+        lat.set_option("fused", 0)
         lat.set_option("kernel_timing", 1)
         lat.step(6)
         n0, ms0 = L.lbm_kernel_time(lat.h, 0)
         n1, ms1 = L.lbm_kernel_time(lat.h, 1)
-    assert n0 == 6 and n1 == 6 and ms0 > 0 and ms1 > 0
+        assert n0 == 6 and n1 == 6 and ms0 > 0 and ms1 > 0
+        # the single-pass step (the default where it applies) is class 2;
+        # a diagnostic step still runs the two kernels
+        lat.set_option("fused", 1)
+        lat.set_option("diag_interval", 4)
+        lat.set_option("kernel_timing", 0)
+        lat.set_option("kernel_timing", 1)
+        lat.step(6)   # steps 6..11: 8 is a diagnostic step
+        n = [L.lbm_kernel_time(lat.h, k)[0] for k in range(3)]
+    assert n == [1, 1, 5]
 
 
 def test_gpu_coexistence_matches_oracle(L):
