@@ -158,7 +158,9 @@ int lbm_set_stream(lbm_handle h, void *stream);
  * shared memory, reading the populations once per step; applies to FP32,
  * FP16-dev and BF16-dev storage when nx % 64 == 0 and ny % 4 == 0, other
  * lattices take the two-kernel step; results equal the two-kernel step
- * bitwise; lbm_get_option answers whether it applies),
+ * bitwise; lbm_get_option answers whether it applies), "fused_fz" (z planes
+ * each block of the fused step marches through; 0 = chosen from the lattice
+ * size and the GPU, the default),
  * "stochastic_rounding" (0/1, default 1 for LBM_F16DEV / LBM_BF16DEV: the
  * stored deviations are rounded up or down with probability given by the
  * discarded fraction, from a hash of the node index and its post-collision

@@ -64,7 +64,7 @@ def _fits(block, nx):
 
 def tune_lattice(nx, ny, nz, precision="f32", patterns=("ab", "aa"), blocks=DEFAULT_BLOCKS,
                  occupancies=DEFAULT_OCC, tau=1.0, G=-6.0, steps=20, use_cache=True,
-                 verbose=False) -> dict:
+                 verbose=False, fused_runs=(8, 16, 32)) -> dict:
     """Best (pattern, fused, block, occupancy) for one lattice; returns a dict
     with the choice and the measured per-step time and GLUPS."""
     import torch
@@ -82,20 +82,23 @@ def tune_lattice(nx, ny, nz, precision="f32", patterns=("ab", "aa"), blocks=DEFA
             lat.init_ligament(min(ny, nz) / 4.0, float(nx), 0.02, 0.0, rl, rv, 2.0)
             lat.set_option("fused", 1)
             if lat.get_option("fused"):
-                lat.step(4)
-                torch.cuda.synchronize()
-                lat.set_option("kernel_timing", 1)
-                lat.step(steps)
-                n2, ms2 = L.lbm_kernel_time(lat.h, 2)
-                lat.set_option("kernel_timing", 0)
-                step_ms = ms2 / max(n2, 1)
-                t = dict(pattern=pattern, fused=1, block=[0, 0, 0], occupancy=0, step_ms=step_ms,
-                         glups=N / (step_ms * 1e-3) / 1e9)
-                trials.append(t)
-                if verbose:
-                    print(json.dumps(t))
-                if best is None or step_ms < best["step_ms"]:
-                    best = t
+                for fz in (0,) + tuple(z for z in fused_runs if z < nz):
+                    lat.set_option("fused_fz", fz)
+                    lat.step(4)
+                    torch.cuda.synchronize()
+                    lat.set_option("kernel_timing", 1)
+                    lat.step(steps)
+                    n2, ms2 = L.lbm_kernel_time(lat.h, 2)
+                    lat.set_option("kernel_timing", 0)
+                    step_ms = ms2 / max(n2, 1)
+                    t = dict(pattern=pattern, fused=1, fused_fz=fz, block=[0, 0, 0], occupancy=0,
+                             step_ms=step_ms, glups=N / (step_ms * 1e-3) / 1e9)
+                    trials.append(t)
+                    if verbose:
+                        print(json.dumps(t))
+                    if best is None or step_ms < best["step_ms"]:
+                        best = t
+                lat.set_option("fused_fz", 0)
             lat.set_option("fused", 0)
             for occ in occupancies:
                 for b in blocks:
@@ -135,6 +138,7 @@ def apply(lat: "L.Lattice", choice: dict) -> None:
     creation: create the lattice with choice['pattern'])."""
     lat.set_option("fused", int(choice.get("fused", 0)))
     if choice.get("fused"):
+        lat.set_option("fused_fz", int(choice.get("fused_fz", 0)))
         return
     for k, v in zip(("block_x", "block_y", "block_z"), (1, 1, 1)):
         lat.set_option(k, v)

@@ -141,17 +141,33 @@ int enqueue_step(lbm_ctx* h, cudaStream_t s, long long step, int cur, bool timed
   const int mode = aa ? ((step & 1) ? MODE_AA_ODD : MODE_AA_EVEN) : MODE_AB;
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   const bool diag_step = h->diag_interval > 0 && step % h->diag_interval == 0;
-  if (h->fused && !aa && !diag_step && h->ph.coll == COLL_SRT && fused_applicable(h->g, prec)) {
-    // single pass: psi of each tile is recomputed from the staged populations
+  const bool fused = h->fused && !aa && h->ph.coll == COLL_SRT && fused_applicable(h->g, prec);
+  // a diagnostic step runs fused too when the scratch holds its partials
+  const bool fused_diag =
+      fused && diag_step && h->d_scratch && fused_diag_scratch_doubles(h->g, prec, h->fused_fz) <= h->scratch_doubles;
+  if (fused && (!diag_step || fused_diag)) {
+    // single pass: psi of each tile is computed from the staged populations
     if (timed) {
       e0 = take_event(h);
       e1 = take_event(h);
       CK(cudaEventRecord(e0, s));
     }
-    CK(launch_fused(prec, h->g, h->ph, src, dst, h->d_flag, s));
+    if (diag_step) {
+      const FusedDiag fd{h->rho_l, h->rho_v, h->d_scratch, h->scratch_doubles, h->d_ring, h->d_ring_count,
+                         lbm_ctx::kRing};
+      CK(launch_fused(prec, h->g, h->ph, src, dst, h->d_flag, h->fused_fz, &fd, s));
+    } else {
+      CK(launch_fused(prec, h->g, h->ph, src, dst, h->d_flag, h->fused_fz, nullptr, s));
+    }
     if (timed) {
       CK(cudaEventRecord(e1, s));
       h->pending.push_back({2, e0, e1});
+    }
+    if (diag_step && h->diag_ccl) {
+      long long* d4 = (long long*)(h->d_small + 32);
+      CK(launch_ccl(prec, layout, h->g, h->ph, src, 0.5 * (h->rho_l + h->rho_v), h->d_labels,
+                    h->d_labels + h->g.N, d4, s));
+      CK(launch_ccl_ring(d4, h->d_ring, h->d_ring_count, lbm_ctx::kRing, s));
     }
     return LBM_OK;
   }
@@ -260,10 +276,19 @@ int capture_chunk(lbm_ctx* h, int phase) {
   return LBM_OK;
 }
 
+// Diagnostics partials: room for the two-kernel reduction and, where the
+// fused step applies, for the fused step's (which depends on its z runs).
 int ensure_scratch(lbm_ctx* h) {
-  if (h->d_scratch) return LBM_OK;
-  h->scratch_doubles = diag_scratch_doubles(h->g);
-  return dev_alloc((void**)&h->d_scratch, h->scratch_doubles * sizeof(double), "diagnostics scratch");
+  size_t need = diag_scratch_doubles(h->g);
+  if (h->fused && h->cfg.pattern == LBM_AB)
+    need = std::max(need, fused_diag_scratch_doubles(h->g, h->cfg.precision, h->fused_fz));
+  if (h->d_scratch && h->scratch_doubles >= need) return LBM_OK;
+  if (h->d_scratch) dev_free(h->d_scratch, h->scratch_doubles * sizeof(double));
+  h->d_scratch = nullptr;
+  h->scratch_doubles = 0;
+  int rc = dev_alloc((void**)&h->d_scratch, need * sizeof(double), "diagnostics scratch");
+  if (rc == LBM_OK) h->scratch_doubles = need;
+  return rc;
 }
 
 int ensure_labels(lbm_ctx* h) {
@@ -534,6 +559,19 @@ int lbm_set_option(lbm_handle h, const char* key, double v) {
   } else if (k == "fused") {
     h->fused = v != 0.0;
     drop_graphs(h);
+    if (h->diag_interval > 0) {
+      int rc = ensure_scratch(h);
+      if (rc) return rc;
+    }
+  } else if (k == "fused_fz") {
+    const long long z = (long long)v;
+    if (z < 0 || z > h->g.nz || (double)z != v) return fail(LBM_ERR_ARG, "fused_fz must be an integer in 0..nz");
+    h->fused_fz = (int)z;
+    drop_graphs(h);
+    if (h->diag_interval > 0) {
+      int rc = ensure_scratch(h);
+      if (rc) return rc;
+    }
   } else if (k == "vector") {
     h->vec = v != 0.0;
     drop_graphs(h);
@@ -600,6 +638,7 @@ int lbm_get_option(lbm_handle h, const char* key, double* v) {
   else if (k == "stochastic_rounding") *v = h->ph.sr;
   else if (k == "fused")
     *v = h->fused && h->cfg.pattern == LBM_AB && h->ph.coll == COLL_SRT && fused_applicable(h->g, h->cfg.precision);
+  else if (k == "fused_fz") *v = h->fused_fz;
   else if (k == "collision") *v = h->ph.coll;
   else if (k == "mrt_s_e") *v = h->ph.s_e;
   else if (k == "mrt_s_eps") *v = h->ph.s_eps;

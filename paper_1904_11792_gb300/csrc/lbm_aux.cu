@@ -151,7 +151,7 @@ __global__ void moments_kernel(Geom g, Phys ph, int layout, const typename Prec<
 // on a time step cost no extra pass over the populations.
 // ---------------------------------------------------------------------------
 constexpr int DX = 32, DY = 8;
-constexpr int NG = 12;  // global partial slots per block
+constexpr int NG = DIAG_NG;  // global partial slots per block
 // slots: 0 mass, 1-3 momentum, 4 volume_w, 5 count, 6 max_u, 7 rho_min,
 // 8 rho_max, 9 bad, 10-11 unused
 
@@ -679,6 +679,16 @@ cudaError_t droplets_t(int layout, const Geom& g, const Phys& ph, const void* f,
 }
 
 }  // namespace
+
+cudaError_t launch_diag_reduce(const Geom& g, int row_blocks, int nblocks, const double* slices,
+                               const double* blocks, double* slice_tot, double* out,
+                               unsigned long long* ring_count, int ring_cap, cudaStream_t s) {
+  diag_slices_kernel<<<(g.nx + 7) / 8, 256, 0, s>>>(g, row_blocks, slices, slice_tot);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  diag_final_kernel<<<1, FT, 0, s>>>(g, nblocks, slice_tot, blocks, out, ring_count, ring_cap);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ccl_ring(const long long* out4, double* ring, const unsigned long long* ring_count,
                             int ring_cap, cudaStream_t s) {

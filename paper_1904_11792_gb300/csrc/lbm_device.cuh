@@ -66,16 +66,30 @@ __device__ __forceinline__ unsigned sr_seed(long long node, double rest) {
 __device__ __forceinline__ unsigned sr_bits(unsigned s, int a) {
   return (s * (0x9E3779B1u + 0x6A09E668u * (unsigned)a)) >> 16;
 }
+// Stochastic rounding by the conversion instruction (cvt.rs, sm_100 and
+// later): two FP32 values to a packed FP16 / BF16 pair, each rounded up with
+// probability equal to the fraction its kept bits discard.  The first value
+// goes to the high half and draws its random bits from rbits[31:16], the
+// second to the low half with rbits[15:0] (checked on the GPU: unbiased, also
+// for FP16 subnormals).
+__device__ __forceinline__ unsigned cvt_rs_f16x2(float hi, float lo, unsigned rbits) {
+  unsigned d;
+  asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+  return d;
+}
+__device__ __forceinline__ unsigned cvt_rs_bf16x2(float hi, float lo, unsigned rbits) {
+  unsigned d;
+  asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+  return d;
+}
+// One value with 16 random bits r16: the low half of a pair conversion, so a
+// value rounds the same alone or as the low or high half of a pair given the
+// same bits.
 __device__ __forceinline__ __half half_sr(float x, unsigned r16) {
-  // FP16 normal range: add 13 random bits below the kept mantissa, truncate
-  if (fabsf(x) >= 6.103515625e-05f && fabsf(x) < 65504.0f)
-    return __float2half_rz(__uint_as_float(__float_as_uint(x) + (r16 & 0x1FFFu)));
-  return __float2half_rn(x);  // subnormal results (and overflow): nearest
+  return __ushort_as_half((unsigned short)(cvt_rs_f16x2(0.0f, x, r16 & 0xFFFFu) & 0xFFFFu));
 }
 __device__ __forceinline__ __nv_bfloat16 bf16_sr(float x, unsigned r16) {
-  const unsigned b = __float_as_uint(x);
-  if ((b & 0x7f800000u) == 0x7f800000u) return __float2bfloat16_rn(x);  // inf / nan
-  return __ushort_as_bfloat16((unsigned short)((b + r16) >> 16));
+  return __ushort_as_bfloat16((unsigned short)(cvt_rs_bf16x2(0.0f, x, r16 & 0xFFFFu) & 0xFFFFu));
 }
 
 // Storage traits.  T = stored type, C = compute type.  The *DEV forms store

@@ -32,6 +32,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -138,10 +139,30 @@ __device__ __forceinline__ void issue_plane(unsigned char* smem, const Maps& m, 
   tma_load_4d(base + S::off_cor + 3 * S::cor_stride, &m.cor, xr, yp, zz, bar);
 }
 
-template <int P>
-__global__ void __launch_bounds__(NT, 3) fused_kernel(const __grid_constant__ Maps maps, Geom g, Phys ph,
-                                                      typename Prec<P>::T* dst, int* flag, int ntx, int nchunks,
-                                                      int fz) {
+// Diagnostics of the step's starting state, reduced in the same pass (DIAG):
+// every thread sums, in the compute precision, the nodes of the planes its
+// block owns (the run z0 .. z1 - 1, not the two halo planes), and the block
+// writes FP64 partials in the layout the diagnostics reduction reads: slice
+// sums [row block][x][2] with one row block per (tile row, z run), and block
+// totals [block][DIAG_NG].
+struct DiagOut {
+  double rho_l, rho_v;
+  double* slices;
+  double* blocks;
+};
+
+// Blocks per SM the register budget must allow: 3 for 4-byte storage (its
+// 73 KB of shared memory allow no more), 4 for 2-byte storage; 2 for the
+// diagnostic variant, which runs once per diagnostic interval.
+template <int P, bool DIAG>
+constexpr int fused_minb() {
+  return DIAG ? 2 : (Prec<P>::dev ? 4 : 3);
+}
+
+template <int P, bool DIAG>
+__global__ void __launch_bounds__(NT, fused_minb<P, DIAG>())
+    fused_kernel(const __grid_constant__ Maps maps, Geom g, Phys ph, typename Prec<P>::T* dst, int* flag, int ntx,
+                 int nchunks, int fz, DiagOut dg) {
   using T = typename Prec<P>::T;
   using C = typename Prec<P>::C;
   using V = typename Pair<P>::V;
@@ -219,6 +240,13 @@ __global__ void __launch_bounds__(NT, 3) fused_kernel(const __grid_constant__ Ma
       issue_plane<P>(smem, maps, k, x0, y0, xl, xr, ym, yp, zplane(k), full + k);
 
   V prev[Q];   // stored populations of this thread's two nodes, previous plane
+  // diagnostics sums (DIAG): block totals and the two x columns of the thread
+  C d_mass = 0, d_jx = 0, d_jy = 0, d_jz = 0, d_vol = 0, d_umax = 0;
+  C d_rmin = (C)3.0e38, d_rmax = (C)-3.0e38;
+  C col_w[2] = {0, 0}, col_n[2] = {0, 0};
+  bool d_bad = false;
+  const C d_thr = (C)(0.5 * (dg.rho_l + dg.rho_v)), d_inv = (C)(1.0 / (dg.rho_l - dg.rho_v)),
+          d_rv = (C)dg.rho_v;
   int k = 0;
   for (; k < np; ++k) {
     const int b = k % NB;
@@ -237,8 +265,39 @@ __global__ void __launch_bounds__(NT, 3) fused_kernel(const __grid_constant__ Ma
       f1[a] += sh;
     }
     C p0, p1;
-    psi_math<C>(ph, rho_of<C>(f0), &p0, flag);
-    psi_math<C>(ph, rho_of<C>(f1), &p1, flag);
+    const C r0 = rho_of<C>(f0), r1 = rho_of<C>(f1);
+    psi_math<C>(ph, r0, &p0, flag);
+    psi_math<C>(ph, r1, &p1, flag);
+    if constexpr (DIAG) {
+      if (k >= 1 && k <= np - 2) {
+#pragma unroll
+        for (int n = 0; n < 2; ++n) {
+          const C* fv = n ? f1 : f0;
+          const C rho = n ? r1 : r0;
+          C jx = 0, jy = 0, jz = 0;
+#pragma unroll
+          for (int a = 0; a < Q; ++a) {
+            if (cx(a)) jx += cx(a) > 0 ? fv[a] : -fv[a];
+            if (cy(a)) jy += cy(a) > 0 ? fv[a] : -fv[a];
+            if (cz(a)) jz += cz(a) > 0 ? fv[a] : -fv[a];
+          }
+          d_mass += rho;
+          d_jx += jx;
+          d_jy += jy;
+          d_jz += jz;
+          C phi = (rho - d_rv) * d_inv;
+          phi = phi < (C)0 ? (C)0 : (phi > (C)1 ? (C)1 : phi);
+          d_vol += phi;
+          col_w[n] += phi;
+          col_n[n] += rho > d_thr ? (C)1 : (C)0;
+          const C um = sqrt(jx * jx + jy * jy + jz * jz) / rho;
+          d_umax = um > d_umax ? um : d_umax;
+          d_rmin = rho < d_rmin ? rho : d_rmin;
+          d_rmax = rho > d_rmax ? rho : d_rmax;
+          d_bad |= !(rho > (C)0) || !(rho <= (C)3.0e38);
+        }
+      }
+    }
     if constexpr (sizeof(C) == 4)
       *reinterpret_cast<float2*>(slot + (ty + 1) * RW + 2 * lane + 2) = make_float2(p0, p1);
     else
@@ -336,6 +395,75 @@ __global__ void __launch_bounds__(NT, 3) fused_kernel(const __grid_constant__ Ma
       for (int j = k; j < k + NB && j < np; ++j) mbar_wait_bounded(full + j % NB, (unsigned)((j / NB) & 1));
     }
   }
+  if constexpr (DIAG) {
+    // the psi ring is free now: it holds the FP64 reduction (TY x 64 x 2
+    // slice values, DIAG_NG x TY warp totals)
+    __syncthreads();
+    double* sh_col = reinterpret_cast<double*>(ring);
+    double* sh_w = sh_col + 2 * TY * TX;
+#pragma unroll
+    for (int n = 0; n < 2; ++n) {
+      sh_col[(ty * TX + 2 * lane + n) * 2 + 0] = (double)col_w[n];
+      sh_col[(ty * TX + 2 * lane + n) * 2 + 1] = (double)col_n[n];
+    }
+    // warp totals: a fixed shuffle tree in the compute precision
+    C v[5] = {d_mass, d_jx, d_jy, d_jz, d_vol};
+    float c_f = 0.0f;
+#pragma unroll
+    for (int n = 0; n < 2; ++n) c_f += (float)col_n[n];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+      c_f += __shfl_down_sync(0xffffffffu, c_f, o);
+      const C um = __shfl_down_sync(0xffffffffu, d_umax, o);
+      const C mn = __shfl_down_sync(0xffffffffu, d_rmin, o);
+      const C mx = __shfl_down_sync(0xffffffffu, d_rmax, o);
+      d_umax = um > d_umax ? um : d_umax;
+      d_rmin = mn < d_rmin ? mn : d_rmin;
+      d_rmax = mx > d_rmax ? mx : d_rmax;
+    }
+    const int anybad = __any_sync(0xffffffffu, d_bad);
+    if (lane == 0) {
+      sh_w[0 * TY + ty] = (double)v[0];
+      sh_w[1 * TY + ty] = (double)v[1];
+      sh_w[2 * TY + ty] = (double)v[2];
+      sh_w[3 * TY + ty] = (double)v[3];
+      sh_w[4 * TY + ty] = (double)v[4];
+      sh_w[5 * TY + ty] = (double)c_f;
+      sh_w[6 * TY + ty] = (double)d_umax;
+      sh_w[7 * TY + ty] = (double)d_rmin;
+      sh_w[8 * TY + ty] = (double)d_rmax;
+      sh_w[9 * TY + ty] = anybad ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const long long rb = (long long)(xy / ntx) * nchunks + chunk;
+    if (tid < TX) {
+      double a = 0.0, c = 0.0;
+      for (int r = 0; r < TY; ++r) {
+        a += sh_col[(r * TX + tid) * 2 + 0];
+        c += sh_col[(r * TX + tid) * 2 + 1];
+      }
+      dg.slices[(rb * g.nx + x0 + tid) * 2 + 0] = a;
+      dg.slices[(rb * g.nx + x0 + tid) * 2 + 1] = c;
+    } else if (tid < TX + DIAG_NG) {
+      const int i = tid - TX;
+      double r;
+      if (i < 6) {
+        r = 0.0;
+        for (int w = 0; w < TY; ++w) r += sh_w[i * TY + w];
+      } else if (i == 7) {
+        r = 1e300;
+        for (int w = 0; w < TY; ++w) r = fmin(r, sh_w[i * TY + w]);
+      } else if (i < 10) {
+        r = -1e300;
+        for (int w = 0; w < TY; ++w) r = fmax(r, sh_w[i * TY + w]);
+      } else {
+        r = 0.0;
+      }
+      dg.blocks[(long long)blockIdx.x * DIAG_NG + i] = r;
+    }
+  }
 }
 
 // ---- tensor maps ------------------------------------------------------------
@@ -400,16 +528,20 @@ cudaError_t maps_for(int precision, const Geom& g, const void* base, Maps* out) 
 }
 
 // z planes per block.  Each block also loads the two planes around its run,
-// and a grid that leaves SMs idle in its last wave wastes their bandwidth;
-// take the run length with the least (waves x planes loaded per block).
+// and a grid that leaves SMs idle in its last wave wastes their bandwidth:
+// the cost of a run length is waves x planes loaded per block.  Long runs
+// also let neighbouring tiles drift apart in z, so the halo rows one tile
+// reads are no longer in L2 from its neighbour's read of the same plane
+// (measured on GB300: 1024x512x512 takes 9.6 ms per step with 16-plane runs,
+// 10.5 ms with 256-plane runs); the factor (1 + fz/256) charges for that.
 int choose_fz(const Geom& g, long long tiles, long long slots) {
   int best = g.nz;
-  long long best_cost = -1;
+  double best_cost = -1.0;
   for (int fz = 4; fz <= g.nz; ++fz) {
     const long long chunks = (g.nz + fz - 1) / fz;
     const long long waves = (tiles * chunks + slots - 1) / slots;
-    const long long cost = waves * (fz + 2);
-    if (best_cost < 0 || cost < best_cost) {
+    const double cost = (double)waves * (fz + 2) * (1.0 + fz / 256.0);
+    if (best_cost < 0.0 || cost < best_cost) {
       best_cost = cost;
       best = fz;
     }
@@ -417,33 +549,72 @@ int choose_fz(const Geom& g, long long tiles, long long slots) {
   return best;
 }
 
+// Grid of the fused step: z run length, runs per tile column, blocks.  The
+// first call per storage type sets the kernels' shared-memory limit and
+// reads the occupancy of the step kernel.
 template <int P>
-cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, int* flag, cudaStream_t s) {
+cudaError_t fused_grid(const Geom& g, int fz_req, int* fz, int* nchunks, long long* blocks) {
   using S = FusedShape<P>;
   static int slots_per_sm = 0, sms = 0;
   if (!slots_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(fused_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(fused_kernel<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fused_kernel<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&slots_per_sm, fused_kernel<P>, NT, S::smem);
+    int slots = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&slots, fused_kernel<P, false>, NT, S::smem);
     if (e != cudaSuccess) return e;
-    if (slots_per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (slots < 1) return cudaErrorInvalidConfiguration;
+    slots_per_sm = slots;
   }
-  Maps m;
-  cudaError_t e = maps_for(P, g, src, &m);
+  const long long tiles = (long long)(g.nx / TX) * (g.ny / TY);
+  *fz = fz_req > 0 ? std::min(fz_req, g.nz) : choose_fz(g, tiles, (long long)slots_per_sm * sms);
+  *nchunks = (g.nz + *fz - 1) / *fz;
+  *blocks = tiles * *nchunks;
+  return *blocks > 0x7fffffffLL ? cudaErrorInvalidConfiguration : cudaSuccess;
+}
+
+template <int P>
+cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, int* flag, int fz_req,
+                    const FusedDiag* diag, cudaStream_t s) {
+  using S = FusedShape<P>;
+  int fz = 0, nchunks = 0;
+  long long blocks = 0;
+  cudaError_t e = fused_grid<P>(g, fz_req, &fz, &nchunks, &blocks);
   if (e != cudaSuccess) return e;
-  const int ntx = g.nx / TX, nty = g.ny / TY;
-  const long long tiles = (long long)ntx * nty;
-  const int fz = choose_fz(g, tiles, (long long)slots_per_sm * sms);
-  const int nchunks = (g.nz + fz - 1) / fz;
-  const long long blocks = tiles * nchunks;
-  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  fused_kernel<P><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (typename Prec<P>::T*)dst, flag, ntx, nchunks,
-                                                        fz);
-  return cudaGetLastError();
+  Maps m;
+  e = maps_for(P, g, src, &m);
+  if (e != cudaSuccess) return e;
+  const int ntx = g.nx / TX;
+  using T = typename Prec<P>::T;
+  if (!diag) {
+    fused_kernel<P, false><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks, fz,
+                                                                 DiagOut{0.0, 0.0, nullptr, nullptr});
+    return cudaGetLastError();
+  }
+  const long long row_blocks = (long long)(g.ny / TY) * nchunks;
+  const size_t need = (size_t)row_blocks * g.nx * 2 + (size_t)blocks * DIAG_NG + (size_t)g.nx * 2;
+  if (need > diag->scratch_doubles) return cudaErrorInvalidValue;
+  double* slices = diag->scratch;
+  double* bl = slices + (size_t)row_blocks * g.nx * 2;
+  double* slice_tot = bl + (size_t)blocks * DIAG_NG;
+  fused_kernel<P, true><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks, fz,
+                                                              DiagOut{diag->rho_l, diag->rho_v, slices, bl});
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_diag_reduce(g, (int)row_blocks, (int)blocks, slices, bl, slice_tot, diag->out, diag->ring_count,
+                            diag->ring_cap, s);
+}
+
+template <int P>
+size_t fused_scratch_t(const Geom& g, int fz_req) {
+  int fz = 0, nchunks = 0;
+  long long blocks = 0;
+  if (fused_grid<P>(g, fz_req, &fz, &nchunks, &blocks) != cudaSuccess) return 0;
+  return (size_t)(g.ny / TY) * nchunks * g.nx * 2 + (size_t)blocks * DIAG_NG + (size_t)g.nx * 2;
 }
 
 }  // namespace
@@ -453,14 +624,24 @@ bool fused_applicable(const Geom& g, int precision) {
 }
 
 cudaError_t launch_fused(int precision, const Geom& g, const Phys& ph, const void* src, void* dst, int* flag,
-                         cudaStream_t s) {
+                         int fz, const FusedDiag* diag, cudaStream_t s) {
   if (!fused_applicable(g, precision)) return cudaErrorInvalidValue;
   switch (precision) {
-    case LBM_F32: return fused_t<LBM_F32>(g, ph, src, dst, flag, s);
-    case LBM_F16DEV: return fused_t<LBM_F16DEV>(g, ph, src, dst, flag, s);
-    case LBM_BF16DEV: return fused_t<LBM_BF16DEV>(g, ph, src, dst, flag, s);
+    case LBM_F32: return fused_t<LBM_F32>(g, ph, src, dst, flag, fz, diag, s);
+    case LBM_F16DEV: return fused_t<LBM_F16DEV>(g, ph, src, dst, flag, fz, diag, s);
+    case LBM_BF16DEV: return fused_t<LBM_BF16DEV>(g, ph, src, dst, flag, fz, diag, s);
   }
   return cudaErrorInvalidValue;
+}
+
+size_t fused_diag_scratch_doubles(const Geom& g, int precision, int fz) {
+  if (!fused_applicable(g, precision)) return 0;
+  switch (precision) {
+    case LBM_F32: return fused_scratch_t<LBM_F32>(g, fz);
+    case LBM_F16DEV: return fused_scratch_t<LBM_F16DEV>(g, fz);
+    case LBM_BF16DEV: return fused_scratch_t<LBM_BF16DEV>(g, fz);
+  }
+  return 0;
 }
 
 }  // namespace lbm

@@ -48,8 +48,21 @@ cudaError_t launch_collide_mrt(int precision, int mode, bool vec, const Geom& g,
 // One kernel per A-B step (psi of each tile and its ring computed in shared
 // memory); 4- and 2-byte storage, nx % 64 == 0, ny % 4 == 0, nz >= 3.
 bool fused_applicable(const Geom& g, int precision);
+// fz: z planes per block (0: chosen from the lattice and the GPU).  diag
+// (nullable): also reduce the diagnostics of the starting state in the same
+// pass and append the record to the ring (or write out[0..DIAG_OUT)); the
+// scratch must hold fused_diag_scratch_doubles(g, precision, fz) doubles.
+struct FusedDiag {
+  double rho_l, rho_v;
+  double* scratch;
+  size_t scratch_doubles;
+  double* out;
+  unsigned long long* ring_count;
+  int ring_cap;
+};
 cudaError_t launch_fused(int precision, const Geom& g, const Phys& ph, const void* src, void* dst,
-                         int* flag, cudaStream_t s);
+                         int* flag, int fz, const FusedDiag* diag, cudaStream_t s);
+size_t fused_diag_scratch_doubles(const Geom& g, int precision, int fz);
 
 // ---- auxiliary kernels (lbm_aux.cu) ---------------------------------------
 struct InitSpec {
@@ -79,6 +92,7 @@ size_t diag_scratch_doubles(const Geom& g);
 // DIAG_CCL, the droplet counts of a step that also ran the labelling
 // (components, components >= 8 nodes, largest, guard error; -1 if it did not).
 constexpr int DIAG_OUT = 13;
+constexpr int DIAG_NG = 12;   // partial slots per block of the diagnostics reduction
 constexpr int DIAG_CCL = 14;
 constexpr int DIAG_STRIDE = 20;
 // psi (nullable): also write psi of every node and raise flag on a bad
@@ -87,6 +101,13 @@ constexpr int DIAG_STRIDE = 20;
 cudaError_t launch_diagnostics(int precision, int layout, const Geom& g, const Phys& ph,
                                const void* f, double rho_l, double rho_v, double* scratch,
                                double* out, void* psi, int* flag,
+                               unsigned long long* ring_count, int ring_cap, cudaStream_t s);
+
+// Second and third stage of the diagnostics reduction from partials
+// slices[row_blocks][nx][2] and blocks[nblocks][DIAG_NG] (slice_tot: 2 nx
+// doubles of scratch); arguments after slice_tot as launch_diagnostics.
+cudaError_t launch_diag_reduce(const Geom& g, int row_blocks, int nblocks, const double* slices,
+                               const double* blocks, double* slice_tot, double* out,
                                unsigned long long* ring_count, int ring_cap, cudaStream_t s);
 
 // Connected components of the liquid mask.  labels: N ints; sizes: N ints;
@@ -152,6 +173,7 @@ struct lbm_ctx {
   int minb = 0;                   // collide kernel register budget variant (0 = auto)
   bool vec = true;                // two nodes per thread (when nx is even)
   bool fused = true;              // single-pass fused step on non-diagnostic A-B steps (where it applies)
+  int fused_fz = 0;               // z planes per block of the fused step (0 = automatic)
 
   // diagnostics inside the time loop: every diag_interval steps the psi
   // pass also reduces the diagnostics into a device ring of records

@@ -1,0 +1,165 @@
+// Multiple-relaxation-time collision arithmetic of one node (used by the
+// collide-stream bodies of lbm_node.cuh when the lattice selects it).
+#pragma once
+
+#include <utility>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Multiple-relaxation-time collision (the operator the conclusions name as
+// the next step; not specified in the paper).  D3Q19 moments of d'Humieres,
+// Ginzburg, Krafczyk, Lallemand and Luo (2002), rows as polynomials of the
+// velocity c, and the forcing of Guo, Zheng and Shi (2002) in moment space:
+//   m* = m - S (m - m_eq(rho, u)) + (I - S/2) M F_guo,  u = (j + F/2)/rho,
+//   f* = M^-1 m* = M^T diag(1/|row|^2) m*.
+// m_eq and M F_guo are the moments of Eq. 2's equilibrium and of Guo's
+// forcing populations, in closed form.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int mrt_coef(int k, int a) {
+  const int x = cx(a), y = cy(a), z = cz(a), c2 = x * x + y * y + z * z;
+  switch (k) {
+    case 0: return 1;
+    case 1: return 19 * c2 - 30;
+    case 2: return (21 * c2 * c2 - 53 * c2 + 24) / 2;
+    case 3: return x;
+    case 4: return (5 * c2 - 9) * x;
+    case 5: return y;
+    case 6: return (5 * c2 - 9) * y;
+    case 7: return z;
+    case 8: return (5 * c2 - 9) * z;
+    case 9: return 3 * x * x - c2;
+    case 10: return (3 * c2 - 5) * (3 * x * x - c2);
+    case 11: return y * y - z * z;
+    case 12: return (3 * c2 - 5) * (y * y - z * z);
+    case 13: return x * y;
+    case 14: return y * z;
+    case 15: return x * z;
+    case 16: return (y * y - z * z) * x;
+    case 17: return (z * z - x * x) * y;
+    default: return (x * x - y * y) * z;
+  }
+}
+__host__ __device__ constexpr int mrt_norm(int k) {
+  int n = 0;
+  for (int a = 0; a < Q; ++a) n += mrt_coef(k, a) * mrt_coef(k, a);
+  return n;
+}
+
+// v (+)= c * x with c a compile-time integer (0, +-1 and other values).
+template <int Cf, typename C>
+__device__ __forceinline__ void mrt_fma(C& v, C x) {
+  if constexpr (Cf == 1) v += x;
+  else if constexpr (Cf == -1) v -= x;
+  else if constexpr (Cf != 0) v += (C)Cf * x;
+}
+// m[K] = sum_a M[K][a] f[a] and f[A] = sum_k M[k][A] w[k], expanded at compile
+// time so that only the non-zero integer coefficients cost instructions.
+template <typename C, int K, int... A>
+__device__ __forceinline__ C mrt_row(const C* f, std::integer_sequence<int, A...>) {
+  C v = 0;
+  (mrt_fma<mrt_coef(K, A)>(v, f[A]), ...);
+  return v;
+}
+template <typename C, int A, int... K>
+__device__ __forceinline__ C mrt_col(const C* w, std::integer_sequence<int, K...>) {
+  C v = 0;
+  (mrt_fma<mrt_coef(K, A)>(v, w[K]), ...);
+  return v;
+}
+template <typename C, int... K>
+__device__ __forceinline__ void mrt_forward(const C* f, C* m, std::integer_sequence<int, K...>) {
+  ((m[K] = mrt_row<C, K>(f, std::make_integer_sequence<int, Q>{})), ...);
+}
+template <typename C, int... K>
+__device__ __forceinline__ void mrt_scale(C* m, std::integer_sequence<int, K...>) {
+  ((m[K] *= (C)(1.0 / (double)mrt_norm(K))), ...);
+}
+template <typename C, int... A>
+__device__ __forceinline__ void mrt_backward(const C* w, C* fs, std::integer_sequence<int, A...>) {
+  ((fs[A + 1] = mrt_col<C, A + 1>(w, std::make_integer_sequence<int, Q>{})), ...);
+}
+
+template <typename C>
+__device__ __forceinline__ void collide_math_mrt(const Phys& ph, const C f[Q], C pc, const C pn[Q],
+                                                 C fs[Q]) {
+  // Eq. 4 and Eq. 5, as in collide_math
+  C rho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    rho += f[a];
+    if (cx(a) > 0) jx += f[a];
+    if (cx(a) < 0) jx -= f[a];
+    if (cy(a) > 0) jy += f[a];
+    if (cy(a) < 0) jy -= f[a];
+    if (cz(a) > 0) jz += f[a];
+    if (cz(a) < 0) jz -= f[a];
+  }
+  C ax = 0, ay = 0, az = 0, dx = 0, dy = 0, dz = 0;
+#pragma unroll
+  for (int a = 1; a < Q; ++a) {
+    const C p = pn[a];
+    if (a <= 6) {
+      if (cx(a)) ax += cx(a) > 0 ? p : -p;
+      if (cy(a)) ay += cy(a) > 0 ? p : -p;
+      if (cz(a)) az += cz(a) > 0 ? p : -p;
+    } else {
+      if (cx(a)) dx += cx(a) > 0 ? p : -p;
+      if (cy(a)) dy += cy(a) > 0 ? p : -p;
+      if (cz(a)) dz += cz(a) > 0 ? p : -p;
+    }
+  }
+  const C w1 = (C)(1.0 / 18.0), w2 = (C)(1.0 / 36.0);
+  const C gp = -(C)ph.G * pc;
+  const C Fx = gp * (w1 * ax + w2 * dx);
+  const C Fy = gp * (w1 * ay + w2 * dy);
+  const C Fz = gp * (w1 * az + w2 * dz);
+  // Guo's velocity
+  const C inv_rho = (C)1 / rho;
+  const C ux = (jx + (C)0.5 * Fx) * inv_rho;
+  const C uy = (jy + (C)0.5 * Fy) * inv_rho;
+  const C uz = (jz + (C)0.5 * Fz) * inv_rho;
+  // moments m = M f
+  C m[Q];
+  mrt_forward<C>(f, m, std::make_integer_sequence<int, Q>{});
+  // equilibrium and forcing moments
+  const C uu = ux * ux + uy * uy + uz * uz, uF = ux * Fx + uy * Fy + uz * Fz;
+  const C pxx = (C)2 * ux * ux - uy * uy - uz * uz, pww = uy * uy - uz * uz;
+  const C fxx = (C)2 * ((C)2 * Fx * ux - Fy * uy - Fz * uz), fww = (C)2 * (Fy * uy - Fz * uz);
+  const C se = (C)ph.s_e, seps = (C)ph.s_eps, sq = (C)ph.s_q, spi = (C)ph.s_pi, sm = (C)ph.s_m;
+  const C snu = (C)1 / (C)ph.tau;
+  auto relax = [](C mk, C meq, C s, C src) { return mk - s * (mk - meq) + ((C)1 - (C)0.5 * s) * src; };
+  C ms[Q];
+  ms[0] = rho;
+  ms[3] = jx + Fx;
+  ms[5] = jy + Fy;
+  ms[7] = jz + Fz;
+  ms[1] = relax(m[1], rho * ((C)19 * uu - (C)11), se, (C)38 * uF);
+  ms[2] = relax(m[2], rho * ((C)3 - (C)5.5 * uu), seps, (C)-11 * uF);
+  const C two3 = (C)(2.0 / 3.0);
+  ms[4] = relax(m[4], -two3 * rho * ux, sq, -two3 * Fx);
+  ms[6] = relax(m[6], -two3 * rho * uy, sq, -two3 * Fy);
+  ms[8] = relax(m[8], -two3 * rho * uz, sq, -two3 * Fz);
+  ms[9] = relax(m[9], rho * pxx, snu, fxx);
+  ms[10] = relax(m[10], (C)-0.5 * rho * pxx, spi, (C)-0.5 * fxx);
+  ms[11] = relax(m[11], rho * pww, snu, fww);
+  ms[12] = relax(m[12], (C)-0.5 * rho * pww, spi, (C)-0.5 * fww);
+  ms[13] = relax(m[13], rho * ux * uy, snu, Fx * uy + Fy * ux);
+  ms[14] = relax(m[14], rho * uy * uz, snu, Fy * uz + Fz * uy);
+  ms[15] = relax(m[15], rho * ux * uz, snu, Fx * uz + Fz * ux);
+  ms[16] = m[16] - sm * m[16];
+  ms[17] = m[17] - sm * m[17];
+  ms[18] = m[18] - sm * m[18];
+  // f* = M^T diag(1/|row|^2) m*; the rest population takes the remainder of
+  // the density so that each collision conserves mass up to one rounding
+  mrt_scale<C>(ms, std::make_integer_sequence<int, Q>{});
+  mrt_backward<C>(ms, fs, std::make_integer_sequence<int, Q - 1>{});
+  C rest = rho;
+#pragma unroll
+  for (int a = 1; a < Q; ++a) rest -= fs[a];
+  fs[0] = rest;
+}
+
+}  // namespace lbm

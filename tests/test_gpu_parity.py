@@ -354,15 +354,15 @@ def test_kernel_timing_counts_launches(L):
         n0, ms0 = L.lbm_kernel_time(lat.h, 0)
         n1, ms1 = L.lbm_kernel_time(lat.h, 1)
         assert n0 == 6 and n1 == 6 and ms0 > 0 and ms1 > 0
-        # the single-pass step (the default where it applies) is class 2;
-        # a diagnostic step still runs the two kernels
+        # the single-pass step (the default where it applies) is class 2,
+        # its diagnostic steps included
         lat.set_option("fused", 1)
         lat.set_option("diag_interval", 4)
         lat.set_option("kernel_timing", 0)
         lat.set_option("kernel_timing", 1)
         lat.step(6)   # steps 6..11: 8 is a diagnostic step
         n = [L.lbm_kernel_time(lat.h, k)[0] for k in range(3)]
-    assert n == [1, 1, 5]
+    assert n == [0, 0, 6]
 
 
 def test_gpu_coexistence_matches_oracle(L):
@@ -401,6 +401,46 @@ def test_diag_history_matches_on_demand(L, coex, pattern, k):
                     "min_slice_count", "min_slice_x", "max_u", "rho_min", "rho_max", "numeric_ok"):
             assert h[key] == w[key], (key, h[key], w[key])
         assert h["mom"] == w["mom"]
+
+
+# Fused diagnostic steps reduce the same per-node values in another grouping:
+# counts and extrema are exact, sums agree to FP32 partial-sum rounding.
+@pytest.mark.parametrize("precision", ["f32", "f16dev"])
+@pytest.mark.parametrize("shape,k", [((64, 16, 12), 4), ((128, 8, 17), 3)])
+def test_fused_diag_history_matches_on_demand(L, coex, precision, shape, k):
+    rl, rv = coex
+    nx, ny, nz = shape
+    steps = 4 * k + 2
+    R0 = min(ny, nz) / 4.0
+
+    def make_lat():
+        lat = make(L, shape, 1.0, G6, precision, "ab", rho_ref=rv if precision.endswith("dev") else 0.0)
+        lat.init_ligament(R0, float(nx), 0.1, 0.0, rl, rv, 2.0)
+        return lat
+
+    with make_lat() as lat:
+        assert lat.get_option("fused") == 1
+        lat.set_option("diag_interval", k)
+        lat.step(steps)
+        hist = lat.diag_history()
+        got_state = lat.populations()
+    want = []
+    with make_lat() as lat:
+        for t in range(steps):
+            if t % k == 0:
+                want.append(lat.diagnostics())
+            lat.step(1)
+        want_state = lat.populations()
+    np.testing.assert_array_equal(got_state, want_state)
+    assert [h["step"] for h in hist] == list(range(0, steps, k))
+    for h, w in zip(hist, want):
+        for key in ("liquid_count", "min_slice_count", "min_slice_x", "max_u", "rho_min", "rho_max",
+                    "numeric_ok"):
+            assert h[key] == w[key], (key, h[key], w[key])
+        for key in ("mass", "liquid_volume_w", "min_slice_area_w"):
+            assert h[key] == pytest.approx(w[key], rel=2e-6), key
+        for c in range(3):
+            assert abs(h["mom"][c] - w["mom"][c]) <= 1e-6 * w["mass"]
 
 
 def test_diag_interval_does_not_change_the_state(L):
