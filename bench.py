@@ -363,15 +363,16 @@ def run_reference(args):
     rc = oracle.coexistence(w.tau, w.G, n=64, tol=1e-10, rho_l0=2.6, rho_v0=0.07)
     f = oracle.init_ligament(w.nx, w.ny, w.nz, w.R0, w.lam, w.eps, w.phase, rc["rho_l"],
                              rc["rho_v"], w.width)
+    # a benchmark step is LBM_PER_STEP lattice steps, as in the GPU arm
     for _ in range(args.warmup):
-        f = oracle.step(f, w.tau, w.G, 1)
+        f = oracle.step(f, w.tau, w.G, LBM_PER_STEP)
     t = time.perf_counter()
     for _ in range(args.steps):
-        f = oracle.step(f, w.tau, w.G, 1)
+        f = oracle.step(f, w.tau, w.G, LBM_PER_STEP)
     el = time.perf_counter() - t
-    value = w.nodes * args.steps / el / 1e9
-    sample = "%d FP64 A-B lattice steps of the %dx%dx%d ligament, one per benchmark step" % (
-        args.steps, w.nx, w.ny, w.nz)
+    value = w.nodes * args.steps * LBM_PER_STEP / el / 1e9
+    sample = "%d FP64 A-B lattice steps of the %dx%dx%d ligament, %d per benchmark step" % (
+        args.steps * LBM_PER_STEP, w.nx, w.ny, w.nz, LBM_PER_STEP)
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -392,8 +393,10 @@ def run_reference(args):
 def run_batch(args):
     """The batched sweep: 48 periodic ligaments of uneven size (R0 in
     {8..24}, box lambda x 4R0 x 4R0, tau in [0.6, 1]), FP32, stepped as one
-    graph-replayed pair of launches per step for the whole batch (block shape
-    from the autotuner), against the same steps as 48 x 2 launches per step."""
+    graph-replayed pair of launches per step for the whole batch (block size
+    and register budget from the autotuner), against the same steps as
+    48 x 2 launches per step, each instance launched as a standalone lattice
+    of its size runs by default."""
     import torch
     from paper_1904_11792_gb300 import autotune, build, lbm as L
     torch.cuda.set_device(dist_env()[2])
@@ -408,8 +411,7 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     with L.Batch(insts, precision=args.precision) as b:
         b.init()
-        tuned = autotune.tune_batch(b, blocks=((128, 2, 1), (64, 4, 1), (32, 8, 1), (64, 2, 2)),
-                                    occupancies=(2, 3), steps=10)
+        tuned = autotune.tune_batch(b, blocks=((256, 1, 1), (128, 1, 1)), occupancies=(2, 3, 4), steps=10)
         b.init()
 
         def timed(fn, nsteps):

@@ -292,10 +292,12 @@ int lbm_batch_set_stream(lbm_batch b, void *stream);
 /* "graph" (0/1), "stochastic_rounding" (0/1, as lbm_set_option),
  * "occupancy" (2, 3, 4; default 2), "vector" (0/1, default 1:
  * instances with even nx update two nodes per thread), "block_x",
- * "block_y", "block_z" (collide-stream block shape of the batched kernel,
- * <= 256 threads; block_x counts node pairs on instances with even nx). */
+ * "block_y", "block_z" (<= 256 threads in all: the batched collide-stream
+ * kernel runs block_x * block_y * block_z threads per block over that many
+ * consecutive nodes, or node pairs, of one instance in linear order; the
+ * per-instance launches of lbm_batch_step_sequential use the shape). */
 int lbm_batch_set_option(lbm_batch b, const char *key, double value);
-/* Total nodes, collide-stream tiles of one launch, block shape (int[3]);
+/* Total nodes, collide-stream blocks of one launch, block shape (int[3]);
  * any pointer may be NULL. */
 int lbm_batch_info(lbm_batch b, long long *total_nodes, int *collide_tiles, int *block3);
 /* Ligament initial condition of every instance; resets the step count. */

@@ -147,9 +147,9 @@ def apply(lat: "L.Lattice", choice: dict) -> None:
     lat.set_option("occupancy", choice["occupancy"])
 
 
-def tune_batch(batch: "L.Batch", blocks=DEFAULT_BLOCKS, occupancies=(3, 4), steps=20,
-               verbose=False) -> dict:
-    """Times the batched step for each block shape / occupancy and leaves the
+def tune_batch(batch: "L.Batch", blocks=((256, 1, 1), (128, 1, 1), (64, 1, 1)), occupancies=(2, 3, 4),
+               steps=20, verbose=False) -> dict:
+    """Times the batched step for each block size / occupancy and leaves the
     batch configured with the fastest; returns the choice."""
     import torch
     best = None

@@ -13,6 +13,17 @@
 
 using namespace lbm;
 
+namespace lbm {
+// Default collide-stream block: 256 threads, as long along x (the
+// contiguous axis) as the lattice allows; with two nodes per thread (nx
+// even) block.x counts node pairs.
+dim3 default_block(const Geom& g) {
+  const int ux = g.nx % 2 == 0 ? g.nx / 2 : g.nx;
+  const unsigned bx = ux >= 256 ? 256 : (ux >= 128 ? 128 : (ux >= 64 ? 64 : 32));
+  return dim3(bx, 256 / bx, 1);
+}
+}  // namespace lbm
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -88,14 +99,6 @@ void sizes_for(const lbm_config* c, size_t* state, size_t* psi) {
   *psi = N * (c->precision == LBM_F64 ? 8 : 4);
 }
 
-// Default collide-stream block: 256 threads, as long along x (the
-// contiguous axis) as the lattice allows; with two nodes per thread (nx
-// even) block.x counts node pairs.
-dim3 default_block(const Geom& g) {
-  const int ux = g.nx % 2 == 0 ? g.nx / 2 : g.nx;
-  const unsigned bx = ux >= 256 ? 256 : (ux >= 128 ? 128 : (ux >= 64 ? 64 : 32));
-  return dim3(bx, 256 / bx, 1);
-}
 
 // ---- per-handle helpers -----------------------------------------------------
 

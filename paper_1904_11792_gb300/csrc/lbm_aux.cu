@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(DX* DY) diag_partial_kernel(Geom g, Phys ph,
       phi = phi < (C)0 ? (C)0 : (phi > (C)1 ? (C)1 : phi);
       s_vol += phi;
       cnt += rho > thr;
-      const C u = sqrt(jx * jx + jy * jy + jz * jz) / rho;
+      const C u = sqrt(xfma(jz, jz, xfma(jy, jy, xmul(jx, jx)))) / rho;
       umax = u > umax ? u : umax;
       rmin = rho < rmin ? rho : rmin;
       rmax = rho > rmax ? rho : rmax;

@@ -22,8 +22,7 @@ struct BatchInst {
   Phys ph;
   long long off_f;    // element offset of the instance's first array in the pool
   long long off_psi;  // element offset of its psi
-  int tile0;          // first collide tile of the instance
-  int tx, ty;         // collide tiles along x and y
+  int tile0;          // first collide-stream block of the instance
   int psi_block0;     // first psi-pass block of the instance
   int vec;            // two nodes per thread (nx even and the batch allows it)
 };
@@ -61,21 +60,26 @@ __global__ void __launch_bounds__(256) batch_psi_kernel(const BatchInst* __restr
   }
 }
 
+// Collide-stream over the batch.  A block covers blockDim.x consecutive
+// nodes (or node pairs) of one instance in linear order, so a warp reads and
+// writes 32 (or 64) consecutive x of a plane, rows continuing across the end
+// of a row, and lattices of any size waste no lanes except at their end.
+// One thread looks up the block's instance and the block shares it.
 template <int P, int MINB>
 __global__ void __launch_bounds__(256, MINB) batch_collide_kernel(const BatchInst* __restrict__ inst,
                                                                   int count,
                                                                   typename Prec<P>::T* pool_f, int cur,
                                                                   const typename Prec<P>::C* pool_psi) {
-  const int k = find_inst(inst, count, blockIdx.x, false);
-  const BatchInst I = inst[k];
-  const int t = blockIdx.x - I.tile0;
-  const int bx = t % I.tx, r = t / I.tx;
-  const int by = r % I.ty, bz = r / I.ty;
-  const int xt = bx * blockDim.x + threadIdx.x;
-  const int y = by * blockDim.y + threadIdx.y;
-  const int z = bz * blockDim.z + threadIdx.z;
-  const int x = I.vec ? 2 * xt : xt;
-  if (x >= I.g.nx || y >= I.g.ny || z >= I.g.nz) return;
+  __shared__ BatchInst sI;
+  if (threadIdx.x == 0) sI = inst[find_inst(inst, count, blockIdx.x, false)];
+  __syncthreads();
+  const BatchInst& I = sI;
+  const long long t = (long long)(blockIdx.x - I.tile0) * blockDim.x + threadIdx.x;
+  const long long i = I.vec ? 2 * t : t;   // first node of the thread (x even when paired)
+  if (i >= I.g.N) return;
+  const int row = (int)(i / I.g.nx);
+  const int x = (int)(i - (long long)row * I.g.nx);
+  const int z = row / I.g.ny, y = row - z * I.g.ny;
   const long long plane = (long long)Q * I.g.N;
   const typename Prec<P>::T* src = pool_f + I.off_f + (long long)cur * plane;
   typename Prec<P>::T* dst = pool_f + I.off_f + (long long)(cur ^ 1) * plane;
@@ -94,15 +98,16 @@ cudaError_t batch_launch_t(const BatchInst* d_inst, int count, int psi_blocks, i
   batch_psi_kernel<P><<<psi_blocks, 256, 0, s>>>(d_inst, count, (const T*)pool_f, cur, (C*)pool_psi, flag);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  const unsigned threads = block.x * block.y * block.z;
   switch (minb) {
     case 2:
-      batch_collide_kernel<P, 2><<<tiles, block, 0, s>>>(d_inst, count, (T*)pool_f, cur, (const C*)pool_psi);
+      batch_collide_kernel<P, 2><<<tiles, threads, 0, s>>>(d_inst, count, (T*)pool_f, cur, (const C*)pool_psi);
       break;
     case 3:
-      batch_collide_kernel<P, 3><<<tiles, block, 0, s>>>(d_inst, count, (T*)pool_f, cur, (const C*)pool_psi);
+      batch_collide_kernel<P, 3><<<tiles, threads, 0, s>>>(d_inst, count, (T*)pool_f, cur, (const C*)pool_psi);
       break;
     default:
-      batch_collide_kernel<P, 4><<<tiles, block, 0, s>>>(d_inst, count, (T*)pool_f, cur, (const C*)pool_psi);
+      batch_collide_kernel<P, 4><<<tiles, threads, 0, s>>>(d_inst, count, (T*)pool_f, cur, (const C*)pool_psi);
       break;
   }
   return cudaGetLastError();
@@ -180,22 +185,21 @@ void drop_graphs(lbm_batch_ctx* b) {
     }
 }
 
-// Recomputes the tile table for the current block shape and uploads it.
+// Recomputes the block table for the current block size and uploads it.
 int layout_tiles(lbm_batch_ctx* b) {
-  int tiles = 0, psi_blocks = 0;
+  long long tiles = 0, psi_blocks = 0;
+  const int threads = (int)(b->block.x * b->block.y * b->block.z);
   for (auto& I : b->inst) {
     I.vec = (b->vec && I.g.nx % 2 == 0) ? 1 : 0;
-    const int ux = I.vec ? I.g.nx / 2 : I.g.nx;
-    I.tile0 = tiles;
-    I.tx = (ux + b->block.x - 1) / b->block.x;
-    I.ty = (I.g.ny + b->block.y - 1) / b->block.y;
-    const int tz = (I.g.nz + b->block.z - 1) / b->block.z;
-    tiles += I.tx * I.ty * tz;
-    I.psi_block0 = psi_blocks;
-    psi_blocks += (int)(((I.vec ? I.g.N / 2 : I.g.N) + 255) / 256);
+    const long long units = I.vec ? I.g.N / 2 : I.g.N;
+    I.tile0 = (int)tiles;
+    tiles += (units + threads - 1) / threads;
+    I.psi_block0 = (int)psi_blocks;
+    psi_blocks += (units + 255) / 256;
   }
-  b->tiles = tiles;
-  b->psi_blocks = psi_blocks;
+  if (tiles > 0x7fffffffLL || psi_blocks > 0x7fffffffLL) return bfail(LBM_ERR_ARG, "batch too large for one grid");
+  b->tiles = (int)tiles;
+  b->psi_blocks = (int)psi_blocks;
   BCK(cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(BatchInst) * b->count, cudaMemcpyHostToDevice,
                       b->stream));
   BCK(cudaStreamSynchronize(b->stream));
@@ -465,7 +469,8 @@ int lbm_batch_step_sequential(lbm_batch b, int n) {
       void* dst = (char*)v.f + (b->cur ? -1 : 1) * (long long)Q * v.g.N * (long long)e;
       const bool vec = b->inst[k].vec != 0;
       BCK(launch_psi(b->precision, LAYOUT_LOCAL, vec, v.g, v.ph, v.f, v.psi, b->d_flag, b->stream));
-      BCK(launch_collide(b->precision, MODE_AB, b->minb, vec, v.g, v.ph, v.f, dst, v.psi, b->block,
+      // as a standalone lattice of this size runs by default
+      BCK(launch_collide(b->precision, MODE_AB, 0, vec, v.g, v.ph, v.f, dst, v.psi, default_block(v.g),
                          b->stream));
     }
     b->cur ^= 1;

@@ -92,6 +92,14 @@ __device__ __forceinline__ __nv_bfloat16 bf16_sr(float x, unsigned r16) {
   return __ushort_as_bfloat16((unsigned short)(cvt_rs_bf16x2(0.0f, x, r16 & 0xFFFFu) & 0xFFFFu));
 }
 
+// Round-to-nearest product and fused multiply-add that the compiler does not
+// contract or split: arithmetic written with them gives the same bits in every
+// kernel that inlines it.
+__device__ __forceinline__ float xmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float xfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double xfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Storage traits.  T = stored type, C = compute type.  The *DEV forms store
 // the deviation g_a = f_a - w_a rho_ref and add it back on load.  load()
 // goes through the read-only data path and is only used on arrays the kernel

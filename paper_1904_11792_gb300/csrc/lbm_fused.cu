@@ -152,11 +152,11 @@ struct DiagOut {
 };
 
 // Blocks per SM the register budget must allow: 3 for 4-byte storage (its
-// 73 KB of shared memory allow no more), 4 for 2-byte storage; 2 for the
-// diagnostic variant, which runs once per diagnostic interval.
+// 73 KB of shared memory allow no more), 4 for 2-byte storage; 3 for the
+// diagnostic variant (no spills at 168 registers).
 template <int P, bool DIAG>
 constexpr int fused_minb() {
-  return DIAG ? 2 : (Prec<P>::dev ? 4 : 3);
+  return DIAG ? 3 : (Prec<P>::dev ? 4 : 3);
 }
 
 template <int P, bool DIAG>
@@ -269,18 +269,20 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG>())
     psi_math<C>(ph, r0, &p0, flag);
     psi_math<C>(ph, r1, &p1, flag);
     if constexpr (DIAG) {
+      // momentum of the two nodes (same order of terms as the two-kernel
+      // diagnostics)
+      C jv[2][3] = {{0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        if (cx(a)) { jv[0][0] += cx(a) > 0 ? f0[a] : -f0[a]; jv[1][0] += cx(a) > 0 ? f1[a] : -f1[a]; }
+        if (cy(a)) { jv[0][1] += cy(a) > 0 ? f0[a] : -f0[a]; jv[1][1] += cy(a) > 0 ? f1[a] : -f1[a]; }
+        if (cz(a)) { jv[0][2] += cz(a) > 0 ? f0[a] : -f0[a]; jv[1][2] += cz(a) > 0 ? f1[a] : -f1[a]; }
+      }
       if (k >= 1 && k <= np - 2) {
 #pragma unroll
         for (int n = 0; n < 2; ++n) {
-          const C* fv = n ? f1 : f0;
           const C rho = n ? r1 : r0;
-          C jx = 0, jy = 0, jz = 0;
-#pragma unroll
-          for (int a = 0; a < Q; ++a) {
-            if (cx(a)) jx += cx(a) > 0 ? fv[a] : -fv[a];
-            if (cy(a)) jy += cy(a) > 0 ? fv[a] : -fv[a];
-            if (cz(a)) jz += cz(a) > 0 ? fv[a] : -fv[a];
-          }
+          const C jx = jv[n][0], jy = jv[n][1], jz = jv[n][2];
           d_mass += rho;
           d_jx += jx;
           d_jy += jy;
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG>())
           d_vol += phi;
           col_w[n] += phi;
           col_n[n] += rho > d_thr ? (C)1 : (C)0;
-          const C um = sqrt(jx * jx + jy * jy + jz * jz) / rho;
+          const C um = sqrt(xfma(jz, jz, xfma(jy, jy, xmul(jx, jx)))) / rho;
           d_umax = um > d_umax ? um : d_umax;
           d_rmin = rho < d_rmin ? rho : d_rmin;
           d_rmax = rho > d_rmax ? rho : d_rmax;

@@ -39,6 +39,9 @@ cudaError_t launch_collide(int precision, int mode, int minb, bool vec, const Ge
                            const Phys& ph, const void* src, void* dst, const void* psi, dim3 block,
                            cudaStream_t s);
 
+// Default collide-stream block shape of a lattice (lbm_api.cu).
+dim3 default_block(const Geom& g);
+
 // force + collision + streaming with the MRT collision (lbm_mrt.cu); the
 // same modes and layouts as launch_collide
 cudaError_t launch_collide_mrt(int precision, int mode, bool vec, const Geom& g, const Phys& ph,

@@ -53,7 +53,7 @@ template <int Cf, typename C>
 __device__ __forceinline__ void mrt_fma(C& v, C x) {
   if constexpr (Cf == 1) v += x;
   else if constexpr (Cf == -1) v -= x;
-  else if constexpr (Cf != 0) v += (C)Cf * x;
+  else if constexpr (Cf != 0) v = xfma((C)Cf, x, v);
 }
 // m[K] = sum_a M[K][a] f[a] and f[A] = sum_k M[k][A] w[k], expanded at compile
 // time so that only the non-zero integer coefficients cost instructions.
@@ -75,7 +75,7 @@ __device__ __forceinline__ void mrt_forward(const C* f, C* m, std::integer_seque
 }
 template <typename C, int... K>
 __device__ __forceinline__ void mrt_scale(C* m, std::integer_sequence<int, K...>) {
-  ((m[K] *= (C)(1.0 / (double)mrt_norm(K))), ...);
+  ((m[K] = xmul(m[K], (C)(1.0 / (double)mrt_norm(K)))), ...);
 }
 template <typename C, int... A>
 __device__ __forceinline__ void mrt_backward(const C* w, C* fs, std::integer_sequence<int, A...>) {
@@ -112,46 +112,55 @@ __device__ __forceinline__ void collide_math_mrt(const Phys& ph, const C f[Q], C
     }
   }
   const C w1 = (C)(1.0 / 18.0), w2 = (C)(1.0 / 36.0);
-  const C gp = -(C)ph.G * pc;
-  const C Fx = gp * (w1 * ax + w2 * dx);
-  const C Fy = gp * (w1 * ay + w2 * dy);
-  const C Fz = gp * (w1 * az + w2 * dz);
+  // products through xmul / xfma: the same bits in every kernel (see
+  // collide_math)
+  const C gp = xmul(-(C)ph.G, pc);
+  const C Fx = xmul(gp, xfma(w1, ax, xmul(w2, dx)));
+  const C Fy = xmul(gp, xfma(w1, ay, xmul(w2, dy)));
+  const C Fz = xmul(gp, xfma(w1, az, xmul(w2, dz)));
   // Guo's velocity
   const C inv_rho = (C)1 / rho;
-  const C ux = (jx + (C)0.5 * Fx) * inv_rho;
-  const C uy = (jy + (C)0.5 * Fy) * inv_rho;
-  const C uz = (jz + (C)0.5 * Fz) * inv_rho;
+  const C ux = xmul(xfma((C)0.5, Fx, jx), inv_rho);
+  const C uy = xmul(xfma((C)0.5, Fy, jy), inv_rho);
+  const C uz = xmul(xfma((C)0.5, Fz, jz), inv_rho);
   // moments m = M f
   C m[Q];
   mrt_forward<C>(f, m, std::make_integer_sequence<int, Q>{});
   // equilibrium and forcing moments
-  const C uu = ux * ux + uy * uy + uz * uz, uF = ux * Fx + uy * Fy + uz * Fz;
-  const C pxx = (C)2 * ux * ux - uy * uy - uz * uz, pww = uy * uy - uz * uz;
-  const C fxx = (C)2 * ((C)2 * Fx * ux - Fy * uy - Fz * uz), fww = (C)2 * (Fy * uy - Fz * uz);
+  const C ux2 = xmul(ux, ux), uy2 = xmul(uy, uy), uz2 = xmul(uz, uz);
+  const C uu = ux2 + uy2 + uz2;
+  const C uF = xfma(uz, Fz, xfma(uy, Fy, xmul(ux, Fx)));
+  const C pxx = xfma((C)2, ux2, -uy2) - uz2, pww = uy2 - uz2;
+  const C fyy = xmul(Fy, uy), fzz = xmul(Fz, uz);
+  const C fxx = xmul((C)2, xfma((C)2, xmul(Fx, ux), -fyy) - fzz), fww = xmul((C)2, fyy - fzz);
   const C se = (C)ph.s_e, seps = (C)ph.s_eps, sq = (C)ph.s_q, spi = (C)ph.s_pi, sm = (C)ph.s_m;
   const C snu = (C)1 / (C)ph.tau;
-  auto relax = [](C mk, C meq, C s, C src) { return mk - s * (mk - meq) + ((C)1 - (C)0.5 * s) * src; };
+  auto relax = [](C mk, C meq, C s, C src) {
+    return xfma(xfma((C)-0.5, s, (C)1), src, xfma(-s, mk - meq, mk));
+  };
   C ms[Q];
   ms[0] = rho;
   ms[3] = jx + Fx;
   ms[5] = jy + Fy;
   ms[7] = jz + Fz;
-  ms[1] = relax(m[1], rho * ((C)19 * uu - (C)11), se, (C)38 * uF);
-  ms[2] = relax(m[2], rho * ((C)3 - (C)5.5 * uu), seps, (C)-11 * uF);
-  const C two3 = (C)(2.0 / 3.0);
-  ms[4] = relax(m[4], -two3 * rho * ux, sq, -two3 * Fx);
-  ms[6] = relax(m[6], -two3 * rho * uy, sq, -two3 * Fy);
-  ms[8] = relax(m[8], -two3 * rho * uz, sq, -two3 * Fz);
-  ms[9] = relax(m[9], rho * pxx, snu, fxx);
-  ms[10] = relax(m[10], (C)-0.5 * rho * pxx, spi, (C)-0.5 * fxx);
-  ms[11] = relax(m[11], rho * pww, snu, fww);
-  ms[12] = relax(m[12], (C)-0.5 * rho * pww, spi, (C)-0.5 * fww);
-  ms[13] = relax(m[13], rho * ux * uy, snu, Fx * uy + Fy * ux);
-  ms[14] = relax(m[14], rho * uy * uz, snu, Fy * uz + Fz * uy);
-  ms[15] = relax(m[15], rho * ux * uz, snu, Fx * uz + Fz * ux);
-  ms[16] = m[16] - sm * m[16];
-  ms[17] = m[17] - sm * m[17];
-  ms[18] = m[18] - sm * m[18];
+  ms[1] = relax(m[1], xmul(rho, xfma((C)19, uu, (C)-11)), se, xmul((C)38, uF));
+  ms[2] = relax(m[2], xmul(rho, xfma((C)-5.5, uu, (C)3)), seps, xmul((C)-11, uF));
+  const C mtwo3 = (C)(-2.0 / 3.0);
+  const C mr = xmul(mtwo3, rho);
+  ms[4] = relax(m[4], xmul(mr, ux), sq, xmul(mtwo3, Fx));
+  ms[6] = relax(m[6], xmul(mr, uy), sq, xmul(mtwo3, Fy));
+  ms[8] = relax(m[8], xmul(mr, uz), sq, xmul(mtwo3, Fz));
+  const C rpxx = xmul(rho, pxx), rpww = xmul(rho, pww);
+  ms[9] = relax(m[9], rpxx, snu, fxx);
+  ms[10] = relax(m[10], xmul((C)-0.5, rpxx), spi, xmul((C)-0.5, fxx));
+  ms[11] = relax(m[11], rpww, snu, fww);
+  ms[12] = relax(m[12], xmul((C)-0.5, rpww), spi, xmul((C)-0.5, fww));
+  ms[13] = relax(m[13], xmul(xmul(rho, ux), uy), snu, xfma(Fy, ux, xmul(Fx, uy)));
+  ms[14] = relax(m[14], xmul(xmul(rho, uy), uz), snu, xfma(Fz, uy, xmul(Fy, uz)));
+  ms[15] = relax(m[15], xmul(xmul(rho, ux), uz), snu, xfma(Fz, ux, xmul(Fx, uz)));
+  ms[16] = xfma(-sm, m[16], m[16]);
+  ms[17] = xfma(-sm, m[17], m[17]);
+  ms[18] = xfma(-sm, m[18], m[18]);
   // f* = M^T diag(1/|row|^2) m*; the rest population takes the remainder of
   // the density so that each collision conserves mass up to one rounding
   mrt_scale<C>(ms, std::make_integer_sequence<int, Q>{});

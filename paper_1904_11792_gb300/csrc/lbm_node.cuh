@@ -166,18 +166,21 @@ __device__ __forceinline__ void collide_math(const Phys& ph, const C f[Q], C pc,
       if (cz(a)) dz += cz(a) > 0 ? p : -p;
     }
   }
+  // Products and sums below go through xmul / xfma (round to nearest, fused
+  // only where written), so every kernel that inlines this function computes
+  // the same bits whatever the compiler's contraction choices around it.
   const C w1 = (C)(1.0 / 18.0), w2 = (C)(1.0 / 36.0);
-  const C gp = -(C)ph.G * pc;
-  const C Fx = gp * (w1 * ax + w2 * dx);
-  const C Fy = gp * (w1 * ay + w2 * dy);
-  const C Fz = gp * (w1 * az + w2 * dz);
+  const C gp = xmul(-(C)ph.G, pc);
+  const C Fx = xmul(gp, xfma(w1, ax, xmul(w2, dx)));
+  const C Fy = xmul(gp, xfma(w1, ay, xmul(w2, dy)));
+  const C Fz = xmul(gp, xfma(w1, az, xmul(w2, dz)));
   // Eq. 6
   const C tau = (C)ph.tau;
   const C inv_rho = (C)1 / rho;
-  const C ux = (jx + tau * Fx) * inv_rho;
-  const C uy = (jy + tau * Fy) * inv_rho;
-  const C uz = (jz + tau * Fz) * inv_rho;
-  const C usq = (C)1.5 * (ux * ux + uy * uy + uz * uz);
+  const C ux = xmul(xfma(tau, Fx, jx), inv_rho);
+  const C uy = xmul(xfma(tau, Fy, jy), inv_rho);
+  const C uz = xmul(xfma(tau, Fz, jz), inv_rho);
+  const C usq = xmul((C)1.5, xfma(uz, uz, xfma(uy, uy, xmul(ux, ux))));
   const C omega = (C)1 / tau;
   // Eq. 2 and Eq. 3.  The moving populations a = 1..18 take f_eq from Eq. 2
   // directly; the rest population takes f_eq_0 = rho - sum_{a>=1} f_eq_a,
@@ -187,20 +190,25 @@ __device__ __forceinline__ void collide_math(const Phys& ph, const C f[Q], C pc,
   // collision create mass of relative order 1e-8 (FP32) in one direction;
   // this form conserves mass up to unbiased rounding.
   C feq_sum = 0;
+  const C one_m_usq = (C)1 - usq;
 #pragma unroll
   for (int a = 1; a < Q; a += 2) {
     const int b = a + 1;  // opp(a)
-    const C cu = cx(a) * ux + cy(a) * uy + cz(a) * uz;
-    const C wr = (C)wgt(a) * rho;
-    const C even = (C)1 + (C)4.5 * cu * cu - usq;
-    const C feq_a = wr * (even + (C)3 * cu);
-    const C feq_b = wr * (even - (C)3 * cu);
+    // c_a . u with c_a components in {-1, 0, 1}: sums only
+    C cu = 0;
+    if (cx(a)) cu = cx(a) > 0 ? cu + ux : cu - ux;
+    if (cy(a)) cu = cy(a) > 0 ? cu + uy : cu - uy;
+    if (cz(a)) cu = cz(a) > 0 ? cu + uz : cu - uz;
+    const C wr = xmul((C)wgt(a), rho);
+    const C even = xfma(xmul((C)4.5, cu), cu, one_m_usq);
+    const C feq_a = xmul(wr, xfma((C)3, cu, even));
+    const C feq_b = xmul(wr, xfma((C)-3, cu, even));
     feq_sum += feq_a + feq_b;
-    fs[a] = f[a] - omega * (f[a] - feq_a);
-    fs[b] = f[b] - omega * (f[b] - feq_b);
+    fs[a] = xfma(-omega, f[a] - feq_a, f[a]);
+    fs[b] = xfma(-omega, f[b] - feq_b, f[b]);
   }
   const C feq_0 = rho - feq_sum;
-  fs[0] = f[0] - omega * (f[0] - feq_0);
+  fs[0] = xfma(-omega, f[0] - feq_0, f[0]);
 }
 
 template <typename C>

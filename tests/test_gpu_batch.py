@@ -59,8 +59,10 @@ def test_batched_equals_standalone_bitwise(L, precision):
 def test_sequential_equals_batched_and_block_shapes(L):
     insts = instances(6)
     res = []
+    # the batched kernel runs block_x * block_y * block_z threads over
+    # consecutive nodes: 256, 128 and a block size that is no power of two
     for mode, block in (("batched", None), ("sequential", None), ("batched", (64, 2, 2)),
-                        ("batched", (32, 4, 1))):
+                        ("batched", (32, 4, 1)), ("batched", (96, 1, 1))):
         with L.Batch(insts) as b:
             if block:
                 for key, v in zip(("block_x", "block_y", "block_z"), (1, 1, 1)):
