@@ -174,7 +174,8 @@ int lbm_set_stream(lbm_handle h, void *stream);
  * paper's conclusions name as its next step: D3Q19 moments of d'Humieres et
  * al. 2002, the Shan-Chen force of Eq. 5 entered by Guo's forcing with
  * u = (j + F/2)/rho; shear moments relax at 1/tau, so nu = (tau - 1/2)/3;
- * the fused step does not apply), "mrt_s_e", "mrt_s_eps", "mrt_s_q",
+ * the fused step and the two-kernel step both have it), "mrt_s_e",
+ * "mrt_s_eps", "mrt_s_q",
  * "mrt_s_pi", "mrt_s_m" (its other rates, each in (0, 2); defaults 1.19,
  * 1.4, 1.2, 1.4, 1.98).  lbm_get_option also answers "step", "nx", "ny", "nz",
  * "precision", "pattern". */

@@ -14,6 +14,8 @@
 using namespace lbm;
 
 namespace lbm {
+inline bool Prec_dev(int precision) { return precision == LBM_F16DEV || precision == LBM_BF16DEV; }
+
 // Default collide-stream block: 256 threads, as long along x (the
 // contiguous axis) as the lattice allows; with two nodes per thread (nx
 // even) block.x counts node pairs.
@@ -144,7 +146,7 @@ int enqueue_step(lbm_ctx* h, cudaStream_t s, long long step, int cur, bool timed
   const int mode = aa ? ((step & 1) ? MODE_AA_ODD : MODE_AA_EVEN) : MODE_AB;
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   const bool diag_step = h->diag_interval > 0 && step % h->diag_interval == 0;
-  const bool fused = h->fused && !aa && h->ph.coll == COLL_SRT && fused_applicable(h->g, prec);
+  const bool fused = h->fused && !aa && fused_applicable(h->g, prec);
   // a diagnostic step runs fused too when the scratch holds its partials
   const bool fused_diag =
       fused && diag_step && h->d_scratch && fused_diag_scratch_doubles(h->g, prec, h->fused_fz) <= h->scratch_doubles;
@@ -166,6 +168,7 @@ int enqueue_step(lbm_ctx* h, cudaStream_t s, long long step, int cur, bool timed
       CK(cudaEventRecord(e1, s));
       h->pending.push_back({2, e0, e1});
     }
+    if (Prec_dev(prec) && h->ph.sr) CK(launch_salt((unsigned*)(h->d_flag + 2), false, 0u, s));
     if (diag_step && h->diag_ccl) {
       long long* d4 = (long long*)(h->d_small + 32);
       CK(launch_ccl(prec, layout, h->g, h->ph, src, 0.5 * (h->rho_l + h->rho_v), h->d_labels,
@@ -201,6 +204,7 @@ int enqueue_step(lbm_ctx* h, cudaStream_t s, long long step, int cur, bool timed
     CK(launch_collide_mrt(prec, mode, vec, h->g, h->ph, src, dst, h->psi, h->block, s));
   else
     CK(launch_collide(prec, mode, minb, vec, h->g, h->ph, src, dst, h->psi, h->block, s));
+  if (Prec_dev(prec) && h->ph.sr) CK(launch_salt((unsigned*)(h->d_flag + 2), false, 0u, s));
   if (timed) {
     CK(cudaEventRecord(e2, s));
     h->pending.push_back({0, e0, e1});
@@ -486,6 +490,7 @@ lbm_handle lbm_create_ex(const lbm_config* cfg) {
     }
   }
   if (rc == LBM_OK) rc = dev_alloc((void**)&h->d_flag, sizeof(int) * 4, "flag");
+  if (rc == LBM_OK) h->ph.salt = (const unsigned*)(h->d_flag + 2);
   if (rc == LBM_OK) rc = dev_alloc((void**)&h->d_small, sizeof(double) * 64, "results");
   if (rc == LBM_OK) {
     e = cudaMemsetAsync(h->d_flag, 0, sizeof(int) * 4, h->stream);
@@ -640,7 +645,7 @@ int lbm_get_option(lbm_handle h, const char* key, double* v) {
   else if (k == "vector") *v = h->vec && (h->g.nx % 2 == 0);
   else if (k == "stochastic_rounding") *v = h->ph.sr;
   else if (k == "fused")
-    *v = h->fused && h->cfg.pattern == LBM_AB && h->ph.coll == COLL_SRT && fused_applicable(h->g, h->cfg.precision);
+    *v = h->fused && h->cfg.pattern == LBM_AB && fused_applicable(h->g, h->cfg.precision);
   else if (k == "fused_fz") *v = h->fused_fz;
   else if (k == "collision") *v = h->ph.coll;
   else if (k == "mrt_s_e") *v = h->ph.s_e;
@@ -665,6 +670,7 @@ int lbm_get_option(lbm_handle h, const char* key, double* v) {
 static int init_common(lbm_handle h, const InitSpec& sp) {
   h->step = 0;
   h->cur = 0;
+  CK(launch_salt((unsigned*)(h->d_flag + 2), true, 0u, h->stream));
   drop_graphs(h);   // the in-loop diagnostics capture the densities
   CK(launch_init(h->cfg.precision, h->g, h->ph, sp, array_ptr(h, 0), h->stream));
   h->initialized = true;
@@ -1009,6 +1015,7 @@ int lbm_load_state(lbm_handle h, const void* host, size_t bytes) {
     return fail(LBM_ERR_ARG, "saved state has another size, precision or pattern");
   h->cur = 0;
   h->step = hd.step;
+  CK(launch_salt((unsigned*)(h->d_flag + 2), true, (unsigned)hd.step, h->stream));
   h->rho_l = hd.rho_l;
   h->rho_v = hd.rho_v;
   CK(cudaMemcpyAsync(array_ptr(h, 0), (const char*)host + sizeof(hd), need - sizeof(hd),

@@ -680,6 +680,15 @@ cudaError_t droplets_t(int layout, const Geom& g, const Phys& ph, const void* f,
 
 }  // namespace
 
+// Stochastic-rounding step salt: set it, or advance it by one (after each
+// time step's collision).
+__global__ void salt_kernel(unsigned* salt, int set, unsigned value) { *salt = set ? value : *salt + 1u; }
+
+cudaError_t launch_salt(unsigned* salt, bool set, unsigned value, cudaStream_t s) {
+  salt_kernel<<<1, 1, 0, s>>>(salt, set ? 1 : 0, value);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_diag_reduce(const Geom& g, int row_blocks, int nblocks, const double* slices,
                                const double* blocks, double* slice_tot, double* out,
                                unsigned long long* ring_count, int ring_cap, cudaStream_t s) {

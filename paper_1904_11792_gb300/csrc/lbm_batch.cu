@@ -207,9 +207,14 @@ int layout_tiles(lbm_batch_ctx* b) {
   return LBM_OK;
 }
 
+bool batch_sr(const lbm_batch_ctx* b) {
+  return (b->precision == LBM_F16DEV || b->precision == LBM_BF16DEV) && !b->inst.empty() && b->inst[0].ph.sr;
+}
+
 int enqueue_batch_step(lbm_batch_ctx* b, cudaStream_t s, int cur) {
   BCK(batch_launch(b->precision, b->d_inst, b->count, b->psi_blocks, b->tiles, b->pool_f, cur, b->pool_psi,
                    b->d_flag, b->block, b->minb, s));
+  if (batch_sr(b)) BCK(launch_salt((unsigned*)(b->d_flag + 2), false, 0u, s));
   return LBM_OK;
 }
 
@@ -350,6 +355,9 @@ lbm_batch lbm_batch_create(const lbm_instance* inst, int count, int precision, i
   if (err == cudaSuccess) err = cudaMalloc(&b->d_flag, sizeof(int) * 4);
   if (err == cudaSuccess) err = cudaMalloc(&b->d_small, sizeof(double) * 64);
   if (err == cudaSuccess) err = cudaMemsetAsync(b->d_flag, 0, sizeof(int) * 4, b->stream);
+  // d_flag[2] is the stochastic-rounding step salt of every instance
+  if (err == cudaSuccess)
+    for (auto& I : b->inst) I.ph.salt = (const unsigned*)(b->d_flag + 2);
   if (err == cudaSuccess) err = cudaMemsetAsync(b->pool_f, 0, b->pool_f_bytes, b->stream);
   if (err != cudaSuccess) {
     bcuda(err, "lbm_batch_create");
@@ -425,6 +433,7 @@ int lbm_batch_init(lbm_batch b) {
   if (!b) return bfail(LBM_ERR_ARG, "null batch");
   b->cur = 0;
   b->step = 0;
+  BCK(launch_salt((unsigned*)(b->d_flag + 2), true, 0u, b->stream));
   for (int k = 0; k < b->count; ++k) {
     const lbm_instance& s = b->spec[k];
     View v = view_of(b, k);
@@ -473,6 +482,7 @@ int lbm_batch_step_sequential(lbm_batch b, int n) {
       BCK(launch_collide(b->precision, MODE_AB, 0, vec, v.g, v.ph, v.f, dst, v.psi, default_block(v.g),
                          b->stream));
     }
+    if (batch_sr(b)) BCK(launch_salt((unsigned*)(b->d_flag + 2), false, 0u, b->stream));
     b->cur ^= 1;
     b->step += 1;
   }

@@ -55,11 +55,17 @@ __device__ __forceinline__ unsigned mix32(unsigned h) {
   h ^= h >> 16;
   return h;
 }
-__device__ __forceinline__ unsigned sr_seed(long long node, float rest) {
-  return mix32((unsigned)node * 0x9E3779B9u ^ (unsigned)(node >> 32) ^ __float_as_uint(rest));
+// Seed of a node's stochastic-rounding bits in one time step: the node
+// index, the bits of its post-collision rest population and the step salt
+// (a per-step counter; without it a node whose state no longer changes would
+// round the same way every step and its rounding error would grow linearly
+// in time instead of averaging out).
+__device__ __forceinline__ unsigned sr_seed(long long node, float rest, unsigned salt) {
+  return mix32((unsigned)node * 0x9E3779B9u ^ (unsigned)(node >> 32) ^ __float_as_uint(rest) ^
+               mix32(salt + 0x6A09E667u));
 }
-__device__ __forceinline__ unsigned sr_seed(long long node, double rest) {
-  return sr_seed(node, (float)rest);
+__device__ __forceinline__ unsigned sr_seed(long long node, double rest, unsigned salt) {
+  return sr_seed(node, (float)rest, salt);
 }
 // 16 random bits for direction a of a node with (well mixed) seed s: the
 // top half of s times a distinct odd constant per direction (one multiply).
@@ -173,8 +179,12 @@ struct Phys {
   // fourth-order stress and the third-order moments (shear moments relax
   // at 1/tau)
   double s_e, s_eps, s_q, s_pi, s_m;
+  // stochastic-rounding step salt in device memory (read at each collision,
+  // advanced once per step by salt_bump_kernel); nullptr reads as 0
+  const unsigned* salt;
 };
 enum Collision { COLL_SRT = 0, COLL_MRT = 1 };
+__device__ __forceinline__ unsigned salt_of(const Phys& ph) { return ph.salt ? __ldg(ph.salt) : 0u; }
 
 // Neighbour index table of one node: x-1, x, x+1 and the 9 row offsets of
 // (y + dy, z + dz), all periodic.  idx(cxa, cya, cza) is the flat index of

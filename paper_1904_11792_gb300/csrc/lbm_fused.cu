@@ -154,13 +154,13 @@ struct DiagOut {
 // Blocks per SM the register budget must allow: 3 for 4-byte storage (its
 // 73 KB of shared memory allow no more), 4 for 2-byte storage; 3 for the
 // diagnostic variant (no spills at 168 registers).
-template <int P, bool DIAG>
+template <int P, bool DIAG, int COLL = COLL_SRT>
 constexpr int fused_minb() {
   return DIAG ? 3 : (Prec<P>::dev ? 4 : 3);
 }
 
-template <int P, bool DIAG>
-__global__ void __launch_bounds__(NT, fused_minb<P, DIAG>())
+template <int P, bool DIAG, int COLL>
+__global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
     fused_kernel(const __grid_constant__ Maps maps, Geom g, Phys ph, typename Prec<P>::T* dst, int* flag, int ntx,
                  int nchunks, int fz, DiagOut dg) {
   using T = typename Prec<P>::T;
@@ -239,6 +239,7 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG>())
     for (int k = 0; k < NB && k < np; ++k)
       issue_plane<P>(smem, maps, k, x0, y0, xl, xr, ym, yp, zplane(k), full + k);
 
+  const unsigned salt = (Prec<P>::dev && ph.sr) ? salt_of(ph) : 0u;
   V prev[Q];   // stored populations of this thread's two nodes, previous plane
   // diagnostics sums (DIAG): block totals and the two x columns of the thread
   C d_mass = 0, d_jx = 0, d_jy = 0, d_jz = 0, d_vol = 0, d_umax = 0;
@@ -366,11 +367,16 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG>())
         pn1[a] = q[cy(a) + 1][cz(a) + 1][2 + cx(a)];
       }
       C fs0[Q], fs1[Q];
-      collide_math<C>(ph, g0, q[1][1][1], pn0, fs0);
-      collide_math<C>(ph, g1, q[1][1][2], pn1, fs1);
+      if constexpr (COLL == COLL_MRT) {
+        collide_math_mrt<C>(ph, g0, q[1][1][1], pn0, fs0);
+        collide_math_mrt<C>(ph, g1, q[1][1][2], pn1, fs1);
+      } else {
+        collide_math<C>(ph, g0, q[1][1][1], pn0, fs0);
+        collide_math<C>(ph, g1, q[1][1][2], pn1, fs1);
+      }
       const int i0 = x + g.nx * (y + g.ny * z);
       const bool sr = Prec<P>::dev && ph.sr;
-      const unsigned seed0 = sr ? sr_seed(i0, fs0[0]) : 0u, seed1 = sr ? sr_seed(i0 + 1, fs1[0]) : 0u;
+      const unsigned seed0 = sr ? sr_seed(i0, fs0[0], salt) : 0u, seed1 = sr ? sr_seed(i0 + 1, fs1[0], salt) : 0u;
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
         const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
@@ -559,15 +565,16 @@ cudaError_t fused_grid(const Geom& g, int fz_req, int* fz, int* nchunks, long lo
   using S = FusedShape<P>;
   static int slots_per_sm = 0, sms = 0;
   if (!slots_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(fused_kernel<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S::smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fused_kernel<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
+    cudaError_t e = cudaSuccess;
+    for (const void* k : {(const void*)fused_kernel<P, false, COLL_SRT>, (const void*)fused_kernel<P, true, COLL_SRT>,
+                          (const void*)fused_kernel<P, false, COLL_MRT>, (const void*)fused_kernel<P, true, COLL_MRT>})
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int slots = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&slots, fused_kernel<P, false>, NT, S::smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&slots, fused_kernel<P, false, COLL_SRT>, NT, S::smem);
     if (e != cudaSuccess) return e;
     if (slots < 1) return cudaErrorInvalidConfiguration;
     slots_per_sm = slots;
@@ -593,8 +600,13 @@ cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, i
   const int ntx = g.nx / TX;
   using T = typename Prec<P>::T;
   if (!diag) {
-    fused_kernel<P, false><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks, fz,
-                                                                 DiagOut{0.0, 0.0, nullptr, nullptr});
+    const DiagOut none{0.0, 0.0, nullptr, nullptr};
+    if (ph.coll == COLL_MRT)
+      fused_kernel<P, false, COLL_MRT><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
+                                                                             fz, none);
+    else
+      fused_kernel<P, false, COLL_SRT><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
+                                                                             fz, none);
     return cudaGetLastError();
   }
   const long long row_blocks = (long long)(g.ny / TY) * nchunks;
@@ -603,8 +615,13 @@ cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, i
   double* slices = diag->scratch;
   double* bl = slices + (size_t)row_blocks * g.nx * 2;
   double* slice_tot = bl + (size_t)blocks * DIAG_NG;
-  fused_kernel<P, true><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks, fz,
-                                                              DiagOut{diag->rho_l, diag->rho_v, slices, bl});
+  const DiagOut dg{diag->rho_l, diag->rho_v, slices, bl};
+  if (ph.coll == COLL_MRT)
+    fused_kernel<P, true, COLL_MRT><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
+                                                                          fz, dg);
+  else
+    fused_kernel<P, true, COLL_SRT><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
+                                                                          fz, dg);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_diag_reduce(g, (int)row_blocks, (int)blocks, slices, bl, slice_tot, diag->out, diag->ring_count,

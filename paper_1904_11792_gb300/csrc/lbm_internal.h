@@ -106,6 +106,9 @@ cudaError_t launch_diagnostics(int precision, int layout, const Geom& g, const P
                                double* out, void* psi, int* flag,
                                unsigned long long* ring_count, int ring_cap, cudaStream_t s);
 
+// Stochastic-rounding step salt (Phys::salt): set to value, or advance by one.
+cudaError_t launch_salt(unsigned* salt, bool set, unsigned value, cudaStream_t s);
+
 // Second and third stage of the diagnostics reduction from partials
 // slices[row_blocks][nx][2] and blocks[nblocks][DIAG_NG] (slice_tot: 2 nx
 // doubles of scratch); arguments after slice_tot as launch_diagnostics.
@@ -158,7 +161,7 @@ struct lbm_ctx {
   bool initialized = false;
   double rho_l = 1.0, rho_v = 0.0;
 
-  int* d_flag = nullptr;          // numeric flag
+  int* d_flag = nullptr;          // [0] numeric / timeout flag, [2] stochastic-rounding step salt
   double* d_small = nullptr;      // small result buffer (diagnostics out etc.)
   double* d_scratch = nullptr;    // diagnostics partials
   size_t scratch_doubles = 0;

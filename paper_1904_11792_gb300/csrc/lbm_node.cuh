@@ -378,7 +378,7 @@ __device__ __forceinline__ void collide_node(const Geom& g, const Phys& ph,
     collide_math_mrt<C>(ph, f, __ldg(psi + i), pn, fs);
   else
     collide_math<C>(ph, f, __ldg(psi + i), pn, fs);
-  const unsigned seed = (Prec<P>::dev && ph.sr) ? sr_seed(i, fs[0]) : 0u;
+  const unsigned seed = (Prec<P>::dev && ph.sr) ? sr_seed(i, fs[0], salt_of(ph)) : 0u;
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
     const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
@@ -486,7 +486,8 @@ __device__ __forceinline__ void collide_pair(const Geom& g, const Phys& ph,
     collide_math<C>(ph, f1, q[1][1][2], pn1, fs1);
   }
   const bool sr = Prec<P>::dev && ph.sr;
-  const unsigned seed0 = sr ? sr_seed(i0, fs0[0]) : 0u, seed1 = sr ? sr_seed(i0 + 1, fs1[0]) : 0u;
+  const unsigned salt = sr ? salt_of(ph) : 0u;
+  const unsigned seed0 = sr ? sr_seed(i0, fs0[0], salt) : 0u, seed1 = sr ? sr_seed(i0 + 1, fs1[0], salt) : 0u;
 
 #pragma unroll
   for (int a = 0; a < Q; ++a) {

@@ -104,7 +104,7 @@ def test_mrt_layouts_and_graphs_are_bitwise_equal(L, precision):
         with mrt_lattice(L, shape, 0.9, precision, pattern, rho_ref=0.1) as lat:
             lat.set_option("vector", vec)
             lat.set_option("graph", graph)
-            assert lat.get_option("fused") == 0      # the fused step is SRT only
+            assert lat.get_option("fused") == 0      # nx % 64 != 0: two-kernel step
             lat.set_populations(f0)
             lat.step(7)
             out.append(lat.populations())
@@ -144,3 +144,20 @@ def test_mrt_options_are_checked(L):
             assert ei.value.status == L.LBM_ERR_ARG
         with pytest.raises(L.LbmError):
             lat.set_option("collision", 2)
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16dev"])
+def test_mrt_fused_equals_two_kernel_step_bitwise(L, coex, precision):
+    rl, rv = coex
+    shape = (64, 16, 12)
+    out = []
+    for fused in (1, 0):
+        with mrt_lattice(L, shape, 0.8, precision, rho_ref=rv if precision.endswith("dev") else 0.0) as lat:
+            lat.set_option("fused", fused)
+            assert lat.get_option("fused") == fused
+            lat.init_ligament(4.0, 64.0, 0.1, 0.0, rl, rv, 2.0)
+            lat.set_option("diag_interval", 5)
+            lat.step(23)
+            out.append((lat.populations(), [h["liquid_count"] for h in lat.diag_history()]))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
