@@ -66,7 +66,10 @@ enum {
 };
 
 /* Storage precision of the populations.  Arithmetic is FP64 for LBM_F64
- * and FP32 otherwise.  The *DEV forms store g_a = f_a - w_a rho_ref. */
+ * and FP32 otherwise.  The *DEV forms store g_a = f_a - s_a with the shift
+ * s_a = w_a rho_ref rounded to the storage precision (FP16 or BF16), which
+ * keeps the shift's subtraction and addition exact in FP32 for liquid and
+ * vapour populations. */
 enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16DEV = 2, LBM_BF16DEV = 3 };
 
 /* Streaming pattern: two arrays (A-B, push), or one array updated in place
@@ -332,7 +335,7 @@ int lbm_batch_diagnostics(lbm_batch b, int k, lbm_diag *out, int want_ccl);
  *            storage layout with slot a of node i at f[a * N + i] (the current
  *            array of an A-B lattice, or an AA lattice after an even number of
  *            steps); for the *DEV precisions the stored deviations from
- *            w_a * rho_ref.
+ *            the shifts s_a (w_a * rho_ref rounded to the storage precision).
  *   out:     device array of 13 doubles: mass, momentum x, y, z, liquid volume
  *            (sum of phi), liquid node count, minimum slice area (phi), minimum
  *            slice node count, its x, max |j|/rho, min rho, max rho, 1 if every

@@ -9,7 +9,7 @@ namespace {
 
 template <int P>
 __device__ __forceinline__ double shift_d(int a, double rho_ref) {
-  return Prec<P>::dev ? wgt(a) * rho_ref : 0.0;
+  return Prec<P>::dev ? (double)storage_shift<P>(a, rho_ref) : 0.0;
 }
 
 __device__ __forceinline__ void coords(const Geom& g, long long i, int& x, int& y, int& z) {
@@ -188,9 +188,9 @@ __global__ void __launch_bounds__(DX* DY) diag_partial_kernel(Geom g, Phys ph,
   C rmin = (C)3.0e38, rmax = (C)-3.0e38;
   int cnt = 0;
   bool bad = false;
-  const C s0 = (C)(Prec<P>::dev ? wgt(0) * ph.rho_ref : 0.0);
-  const C s1 = (C)(Prec<P>::dev ? wgt(1) * ph.rho_ref : 0.0);
-  const C s2 = (C)(Prec<P>::dev ? wgt(7) * ph.rho_ref : 0.0);
+  const C s0 = (C)shift_d<P>(0, ph.rho_ref);
+  const C s1 = (C)shift_d<P>(1, ph.rho_ref);
+  const C s2 = (C)shift_d<P>(7, ph.rho_ref);
   if (x < g.nx) {
 #pragma unroll 2
     for (long long r = (long long)blockIdx.y * DY + ty; r < rows; r += (long long)DY * gridDim.y) {

@@ -26,7 +26,7 @@ template <int P>
 __device__ __forceinline__ typename Prec<P>::C shift_of(int a, double rho_ref) {
   using C = typename Prec<P>::C;
   if constexpr (Prec<P>::dev) {
-    return (C)(wgt(a) * rho_ref);
+    return (C)storage_shift<P>(a, rho_ref);
   } else {
     return (C)0;
   }
