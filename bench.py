@@ -335,7 +335,10 @@ def run_e2e(args, lat, L, torch, N):
     steps = args.steps * LBM_PER_STEP
     return {"value": round(N * steps / (t1 - t0) / 1e9, 4), "unit": UNIT,
             "h2d_bytes_per_step": int(nbytes // args.steps),
-            "d2h_bytes_per_step": int(ctypes.sizeof(L.lbm_diag) + 8 * N // args.steps)}
+            "d2h_bytes_per_step": int(ctypes.sizeof(L.lbm_diag) + 8 * N // args.steps),
+            "note": "host wall clock around the C ABI calls: state upload, graph-replayed steps "
+                    "with a diagnostics read-back each benchmark step, density download; the "
+                    "device-timed value records per-kernel events, so its launches are eager"}
 
 
 def cpu_baseline(w, rho_l, rho_v, budget_s: float = 12.0):

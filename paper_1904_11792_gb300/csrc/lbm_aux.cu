@@ -33,16 +33,11 @@ __device__ __forceinline__ void node_rho_j(const Geom& g, const Phys& ph, int la
                                            const typename Prec<P>::T* f, const Nbr& nb,
                                            typename Prec<P>::C& rho, typename Prec<P>::C j[3]) {
   using C = typename Prec<P>::C;
-  rho = 0;
-  j[0] = j[1] = j[2] = 0;
+  C v[Q];
 #pragma unroll
-  for (int a = 0; a < Q; ++a) {
-    const C v = Prec<P>::load(f + slot_index(g, layout, a, nb), (C)shift_d<P>(a, ph.rho_ref));
-    rho += v;
-    if (cx(a)) j[0] += cx(a) > 0 ? v : -v;
-    if (cy(a)) j[1] += cy(a) > 0 ? v : -v;
-    if (cz(a)) j[2] += cz(a) > 0 ? v : -v;
-  }
+  for (int a = 0; a < Q; ++a) v[a] = Prec<P>::load(f + slot_index(g, layout, a, nb), (C)shift_d<P>(a, ph.rho_ref));
+  rho = rho_of<C>(v);
+  mom_of<C>(v, j[0], j[1], j[2]);
 }
 
 // ---------------------------------------------------------------------------
@@ -208,14 +203,9 @@ __global__ void __launch_bounds__(DX* DY) diag_partial_kernel(Geom g, Phys ph,
           fv[a] = Prec<P>::load(f + (long long)opp(a) * g.N + nb.idx(-cx(a), -cy(a), -cz(a)),
                                 a == 0 ? s0 : (a <= 6 ? s1 : s2));
       }
-      C rho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        rho += fv[a];
-        if (cx(a)) jx += cx(a) > 0 ? fv[a] : -fv[a];
-        if (cy(a)) jy += cy(a) > 0 ? fv[a] : -fv[a];
-        if (cz(a)) jz += cz(a) > 0 ? fv[a] : -fv[a];
-      }
+      const C rho = rho_of<C>(fv);
+      C jx, jy, jz;
+      mom_of<C>(fv, jx, jy, jz);
       if constexpr (WRITE_PSI) psi[i] = psi_of<C>(rho, ph.psi_form, (C)ph.rho0);
       s_mass += rho;
       s_jx += jx;

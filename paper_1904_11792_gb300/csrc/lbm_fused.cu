@@ -270,15 +270,11 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
     psi_math<C>(ph, r0, &p0, flag);
     psi_math<C>(ph, r1, &p1, flag);
     if constexpr (DIAG) {
-      // momentum of the two nodes (same order of terms as the two-kernel
+      // momentum of the two nodes (the summation order of the two-kernel
       // diagnostics)
-      C jv[2][3] = {{0, 0, 0}, {0, 0, 0}};
-#pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        if (cx(a)) { jv[0][0] += cx(a) > 0 ? f0[a] : -f0[a]; jv[1][0] += cx(a) > 0 ? f1[a] : -f1[a]; }
-        if (cy(a)) { jv[0][1] += cy(a) > 0 ? f0[a] : -f0[a]; jv[1][1] += cy(a) > 0 ? f1[a] : -f1[a]; }
-        if (cz(a)) { jv[0][2] += cz(a) > 0 ? f0[a] : -f0[a]; jv[1][2] += cz(a) > 0 ? f1[a] : -f1[a]; }
-      }
+      C jv[2][3];
+      mom_of<C>(f0, jv[0][0], jv[0][1], jv[0][2]);
+      mom_of<C>(f1, jv[1][0], jv[1][1], jv[1][2]);
       if (k >= 1 && k <= np - 2) {
 #pragma unroll
         for (int n = 0; n < 2; ++n) {

@@ -86,31 +86,11 @@ template <typename C>
 __device__ __forceinline__ void collide_math_mrt(const Phys& ph, const C f[Q], C pc, const C pn[Q],
                                                  C fs[Q]) {
   // Eq. 4 and Eq. 5, as in collide_math
-  C rho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-  for (int a = 0; a < Q; ++a) {
-    rho += f[a];
-    if (cx(a) > 0) jx += f[a];
-    if (cx(a) < 0) jx -= f[a];
-    if (cy(a) > 0) jy += f[a];
-    if (cy(a) < 0) jy -= f[a];
-    if (cz(a) > 0) jz += f[a];
-    if (cz(a) < 0) jz -= f[a];
-  }
-  C ax = 0, ay = 0, az = 0, dx = 0, dy = 0, dz = 0;
-#pragma unroll
-  for (int a = 1; a < Q; ++a) {
-    const C p = pn[a];
-    if (a <= 6) {
-      if (cx(a)) ax += cx(a) > 0 ? p : -p;
-      if (cy(a)) ay += cy(a) > 0 ? p : -p;
-      if (cz(a)) az += cz(a) > 0 ? p : -p;
-    } else {
-      if (cx(a)) dx += cx(a) > 0 ? p : -p;
-      if (cy(a)) dy += cy(a) > 0 ? p : -p;
-      if (cz(a)) dz += cz(a) > 0 ? p : -p;
-    }
-  }
+  const C rho = rho_of<C>(f);
+  C jx, jy, jz;
+  mom_of<C>(f, jx, jy, jz);
+  C ax, ay, az, dx, dy, dz;
+  link_sums<C>(pn, ax, ay, az, dx, dy, dz);
   const C w1 = (C)(1.0 / 18.0), w2 = (C)(1.0 / 36.0);
   // products through xmul / xfma: the same bits in every kernel (see
   // collide_math)

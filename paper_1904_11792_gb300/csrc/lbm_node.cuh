@@ -126,46 +126,18 @@ __device__ __forceinline__ void store_pop(const Phys& ph, typename Prec<P>::T* p
 // arithmetic of one node
 // ---------------------------------------------------------------------------
 
-template <typename C>
-__device__ __forceinline__ C rho_of(const C f[Q]) {
-  C rho = 0;
-#pragma unroll
-  for (int a = 0; a < Q; ++a) rho += f[a];
-  return rho;
-}
-
 // Post-collision populations fs of a node with populations f, psi(x) = pc
 // and neighbour values pn[a] = psi(x + c_a) (a = 1..18).
 template <typename C>
 __device__ __forceinline__ void collide_math(const Phys& ph, const C f[Q], C pc, const C pn[Q],
                                              C fs[Q]) {
   // Eq. 4
-  C rho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-  for (int a = 0; a < Q; ++a) {
-    rho += f[a];
-    if (cx(a) > 0) jx += f[a];
-    if (cx(a) < 0) jx -= f[a];
-    if (cy(a) > 0) jy += f[a];
-    if (cy(a) < 0) jy -= f[a];
-    if (cz(a) > 0) jz += f[a];
-    if (cz(a) < 0) jz -= f[a];
-  }
+  const C rho = rho_of<C>(f);
+  C jx, jy, jz;
+  mom_of<C>(f, jx, jy, jz);
   // Eq. 5: sum_a w_a psi(x + c_a) c_a, split by weight class
-  C ax = 0, ay = 0, az = 0, dx = 0, dy = 0, dz = 0;
-#pragma unroll
-  for (int a = 1; a < Q; ++a) {
-    const C p = pn[a];
-    if (a <= 6) {
-      if (cx(a)) ax += cx(a) > 0 ? p : -p;
-      if (cy(a)) ay += cy(a) > 0 ? p : -p;
-      if (cz(a)) az += cz(a) > 0 ? p : -p;
-    } else {
-      if (cx(a)) dx += cx(a) > 0 ? p : -p;
-      if (cy(a)) dy += cy(a) > 0 ? p : -p;
-      if (cz(a)) dz += cz(a) > 0 ? p : -p;
-    }
-  }
+  C ax, ay, az, dx, dy, dz;
+  link_sums<C>(pn, ax, ay, az, dx, dy, dz);
   // Products and sums below go through xmul / xfma (round to nearest, fused
   // only where written), so every kernel that inlines this function computes
   // the same bits whatever the compiler's contraction choices around it.
