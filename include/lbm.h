@@ -163,7 +163,11 @@ int lbm_set_stream(lbm_handle h, void *stream);
  * lattices take the two-kernel step; results equal the two-kernel step
  * bitwise; lbm_get_option answers whether it applies), "fused_fz" (z planes
  * each block of the fused step marches through; 0 = chosen from the lattice
- * size and the GPU, the default),
+ * size and the GPU, the default), "fused_stall_test" (a test hook of the
+ * failure path, in ms, 0..10, default 0: while > 0 every block of the fused
+ * step also waits that long on a barrier that nothing completes, so its
+ * bounded wait gives up, the step's result is void and lbm_sync returns
+ * LBM_ERR_TIMEOUT; the waits on real copies give up after 2 s),
  * "stochastic_rounding" (0/1, default 1 for LBM_F16DEV / LBM_BF16DEV: the
  * stored deviations are rounded up or down with probability given by the
  * discarded fraction, from a hash of the node index and its post-collision

@@ -160,9 +160,9 @@ int enqueue_step(lbm_ctx* h, cudaStream_t s, long long step, int cur, bool timed
     if (diag_step) {
       const FusedDiag fd{h->rho_l, h->rho_v, h->d_scratch, h->scratch_doubles, h->d_ring, h->d_ring_count,
                          lbm_ctx::kRing};
-      CK(launch_fused(prec, h->g, h->ph, src, dst, h->d_flag, h->fused_fz, &fd, s));
+      CK(launch_fused(prec, h->g, h->ph, src, dst, h->d_flag, h->fused_fz, &fd, h->fused_stall_test_ns, s));
     } else {
-      CK(launch_fused(prec, h->g, h->ph, src, dst, h->d_flag, h->fused_fz, nullptr, s));
+      CK(launch_fused(prec, h->g, h->ph, src, dst, h->d_flag, h->fused_fz, nullptr, h->fused_stall_test_ns, s));
     }
     if (timed) {
       CK(cudaEventRecord(e1, s));
@@ -571,6 +571,10 @@ int lbm_set_option(lbm_handle h, const char* key, double v) {
       int rc = ensure_scratch(h);
       if (rc) return rc;
     }
+  } else if (k == "fused_stall_test") {
+    if (!(v >= 0.0 && v <= 10.0)) return fail(LBM_ERR_ARG, "fused_stall_test must be in 0..10 ms");
+    h->fused_stall_test_ns = (unsigned long long)(v * 1e6);
+    drop_graphs(h);
   } else if (k == "fused_fz") {
     const long long z = (long long)v;
     if (z < 0 || z > h->g.nz || (double)z != v) return fail(LBM_ERR_ARG, "fused_fz must be an integer in 0..nz");
@@ -647,6 +651,7 @@ int lbm_get_option(lbm_handle h, const char* key, double* v) {
   else if (k == "fused")
     *v = h->fused && h->cfg.pattern == LBM_AB && fused_applicable(h->g, h->cfg.precision);
   else if (k == "fused_fz") *v = h->fused_fz;
+  else if (k == "fused_stall_test") *v = h->fused_stall_test_ns * 1e-6;
   else if (k == "collision") *v = h->ph.coll;
   else if (k == "mrt_s_e") *v = h->ph.s_e;
   else if (k == "mrt_s_eps") *v = h->ph.s_eps;

@@ -52,7 +52,7 @@ constexpr int RW = TX + 4;   // ring row: position x - x0 + 2 (pairs start 8-byt
 constexpr int RH = TY + 2;
 constexpr int HC = 2 * (TX + 2) + 2 * TY;   // halo cells of a plane
 constexpr int HPT = (HC + NT - 1) / NT;     // halo cells per thread
-constexpr long long kWaitLimit = 1ll << 22;  // bounded mbarrier polls (seconds)
+constexpr unsigned long long kWaitNs = 2000000000ull;   // a wait on a plane gives up after 2 s
 
 __host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) & ~size_t(127); }
 
@@ -76,7 +76,7 @@ template <int P> struct FusedShape {
   static constexpr size_t off_ring = NB * plane;
   static constexpr size_t ring_bytes = align128((size_t)NR * RH * RW * sizeof(C));
   static constexpr size_t off_bar = off_ring + ring_bytes;
-  static constexpr size_t smem = off_bar + NB * sizeof(unsigned long long);
+  static constexpr size_t smem = off_bar + (NB + 1) * sizeof(unsigned long long);   // + the test barrier
   static constexpr unsigned tx_bytes = (unsigned)(int_bytes + 2 * row_bytes + 2 * col_bytes + 4 * cor_bytes);
 };
 
@@ -100,11 +100,21 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return ok != 0;
 }
-// Polls the barrier at most kWaitLimit times; false if it did not complete.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
-  for (long long it = 0; it < kWaitLimit; ++it)
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Polls the barrier until its phase completes or limit_ns of wall time have
+// passed (the global nanosecond timer); false if it did not complete.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  unsigned long long limit_ns = kWaitNs) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-  return false;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
 }
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2,
                                             unsigned long long* bar) {
@@ -149,6 +159,9 @@ struct DiagOut {
   double rho_l, rho_v;
   double* slices;
   double* blocks;
+  // test hook (the timeout path of the bounded waits): > 0 makes every block
+  // also wait, for at most this many ns, on a barrier nothing completes
+  unsigned long long stall_test_ns;
 };
 
 // Blocks per SM the register budget must allow: 3 for 4-byte storage (its
@@ -230,7 +243,7 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
     // bit 2 of the flag: a block (of this launch or an earlier one) gave up
     // on a wait, the result is void; skip the work
     s_abort = (*(volatile int*)flag & 2) != 0;
-    for (int b = 0; b < NB; ++b) mbar_init(full + b, 1);
+    for (int b = 0; b < NB + 1; ++b) mbar_init(full + b, 1);   // full[NB]: the test barrier
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
@@ -251,7 +264,8 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
   int k = 0;
   for (; k < np; ++k) {
     const int b = k % NB;
-    const bool ok = mbar_wait_bounded(full + b, (unsigned)((k / NB) & 1));
+    bool ok = mbar_wait_bounded(full + b, (unsigned)((k / NB) & 1));
+    if (k == 0 && dg.stall_test_ns) ok = ok && mbar_wait_bounded(full + NB, 0u, dg.stall_test_ns);
     const T* buf = reinterpret_cast<const T*>(smem + (size_t)b * S::plane);
     C* slot = ring + (k % NR) * RH * RW;
     // psi of this thread's two nodes of plane zplane(k)
@@ -584,7 +598,7 @@ cudaError_t fused_grid(const Geom& g, int fz_req, int* fz, int* nchunks, long lo
 
 template <int P>
 cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, int* flag, int fz_req,
-                    const FusedDiag* diag, cudaStream_t s) {
+                    const FusedDiag* diag, unsigned long long stall_ns, cudaStream_t s) {
   using S = FusedShape<P>;
   int fz = 0, nchunks = 0;
   long long blocks = 0;
@@ -596,7 +610,7 @@ cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, i
   const int ntx = g.nx / TX;
   using T = typename Prec<P>::T;
   if (!diag) {
-    const DiagOut none{0.0, 0.0, nullptr, nullptr};
+    const DiagOut none{0.0, 0.0, nullptr, nullptr, stall_ns};
     if (ph.coll == COLL_MRT)
       fused_kernel<P, false, COLL_MRT><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
                                                                              fz, none);
@@ -611,7 +625,7 @@ cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, i
   double* slices = diag->scratch;
   double* bl = slices + (size_t)row_blocks * g.nx * 2;
   double* slice_tot = bl + (size_t)blocks * DIAG_NG;
-  const DiagOut dg{diag->rho_l, diag->rho_v, slices, bl};
+  const DiagOut dg{diag->rho_l, diag->rho_v, slices, bl, stall_ns};
   if (ph.coll == COLL_MRT)
     fused_kernel<P, true, COLL_MRT><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
                                                                           fz, dg);
@@ -639,12 +653,12 @@ bool fused_applicable(const Geom& g, int precision) {
 }
 
 cudaError_t launch_fused(int precision, const Geom& g, const Phys& ph, const void* src, void* dst, int* flag,
-                         int fz, const FusedDiag* diag, cudaStream_t s) {
+                         int fz, const FusedDiag* diag, unsigned long long stall_ns, cudaStream_t s) {
   if (!fused_applicable(g, precision)) return cudaErrorInvalidValue;
   switch (precision) {
-    case LBM_F32: return fused_t<LBM_F32>(g, ph, src, dst, flag, fz, diag, s);
-    case LBM_F16DEV: return fused_t<LBM_F16DEV>(g, ph, src, dst, flag, fz, diag, s);
-    case LBM_BF16DEV: return fused_t<LBM_BF16DEV>(g, ph, src, dst, flag, fz, diag, s);
+    case LBM_F32: return fused_t<LBM_F32>(g, ph, src, dst, flag, fz, diag, stall_ns, s);
+    case LBM_F16DEV: return fused_t<LBM_F16DEV>(g, ph, src, dst, flag, fz, diag, stall_ns, s);
+    case LBM_BF16DEV: return fused_t<LBM_BF16DEV>(g, ph, src, dst, flag, fz, diag, stall_ns, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -63,8 +63,10 @@ struct FusedDiag {
   unsigned long long* ring_count;
   int ring_cap;
 };
+// stall_ns > 0 (test hook): every block also waits that long, bounded, on a
+// barrier nothing completes, so the launch takes its timeout path.
 cudaError_t launch_fused(int precision, const Geom& g, const Phys& ph, const void* src, void* dst,
-                         int* flag, int fz, const FusedDiag* diag, cudaStream_t s);
+                         int* flag, int fz, const FusedDiag* diag, unsigned long long stall_ns, cudaStream_t s);
 size_t fused_diag_scratch_doubles(const Geom& g, int precision, int fz);
 
 // ---- auxiliary kernels (lbm_aux.cu) ---------------------------------------
@@ -180,6 +182,7 @@ struct lbm_ctx {
   bool vec = true;                // two nodes per thread (when nx is even)
   bool fused = true;              // single-pass fused step on non-diagnostic A-B steps (where it applies)
   int fused_fz = 0;               // z planes per block of the fused step (0 = automatic)
+  unsigned long long fused_stall_test_ns = 0;   // test hook of the fused step's timeout path
 
   // diagnostics inside the time loop: every diag_interval steps the psi
   // pass also reduces the diagnostics into a device ring of records

@@ -600,3 +600,30 @@ def test_uniform_liquid_keeps_its_mass(L, coex, precision, tol):
         lat.step(2000)
         m1 = lat.diagnostics()["mass"]
     assert abs(m1 / m0 - 1.0) < tol
+
+
+# Failure detection without a GPU fault: the fused step's waits on its plane
+# copies are bounded in time.  The test hook makes every block also wait
+# (1 ms) on a barrier nothing completes; the step is reported void through
+# LBM_ERR_TIMEOUT, and the context keeps working.
+def test_fused_wait_timeout_is_reported_and_recoverable(L):
+    shape = (64, 16, 12)
+    f0 = lbm_inputs.random_populations(*shape, seed=7)
+    with make(L, shape, 0.9, -5.5, "f32") as lat:
+        assert lat.get_option("fused") == 1
+        lat.set_populations(f0)
+        lat.set_option("fused_stall_test", 1.0)
+        lat.step(1)
+        with pytest.raises(L.LbmError) as ei:
+            lat.sync()
+        assert ei.value.status == L.LBM_ERR_TIMEOUT
+        lat.set_option("fused_stall_test", 0)
+        lat.set_populations(f0)
+        lat.step(3)
+        lat.sync()
+        got = lat.populations()
+    with make(L, shape, 0.9, -5.5, "f32") as lat:
+        lat.set_populations(f0)
+        lat.step(3)
+        want = lat.populations()
+    np.testing.assert_array_equal(got, want)
