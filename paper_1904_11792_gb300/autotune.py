@@ -64,9 +64,10 @@ def _fits(block, nx):
 
 def tune_lattice(nx, ny, nz, precision="f32", patterns=("ab", "aa"), blocks=DEFAULT_BLOCKS,
                  occupancies=DEFAULT_OCC, tau=1.0, G=-6.0, steps=20, use_cache=True,
-                 verbose=False, fused_runs=(8, 16, 32)) -> dict:
+                 verbose=False, fused_runs=(8, 16, 32), reps=3) -> dict:
     """Best (pattern, fused, block, occupancy) for one lattice; returns a dict
-    with the choice and the measured per-step time and GLUPS."""
+    with the choice and the measured per-step time (best of `reps` timings of
+    `steps` steps) and GLUPS."""
     import torch
     key = _key("lattice", (nx, ny, nz), precision, ",".join(patterns))
     cache = _load_cache() if use_cache else {}
@@ -81,16 +82,23 @@ def tune_lattice(nx, ny, nz, precision="f32", patterns=("ab", "aa"), blocks=DEFA
                        rho_ref=rv if precision.endswith("dev") else 0.0) as lat:
             lat.init_ligament(min(ny, nz) / 4.0, float(nx), 0.02, 0.0, rl, rv, 2.0)
             lat.set_option("fused", 1)
+            # the GPU leaves its idle clocks during the first few milliseconds
+            # of work: warm up before the first trial, and keep the best of
+            # `reps` timings of each candidate
+            lat.step(max(40, steps))
+            torch.cuda.synchronize()
             if lat.get_option("fused"):
                 for fz in (0,) + tuple(z for z in fused_runs if z < nz):
                     lat.set_option("fused_fz", fz)
                     lat.step(4)
                     torch.cuda.synchronize()
-                    lat.set_option("kernel_timing", 1)
-                    lat.step(steps)
-                    n2, ms2 = L.lbm_kernel_time(lat.h, 2)
-                    lat.set_option("kernel_timing", 0)
-                    step_ms = ms2 / max(n2, 1)
+                    step_ms = float("inf")
+                    for _ in range(reps):
+                        lat.set_option("kernel_timing", 1)
+                        lat.step(steps)
+                        n2, ms2 = L.lbm_kernel_time(lat.h, 2)
+                        lat.set_option("kernel_timing", 0)
+                        step_ms = min(step_ms, ms2 / max(n2, 1))
                     t = dict(pattern=pattern, fused=1, fused_fz=fz, block=[0, 0, 0], occupancy=0,
                              step_ms=step_ms, glups=N / (step_ms * 1e-3) / 1e9)
                     trials.append(t)
@@ -111,12 +119,14 @@ def tune_lattice(nx, ny, nz, precision="f32", patterns=("ab", "aa"), blocks=DEFA
                     lat.set_option("occupancy", occ)
                     lat.step(4)
                     torch.cuda.synchronize()
-                    lat.set_option("kernel_timing", 1)
-                    lat.step(steps)
-                    n0, ms0 = L.lbm_kernel_time(lat.h, 0)
-                    n1, ms1 = L.lbm_kernel_time(lat.h, 1)
-                    lat.set_option("kernel_timing", 0)
-                    step_ms = ms0 / max(n0, 1) + ms1 / max(n1, 1)
+                    step_ms = float("inf")
+                    for _ in range(reps):
+                        lat.set_option("kernel_timing", 1)
+                        lat.step(steps)
+                        n0, ms0 = L.lbm_kernel_time(lat.h, 0)
+                        n1, ms1 = L.lbm_kernel_time(lat.h, 1)
+                        lat.set_option("kernel_timing", 0)
+                        step_ms = min(step_ms, ms0 / max(n0, 1) + ms1 / max(n1, 1))
                     t = dict(pattern=pattern, fused=0, block=list(b), occupancy=occ, step_ms=step_ms,
                              glups=N / (step_ms * 1e-3) / 1e9)
                     trials.append(t)

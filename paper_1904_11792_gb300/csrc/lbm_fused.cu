@@ -50,8 +50,6 @@ constexpr int NB = 2;    // plane buffers
 constexpr int NR = 4;    // psi ring slots
 constexpr int RW = TX + 4;   // ring row: position x - x0 + 2 (pairs start 8-byte aligned)
 constexpr int RH = TY + 2;
-constexpr int HC = 2 * (TX + 2) + 2 * TY;   // halo cells of a plane
-constexpr int HPT = (HC + NT - 1) / NT;     // halo cells per thread
 constexpr unsigned long long kWaitNs = 2000000000ull;   // a wait on a plane gives up after 2 s
 
 __host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) & ~size_t(127); }
@@ -202,40 +200,32 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
   auto zwrap = [&](int p) { return p < 0 ? p + g.nz : (p >= g.nz ? p - g.nz : p); };
   auto zplane = [&](int k) { return zwrap(dir > 0 ? z0 - 1 + k : z1 - k); };   // plane of march index k
 
-  // this thread's halo cells: element offset in a plane buffer, stride
-  // between directions, and ring position
-  int h_off[HPT], h_str[HPT], h_ring[HPT];
-#pragma unroll
-  for (int j = 0; j < HPT; ++j) {
-    const int h = tid + j * NT;
-    int off = 0, str = 0, rr = 0, c = 0;
-    if (h < 2 * (TX + 2)) {
-      const int side = h >= TX + 2;             // 0: row y0 - 1, 1: row y0 + TY
-      const int i = h - side * (TX + 2);        // 0 .. TX + 1 <-> x0 - 1 .. x0 + TX
-      rr = side ? TY + 1 : 0;
-      c = i;
-      if (i == 0 || i == TX + 1) {
-        const int corner = 2 * side + (i == 0 ? 0 : 1);
-        off = (int)((S::off_cor + corner * S::cor_stride) / S::E) + (i == 0 ? S::CW - 1 : 0);
-        str = S::CW;
-      } else {
-        off = (int)((side ? S::off_bot : S::off_top) / S::E) + (i - 1);
-        str = TX;
-      }
-    } else if (h < HC) {
-      const int i = h - 2 * (TX + 2);
-      const int side = i >= TY;                 // 0: column x0 - 1, 1: column x0 + TX
-      const int r = i - side * TY;
-      rr = r + 1;
-      c = side ? TX + 1 : 0;
-      off = (int)((side ? S::off_rgt : S::off_lft) / S::E) + r * S::CW + (side ? 0 : S::CW - 1);
-      str = TY * S::CW;
+  // psi of the halo ring of a plane: warps 0 and 1 take the rows y0 - 1 and
+  // y0 + TY over x0 .. x0 + TX - 1 as x pairs (like the interior), warps
+  // 2 .. TY - 1 the four corners and the 2 TY column cells, one per lane, so
+  // every warp makes one pass.  h_off: element offset in a plane buffer (-1:
+  // no cell), h_str: stride between directions (scalar cells), h_ring: ring
+  // position.
+  constexpr int SC = 4 + 2 * TY;                      // scalar halo cells
+  constexpr int SPW = (SC + TY - 3) / (TY - 2);       // scalar cells per warp
+  static_assert(TY >= 3 && SPW <= 32, "halo split needs two row warps and room for the cells");
+  int h_off = -1, h_str = 0, h_ring = 0;
+  if (ty < 2) {
+    h_off = (int)((ty ? S::off_bot : S::off_top) / S::E) + 2 * lane;
+    h_ring = (ty ? TY + 1 : 0) * RW + 2 * lane + 2;
+  } else if (lane < SPW && (ty - 2) * SPW + lane < SC) {
+    const int h = (ty - 2) * SPW + lane;
+    if (h < 4) {
+      const int side = h >> 1, right = h & 1;   // corners in the copy order of issue_plane
+      h_off = (int)((S::off_cor + h * S::cor_stride) / S::E) + (right ? 0 : S::CW - 1);
+      h_str = S::CW;
+      h_ring = (side ? TY + 1 : 0) * RW + (right ? TX + 2 : 1);
     } else {
-      off = -1;
+      const int i = h - 4, side = i >= TY, r = i - side * TY;   // side 0: column x0 - 1, 1: x0 + TX
+      h_off = (int)((side ? S::off_rgt : S::off_lft) / S::E) + r * S::CW + (side ? 0 : S::CW - 1);
+      h_str = TY * S::CW;
+      h_ring = (r + 1) * RW + (side ? TX + 2 : 1);
     }
-    h_off[j] = off;
-    h_str[j] = str;
-    h_ring[j] = rr * RW + c + 1;
   }
 
   __shared__ int s_abort;
@@ -276,8 +266,10 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
       cur[a] = *reinterpret_cast<const V*>(buf + (a * TY + ty) * TX + 2 * lane);
       Pair<P>::unpack(cur[a], f0[a], f1[a]);
       const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
-      f0[a] += sh;
-      f1[a] += sh;
+      if constexpr (Prec<P>::dev) {
+        f0[a] += sh;
+        f1[a] += sh;
+      }
     }
     C p0, p1;
     const C r0 = rho_of<C>(f0), r1 = rho_of<C>(f1);
@@ -316,15 +308,30 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
     else
       *reinterpret_cast<double2*>(slot + (ty + 1) * RW + 2 * lane + 2) = make_double2(p0, p1);
     // psi of this thread's halo cells
+    if (ty < 2) {
+      C fa[Q], fb[Q];
 #pragma unroll
-    for (int j = 0; j < HPT; ++j) {
-      if (h_off[j] >= 0) {
-        C fv[Q];
-#pragma unroll
-        for (int a = 0; a < Q; ++a)
-          fv[a] = Prec<P>::load_rw(buf + h_off[j] + a * h_str[j], a == 0 ? s0 : (a <= 6 ? s1 : s2));
-        psi_math<C>(ph, rho_of<C>(fv), slot + h_ring[j], flag);
+      for (int a = 0; a < Q; ++a) {
+        Pair<P>::unpack(*reinterpret_cast<const V*>(buf + h_off + a * TX), fa[a], fb[a]);
+        const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
+        if constexpr (Prec<P>::dev) {
+          fa[a] += sh;
+          fb[a] += sh;
+        }
       }
+      C pa, pb;
+      psi_math<C>(ph, rho_of<C>(fa), &pa, flag);
+      psi_math<C>(ph, rho_of<C>(fb), &pb, flag);
+      if constexpr (sizeof(C) == 4)
+        *reinterpret_cast<float2*>(slot + h_ring) = make_float2(pa, pb);
+      else
+        *reinterpret_cast<double2*>(slot + h_ring) = make_double2(pa, pb);
+    } else if (h_off >= 0) {
+      C fv[Q];
+#pragma unroll
+      for (int a = 0; a < Q; ++a)
+        fv[a] = Prec<P>::load_rw(buf + h_off + a * h_str, a == 0 ? s0 : (a <= 6 ? s1 : s2));
+      psi_math<C>(ph, rho_of<C>(fv), slot + h_ring, flag);
     }
     // every psi of plane zplane(k) is in the ring and buffer b is read out
     if (__syncthreads_or(!ok)) break;
@@ -367,8 +374,10 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
       for (int a = 0; a < Q; ++a) {
         Pair<P>::unpack(prev[a], g0[a], g1[a]);
         const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
-        g0[a] += sh;
-        g1[a] += sh;
+        if constexpr (Prec<P>::dev) {
+          g0[a] += sh;
+          g1[a] += sh;
+        }
       }
       pn0[0] = pn1[0] = 0;
 #pragma unroll

@@ -80,7 +80,9 @@ template <> struct Pair<LBM_BF16DEV> {
 };
 
 // Loads populations x and x + 1 (RO: read-only path; else a plain load for
-// in-place updates) and adds the deviation shift.
+// in-place updates) and adds the deviation shift.  Full-precision storage has
+// no shift and skips the add (x + 0 is not x for x = -0, so the compiler
+// keeps it otherwise), as Prec<P>::load does.
 template <int P, bool RO>
 __device__ __forceinline__ void load_pair(const typename Prec<P>::T* p, typename Prec<P>::C sh,
                                           typename Prec<P>::C& a, typename Prec<P>::C& b) {
@@ -91,8 +93,10 @@ __device__ __forceinline__ void load_pair(const typename Prec<P>::T* p, typename
   else
     v = *reinterpret_cast<const V*>(p);
   Pair<P>::unpack(v, a, b);
-  a += sh;
-  b += sh;
+  if constexpr (Prec<P>::dev) {
+    a += sh;
+    b += sh;
+  }
 }
 
 template <int P>
@@ -289,10 +293,10 @@ __device__ __forceinline__ void psi_quad(const Geom& g, const Phys& ph, const ty
     const typename Prec<P>::T* p = f + (long long)a * g.N + i;
     if constexpr (P == LBM_F32) {
       const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-      fv[0][a] = v.x + sh;
-      fv[1][a] = v.y + sh;
-      fv[2][a] = v.z + sh;
-      fv[3][a] = v.w + sh;
+      fv[0][a] = v.x;
+      fv[1][a] = v.y;
+      fv[2][a] = v.z;
+      fv[3][a] = v.w;
     } else {
       const uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
       typename Pair<P>::V lo, hi;
