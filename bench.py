@@ -98,17 +98,21 @@ def kernel_digest(fused: bool = False) -> str:
     return h.hexdigest()
 
 
-def ncu_traffic(precision: str, pattern: str, fused: bool = False):
+def ncu_traffic(workload: str, precision: str, pattern: str, fused: bool = False, fused_fz: int = 0,
+                fused_group: int = 0):
     """DRAM bytes per launch of the dominant kernel (collide-stream, or the
-    fused step) from the committed ncu summary, if it was taken on the
-    current kernel source; else None."""
+    fused step) from the committed ncu summary, if it was taken on this
+    workload, on the current kernel source and (fused step) with the same
+    run length and group options; else None."""
     p = os.path.join(ROOT, "profiles", "collide_stream_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    e = d.get("workloads", {}).get("%s/%s%s" % (precision, pattern, "/fused" if fused else ""))
+    e = d.get("workloads", {}).get("%s/%s/%s%s" % (workload, precision, pattern, "/fused" if fused else ""))
     if not e or e.get("kernel_source_sha256") != kernel_digest(fused):
+        return None
+    if fused and (e.get("fused_fz", 0), e.get("fused_group", 0)) != (fused_fz, fused_group):
         return None
     return float(e["dram_bytes_per_launch_full_size"])
 
@@ -185,7 +189,11 @@ def run_ours(args):
     torch.cuda.set_device(local)
     build.build()
     L.load()
-    w = WORKLOAD
+    w = lbm_inputs.GRID_1024 if args.workload == "grid1024" else WORKLOAD
+    if args.workload == "grid1024":
+        # 40.8 GB of FP32 populations: no host-buffer end-to-end leg and no
+        # CPU oracle sample at this size
+        args.no_extras = True
     N = w.nodes
     if args.rho_l and args.rho_v:
         rho_l, rho_v = args.rho_l, args.rho_v
@@ -196,7 +204,8 @@ def run_ours(args):
     from paper_1904_11792_gb300 import autotune
     patterns = ("ab", "aa") if args.pattern == "auto" else (args.pattern,)
     if args.no_tune:
-        choice = dict(pattern=patterns[-1], block=(128, 2, 1), occupancy=0, fused=int(args.fused))
+        choice = dict(pattern=patterns[-1], block=(128, 2, 1), occupancy=0, fused=int(args.fused),
+                      fused_fz=args.fused_fz, fused_group=args.fused_group)
     else:
         choice = autotune.tune_lattice(w.nx, w.ny, w.nz, precision=args.precision,
                                        patterns=patterns,
@@ -265,7 +274,8 @@ def run_ours(args):
     if args.precision.endswith("dev"):
         launches_per_step += LBM_PER_STEP   # the stochastic-rounding salt advance of each step
     achieved = bpl * N / (avg * 1e-3) / 1e9
-    traffic = ncu_traffic(args.precision, pattern, fused)
+    traffic = ncu_traffic(args.workload, args.precision, pattern, fused,
+                          int(choice.get("fused_fz", 0) or 0), int(choice.get("fused_group", 0) or 0))
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
@@ -278,7 +288,7 @@ def run_ours(args):
                         "streaming" % (w.nx, w.ny, w.nz, w.R0, w.lam, w.eps, w.tau, w.G,
                                        args.precision, pattern.upper()),
             "tuned": {"pattern": pattern, "fused": fused, "fused_fz": choice.get("fused_fz", 0),
-                      "block": choice["block"],
+                      "fused_group": choice.get("fused_group", 0), "block": choice["block"],
                       "occupancy": choice["occupancy"], "vector": True},
             "nodes": N, "lattice_steps_per_step": LBM_PER_STEP, "diagnostics_every": LBM_PER_STEP,
             "parallelism": "replicas" if world > 1 else "single GPU",
@@ -475,8 +485,9 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("grid256", "batch48"), default="grid256",
-                    help="grid256: the headline ligament; batch48: the batched sweep")
+    ap.add_argument("--workload", choices=("grid256", "grid1024", "batch48"), default="grid256",
+                    help="grid256: the headline ligament; grid1024: the 1024x512x512 ligament "
+                         "(268 M nodes; device legs only); batch48: the batched sweep")
     ap.add_argument("--precision", choices=("f32", "f64", "f16dev", "bf16dev"), default="f32")
     ap.add_argument("--pattern", choices=("auto", "ab", "aa"), default="auto",
                     help="streaming pattern; auto = the autotuner's choice")
@@ -486,6 +497,10 @@ def main():
     ap.add_argument("--fused", action="store_true",
                     help="with --no-tune: the single-pass fused step on non-diagnostic A-B steps "
                          "(the autotuner otherwise chooses)")
+    ap.add_argument("--fused-fz", type=int, default=0,
+                    help="with --no-tune --fused: z planes per block (0 = automatic)")
+    ap.add_argument("--fused-group", type=int, default=0,
+                    help="with --no-tune --fused: z runs per group of the block order (0 = automatic)")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (default launch configuration; profiling runs)")
     ap.add_argument("--no-extras", action="store_true",

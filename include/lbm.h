@@ -163,7 +163,11 @@ int lbm_set_stream(lbm_handle h, void *stream);
  * lattices take the two-kernel step; results equal the two-kernel step
  * bitwise; lbm_get_option answers whether it applies), "fused_fz" (z planes
  * each block of the fused step marches through; 0 = chosen from the lattice
- * size and the GPU, the default), "fused_stall_test" (a test hook of the
+ * size and the GPU, the default), "fused_group" (the fused step launches
+ * its blocks in groups of this many consecutive z runs, the run varying
+ * fastest inside a group, then the tile x, then the tile y; 0 = one run
+ * per 8 tile columns of 64 nodes, at least one, the default; any value
+ * gives the same results), "fused_stall_test" (a test hook of the
  * failure path, in ms, 0..10, default 0: while > 0 every block of the fused
  * step also waits that long on a barrier that nothing completes, so its
  * bounded wait gives up, the step's result is void and lbm_sync returns

@@ -64,7 +64,8 @@ def _fits(block, nx):
 
 def tune_lattice(nx, ny, nz, precision="f32", patterns=("ab", "aa"), blocks=DEFAULT_BLOCKS,
                  occupancies=DEFAULT_OCC, tau=1.0, G=-6.0, steps=20, use_cache=True,
-                 verbose=False, fused_runs=(8, 16, 32), reps=3) -> dict:
+                 verbose=False, fused_runs=(8, 12, 16, 24, 32), fused_groups=(1, 2, 4),
+                 reps=3) -> dict:
     """Best (pattern, fused, block, occupancy) for one lattice; returns a dict
     with the choice and the measured per-step time (best of `reps` timings of
     `steps` steps) and GLUPS."""
@@ -88,8 +89,10 @@ def tune_lattice(nx, ny, nz, precision="f32", patterns=("ab", "aa"), blocks=DEFA
             lat.step(max(40, steps))
             torch.cuda.synchronize()
             if lat.get_option("fused"):
-                for fz in (0,) + tuple(z for z in fused_runs if z < nz):
+                for fz, grp in [(z, gr) for z in (0,) + tuple(z for z in fused_runs if z < nz)
+                                for gr in (0,) + tuple(fused_groups)]:
                     lat.set_option("fused_fz", fz)
+                    lat.set_option("fused_group", grp)
                     lat.step(4)
                     torch.cuda.synchronize()
                     step_ms = float("inf")
@@ -99,7 +102,7 @@ def tune_lattice(nx, ny, nz, precision="f32", patterns=("ab", "aa"), blocks=DEFA
                         n2, ms2 = L.lbm_kernel_time(lat.h, 2)
                         lat.set_option("kernel_timing", 0)
                         step_ms = min(step_ms, ms2 / max(n2, 1))
-                    t = dict(pattern=pattern, fused=1, fused_fz=fz, block=[0, 0, 0], occupancy=0,
+                    t = dict(pattern=pattern, fused=1, fused_fz=fz, fused_group=grp, block=[0, 0, 0], occupancy=0,
                              step_ms=step_ms, glups=N / (step_ms * 1e-3) / 1e9)
                     trials.append(t)
                     if verbose:
@@ -107,6 +110,7 @@ def tune_lattice(nx, ny, nz, precision="f32", patterns=("ab", "aa"), blocks=DEFA
                     if best is None or step_ms < best["step_ms"]:
                         best = t
                 lat.set_option("fused_fz", 0)
+                lat.set_option("fused_group", 0)
             lat.set_option("fused", 0)
             for occ in occupancies:
                 for b in blocks:
@@ -149,6 +153,7 @@ def apply(lat: "L.Lattice", choice: dict) -> None:
     lat.set_option("fused", int(choice.get("fused", 0)))
     if choice.get("fused"):
         lat.set_option("fused_fz", int(choice.get("fused_fz", 0)))
+        lat.set_option("fused_group", int(choice.get("fused_group", 0)))
         return
     for k, v in zip(("block_x", "block_y", "block_z"), (1, 1, 1)):
         lat.set_option(k, v)

@@ -160,9 +160,9 @@ int enqueue_step(lbm_ctx* h, cudaStream_t s, long long step, int cur, bool timed
     if (diag_step) {
       const FusedDiag fd{h->rho_l, h->rho_v, h->d_scratch, h->scratch_doubles, h->d_ring, h->d_ring_count,
                          lbm_ctx::kRing};
-      CK(launch_fused(prec, h->g, h->ph, src, dst, h->d_flag, h->fused_fz, &fd, h->fused_stall_test_ns, s));
+      CK(launch_fused(prec, h->g, h->ph, src, dst, h->d_flag, h->fused_fz, h->fused_group, &fd, h->fused_stall_test_ns, s));
     } else {
-      CK(launch_fused(prec, h->g, h->ph, src, dst, h->d_flag, h->fused_fz, nullptr, h->fused_stall_test_ns, s));
+      CK(launch_fused(prec, h->g, h->ph, src, dst, h->d_flag, h->fused_fz, h->fused_group, nullptr, h->fused_stall_test_ns, s));
     }
     if (timed) {
       CK(cudaEventRecord(e1, s));
@@ -575,6 +575,12 @@ int lbm_set_option(lbm_handle h, const char* key, double v) {
     if (!(v >= 0.0 && v <= 10.0)) return fail(LBM_ERR_ARG, "fused_stall_test must be in 0..10 ms");
     h->fused_stall_test_ns = (unsigned long long)(v * 1e6);
     drop_graphs(h);
+  } else if (k == "fused_group") {
+    const long long gr = (long long)v;
+    if (gr < 0 || gr > (1LL << 20) || (double)gr != v)
+      return fail(LBM_ERR_ARG, "fused_group must be a non-negative integer");
+    h->fused_group = (int)gr;
+    drop_graphs(h);
   } else if (k == "fused_fz") {
     const long long z = (long long)v;
     if (z < 0 || z > h->g.nz || (double)z != v) return fail(LBM_ERR_ARG, "fused_fz must be an integer in 0..nz");
@@ -651,6 +657,7 @@ int lbm_get_option(lbm_handle h, const char* key, double* v) {
   else if (k == "fused")
     *v = h->fused && h->cfg.pattern == LBM_AB && fused_applicable(h->g, h->cfg.precision);
   else if (k == "fused_fz") *v = h->fused_fz;
+  else if (k == "fused_group") *v = h->fused_group;
   else if (k == "fused_stall_test") *v = h->fused_stall_test_ns * 1e-6;
   else if (k == "collision") *v = h->ph.coll;
   else if (k == "mrt_s_e") *v = h->ph.s_e;

@@ -173,7 +173,7 @@ constexpr int fused_minb() {
 template <int P, bool DIAG, int COLL>
 __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
     fused_kernel(const __grid_constant__ Maps maps, Geom g, Phys ph, typename Prec<P>::T* dst, int* flag, int ntx,
-                 int nchunks, int fz, DiagOut dg) {
+                 int nchunks, int fz, int grp, DiagOut dg) {
   using T = typename Prec<P>::T;
   using C = typename Prec<P>::C;
   using V = typename Pair<P>::V;
@@ -183,7 +183,15 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
   C* ring = reinterpret_cast<C*>(smem + S::off_ring);
 
   const int u = blockIdx.x;
-  const int chunk = u % nchunks, xy = u / nchunks;
+  // Block order: z runs in groups of grp consecutive runs; inside a group
+  // the run index varies fastest, then the tile x, then the tile y.  Blocks
+  // that share planes (the two runs either side of a run boundary, x- and
+  // y-neighbour tiles) are then launched close together, so the planes and
+  // halo rows they share are still in L2 when the second one reads them.
+  const int tiles = ntx * (g.ny / TY);
+  const int zg = u / (grp * tiles), r = u - zg * grp * tiles;
+  const int gs = min(grp, nchunks - zg * grp);   // runs in this group
+  const int chunk = zg * grp + r % gs, xy = r / gs;
   const int x0 = (xy % ntx) * TX, y0 = (xy / ntx) * TY;
   const int z0 = chunk * fz, z1 = min(z0 + fz, g.nz);
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
@@ -580,7 +588,8 @@ int choose_fz(const Geom& g, long long tiles, long long slots) {
 // first call per storage type sets the kernels' shared-memory limit and
 // reads the occupancy of the step kernel.
 template <int P>
-cudaError_t fused_grid(const Geom& g, int fz_req, int* fz, int* nchunks, long long* blocks) {
+cudaError_t fused_grid(const Geom& g, int fz_req, int grp_req, int* fz, int* nchunks, int* grp,
+                       long long* blocks) {
   using S = FusedShape<P>;
   static int slots_per_sm = 0, sms = 0;
   if (!slots_per_sm) {
@@ -602,16 +611,24 @@ cudaError_t fused_grid(const Geom& g, int fz_req, int* fz, int* nchunks, long lo
   *fz = fz_req > 0 ? std::min(fz_req, g.nz) : choose_fz(g, tiles, (long long)slots_per_sm * sms);
   *nchunks = (g.nz + *fz - 1) / *fz;
   *blocks = tiles * *nchunks;
+  // runs per group (a tile's y neighbours are ntx x grp blocks apart in the
+  // launch order).  Measured on GB300 (FP32, A-B): 256x128x128 is fastest
+  // with one run per group (0.117 ms against 0.127 ms with all 7 runs of a
+  // tile together), 512x256x256 within 2 % for 1 to 4, 1024x512x512 with 2
+  // (6.45 ms; 6.75 ms with 1, 7.21 ms with 4, 9.83 ms with all 32): one run
+  // per 8 tile columns
+  const int ntx = g.nx / TX;
+  *grp = std::min(grp_req > 0 ? grp_req : std::max(1, ntx / 8), *nchunks);
   return *blocks > 0x7fffffffLL ? cudaErrorInvalidConfiguration : cudaSuccess;
 }
 
 template <int P>
 cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, int* flag, int fz_req,
-                    const FusedDiag* diag, unsigned long long stall_ns, cudaStream_t s) {
+                    int grp_req, const FusedDiag* diag, unsigned long long stall_ns, cudaStream_t s) {
   using S = FusedShape<P>;
-  int fz = 0, nchunks = 0;
+  int fz = 0, nchunks = 0, grp = 0;
   long long blocks = 0;
-  cudaError_t e = fused_grid<P>(g, fz_req, &fz, &nchunks, &blocks);
+  cudaError_t e = fused_grid<P>(g, fz_req, grp_req, &fz, &nchunks, &grp, &blocks);
   if (e != cudaSuccess) return e;
   Maps m;
   e = maps_for(P, g, src, &m);
@@ -622,10 +639,10 @@ cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, i
     const DiagOut none{0.0, 0.0, nullptr, nullptr, stall_ns};
     if (ph.coll == COLL_MRT)
       fused_kernel<P, false, COLL_MRT><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
-                                                                             fz, none);
+                                                                             fz, grp, none);
     else
       fused_kernel<P, false, COLL_SRT><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
-                                                                             fz, none);
+                                                                             fz, grp, none);
     return cudaGetLastError();
   }
   const long long row_blocks = (long long)(g.ny / TY) * nchunks;
@@ -637,10 +654,10 @@ cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, i
   const DiagOut dg{diag->rho_l, diag->rho_v, slices, bl, stall_ns};
   if (ph.coll == COLL_MRT)
     fused_kernel<P, true, COLL_MRT><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
-                                                                          fz, dg);
+                                                                          fz, grp, dg);
   else
     fused_kernel<P, true, COLL_SRT><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
-                                                                          fz, dg);
+                                                                          fz, grp, dg);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_diag_reduce(g, (int)row_blocks, (int)blocks, slices, bl, slice_tot, diag->out, diag->ring_count,
@@ -649,9 +666,9 @@ cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, i
 
 template <int P>
 size_t fused_scratch_t(const Geom& g, int fz_req) {
-  int fz = 0, nchunks = 0;
+  int fz = 0, nchunks = 0, grp = 0;
   long long blocks = 0;
-  if (fused_grid<P>(g, fz_req, &fz, &nchunks, &blocks) != cudaSuccess) return 0;
+  if (fused_grid<P>(g, fz_req, 0, &fz, &nchunks, &grp, &blocks) != cudaSuccess) return 0;
   return (size_t)(g.ny / TY) * nchunks * g.nx * 2 + (size_t)blocks * DIAG_NG + (size_t)g.nx * 2;
 }
 
@@ -662,12 +679,12 @@ bool fused_applicable(const Geom& g, int precision) {
 }
 
 cudaError_t launch_fused(int precision, const Geom& g, const Phys& ph, const void* src, void* dst, int* flag,
-                         int fz, const FusedDiag* diag, unsigned long long stall_ns, cudaStream_t s) {
+                         int fz, int grp, const FusedDiag* diag, unsigned long long stall_ns, cudaStream_t s) {
   if (!fused_applicable(g, precision)) return cudaErrorInvalidValue;
   switch (precision) {
-    case LBM_F32: return fused_t<LBM_F32>(g, ph, src, dst, flag, fz, diag, stall_ns, s);
-    case LBM_F16DEV: return fused_t<LBM_F16DEV>(g, ph, src, dst, flag, fz, diag, stall_ns, s);
-    case LBM_BF16DEV: return fused_t<LBM_BF16DEV>(g, ph, src, dst, flag, fz, diag, stall_ns, s);
+    case LBM_F32: return fused_t<LBM_F32>(g, ph, src, dst, flag, fz, grp, diag, stall_ns, s);
+    case LBM_F16DEV: return fused_t<LBM_F16DEV>(g, ph, src, dst, flag, fz, grp, diag, stall_ns, s);
+    case LBM_BF16DEV: return fused_t<LBM_BF16DEV>(g, ph, src, dst, flag, fz, grp, diag, stall_ns, s);
   }
   return cudaErrorInvalidValue;
 }

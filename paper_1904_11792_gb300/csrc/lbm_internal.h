@@ -65,8 +65,11 @@ struct FusedDiag {
 };
 // stall_ns > 0 (test hook): every block also waits that long, bounded, on a
 // barrier nothing completes, so the launch takes its timeout path.
+// fz: z planes per block (0 = automatic); grp: z runs per group of the
+// block order (0 = automatic).
 cudaError_t launch_fused(int precision, const Geom& g, const Phys& ph, const void* src, void* dst,
-                         int* flag, int fz, const FusedDiag* diag, unsigned long long stall_ns, cudaStream_t s);
+                         int* flag, int fz, int grp, const FusedDiag* diag, unsigned long long stall_ns,
+                         cudaStream_t s);
 size_t fused_diag_scratch_doubles(const Geom& g, int precision, int fz);
 
 // ---- auxiliary kernels (lbm_aux.cu) ---------------------------------------
@@ -182,6 +185,7 @@ struct lbm_ctx {
   bool vec = true;                // two nodes per thread (when nx is even)
   bool fused = true;              // single-pass fused step on non-diagnostic A-B steps (where it applies)
   int fused_fz = 0;               // z planes per block of the fused step (0 = automatic)
+  int fused_group = 0;            // z runs per group of its block order (0 = automatic)
   unsigned long long fused_stall_test_ns = 0;   // test hook of the fused step's timeout path
 
   // diagnostics inside the time loop: every diag_interval steps the psi
