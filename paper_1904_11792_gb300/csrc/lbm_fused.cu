@@ -127,6 +127,41 @@ struct Maps {
   CUtensorMap interior, row, col, cor;
 };
 
+// Stored value to compute precision plus the deviation shift.  For 2-byte
+// storage one widening add (add.rn.f32.f16 / .bf16, sm_100 and later) does
+// both: the conversion is exact, so the result is the FP32 sum of the
+// converted value and the shift rounded once to nearest, the bits of the
+// conversion-then-add of the two-kernel step.
+__device__ __forceinline__ float add_wide(__half h, float c) {
+  float d;
+  asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(__half_as_ushort(h)), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float add_wide(__nv_bfloat16 h, float c) {
+  float d;
+  asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(__bfloat16_as_ushort(h)), "f"(c));
+  return d;
+}
+template <int P>
+__device__ __forceinline__ void unpack_shifted(typename Pair<P>::V v, float sh, float& a, float& b) {
+  if constexpr (P == LBM_F16DEV) {
+    a = add_wide(__low2half(v), sh);
+    b = add_wide(__high2half(v), sh);
+  } else if constexpr (P == LBM_BF16DEV) {
+    a = add_wide(__low2bfloat16(v), sh);
+    b = add_wide(__high2bfloat16(v), sh);
+  } else {
+    Pair<P>::unpack(v, a, b);   // full precision: no shift
+  }
+}
+template <int P>
+__device__ __forceinline__ float load_shifted(const typename Prec<P>::T* p, float sh) {
+  if constexpr (Prec<P>::dev)
+    return add_wide(*p, sh);
+  else
+    return *p;
+}
+
 // Issues the nine copies of plane zz into buffer b (one thread).
 template <int P>
 __device__ __forceinline__ void issue_plane(unsigned char* smem, const Maps& m, int b, int x0, int y0, int xl,
@@ -272,12 +307,7 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
       cur[a] = *reinterpret_cast<const V*>(buf + (a * TY + ty) * TX + 2 * lane);
-      Pair<P>::unpack(cur[a], f0[a], f1[a]);
-      const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
-      if constexpr (Prec<P>::dev) {
-        f0[a] += sh;
-        f1[a] += sh;
-      }
+      unpack_shifted<P>(cur[a], a == 0 ? s0 : (a <= 6 ? s1 : s2), f0[a], f1[a]);
     }
     C p0, p1;
     const C r0 = rho_of<C>(f0), r1 = rho_of<C>(f1);
@@ -320,12 +350,8 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
       C fa[Q], fb[Q];
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
-        Pair<P>::unpack(*reinterpret_cast<const V*>(buf + h_off + a * TX), fa[a], fb[a]);
-        const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
-        if constexpr (Prec<P>::dev) {
-          fa[a] += sh;
-          fb[a] += sh;
-        }
+        unpack_shifted<P>(*reinterpret_cast<const V*>(buf + h_off + a * TX), a == 0 ? s0 : (a <= 6 ? s1 : s2),
+                          fa[a], fb[a]);
       }
       C pa, pb;
       psi_math<C>(ph, rho_of<C>(fa), &pa, flag);
@@ -338,7 +364,7 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
       C fv[Q];
 #pragma unroll
       for (int a = 0; a < Q; ++a)
-        fv[a] = Prec<P>::load_rw(buf + h_off + a * h_str, a == 0 ? s0 : (a <= 6 ? s1 : s2));
+        fv[a] = load_shifted<P>(buf + h_off + a * h_str, a == 0 ? s0 : (a <= 6 ? s1 : s2));
       psi_math<C>(ph, rho_of<C>(fv), slot + h_ring, flag);
     }
     // every psi of plane zplane(k) is in the ring and buffer b is read out
@@ -380,12 +406,7 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
       C g0[Q], g1[Q], pn0[Q], pn1[Q];
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
-        Pair<P>::unpack(prev[a], g0[a], g1[a]);
-        const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
-        if constexpr (Prec<P>::dev) {
-          g0[a] += sh;
-          g1[a] += sh;
-        }
+        unpack_shifted<P>(prev[a], a == 0 ? s0 : (a <= 6 ? s1 : s2), g0[a], g1[a]);
       }
       pn0[0] = pn1[0] = 0;
 #pragma unroll
