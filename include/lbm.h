@@ -167,7 +167,10 @@ int lbm_set_stream(lbm_handle h, void *stream);
  * its blocks in groups of this many consecutive z runs, the run varying
  * fastest inside a group, then the tile x, then the tile y; 0 = one run
  * per 8 tile columns of 64 nodes, at least one, the default; any value
- * gives the same results), "fused_stall_test" (a test hook of the
+ * gives the same results), "fused_fz_used" and "fused_group_used" (get
+ * only: the run length and runs per group the fused step launches with for
+ * the current options; 0 where the fused step does not apply),
+ * "fused_stall_test" (a test hook of the
  * failure path, in ms, 0..10, default 0: while > 0 every block of the fused
  * step also waits that long on a barrier that nothing completes, so its
  * bounded wait gives up, the step's result is void and lbm_sync returns

@@ -658,6 +658,14 @@ int lbm_get_option(lbm_handle h, const char* key, double* v) {
     *v = h->fused && h->cfg.pattern == LBM_AB && fused_applicable(h->g, h->cfg.precision);
   else if (k == "fused_fz") *v = h->fused_fz;
   else if (k == "fused_group") *v = h->fused_group;
+  else if (k == "fused_fz_used" || k == "fused_group_used") {
+    int fz = 0, grp = 0;
+    if (fused_applicable(h->g, h->cfg.precision)) {
+      const cudaError_t e = fused_launch_shape(h->cfg.precision, h->g, h->fused_fz, h->fused_group, &fz, &grp);
+      if (e != cudaSuccess) return cuda_fail(e, "fused launch shape");
+    }
+    *v = k == "fused_fz_used" ? fz : grp;
+  }
   else if (k == "fused_stall_test") *v = h->fused_stall_test_ns * 1e-6;
   else if (k == "collision") *v = h->ph.coll;
   else if (k == "mrt_s_e") *v = h->ph.s_e;

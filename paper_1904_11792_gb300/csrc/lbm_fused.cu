@@ -585,17 +585,21 @@ cudaError_t maps_for(int precision, const Geom& g, const void* base, Maps* out) 
 
 // z planes per block.  Each block also loads the two planes around its run,
 // and a grid that leaves SMs idle in its last wave wastes their bandwidth:
-// the cost of a run length is waves x planes loaded per block.  Long runs
-// also let neighbouring tiles drift apart in z, so the halo rows one tile
-// reads are no longer in L2 from its neighbour's read of the same plane
-// (measured on GB300: 1024x512x512 takes 9.6 ms per step with 16-plane runs,
-// 10.5 ms with 256-plane runs); the factor (1 + fz/256) charges for that.
+// the cost of a run length is waves x planes loaded per block, times
+// (1 + fz/256) for long runs.  On grids of many waves long runs cost more
+// than that (measured on GB300, 1024x512x512 in groups of runs: 12-, 16-,
+// 19-, 24- and 32-plane runs take 6.5, 6.4, 7.0, 7.7 and 8.2 ms per step:
+// the longer a block lives, the further apart in time neighbouring tiles
+// read the rows they share), so there runs stop at 16 planes; small grids
+// (256x128x128: 1.96 waves of 19-plane runs, 0.114 ms, against 0.126 ms for
+// 16-plane runs in 2.25 waves) keep the wave count low instead.
 int choose_fz(const Geom& g, long long tiles, long long slots) {
   int best = g.nz;
   double best_cost = -1.0;
   for (int fz = 4; fz <= g.nz; ++fz) {
     const long long chunks = (g.nz + fz - 1) / fz;
     const long long waves = (tiles * chunks + slots - 1) / slots;
+    if (fz > 16 && waves > 8) continue;
     const double cost = (double)waves * (fz + 2) * (1.0 + fz / 256.0);
     if (best_cost < 0.0 || cost < best_cost) {
       best_cost = cost;
@@ -694,6 +698,17 @@ size_t fused_scratch_t(const Geom& g, int fz_req) {
 }
 
 }  // namespace
+
+cudaError_t fused_launch_shape(int precision, const Geom& g, int fz_req, int grp_req, int* fz, int* grp) {
+  int nchunks = 0;
+  long long blocks = 0;
+  switch (precision) {
+    case LBM_F32: return fused_grid<LBM_F32>(g, fz_req, grp_req, fz, &nchunks, grp, &blocks);
+    case LBM_F16DEV: return fused_grid<LBM_F16DEV>(g, fz_req, grp_req, fz, &nchunks, grp, &blocks);
+    case LBM_BF16DEV: return fused_grid<LBM_BF16DEV>(g, fz_req, grp_req, fz, &nchunks, grp, &blocks);
+  }
+  return cudaErrorInvalidValue;
+}
 
 bool fused_applicable(const Geom& g, int precision) {
   return precision != LBM_F64 && g.nx % TX == 0 && g.ny % TY == 0 && g.nz >= 3;

@@ -65,6 +65,9 @@ struct FusedDiag {
 };
 // stall_ns > 0 (test hook): every block also waits that long, bounded, on a
 // barrier nothing completes, so the launch takes its timeout path.
+// The run length and runs per group the fused step launches with for the
+// requested values (0 = automatic).
+cudaError_t fused_launch_shape(int precision, const Geom& g, int fz_req, int grp_req, int* fz, int* grp);
 // fz: z planes per block (0 = automatic); grp: z runs per group of the
 // block order (0 = automatic).
 cudaError_t launch_fused(int precision, const Geom& g, const Phys& ph, const void* src, void* dst,

@@ -655,3 +655,19 @@ def test_fused_group_order_is_bitwise_neutral(L, precision):
         np.testing.assert_array_equal(f, ref_f, err_msg=str(key))
         if key[0] == 1:
             assert tuple(diag) == ref_diag, key
+
+
+def test_fused_launch_shape_is_reported(L):
+    # the run length and runs per group the fused step launches with
+    with make(L, (128, 8, 40), 0.9, -5.5, "f32") as lat:
+        lat.set_option("fused_fz", 8)
+        lat.set_option("fused_group", 2)
+        assert (lat.get_option("fused_fz_used"), lat.get_option("fused_group_used")) == (8, 2)
+        lat.set_option("fused_group", 100)          # at most the 5 runs there are
+        assert lat.get_option("fused_group_used") == 5
+        lat.set_option("fused_fz", 0)
+        lat.set_option("fused_group", 0)
+        fz, grp = lat.get_option("fused_fz_used"), lat.get_option("fused_group_used")
+        assert 4 <= fz <= 40 and 1 <= grp <= -(-40 // fz)
+    with make(L, (64, 8, 8), 0.9, -5.5, "f64") as lat:    # no fused step in FP64
+        assert (lat.get_option("fused_fz_used"), lat.get_option("fused_group_used")) == (0, 0)
