@@ -94,7 +94,7 @@ def kernel_digest(fused: bool = False) -> str:
     """sha256 over the sources of the time-step kernels (two-kernel step, or
     the single-pass fused step)."""
     h = hashlib.sha256()
-    names = ("lbm_node.cuh", "lbm_fused.cu", "lbm_device.cuh") if fused else (
+    names = ("lbm_node.cuh", "lbm_fused_kernel.cuh", "lbm_device.cuh") if fused else (
         "lbm_node.cuh", "lbm_step.cu", "lbm_device.cuh")
     for name in names:
         with open(os.path.join(ROOT, "paper_1904_11792_gb300", "csrc", name), "rb") as fh:

@@ -1,0 +1,545 @@
+// Fused time step: one kernel, one pass over the populations per step.
+//
+// The two-kernel step reads every population twice (the psi pass needs rho of
+// every node before any collision, because the force of Eq. 5 at x needs psi
+// at all 18 neighbours).  Here a block owns a 64 x TY tile of (x, y) (32
+// lanes x two nodes per row, one warp per row) and a run of z planes, and
+// marches through the run:
+//
+//   iteration k, plane p = z0 - 1 + k (periodic; odd runs march downwards):
+//     psi of plane p over the tile and its one-node ring  -> psi ring slot
+//     barrier
+//     collide + stream plane p - 1 (psi of planes p - 2 .. p now known)
+//
+// Populations reach shared memory by Blackwell TMA: per plane nine
+// cp.async.bulk.tensor copies from 4-D tensor maps [19][nz][ny][nx] (the
+// 64 x TY interior, the two halo rows, the two halo columns and the four
+// corners as 16-byte wide boxes, every box at in-range coordinates so the
+// periodic wrap needs no fill), completing on the buffer's mbarrier.  Two
+// plane buffers: the copies of plane p + 2 start as soon as psi of plane p
+// has been read out of its buffer, a full iteration ahead.  A thread keeps
+// the stored populations of its two nodes in registers from the psi step of
+// plane p to their collision in the next iteration, so a buffer is free
+// after the psi step.  The psi values of four planes sit in a ring (the
+// collision of plane p - 1 reads slots p - 2 .. p while faster warps already
+// write p + 1), so one block barrier per plane suffices.  Populations leave
+// DRAM once per step (halo boxes and the two boundary planes of a run are
+// read by neighbouring blocks at about the same time and mostly hit L2),
+// psi never goes to DRAM.  The arithmetic is psi_math and collide_math of
+// lbm_node.cuh and the stores are those of collide_pair, so the results
+// equal the two-kernel step bitwise.  A-B streaming, 4- and 2-byte storage,
+// lattices with nx % 64 == 0 and ny % 4 == 0.
+//
+// This header holds the kernel and its device helpers; lbm_fused.cu holds
+// the host side (tensor maps, launch shape, launches).  Include it from one
+// translation unit only: its definitions have internal linkage.
+#pragma once
+
+#include <cuda.h>
+
+#include "lbm_node.cuh"
+
+namespace lbm {
+
+namespace {
+
+constexpr int TX = 64;   // tile along x: 32 lanes x 2 nodes
+constexpr int TY = 4;    // tile along y: one warp per row
+constexpr int NT = 32 * TY;
+constexpr int NB = 2;    // plane buffers
+constexpr int NR = 4;    // psi ring slots
+constexpr int RW = TX + 4;   // ring row: position x - x0 + 2 (pairs start 8-byte aligned)
+constexpr int RH = TY + 2;
+constexpr unsigned long long kWaitNs = 2000000000ull;   // a wait on a plane gives up after 2 s
+
+__host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) & ~size_t(127); }
+
+template <int P> struct FusedShape {
+  using T = typename Prec<P>::T;
+  using C = typename Prec<P>::C;
+  static constexpr int E = sizeof(T);
+  static constexpr int CW = 16 / E;                               // one 16-byte TMA unit along x
+  static constexpr size_t int_bytes = (size_t)Q * TY * TX * E;    // box (64, TY, 1, 19)
+  static constexpr size_t row_bytes = (size_t)Q * TX * E;         // box (64, 1, 1, 19)
+  static constexpr size_t col_bytes = (size_t)Q * TY * CW * E;    // box (CW, TY, 1, 19)
+  static constexpr size_t cor_bytes = (size_t)Q * CW * E;         // box (CW, 1, 1, 19)
+  static constexpr size_t off_int = 0;
+  static constexpr size_t off_top = align128(off_int + int_bytes);
+  static constexpr size_t off_bot = align128(off_top + row_bytes);
+  static constexpr size_t off_lft = align128(off_bot + row_bytes);
+  static constexpr size_t off_rgt = align128(off_lft + col_bytes);
+  static constexpr size_t off_cor = align128(off_rgt + col_bytes);  // 4 corners, cor_stride apart
+  static constexpr size_t cor_stride = align128(cor_bytes);
+  static constexpr size_t plane = align128(off_cor + 4 * cor_stride);
+  static constexpr size_t off_ring = NB * plane;
+  static constexpr size_t ring_bytes = align128((size_t)NR * RH * RW * sizeof(C));
+  static constexpr size_t off_bar = off_ring + ring_bytes;
+  static constexpr size_t smem = off_bar + (NB + 1) * sizeof(unsigned long long);   // + the test barrier
+  static constexpr unsigned tx_bytes = (unsigned)(int_bytes + 2 * row_bytes + 2 * col_bytes + 4 * cor_bytes);
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Polls the barrier until its phase completes or limit_ns of wall time have
+// passed (the global nanosecond timer); false if it did not complete.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  unsigned long long limit_ns = kWaitNs) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];\n" ::"r"(smem_addr(dst)),
+      "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(0), "r"(smem_addr(bar))
+      : "memory");
+}
+
+struct Maps {
+  CUtensorMap interior, row, col, cor;
+};
+
+// Stored value to compute precision plus the deviation shift.  For 2-byte
+// storage one widening add (add.rn.f32.f16 / .bf16, sm_100 and later) does
+// both: the conversion is exact, so the result is the FP32 sum of the
+// converted value and the shift rounded once to nearest, the bits of the
+// conversion-then-add of the two-kernel step.
+__device__ __forceinline__ float add_wide(__half h, float c) {
+  float d;
+  asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(__half_as_ushort(h)), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float add_wide(__nv_bfloat16 h, float c) {
+  float d;
+  asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(__bfloat16_as_ushort(h)), "f"(c));
+  return d;
+}
+template <int P>
+__device__ __forceinline__ void unpack_shifted(typename Pair<P>::V v, float sh, float& a, float& b) {
+  if constexpr (P == LBM_F16DEV) {
+    a = add_wide(__low2half(v), sh);
+    b = add_wide(__high2half(v), sh);
+  } else if constexpr (P == LBM_BF16DEV) {
+    a = add_wide(__low2bfloat16(v), sh);
+    b = add_wide(__high2bfloat16(v), sh);
+  } else {
+    Pair<P>::unpack(v, a, b);   // full precision: no shift
+  }
+}
+template <int P>
+__device__ __forceinline__ float load_shifted(const typename Prec<P>::T* p, float sh) {
+  if constexpr (Prec<P>::dev)
+    return add_wide(*p, sh);
+  else
+    return *p;
+}
+
+// Issues the nine copies of plane zz into buffer b (one thread).
+template <int P>
+__device__ __forceinline__ void issue_plane(unsigned char* smem, const Maps& m, int b, int x0, int y0, int xl,
+                                            int xr, int ym, int yp, int zz, unsigned long long* bar) {
+  using S = FusedShape<P>;
+  unsigned char* base = smem + (size_t)b * S::plane;
+  // order earlier generic-proxy reads of this buffer before the async writes
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  mbar_expect_tx(bar, S::tx_bytes);
+  tma_load_4d(base + S::off_int, &m.interior, x0, y0, zz, bar);
+  tma_load_4d(base + S::off_top, &m.row, x0, ym, zz, bar);
+  tma_load_4d(base + S::off_bot, &m.row, x0, yp, zz, bar);
+  tma_load_4d(base + S::off_lft, &m.col, xl, y0, zz, bar);
+  tma_load_4d(base + S::off_rgt, &m.col, xr, y0, zz, bar);
+  tma_load_4d(base + S::off_cor + 0 * S::cor_stride, &m.cor, xl, ym, zz, bar);
+  tma_load_4d(base + S::off_cor + 1 * S::cor_stride, &m.cor, xr, ym, zz, bar);
+  tma_load_4d(base + S::off_cor + 2 * S::cor_stride, &m.cor, xl, yp, zz, bar);
+  tma_load_4d(base + S::off_cor + 3 * S::cor_stride, &m.cor, xr, yp, zz, bar);
+}
+
+// Diagnostics of the step's starting state, reduced in the same pass (DIAG):
+// every thread sums, in the compute precision, the nodes of the planes its
+// block owns (the run z0 .. z1 - 1, not the two halo planes), and the block
+// writes FP64 partials in the layout the diagnostics reduction reads: slice
+// sums [row block][x][2] with one row block per (tile row, z run), and block
+// totals [block][DIAG_NG].
+struct DiagOut {
+  double rho_l, rho_v;
+  double* slices;
+  double* blocks;
+  // test hook (the timeout path of the bounded waits): > 0 makes every block
+  // also wait, for at most this many ns, on a barrier nothing completes
+  unsigned long long stall_test_ns;
+};
+
+// Blocks per SM the register budget must allow: 3 for 4-byte storage (its
+// 73 KB of shared memory allow no more), 4 for 2-byte storage (44 KB), the
+// diagnostic variants included (no spills at 168 and 128 registers).
+template <int P, bool DIAG, int COLL = COLL_SRT>
+constexpr int fused_minb() {
+  return Prec<P>::dev ? 4 : 3;
+}
+
+template <int P, bool DIAG, int COLL>
+__global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
+    fused_kernel(const __grid_constant__ Maps maps, Geom g, Phys ph, typename Prec<P>::T* dst, int* flag, int ntx,
+                 int nchunks, int fz, int grp, DiagOut dg) {
+  using T = typename Prec<P>::T;
+  using C = typename Prec<P>::C;
+  using V = typename Pair<P>::V;
+  using S = FusedShape<P>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + S::off_bar);
+  C* ring = reinterpret_cast<C*>(smem + S::off_ring);
+
+  const int u = blockIdx.x;
+  // Block order: z runs in groups of grp consecutive runs; inside a group
+  // the run index varies fastest, then the tile x, then the tile y.  Blocks
+  // that share planes (the two runs either side of a run boundary, x- and
+  // y-neighbour tiles) are then launched close together, so the planes and
+  // halo rows they share are still in L2 when the second one reads them.
+  const int tiles = ntx * (g.ny / TY);
+  const int zg = u / (grp * tiles), r = u - zg * grp * tiles;
+  const int gs = min(grp, nchunks - zg * grp);   // runs in this group
+  const int chunk = zg * grp + r % gs, xy = r / gs;
+  const int x0 = (xy % ntx) * TX, y0 = (xy / ntx) * TY;
+  const int z0 = chunk * fz, z1 = min(z0 + fz, g.nz);
+  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+  const int np = (z1 - z0) + 2;        // planes z0 - 1 .. z1, march index k in buffer k % NB
+  // Even runs march up (z0 - 1 first), odd runs down (z1 first), so the plane
+  // two neighbouring runs share is read by both near the same time (at the
+  // start of both, or at the end of both) and the second read hits L2.
+  const int dir = (chunk & 1) ? -1 : 1;
+  const long long N = g.N;
+  const int ym = y0 == 0 ? g.ny - 1 : y0 - 1, yp = y0 + TY == g.ny ? 0 : y0 + TY;
+  const int xl = x0 == 0 ? g.nx - S::CW : x0 - S::CW, xr = x0 + TX == g.nx ? 0 : x0 + TX;
+  const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
+          s2 = shift_of<P>(7, ph.rho_ref);
+  auto zwrap = [&](int p) { return p < 0 ? p + g.nz : (p >= g.nz ? p - g.nz : p); };
+  auto zplane = [&](int k) { return zwrap(dir > 0 ? z0 - 1 + k : z1 - k); };   // plane of march index k
+
+  // psi of the halo ring of a plane: warps 0 and 1 take the rows y0 - 1 and
+  // y0 + TY over x0 .. x0 + TX - 1 as x pairs (like the interior), warps
+  // 2 .. TY - 1 the four corners and the 2 TY column cells, one per lane, so
+  // every warp makes one pass.  h_off: element offset in a plane buffer (-1:
+  // no cell), h_str: stride between directions (scalar cells), h_ring: ring
+  // position.
+  constexpr int SC = 4 + 2 * TY;                      // scalar halo cells
+  constexpr int SPW = (SC + TY - 3) / (TY - 2);       // scalar cells per warp
+  static_assert(TY >= 3 && SPW <= 32, "halo split needs two row warps and room for the cells");
+  int h_off = -1, h_str = 0, h_ring = 0;
+  if (ty < 2) {
+    h_off = (int)((ty ? S::off_bot : S::off_top) / S::E) + 2 * lane;
+    h_ring = (ty ? TY + 1 : 0) * RW + 2 * lane + 2;
+  } else if (lane < SPW && (ty - 2) * SPW + lane < SC) {
+    const int h = (ty - 2) * SPW + lane;
+    if (h < 4) {
+      const int side = h >> 1, right = h & 1;   // corners in the copy order of issue_plane
+      h_off = (int)((S::off_cor + h * S::cor_stride) / S::E) + (right ? 0 : S::CW - 1);
+      h_str = S::CW;
+      h_ring = (side ? TY + 1 : 0) * RW + (right ? TX + 2 : 1);
+    } else {
+      const int i = h - 4, side = i >= TY, r = i - side * TY;   // side 0: column x0 - 1, 1: x0 + TX
+      h_off = (int)((side ? S::off_rgt : S::off_lft) / S::E) + r * S::CW + (side ? 0 : S::CW - 1);
+      h_str = TY * S::CW;
+      h_ring = (r + 1) * RW + (side ? TX + 2 : 1);
+    }
+  }
+
+  // dst + a N, the start of direction a in the destination array: with
+  // 2-byte storage (bound by instruction issue) the stores address a
+  // direction by this base and a 32-bit offset in it (N < 2^31), which saves
+  // the 64-bit arithmetic per direction and plane (measured: 1.4 % faster;
+  // the latency-bound FP32 step was 3 % slower this way)
+  __shared__ T* s_dir[Q];
+  if (Prec<P>::dev && tid < Q) s_dir[tid] = dst + (long long)tid * N;
+  __shared__ int s_abort;
+  if (tid == 0) {
+    // bit 2 of the flag: a block (of this launch or an earlier one) gave up
+    // on a wait, the result is void; skip the work
+    s_abort = (*(volatile int*)flag & 2) != 0;
+    for (int b = 0; b < NB + 1; ++b) mbar_init(full + b, 1);   // full[NB]: the test barrier
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (s_abort) return;
+  if (tid == 0)
+    for (int k = 0; k < NB && k < np; ++k)
+      issue_plane<P>(smem, maps, k, x0, y0, xl, xr, ym, yp, zplane(k), full + k);
+
+  const unsigned salt = (Prec<P>::dev && ph.sr) ? salt_of(ph) : 0u;
+  V prev[Q];   // stored populations of this thread's two nodes, previous plane
+  // diagnostics sums (DIAG): block totals and the two x columns of the thread
+  C d_mass = 0, d_jx = 0, d_jy = 0, d_jz = 0, d_vol = 0, d_umax = 0;
+  C d_rmin = (C)3.0e38, d_rmax = (C)-3.0e38;
+  C col_w[2] = {0, 0}, col_n[2] = {0, 0};
+  bool d_bad = false;
+  const C d_thr = (C)(0.5 * (dg.rho_l + dg.rho_v)), d_inv = (C)(1.0 / (dg.rho_l - dg.rho_v)),
+          d_rv = (C)dg.rho_v;
+  int k = 0;
+  for (; k < np; ++k) {
+    const int b = k % NB;
+    bool ok = mbar_wait_bounded(full + b, (unsigned)((k / NB) & 1));
+    if (k == 0 && dg.stall_test_ns) ok = ok && mbar_wait_bounded(full + NB, 0u, dg.stall_test_ns);
+    const T* buf = reinterpret_cast<const T*>(smem + (size_t)b * S::plane);
+    C* slot = ring + (k % NR) * RH * RW;
+    // psi of this thread's two nodes of plane zplane(k)
+    V cur[Q];
+    C f0[Q], f1[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      cur[a] = *reinterpret_cast<const V*>(buf + (a * TY + ty) * TX + 2 * lane);
+      unpack_shifted<P>(cur[a], a == 0 ? s0 : (a <= 6 ? s1 : s2), f0[a], f1[a]);
+    }
+    C p0, p1;
+    const C r0 = rho_of<C>(f0), r1 = rho_of<C>(f1);
+    psi_math<C>(ph, r0, &p0, flag);
+    psi_math<C>(ph, r1, &p1, flag);
+    if constexpr (DIAG) {
+      // momentum of the two nodes (the summation order of the two-kernel
+      // diagnostics)
+      C jv[2][3];
+      mom_of<C>(f0, jv[0][0], jv[0][1], jv[0][2]);
+      mom_of<C>(f1, jv[1][0], jv[1][1], jv[1][2]);
+      if (k >= 1 && k <= np - 2) {
+#pragma unroll
+        for (int n = 0; n < 2; ++n) {
+          const C rho = n ? r1 : r0;
+          const C jx = jv[n][0], jy = jv[n][1], jz = jv[n][2];
+          d_mass += rho;
+          d_jx += jx;
+          d_jy += jy;
+          d_jz += jz;
+          C phi = (rho - d_rv) * d_inv;
+          phi = phi < (C)0 ? (C)0 : (phi > (C)1 ? (C)1 : phi);
+          d_vol += phi;
+          col_w[n] += phi;
+          col_n[n] += rho > d_thr ? (C)1 : (C)0;
+          const C um = sqrt(xfma(jz, jz, xfma(jy, jy, xmul(jx, jx)))) / rho;
+          d_umax = um > d_umax ? um : d_umax;
+          d_rmin = rho < d_rmin ? rho : d_rmin;
+          d_rmax = rho > d_rmax ? rho : d_rmax;
+          d_bad |= !(rho > (C)0) || !(rho <= (C)3.0e38);
+        }
+      }
+    }
+    if constexpr (sizeof(C) == 4)
+      *reinterpret_cast<float2*>(slot + (ty + 1) * RW + 2 * lane + 2) = make_float2(p0, p1);
+    else
+      *reinterpret_cast<double2*>(slot + (ty + 1) * RW + 2 * lane + 2) = make_double2(p0, p1);
+    // psi of this thread's halo cells
+    if (ty < 2) {
+      C fa[Q], fb[Q];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        unpack_shifted<P>(*reinterpret_cast<const V*>(buf + h_off + a * TX), a == 0 ? s0 : (a <= 6 ? s1 : s2),
+                          fa[a], fb[a]);
+      }
+      C pa, pb;
+      psi_math<C>(ph, rho_of<C>(fa), &pa, flag);
+      psi_math<C>(ph, rho_of<C>(fb), &pb, flag);
+      if constexpr (sizeof(C) == 4)
+        *reinterpret_cast<float2*>(slot + h_ring) = make_float2(pa, pb);
+      else
+        *reinterpret_cast<double2*>(slot + h_ring) = make_double2(pa, pb);
+    } else if (h_off >= 0) {
+      C fv[Q];
+#pragma unroll
+      for (int a = 0; a < Q; ++a)
+        fv[a] = load_shifted<P>(buf + h_off + a * h_str, a == 0 ? s0 : (a <= 6 ? s1 : s2));
+      psi_math<C>(ph, rho_of<C>(fv), slot + h_ring, flag);
+    }
+    // every psi of plane zplane(k) is in the ring and buffer b is read out
+    if (__syncthreads_or(!ok)) break;
+    if (tid == 0 && k + NB < np)
+      issue_plane<P>(smem, maps, b, x0, y0, xl, xr, ym, yp, zplane(k + NB), full + b);
+
+    if (k >= 2) {
+      // collide + stream the two nodes (x0 + 2 lane, y0 + ty) of plane z =
+      // zplane(k - 1); plane z + dz has march index k - 1 + dir dz
+      const int z = zplane(k - 1);
+      const int x = x0 + 2 * lane, y = y0 + ty;
+      const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x + 2 == g.nx ? 0 : x + 2;
+      const int yv[3] = {y == 0 ? g.ny - 1 : y - 1, y, y == g.ny - 1 ? 0 : y + 1};
+      const int zv[3] = {z == 0 ? g.nz - 1 : z - 1, z, z == g.nz - 1 ? 0 : z + 1};
+      C q[3][3][4];
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+          const C* row = ring + ((k - 1 + dir * dz) % NR) * RH * RW + (ty + 1 + dy) * RW + 2 * lane + 2;
+          if constexpr (sizeof(C) == 4) {
+            const float2 v = *reinterpret_cast<const float2*>(row);
+            q[dy + 1][dz + 1][1] = v.x;
+            q[dy + 1][dz + 1][2] = v.y;
+          } else {
+            const double2 v = *reinterpret_cast<const double2*>(row);
+            q[dy + 1][dz + 1][1] = v.x;
+            q[dy + 1][dz + 1][2] = v.y;
+          }
+          if (dy == 0 || dz == 0) {
+            q[dy + 1][dz + 1][0] = row[-1];
+            q[dy + 1][dz + 1][3] = row[2];
+          } else {
+            q[dy + 1][dz + 1][0] = 0;
+            q[dy + 1][dz + 1][3] = 0;
+          }
+        }
+      C g0[Q], g1[Q], pn0[Q], pn1[Q];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        unpack_shifted<P>(prev[a], a == 0 ? s0 : (a <= 6 ? s1 : s2), g0[a], g1[a]);
+      }
+      pn0[0] = pn1[0] = 0;
+#pragma unroll
+      for (int a = 1; a < Q; ++a) {
+        pn0[a] = q[cy(a) + 1][cz(a) + 1][1 + cx(a)];
+        pn1[a] = q[cy(a) + 1][cz(a) + 1][2 + cx(a)];
+      }
+      C fs0[Q], fs1[Q];
+      if constexpr (COLL == COLL_MRT) {
+        collide_math_mrt<C>(ph, g0, q[1][1][1], pn0, fs0);
+        collide_math_mrt<C>(ph, g1, q[1][1][2], pn1, fs1);
+      } else {
+        collide_math<C>(ph, g0, q[1][1][1], pn0, fs0);
+        collide_math<C>(ph, g1, q[1][1][2], pn1, fs1);
+      }
+      const int i0 = x + g.nx * (y + g.ny * z);
+      const bool sr = Prec<P>::dev && ph.sr;
+      const unsigned seed0 = sr ? sr_seed(i0, fs0[0], salt) : 0u, seed1 = sr ? sr_seed(i0 + 1, fs1[0], salt) : 0u;
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
+        const int row = g.nx * (yv[1 + cy(a)] + g.ny * zv[1 + cz(a)]);
+        if constexpr (Prec<P>::dev) {
+          T* const base = s_dir[a];
+          if (cx(a) == 0) {
+            if (sr)
+              store_pair_sr<P>(base + (row + x), fs0[a], fs1[a], sh, sr_bits(seed0, a), sr_bits(seed1, a));
+            else
+              store_pair<P>(base + (row + x), fs0[a], fs1[a], sh);
+          } else {
+            store_pop<P>(ph, base + (row + (cx(a) > 0 ? x + 1 : xm)), fs0[a], sh, seed0, a);
+            store_pop<P>(ph, base + (row + (cx(a) > 0 ? xp : x)), fs1[a], sh, seed1, a);
+          }
+        } else {
+          T* base = dst + (long long)a * N + row;
+          if (cx(a) == 0) {
+            store_pair<P>(base + x, fs0[a], fs1[a], sh);
+          } else {
+            store_pop<P>(ph, base + (cx(a) > 0 ? x + 1 : xm), fs0[a], sh, seed0, a);
+            store_pop<P>(ph, base + (cx(a) > 0 ? xp : x), fs1[a], sh, seed1, a);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < Q; ++a) prev[a] = cur[a];
+  }
+  if (k < np) {
+    // a wait gave up: record it, and let the copies already issued land
+    // before the block's shared memory is released
+    if (tid == 0) {
+      atomicOr(flag, 2);
+      for (int j = k; j < k + NB && j < np; ++j) mbar_wait_bounded(full + j % NB, (unsigned)((j / NB) & 1));
+    }
+  }
+  if constexpr (DIAG) {
+    // the psi ring is free now: it holds the FP64 reduction (TY x 64 x 2
+    // slice values, DIAG_NG x TY warp totals)
+    __syncthreads();
+    double* sh_col = reinterpret_cast<double*>(ring);
+    double* sh_w = sh_col + 2 * TY * TX;
+#pragma unroll
+    for (int n = 0; n < 2; ++n) {
+      sh_col[(ty * TX + 2 * lane + n) * 2 + 0] = (double)col_w[n];
+      sh_col[(ty * TX + 2 * lane + n) * 2 + 1] = (double)col_n[n];
+    }
+    // warp totals: a fixed shuffle tree in the compute precision
+    C v[5] = {d_mass, d_jx, d_jy, d_jz, d_vol};
+    float c_f = 0.0f;
+#pragma unroll
+    for (int n = 0; n < 2; ++n) c_f += (float)col_n[n];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+      c_f += __shfl_down_sync(0xffffffffu, c_f, o);
+      const C um = __shfl_down_sync(0xffffffffu, d_umax, o);
+      const C mn = __shfl_down_sync(0xffffffffu, d_rmin, o);
+      const C mx = __shfl_down_sync(0xffffffffu, d_rmax, o);
+      d_umax = um > d_umax ? um : d_umax;
+      d_rmin = mn < d_rmin ? mn : d_rmin;
+      d_rmax = mx > d_rmax ? mx : d_rmax;
+    }
+    const int anybad = __any_sync(0xffffffffu, d_bad);
+    if (lane == 0) {
+      sh_w[0 * TY + ty] = (double)v[0];
+      sh_w[1 * TY + ty] = (double)v[1];
+      sh_w[2 * TY + ty] = (double)v[2];
+      sh_w[3 * TY + ty] = (double)v[3];
+      sh_w[4 * TY + ty] = (double)v[4];
+      sh_w[5 * TY + ty] = (double)c_f;
+      sh_w[6 * TY + ty] = (double)d_umax;
+      sh_w[7 * TY + ty] = (double)d_rmin;
+      sh_w[8 * TY + ty] = (double)d_rmax;
+      sh_w[9 * TY + ty] = anybad ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const long long rb = (long long)(xy / ntx) * nchunks + chunk;
+    if (tid < TX) {
+      double a = 0.0, c = 0.0;
+      for (int r = 0; r < TY; ++r) {
+        a += sh_col[(r * TX + tid) * 2 + 0];
+        c += sh_col[(r * TX + tid) * 2 + 1];
+      }
+      dg.slices[(rb * g.nx + x0 + tid) * 2 + 0] = a;
+      dg.slices[(rb * g.nx + x0 + tid) * 2 + 1] = c;
+    } else if (tid < TX + DIAG_NG) {
+      const int i = tid - TX;
+      double r;
+      if (i < 6) {
+        r = 0.0;
+        for (int w = 0; w < TY; ++w) r += sh_w[i * TY + w];
+      } else if (i == 7) {
+        r = 1e300;
+        for (int w = 0; w < TY; ++w) r = fmin(r, sh_w[i * TY + w]);
+      } else if (i < 10) {
+        r = -1e300;
+        for (int w = 0; w < TY; ++w) r = fmax(r, sh_w[i * TY + w]);
+      } else {
+        r = 0.0;
+      }
+      dg.blocks[(long long)blockIdx.x * DIAG_NG + i] = r;
+    }
+  }
+}
+
+}  // namespace
+
+}  // namespace lbm
