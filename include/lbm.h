@@ -166,7 +166,8 @@ int lbm_set_stream(lbm_handle h, void *stream);
  * size and the GPU, the default), "fused_group" (the fused step launches
  * its blocks in groups of this many consecutive z runs, the run varying
  * fastest inside a group, then the tile x, then the tile y; 0 = one run
- * per 4 tile columns of 64 nodes, at least one, the default; any value
+ * per 4 tile columns of 64 nodes (FP32; one run for 2-byte storage), at
+ * least one, the default; any value
  * gives the same results), "fused_fz_used" and "fused_group_used" (get
  * only: the run length and runs per group the fused step launches with for
  * the current options; 0 where the fused step does not apply),

@@ -67,10 +67,23 @@ __device__ __forceinline__ unsigned sr_seed(long long node, float rest, unsigned
 __device__ __forceinline__ unsigned sr_seed(long long node, double rest, unsigned salt) {
   return sr_seed(node, (float)rest, salt);
 }
-// 16 random bits for direction a of a node with (well mixed) seed s: the
-// top half of s times a distinct odd constant per direction (one multiply).
+// 32 random bits shared by the opposite directions 2j - 1 and 2j of a node
+// with (well mixed) seed s (j = 1..9; j = 0: the rest population).  The
+// product w = s K_j (mod 2^32) with a distinct odd constant per pair is a
+// bijection of s, and its high half is well mixed: it gives the high 16 bits.
+// Its low half depends on the low half of s only (the same for every pair),
+// so the low 16 bits are that half xor the high one.  (The high word of the
+// 64-bit product is no use here: it is uniform on [0, K_j) only.)
+__device__ __forceinline__ unsigned sr_word(unsigned s, int j) {
+  const unsigned w = s * (0x9E3779B1u + 0x6A09E668u * (unsigned)j);
+  return w ^ (w >> 16);
+}
+// 16 random bits for direction a: the high half of its pair's word for odd
+// a and the rest population, the low half for even a > 0 (so one conversion
+// of the pair (a, a + 1), a odd, takes exactly these bits for each value).
 __device__ __forceinline__ unsigned sr_bits(unsigned s, int a) {
-  return (s * (0x9E3779B1u + 0x6A09E668u * (unsigned)a)) >> 16;
+  const unsigned w = sr_word(s, (a + 1) >> 1);
+  return (a == 0 || (a & 1)) ? w >> 16 : w & 0xFFFFu;
 }
 // Stochastic rounding by the conversion instruction (cvt.rs, sm_100 and
 // later): two FP32 values to a packed FP16 / BF16 pair, each rounded up with

@@ -84,16 +84,18 @@ cudaError_t maps_for(int precision, const Geom& g, const void* base, Maps* out) 
 // 19-, 24- and 32-plane runs take 6.5, 6.4-7.8, 7.0, 7.7 and 8.2 ms per
 // step: the longer a block lives, the further apart in time neighbouring
 // tiles read the rows they share), so on lattices with more tiles than
-// resident blocks runs stop at 12 planes; small grids (256x128x128: 1.96
-// waves of 19-plane runs, 0.114 ms, against 0.126 ms for 16-plane runs in
-// 2.25 waves) keep the wave count low instead.
-int choose_fz(const Geom& g, long long tiles, long long slots) {
+// resident blocks runs stop at 12 planes (cap); small grids (256x128x128:
+// 1.96 waves of 19-plane runs, 0.114 ms, against 0.126 ms for 16-plane runs
+// in 2.25 waves) keep the wave count low instead.  2-byte storage, bound by
+// instruction issue and with half the bytes per plane in L2, has no cap
+// (1024x512x512 FP16: 32-plane runs 6.20 ms, 12-plane runs in fours 6.57).
+int choose_fz(const Geom& g, long long tiles, long long slots, bool cap) {
   int best = g.nz;
   double best_cost = -1.0;
   for (int fz = 4; fz <= g.nz; ++fz) {
     const long long chunks = (g.nz + fz - 1) / fz;
     const long long waves = (tiles * chunks + slots - 1) / slots;
-    if (fz > 12 && tiles > slots) continue;
+    if (cap && fz > 12 && tiles > slots) continue;
     const double cost = (double)waves * (fz + 2) * (1.0 + fz / 256.0);
     if (best_cost < 0.0 || cost < best_cost) {
       best_cost = cost;
@@ -127,7 +129,7 @@ cudaError_t fused_grid(const Geom& g, int fz_req, int grp_req, int* fz, int* nch
     slots_per_sm = slots;
   }
   const long long tiles = (long long)(g.nx / TX) * (g.ny / TY);
-  *fz = fz_req > 0 ? std::min(fz_req, g.nz) : choose_fz(g, tiles, (long long)slots_per_sm * sms);
+  *fz = fz_req > 0 ? std::min(fz_req, g.nz) : choose_fz(g, tiles, (long long)slots_per_sm * sms, !Prec<P>::dev);
   *nchunks = (g.nz + *fz - 1) / *fz;
   *blocks = tiles * *nchunks;
   // runs per group (a tile's y neighbours are ntx x grp blocks apart in the
@@ -136,9 +138,10 @@ cudaError_t fused_grid(const Geom& g, int fz_req, int grp_req, int* fz, int* nch
   // tile together), 512x256x256 within 2 % for 1 to 4, 1024x512x512 with
   // 12-plane runs in groups of 4 (6.5 ms and 21.8 GB of DRAM reads in every
   // launch; 16-plane runs in pairs took 6.4 to 7.8 ms, reading 22 to 29 GB):
-  // one run per 4 tile columns
+  // one run per 4 tile columns (2-byte storage: one run per group, 32-plane
+  // runs in ones 6.20 ms on 1024x512x512 FP16, in pairs 6.33 ms)
   const int ntx = g.nx / TX;
-  *grp = std::min(grp_req > 0 ? grp_req : std::max(1, ntx / 4), *nchunks);
+  *grp = std::min(grp_req > 0 ? grp_req : (Prec<P>::dev ? 1 : std::max(1, ntx / 4)), *nchunks);
   return *blocks > 0x7fffffffLL ? cudaErrorInvalidConfiguration : cudaSuccess;
 }
 

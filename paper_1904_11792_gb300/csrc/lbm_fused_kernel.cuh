@@ -154,6 +154,15 @@ __device__ __forceinline__ void unpack_shifted(typename Pair<P>::V v, float sh, 
     Pair<P>::unpack(v, a, b);   // full precision: no shift
   }
 }
+// Two FP32 values to a packed 2-byte pair with stochastic rounding: hi takes
+// the random bits rbits[31:16], lo rbits[15:0].
+template <int P>
+__device__ __forceinline__ unsigned cvt_pair_sr(float hi, float lo, unsigned rbits) {
+  if constexpr (P == LBM_BF16DEV)
+    return cvt_rs_bf16x2(hi, lo, rbits);
+  else
+    return cvt_rs_f16x2(hi, lo, rbits);
+}
 template <int P>
 __device__ __forceinline__ float load_shifted(const typename Prec<P>::T* p, float sh) {
   if constexpr (Prec<P>::dev)
@@ -443,10 +452,27 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
               store_pair_sr<P>(base + (row + x), fs0[a], fs1[a], sh, sr_bits(seed0, a), sr_bits(seed1, a));
             else
               store_pair<P>(base + (row + x), fs0[a], fs1[a], sh);
-          } else {
+          } else if (!sr) {
             store_pop<P>(ph, base + (row + (cx(a) > 0 ? x + 1 : xm)), fs0[a], sh, seed0, a);
             store_pop<P>(ph, base + (row + (cx(a) > 0 ? xp : x)), fs1[a], sh, seed1, a);
+          } else if (a & 1) {
+            // a and its opposite a + 1 (c_x != 0, the same weight and shift):
+            // one conversion per node rounds both with the bits sr_bits gives
+            // them (the high half a, the low half a + 1), so the stored values
+            // equal those of the one-value conversions of the two-kernel step
+            T* const base_b = s_dir[a + 1];
+            const int row_b = g.nx * (yv[1 + cy(a + 1)] + g.ny * zv[1 + cz(a + 1)]);
+            const unsigned j = (unsigned)(a + 1) >> 1;
+            const unsigned d0 = cvt_pair_sr<P>(fs0[a] - sh, fs0[a + 1] - sh, sr_word(seed0, j));
+            const unsigned d1 = cvt_pair_sr<P>(fs1[a] - sh, fs1[a + 1] - sh, sr_word(seed1, j));
+            unsigned short* const pa = reinterpret_cast<unsigned short*>(base + row);
+            unsigned short* const pb = reinterpret_cast<unsigned short*>(base_b + row_b);
+            pa[cx(a) > 0 ? x + 1 : xm] = (unsigned short)(d0 >> 16);
+            pa[cx(a) > 0 ? xp : x] = (unsigned short)(d1 >> 16);
+            pb[cx(a + 1) > 0 ? x + 1 : xm] = (unsigned short)d0;
+            pb[cx(a + 1) > 0 ? xp : x] = (unsigned short)d1;
           }
+          // even a with c_x != 0 under stochastic rounding: stored with a - 1
         } else {
           T* base = dst + (long long)a * N + row;
           if (cx(a) == 0) {
