@@ -288,8 +288,6 @@ def run_ours(args):
         kname, bpl, avg, launches = "collide_stream", K2_BYTES_PER_LU[args.precision], k2_avg, n_k2
         step_model = STEP_BYTES_PER_LU[args.precision]
         launches_per_step = 2 * (LBM_PER_STEP - 1) + 4
-    if args.precision.endswith("dev"):
-        launches_per_step += LBM_PER_STEP   # the stochastic-rounding salt advance of each step
     achieved = bpl * N / (avg * 1e-3) / 1e9
     fz_used = int(lat.get_option("fused_fz_used")) if fused else 0
     grp_used = int(lat.get_option("fused_group_used")) if fused else 0

@@ -134,6 +134,12 @@ cudaEvent_t take_event(lbm_ctx* h) {
   return e;
 }
 
+// The word of the salt pair step `step` reads: the A-B array index, or the
+// step parity for AA (whose graph chunks hold an even number of steps).
+int salt_word(const lbm_ctx* h, long long step, int cur) {
+  return h->cfg.pattern == LBM_AA ? (int)(step & 1) : (cur & 1);
+}
+
 // Enqueues one time step on stream s.  `phase` is the step parity (AA) or
 // the index of the current array (A-B).  With timing on, each kernel is
 // bracketed by events on s.
@@ -147,6 +153,15 @@ int enqueue_step(lbm_ctx* h, cudaStream_t s, long long step, int cur, bool timed
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   const bool diag_step = h->diag_interval > 0 && step % h->diag_interval == 0;
   const bool fused = h->fused && !aa && fused_applicable(h->g, prec);
+  // stochastic-rounding salt: a pair of words, read and advanced by the
+  // step's collision kernel; the word a step reads follows the A-B array
+  // (AA: the step parity), so graph replays and eager steps agree
+  Phys ph = h->ph;
+  if (Prec_dev(prec) && h->ph.sr) {
+    const int w = salt_word(h, step, cur);
+    ph.salt = (const unsigned*)(h->d_flag + 2 + w);
+    ph.salt_next = (unsigned*)(h->d_flag + 2 + (w ^ 1));
+  }
   // a diagnostic step runs fused too when the scratch holds its partials
   const bool fused_diag =
       fused && diag_step && h->d_scratch && fused_diag_scratch_doubles(h->g, prec, h->fused_fz) <= h->scratch_doubles;
@@ -160,15 +175,14 @@ int enqueue_step(lbm_ctx* h, cudaStream_t s, long long step, int cur, bool timed
     if (diag_step) {
       const FusedDiag fd{h->rho_l, h->rho_v, h->d_scratch, h->scratch_doubles, h->d_ring, h->d_ring_count,
                          lbm_ctx::kRing};
-      CK(launch_fused(prec, h->g, h->ph, src, dst, h->d_flag, h->fused_fz, h->fused_group, &fd, h->fused_stall_test_ns, s));
+      CK(launch_fused(prec, h->g, ph, src, dst, h->d_flag, h->fused_fz, h->fused_group, &fd, h->fused_stall_test_ns, s));
     } else {
-      CK(launch_fused(prec, h->g, h->ph, src, dst, h->d_flag, h->fused_fz, h->fused_group, nullptr, h->fused_stall_test_ns, s));
+      CK(launch_fused(prec, h->g, ph, src, dst, h->d_flag, h->fused_fz, h->fused_group, nullptr, h->fused_stall_test_ns, s));
     }
     if (timed) {
       CK(cudaEventRecord(e1, s));
       h->pending.push_back({2, e0, e1});
     }
-    if (Prec_dev(prec) && h->ph.sr) CK(launch_salt((unsigned*)(h->d_flag + 2), false, 0u, s));
     if (diag_step && h->diag_ccl) {
       long long* d4 = (long long*)(h->d_small + 32);
       CK(launch_ccl(prec, layout, h->g, h->ph, src, 0.5 * (h->rho_l + h->rho_v), h->d_labels,
@@ -201,10 +215,9 @@ int enqueue_step(lbm_ctx* h, cudaStream_t s, long long step, int cur, bool timed
   const bool vec = h->vec && (h->g.nx % 2 == 0);
   const int minb = h->minb ? h->minb : (vec ? 2 : 3);
   if (h->ph.coll == COLL_MRT)
-    CK(launch_collide_mrt(prec, mode, vec, h->g, h->ph, src, dst, h->psi, h->block, s));
+    CK(launch_collide_mrt(prec, mode, vec, h->g, ph, src, dst, h->psi, h->block, s));
   else
-    CK(launch_collide(prec, mode, minb, vec, h->g, h->ph, src, dst, h->psi, h->block, s));
-  if (Prec_dev(prec) && h->ph.sr) CK(launch_salt((unsigned*)(h->d_flag + 2), false, 0u, s));
+    CK(launch_collide(prec, mode, minb, vec, h->g, ph, src, dst, h->psi, h->block, s));
   if (timed) {
     CK(cudaEventRecord(e2, s));
     h->pending.push_back({0, e0, e1});
@@ -1035,7 +1048,7 @@ int lbm_load_state(lbm_handle h, const void* host, size_t bytes) {
     return fail(LBM_ERR_ARG, "saved state has another size, precision or pattern");
   h->cur = 0;
   h->step = hd.step;
-  CK(launch_salt((unsigned*)(h->d_flag + 2), true, (unsigned)hd.step, h->stream));
+  CK(launch_salt((unsigned*)(h->d_flag + 2 + salt_word(h, h->step, h->cur)), true, (unsigned)hd.step, h->stream));
   h->rho_l = hd.rho_l;
   h->rho_v = hd.rho_v;
   CK(cudaMemcpyAsync(array_ptr(h, 0), (const char*)host + sizeof(hd), need - sizeof(hd),

@@ -247,12 +247,22 @@ struct Phys {
   // fourth-order stress and the third-order moments (shear moments relax
   // at 1/tau)
   double s_e, s_eps, s_q, s_pi, s_m;
-  // stochastic-rounding step salt in device memory (read at each collision,
-  // advanced once per step by salt_bump_kernel); nullptr reads as 0
+  // stochastic-rounding step salt in device memory (read at each collision);
+  // nullptr reads as 0
   const unsigned* salt;
+  // where the collision kernel of a step writes the next step's salt (the
+  // other word of a pair; nullptr: a separate one-thread kernel advances it)
+  unsigned* salt_next = nullptr;
 };
 enum Collision { COLL_SRT = 0, COLL_MRT = 1 };
 __device__ __forceinline__ unsigned salt_of(const Phys& ph) { return ph.salt ? __ldg(ph.salt) : 0u; }
+// One thread of a step's collision kernel writes salt + 1 for the next step
+// into the other word of the pair, which nothing of this step reads.
+__device__ __forceinline__ void advance_salt(const Phys& ph) {
+  if (ph.salt_next && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
+      threadIdx.y == 0 && threadIdx.z == 0)
+    *ph.salt_next = salt_of(ph) + 1u;
+}
 
 // Neighbour index table of one node: x-1, x, x+1 and the 9 row offsets of
 // (y + dy, z + dz), all periodic.  idx(cxa, cya, cza) is the flat index of

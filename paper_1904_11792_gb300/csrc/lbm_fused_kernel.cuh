@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
   unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + S::off_bar);
   C* ring = reinterpret_cast<C*>(smem + S::off_ring);
 
+  advance_salt(ph);
   const int u = blockIdx.x;
   // Block order: z runs in groups of grp consecutive runs; inside a group
   // the run index varies fastest, then the tile x, then the tile y.  Blocks

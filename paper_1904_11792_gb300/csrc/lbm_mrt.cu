@@ -18,6 +18,7 @@ __global__ void __launch_bounds__(256, 2) collide_mrt_kernel(Geom g, Phys ph, co
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z * blockDim.z + threadIdx.z;
   if (x >= g.nx || y >= g.ny || z >= g.nz) return;
+  advance_salt(ph);
   collide_node<P, MODE, COLL_MRT>(g, ph, src, dst, psi, x, y, z);
 }
 
@@ -30,6 +31,7 @@ __global__ void __launch_bounds__(256, 2) collide_pair_mrt_kernel(Geom g, Phys p
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z * blockDim.z + threadIdx.z;
   if (x0 >= g.nx || y >= g.ny || z >= g.nz) return;
+  advance_salt(ph);
   collide_pair<P, MODE, COLL_MRT>(g, ph, src, dst, psi, x0, y, z);
 }
 

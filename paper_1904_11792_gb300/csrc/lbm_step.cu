@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(256, MINB) collide_kernel(Geom g, Phys ph,
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z * blockDim.z + threadIdx.z;
   if (x >= g.nx || y >= g.ny || z >= g.nz) return;
+  advance_salt(ph);
   collide_node<P, MODE>(g, ph, src, dst, psi, x, y, z);
 }
 
@@ -64,6 +65,7 @@ __global__ void __launch_bounds__(256, MINB) collide_pair_kernel(Geom g, Phys ph
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z * blockDim.z + threadIdx.z;
   if (x0 >= g.nx || y >= g.ny || z >= g.nz) return;
+  advance_salt(ph);
   collide_pair<P, MODE>(g, ph, src, dst, psi, x0, y, z);
 }
 
