@@ -453,6 +453,7 @@ lbm_handle lbm_create_ex(const lbm_config* cfg) {
   // stochastic rounding is on by default for the reduced-precision forms
   h->ph = Phys{cfg->tau, cfg->G, cfg->rho0, cfg->rho_ref, cfg->psi_form,
                cfg->precision >= LBM_F16DEV ? 1 : 0, COLL_SRT, 1.19, 1.4, 1.2, 1.4, 1.98};
+  h->ph.inv_rho0 = 1.0 / cfg->rho0;
   h->block = (cfg->block_x && cfg->block_y && cfg->block_z)
                  ? dim3(cfg->block_x, cfg->block_y, cfg->block_z)
                  : default_block(h->g);

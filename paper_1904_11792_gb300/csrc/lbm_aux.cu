@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(DX* DY) diag_partial_kernel(Geom g, Phys ph,
       const C rho = rho_of<C>(fv);
       C jx, jy, jz;
       mom_of<C>(fv, jx, jy, jz);
-      if constexpr (WRITE_PSI) psi[i] = psi_of<C>(rho, ph.psi_form, (C)ph.rho0);
+      if constexpr (WRITE_PSI) psi[i] = psi_of<C>(rho, ph);
       s_mass += rho;
       s_jx += jx;
       s_jy += jy;

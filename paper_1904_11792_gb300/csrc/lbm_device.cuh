@@ -247,6 +247,9 @@ struct Phys {
   // fourth-order stress and the third-order moments (shear moments relax
   // at 1/tau)
   double s_e, s_eps, s_q, s_pi, s_m;
+  // 1 / rho0 (FP32 psi multiplies by it instead of dividing by rho0: the
+  // same bits for rho0 = 1, within one rounding otherwise)
+  double inv_rho0 = 1.0;
   // stochastic-rounding step salt in device memory (read at each collision);
   // nullptr reads as 0
   const unsigned* salt;
@@ -304,12 +307,12 @@ __device__ __forceinline__ void raise_flag(bool bad, int* flag) {
 
 // psi(rho) (definition after Eq. 5).
 template <typename C>
-__device__ __forceinline__ C psi_of(C rho, int form, C rho0) {
-  if (form == LBM_PSI_RHO) return rho;
+__device__ __forceinline__ C psi_of(C rho, const Phys& ph) {
+  if (ph.psi_form == LBM_PSI_RHO) return rho;
   if constexpr (sizeof(C) == 8) {
-    return rho0 * (1.0 - exp(-rho / rho0));
+    return ph.rho0 * (1.0 - exp(-rho / ph.rho0));
   } else {
-    return rho0 * (1.0f - expf(-rho / rho0));
+    return (float)ph.rho0 * (1.0f - expf(-rho * (float)ph.inv_rho0));
   }
 }
 

@@ -189,7 +189,7 @@ __device__ __forceinline__ void collide_math(const Phys& ph, const C f[Q], C pc,
 
 template <typename C>
 __device__ __forceinline__ void psi_math(const Phys& ph, C rho, C* out, int* flag) {
-  *out = psi_of<C>(rho, ph.psi_form, (C)ph.rho0);
+  *out = psi_of<C>(rho, ph);
   // non-positive, NaN or infinite density
   raise_flag(!(rho > (C)0) || !(rho <= (C)3.0e38), flag);
 }
