@@ -158,32 +158,46 @@ def test_aa_equals_ab_bitwise(L, precision, nsteps):
     np.testing.assert_array_equal(out[0][1], out[1][1])
 
 
+# Graph replay and eager steps give the same bits, including the
+# stochastic-rounding salt of the 2-byte forms (a pair of device words the
+# collision kernels advance; the word a step reads follows the A-B array, or
+# the step parity for AA) and graph chunks of odd length (diag_interval 3).
 @pytest.mark.parametrize("pattern", ["ab", "aa"])
-def test_graph_equals_eager_bitwise(L, pattern):
-    shape = (40, 12, 8)
+@pytest.mark.parametrize("precision", ["f32", "f16dev", "bf16dev"])
+@pytest.mark.parametrize("shape,k", [((40, 12, 8), 0), ((64, 8, 10), 0), ((64, 8, 10), 3)])
+def test_graph_equals_eager_bitwise(L, pattern, precision, shape, k):
     f0 = lbm_inputs.random_populations(*shape, seed=17)
     out = []
     for graph in (1, 0):
-        with make(L, shape, 0.9, G6, "f32", pattern) as lat:
+        with make(L, shape, 0.9, G6, precision, pattern, rho_ref=0.1) as lat:
             lat.set_option("graph", graph)
+            if k:
+                lat.set_option("diag_interval", k)
             lat.set_populations(f0)
             lat.step(3)
             lat.step(10)
+            lat.step(7)
             out.append(lat.populations())
     np.testing.assert_array_equal(out[0], out[1])
 
 
+# A saved state resumes bitwise, the stochastic-rounding salt of the 2-byte
+# forms restored from the step count (an odd one here), on the two-kernel
+# (48 wide) and the fused (64 wide, A-B) step.
 @pytest.mark.parametrize("pattern", ["ab", "aa"])
-def test_checkpoint_resume_bitwise(L, coex, pattern):
+@pytest.mark.parametrize("precision", ["f32", "f16dev"])
+@pytest.mark.parametrize("nx", [48, 64])
+def test_checkpoint_resume_bitwise(L, coex, pattern, precision, nx):
     rl, rv = coex
-    shape = (48, 24, 24)
-    with make(L, shape, 1.0, G6, "f32", pattern) as lat:
-        lat.init_ligament(6.0, 48.0, 0.05, 0.0, rl, rv, 2.0)
+    shape = (nx, 24, 24)
+    kw = dict(rho_ref=rv) if precision.endswith("dev") else {}
+    with make(L, shape, 1.0, G6, precision, pattern, **kw) as lat:
+        lat.init_ligament(6.0, float(nx), 0.05, 0.0, rl, rv, 2.0)
         lat.step(25)
         buf = lat.save_state()
         lat.step(30)
         full = lat.populations()
-    with make(L, shape, 1.0, G6, "f32", pattern) as lat:
+    with make(L, shape, 1.0, G6, precision, pattern, **kw) as lat:
         lat.load_state(buf)
         assert lat.step_count == 25
         lat.step(30)
