@@ -248,14 +248,16 @@ struct Phys {
   // at 1/tau)
   double s_e, s_eps, s_q, s_pi, s_m;
   // 1 / rho0 (FP32 psi multiplies by it instead of dividing by rho0: the
-  // same bits for rho0 = 1, within one rounding otherwise)
-  double inv_rho0 = 1.0;
+  // same bits for rho0 = 1, within one rounding otherwise); set by whoever
+  // builds a Phys (no default member initializers: Phys stays a trivial
+  // aggregate, which shared-memory copies of it need)
+  double inv_rho0;
   // stochastic-rounding step salt in device memory (read at each collision);
   // nullptr reads as 0
   const unsigned* salt;
   // where the collision kernel of a step writes the next step's salt (the
   // other word of a pair; nullptr: a separate one-thread kernel advances it)
-  unsigned* salt_next = nullptr;
+  unsigned* salt_next;
 };
 enum Collision { COLL_SRT = 0, COLL_MRT = 1 };
 __device__ __forceinline__ unsigned salt_of(const Phys& ph) { return ph.salt ? __ldg(ph.salt) : 0u; }

@@ -74,7 +74,8 @@ int lbm_diagnostics_noalloc(const void* f, int nx, int ny, int nz, int precision
   }
   // The partial kernel writes every slot the final kernel reads, so nothing
   // in the scratch has to start at zero.
-  const Phys ph{1.0, 0.0, 1.0, rho_ref, LBM_PSI_EXP, 0};
+  Phys ph{1.0, 0.0, 1.0, rho_ref, LBM_PSI_EXP, 0};
+  ph.inv_rho0 = 1.0;
   e = launch_diagnostics(precision, LAYOUT_LOCAL, g, ph, f, rho_l, rho_v, scratch, out, nullptr,
                          nullptr, nullptr, 0, (cudaStream_t)stream);
   if (e != cudaSuccess) return nfail(LBM_ERR_CUDA, std::string("diagnostics launch: ") + cudaGetErrorString(e));
