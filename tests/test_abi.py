@@ -55,13 +55,16 @@ def test_strerror(lbm):
     assert lbm.lbm_strerror(99) == "unknown status"
 
 
+# the last case is the smallest cube with more than 2^31 - 1 nodes (in-plane
+# indices are 32-bit)
 @pytest.mark.parametrize("args", [(2, 8, 8, 1.0, -6.0), (8, 8, 8, 0.5, -6.0),
-                                  (8, 8, 8, float("nan"), -6.0), (8, 8, 8, 1.0, float("inf"))])
+                                  (8, 8, 8, float("nan"), -6.0), (8, 8, 8, 1.0, float("inf")),
+                                  (1291, 1291, 1291, 1.0, -6.0)])
 def test_argument_validation_without_gpu(lbm, args):
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_create(*args)
     msg = str(ei.value)
-    assert "tau" in msg or "dimension" in msg or "G must" in msg
+    assert "tau" in msg or "dimension" in msg or "G must" in msg or "2^31-1 nodes" in msg
 
 
 def test_required_bytes(lbm):
