@@ -321,6 +321,46 @@ def test_full_size_sampled_one_step(L, coex):
     assert abs(d["mass"] - f.sum()) <= 1e-6 * f.sum()
 
 
+# The same full-size sampled step with FP16 / BF16 deviation storage (the
+# fused step with stochastic rounding, as the benchmark runs it): the oracle
+# steps the decoded stored state; the GPU result, computed in FP32, is stored
+# as a deviation from the shift w_a rho_ref rounded to the storage format, so
+# it may differ from the oracle by under one storage ulp of that deviation
+# (2^-10 or 2^-7 of it, 2^-24 absolute for FP16 subnormals) plus the FP32
+# arithmetic (a few 1e-7 of f).
+@pytest.mark.parametrize("precision,eps", [("f16dev", 2.0 ** -10), ("bf16dev", 2.0 ** -7)])
+def test_full_size_sampled_one_step_deviation_storage(L, coex, precision, eps):
+    rl, rv = coex
+    w = lbm_inputs.GRID_256
+    shape = (w.nx, w.ny, w.nz)
+    with make(L, shape, w.tau, w.G, precision, rho_ref=rv) as lat:
+        assert lat.get_option("fused") == 1 and lat.get_option("stochastic_rounding") == 1
+        lat.init_ligament(w.R0, w.lam, w.eps, w.phase, rl, rv, w.width)
+        lat.step(50)
+        f = lat.populations()
+        lat.step(1)
+        g = lat.populations()
+    N = w.nx * w.ny * w.nz
+    u = lbm_inputs.uniform(4243, 400)
+    nodes = np.unique(np.concatenate([(u * N).astype(np.int64),
+                                      [0, N - 1, w.nx - 1, (w.ny // 2) * w.nx + (w.nz // 2) * w.nx * w.ny + 24]]))
+    want = oracle.step_nodes(f, nodes, w.tau, w.G)
+    got = g.reshape(19, -1)[:, nodes].T
+    wts = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    cast = np.float16 if precision == "f16dev" else None
+    shift = wts * rv
+    if cast is not None:
+        shift = shift.astype(np.float32).astype(cast).astype(np.float64)
+    else:   # BF16: keep the top 16 bits of the FP32 value, rounded to nearest even
+        b = shift.astype(np.float32).view(np.uint32).astype(np.uint64)
+        b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+        shift = b.astype(np.uint32).view(np.float32).astype(np.float64)
+    dev = np.abs(want - shift[None, :])
+    tol = 1.01 * (eps * dev + 2.0 ** -24) + 4e-7 * np.abs(want)
+    err = np.abs(got - want)
+    assert (err <= tol).all(), float((err / tol).max())
+
+
 # ---------------------------------------------------------------------------
 # failure handling without faulting the GPU
 # ---------------------------------------------------------------------------
