@@ -361,6 +361,28 @@ def test_full_size_sampled_one_step_deviation_storage(L, coex, precision, eps):
     assert (err <= tol).all(), float((err / tol).max())
 
 
+# The 1024x512x512 ligament (268 M nodes, 40.8 GB of FP32 populations) in the
+# launch shape its benchmark uses: too large to step node by node on the
+# host, so checked by what holds at any size: the fused step keeps the mass
+# (FP32 storage: to rounding) and the total momentum of the periodic box (the
+# pair forces of Eq. 5 cancel), and every density stays finite.
+def test_grid1024_fused_conserves_mass_and_momentum(L, coex):
+    rl, rv = coex
+    w = lbm_inputs.GRID_1024
+    with make(L, (w.nx, w.ny, w.nz), w.tau, w.G, "f32") as lat:
+        assert lat.get_option("fused") == 1
+        lat.init_ligament(w.R0, w.lam, w.eps, w.phase, rl, rv, w.width)
+        d0 = lat.diagnostics()
+        lat.step(20)
+        lat.sync()
+        d1 = lat.diagnostics()
+    assert d0["numeric_ok"] == 1 and d1["numeric_ok"] == 1
+    assert abs(d1["mass"] / d0["mass"] - 1) < 1e-6
+    for k in range(3):
+        assert abs(d1["mom"][k] - d0["mom"][k]) < 1e-6 * d0["mass"]
+    assert d1["liquid_count"] > 0 and d1["rho_max"] < 1.2 * rl
+
+
 # ---------------------------------------------------------------------------
 # failure handling without faulting the GPU
 # ---------------------------------------------------------------------------
