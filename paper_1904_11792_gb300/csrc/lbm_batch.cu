@@ -84,8 +84,10 @@ __global__ void __launch_bounds__(256, MINB) batch_collide_kernel(const BatchIns
   const long long t = (long long)(blockIdx.x - I.tile0) * blockDim.x + threadIdx.x;
   const long long i = I.vec ? 2 * t : t;   // first node of the thread (x even when paired)
   if (i >= I.g.N) return;
-  const int row = (int)(i / I.g.nx);
-  const int x = (int)(i - (long long)row * I.g.nx);
+  // 32-bit index arithmetic (N < 2^31)
+  const int ii = (int)i;
+  const int row = ii / I.g.nx;
+  const int x = ii - row * I.g.nx;
   const int z = row / I.g.ny, y = row - z * I.g.ny;
   const long long plane = (long long)Q * I.g.N;
   const typename Prec<P>::T* src = pool_f + I.off_f + (long long)cur * plane;
