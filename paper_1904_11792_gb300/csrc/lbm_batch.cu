@@ -36,6 +36,10 @@ static_assert(std::is_trivially_default_constructible<BatchInst>::value &&
 
 namespace {
 
+// Chunks of blockDim.x nodes (node pairs) a collide-stream block covers, one
+// after the other: the block's instance lookup is paid once per chunks.
+constexpr int kChunks = 4;
+
 // Instance of a block: largest k with start[k] <= b (binary search over the
 // batch's cumulative tile starts, kept in the descriptors).
 __device__ __forceinline__ int find_inst(const BatchInst* __restrict__ inst, int count, int b,
@@ -67,36 +71,39 @@ __global__ void __launch_bounds__(256) batch_psi_kernel(const BatchInst* __restr
   }
 }
 
-// Collide-stream over the batch.  A block covers blockDim.x consecutive
-// nodes (or node pairs) of one instance in linear order, so a warp reads and
+// Collide-stream over the batch.  A block covers kChunks x blockDim.x
+// consecutive nodes (or node pairs) of one instance in linear order, blockDim.x
+// at a time, so a warp reads and
 // writes 32 (or 64) consecutive x of a plane, rows continuing across the end
 // of a row, and lattices of any size waste no lanes except at their end.
-// One thread looks up the block's instance and the block shares it.
+// Every thread looks up the block's instance (the same few cached loads).
 template <int P, int MINB>
 __global__ void __launch_bounds__(256, MINB) batch_collide_kernel(const BatchInst* __restrict__ inst,
                                                                   int count,
                                                                   typename Prec<P>::T* pool_f, int cur,
                                                                   const typename Prec<P>::C* pool_psi) {
-  __shared__ BatchInst sI;
-  if (threadIdx.x == 0) sI = inst[find_inst(inst, count, blockIdx.x, false)];
-  __syncthreads();
-  const BatchInst& I = sI;
-  const long long t = (long long)(blockIdx.x - I.tile0) * blockDim.x + threadIdx.x;
-  const long long i = I.vec ? 2 * t : t;   // first node of the thread (x even when paired)
-  if (i >= I.g.N) return;
-  // 32-bit index arithmetic (N < 2^31)
-  const int ii = (int)i;
-  const int row = ii / I.g.nx;
-  const int x = ii - row * I.g.nx;
-  const int z = row / I.g.ny, y = row - z * I.g.ny;
+  // every thread finds the block's instance itself (a few cached loads):
+  // sharing one thread's lookup through shared memory put the whole block
+  // behind a barrier for the length of that lookup
+  const BatchInst& I = inst[find_inst(inst, count, blockIdx.x, false)];
   const long long plane = (long long)Q * I.g.N;
   const typename Prec<P>::T* src = pool_f + I.off_f + (long long)cur * plane;
   typename Prec<P>::T* dst = pool_f + I.off_f + (long long)(cur ^ 1) * plane;
-  // the branch is uniform over a block (one instance per block)
-  if (I.vec)
-    collide_pair<P, MODE_AB>(I.g, I.ph, src, dst, pool_psi + I.off_psi, x, y, z);
-  else
-    collide_node<P, MODE_AB>(I.g, I.ph, src, dst, pool_psi + I.off_psi, x, y, z);
+  for (int c = 0; c < kChunks; ++c) {
+    const long long t = ((long long)(blockIdx.x - I.tile0) * kChunks + c) * blockDim.x + threadIdx.x;
+    const long long i = I.vec ? 2 * t : t;   // first node of the thread (x even when paired)
+    if (i >= I.g.N) return;
+    // 32-bit index arithmetic (N < 2^31)
+    const int ii = (int)i;
+    const int row = ii / I.g.nx;
+    const int x = ii - row * I.g.nx;
+    const int z = row / I.g.ny, y = row - z * I.g.ny;
+    // the branch is uniform over a block (one instance per block)
+    if (I.vec)
+      collide_pair<P, MODE_AB>(I.g, I.ph, src, dst, pool_psi + I.off_psi, x, y, z);
+    else
+      collide_node<P, MODE_AB>(I.g, I.ph, src, dst, pool_psi + I.off_psi, x, y, z);
+  }
 }
 
 template <int P>
@@ -202,7 +209,7 @@ int layout_tiles(lbm_batch_ctx* b) {
     I.vec = (b->vec && I.g.nx % 2 == 0) ? 1 : 0;
     const long long units = I.vec ? I.g.N / 2 : I.g.N;
     I.tile0 = (int)tiles;
-    tiles += (units + threads - 1) / threads;
+    tiles += (units + (long long)threads * kChunks - 1) / ((long long)threads * kChunks);
     I.psi_block0 = (int)psi_blocks;
     psi_blocks += (units + 255) / 256;
   }
