@@ -147,6 +147,44 @@ def test_mass_and_momentum_conservation():
     assert np.abs(F.sum(axis=(1, 2, 3))).max() <= 1e-13 * np.abs(F).sum()
 
 
+# The exported velocity of reading R7, u = (j + F/2)/rho.  At a converged
+# flat interface (a periodic slab, uniform across y and z) the discrete step
+# itself fixes j + F/2 = 0 at every node: steady mass balance makes the
+# population flux Phi through every x face the same, and the total momentum
+# (zero at the start, conserved because sum F = 0) makes it zero; the
+# pre-collision momentum at x is the flux in from both faces' post-collision
+# populations and the post-collision momentum (j + F under the velocity
+# shift of Eq. 6) the flux out, so j + (j + F) = Phi(x - 1/2) + Phi(x + 1/2)
+# = 0.  The bare j/rho = -F/(2 rho) there is of order 1e-2, so a wrong
+# half-force factor (0, 1, -1/2) fails.
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tau,G", [(1.0, -6.0), (0.8, -5.3)])
+def test_r7_velocity_vanishes_at_a_steady_flat_interface(tau, G):
+    r = oracle.coexistence(tau, G, n=48, tol=1e-13, rho_l0=2.4, rho_v0=0.1)
+    f = r["f"]
+    rho, ux, uy, uz = oracle.moments(f, G)
+    _, bx, by, bz = oracle.moments(f, G, bare=True)
+    assert np.abs(bx).max() > 5e-3                       # the force does act on the interface
+    assert max(np.abs(ux).max(), np.abs(uy).max(), np.abs(uz).max()) < 1e-9
+    assert np.abs(by).max() < 1e-14 and np.abs(bz).max() < 1e-14
+
+
+def test_r7_velocity_total_momentum_is_sum_j():
+    # sum_x rho u = sum_x j + sum_x F/2 = sum_x j on a periodic box (sum F = 0)
+    c, _, _ = oracle.lattice()
+    f = lbm_inputs.random_populations(10, 9, 7, seed=31)
+    rho, ux, uy, uz = oracle.moments(f, -5.8)
+    J = np.einsum("ak,azyx->k", c.astype(float), f)
+    P = np.array([(rho * u).sum() for u in (ux, uy, uz)])
+    assert np.abs(P - J).max() <= 1e-12 * rho.sum()
+    # and node by node the velocity differs from the bare one by F/(2 rho)
+    F = oracle.force(f, -5.8)
+    _, bx, by, bz = oracle.moments(f, -5.8, bare=True)
+    np.testing.assert_allclose(np.stack([ux, uy, uz]) - np.stack([bx, by, bz]),
+                               0.5 * F / rho[None], rtol=1e-12, atol=1e-15)
+
+
 # --------------------------------------------------------------------------
 # P6: brute force against the independent NumPy oracle
 # --------------------------------------------------------------------------
@@ -248,6 +286,49 @@ def test_ligament_init_geometry():
     xs = np.arange(nx)
     z = (est * np.exp(-2j * math.pi * xs / lam)).sum() * 2 / nx
     assert abs(abs(z) - eps * R0) < 1e-9 and abs(np.angle(z) - ph) < 1e-9
+
+
+# Tabulated-profile initial condition (reading R15): rho = prof(d) with d the
+# signed distance to the perturbed interface, linear interpolation between
+# the table's nodes and clamped beyond its ends.  Pinned to numpy's own
+# piecewise-linear interpolation (np.interp, which clamps the same way) on a
+# non-monotone table whose range leaves nodes clamped at both ends, and to
+# the pinned tanh initial condition: a finely tabulated tanh profile must
+# reproduce orc_init_ligament to the interpolation error.
+# --------------------------------------------------------------------------
+
+def _signed_distance(nx, ny, nz, R0, lam, eps, ph):
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    R = R0 * (1.0 + eps * np.cos(2 * math.pi * xx / lam + ph))
+    return np.hypot(yy - 0.5 * (ny - 1), zz - 0.5 * (nz - 1)) - R
+
+
+def test_init_profile_is_clamped_linear_interpolation():
+    nx, ny, nz = 20, 22, 22
+    R0, lam, eps, ph = 5.0, 20.0, 0.15, 0.9
+    prof = 0.05 + 2.6 * lbm_inputs.uniform(77, 23)      # not monotone: every segment differs
+    d0, dd = -3.1, 0.45                                  # table covers d in [-3.1, 6.8]
+    f = oracle.init_profile(nx, ny, nz, R0, lam, eps, ph, prof, d0, dd)
+    _, w, _ = oracle.lattice()
+    d = _signed_distance(nx, ny, nz, R0, lam, eps, ph)
+    assert (d < d0).any() and (d > d0 + dd * (prof.size - 1)).any()   # both clamps used
+    rho = np.interp(d, d0 + dd * np.arange(prof.size), prof)
+    np.testing.assert_allclose(f, w[:, None, None, None] * rho[None], rtol=1e-13, atol=0)
+
+
+def test_init_profile_of_a_fine_tanh_table_is_the_tanh_start():
+    nx, ny, nz = 24, 26, 26
+    R0, lam, eps, ph, rl, rv, W = 6.0, 24.0, 0.1, 0.4, 2.6, 0.07, 2.0
+    d0, dd = -20.0, 0.01
+    dk = d0 + dd * np.arange(4001)
+    prof = rv + 0.5 * (rl - rv) * (1.0 - np.tanh(2.0 * dk / W))
+    f = oracle.init_profile(nx, ny, nz, R0, lam, eps, ph, prof, d0, dd)
+    g = oracle.init_ligament(nx, ny, nz, R0, lam, eps, ph, rl, rv, W)
+    # linear interpolation error <= dd^2/8 max|rho''|; |rho''| <= 0.77 (rl - rv)(2/W)^2 / 2
+    bound = dd * dd / 8 * 0.77 * (rl - rv) * (2.0 / W) ** 2 / 2 / 3   # times w_0 = 1/3
+    err = np.abs(f - g).max()
+    assert err <= 1.05 * bound, (err, bound)
+    assert err > 0.05 * bound         # the table really is interpolated, not evaluated
 
 
 # --------------------------------------------------------------------------
