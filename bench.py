@@ -1,29 +1,36 @@
 """Benchmark of the D3Q19 Shan-Chen time step: GLUPS and fraction of the HBM roofline.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--workload grid1024|grid256|batch48]
 
-Workload: the grid-convergence ligament, periodic 256 x 128 x 128 (4.19 M
-nodes), R0 = 32, lambda = 256, eps = 0.02, tau = 1, G = -6, psi =
-1 - exp(-rho), FP32 storage and arithmetic, A-B streaming; liquid and
-vapour densities from a flat-interface run on the GPU.  One benchmark step
-= 10 lattice time steps plus the FP64 diagnostics of the state (mass,
-momentum, liquid volume, neck area), the diagnostic interval of this
-workload.  Each lattice step runs as the single-pass fused step (whose
-diagnostic-step variant also reduces the diagnostics) or as the two kernels
-(psi pass, with the diagnostics on the diagnostic step, then
-force/collide/stream), whichever the autotuner (run before the timed region)
-finds faster on this GPU.  The timed region replays the library's captured
-10-step graph once per benchmark step, as a user's lbm_step(10) does; the
-per-kernel times for the roofline come from a second pass of the same number
-of steps with an event pair around every kernel.  The populations (637 MB
-for both arrays) exceed the 129 MB L2, so no cache flush is needed between
-steps.  --workload grid1024 runs the same ligament form on 1024 x 512 x 512
-(268 M nodes, 40.8 GB of FP32 populations).
+Workload (default, grid1024): the large periodic ligament, 1024 x 512 x 512
+(268 M nodes), R0 = 96, lambda = 1024, eps = 0.01, G = -6, psi =
+1 - exp(-rho), tanh start of width 2 at the flat-interface densities of a GPU
+run; tau = 1 (tau = 0.7 goes non-finite for this collision at G = -6 from
+either start, so the lattice runs at the grid-convergence ligament's tau).
+Headline: FP32 storage and arithmetic, the step form the autotuner (run
+before the timed region) finds fastest on this GPU: the single-pass fused
+A-B step, or the two-kernel A-B / AA step with its block shape.  One
+benchmark step = 10 lattice time steps with the FP64 diagnostics of the
+first (mass, momentum, liquid volume, neck area) reduced inside the loop;
+the timed region replays the library's captured 10-step graph once per
+benchmark step, as a user's lbm_step(10) does.  The populations (40.8 GB
+A-B) exceed the 129 MB L2 many times over: no cache flush is needed.
 
---impl reference times the CPU FP64 oracle on this machine's cores on the
-same box (one lattice step per benchmark step, a bounded sample).
-With N > 1 (torchrun) every rank runs its own replica: the step has no
-data-path collective.
+The same JSON line carries the metric's comparisons ("variants"): FP16 and
+BF16 deviation storage (FP32 arithmetic) in the fused A-B step, FP32 and
+FP16-dev with AA in-place streaming (the two-kernel step), and the batched
+sweep of 48 uneven ligaments as one graph-captured pair of launches per step
+against 48 x 2 launches per step.  The dominant kernel's launch time comes
+from graph replay of plain (diagnostic-free) steps, one fused launch each.
+
+--workload grid256 runs the headline on the 256 x 128 x 128 grid-convergence
+ligament; --workload batch48 prints the batched sweep as its own line.
+--impl reference times the CPU FP64 oracle on this machine's cores on a
+bounded sample of the same workload (a 1024 x 512 x 8 slab: the full FP64
+A-B state would need 82 GB of host memory; the oracle's work per node does
+not depend on the box).  With N > 1 (torchrun) every rank runs its own
+replica: the step has no data-path collective.
 """
 from __future__ import annotations
 
@@ -42,19 +49,22 @@ sys.path.insert(0, ROOT)
 
 import lbm_inputs  # noqa: E402
 
-WORKLOAD = lbm_inputs.GRID_256
+WORKLOADS = {"grid1024": lbm_inputs.GRID_1024, "grid256": lbm_inputs.GRID_256}
 LBM_PER_STEP = 10
 METRIC = "D3Q19 Shan-Chen GLUPS (giga lattice-node updates per second)"
 UNIT = "GLUPS"
-# algorithmic bytes per lattice update of the collide-stream kernel (FP32):
-# read 19 f + write 19 f + read psi(x) once
-K2_BYTES_PER_LU = {"f64": 19 * 8 * 2 + 8, "f32": 19 * 4 * 2 + 4, "f16dev": 19 * 2 * 2 + 4,
-                   "bf16dev": 19 * 2 * 2 + 4}
-# two-pass model of the whole step (psi pass reads 19 f and writes psi)
-STEP_BYTES_PER_LU = {"f64": 3 * 19 * 8 + 16, "f32": 3 * 19 * 4 + 8, "f16dev": 3 * 19 * 2 + 8,
-                     "bf16dev": 3 * 19 * 2 + 8}
+ELEM = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
+# algorithmic bytes per lattice update (s = bytes per stored population):
+# collide-stream kernel: read 19 f + psi(x), write 19 f
+K2_BYTES_PER_LU = {p: 19 * s * 2 + (8 if p == "f64" else 4) for p, s in ELEM.items()}
+# two-kernel step: the psi pass reads 19 f and writes psi, then collide-stream
+STEP_BYTES_PER_LU = {p: 3 * 19 * s + (16 if p == "f64" else 8) for p, s in ELEM.items()}
 # single-pass fused step: read 19 f and write 19 f (psi stays on chip)
-FUSED_BYTES_PER_LU = {"f32": 19 * 4 * 2, "f16dev": 19 * 2 * 2, "bf16dev": 19 * 2 * 2}
+FUSED_BYTES_PER_LU = {p: 19 * s * 2 for p, s in ELEM.items() if p != "f64"}
+# variants carried in the headline line: (name, precision, pattern)
+VARIANTS = (("f16dev_ab", "f16dev", "ab"), ("bf16dev_ab", "bf16dev", "ab"), ("f32_aa", "f32", "aa"),
+            ("f16dev_aa", "f16dev", "aa"))
+SLAB_NZ = 8     # z planes of the oracle's sample of the 1024 x 512 x 512 workload
 
 
 def dist_env():
@@ -131,15 +141,16 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_ms: int = 50):
         self.index = index
+        self.period_ms = period_ms
         self.proc = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -176,7 +187,7 @@ class Clocks:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(r["sm"] for r in rows),
                 "sm_max_mhz": max(r["smax"] for r in rows), "reasons": sorted(reasons),
-                "samples": len(rows)}
+                "samples": len(rows), "period_ms": self.period_ms}
 
 
 def coexistence_densities(G, tau):
@@ -185,10 +196,94 @@ def coexistence_densities(G, tau):
     return r["rho_l"], r["rho_v"]
 
 
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def measure_lattice(torch, L, autotune, w, precision, patterns, args, rho_l, rho_v, world=1, clocks=None,
+                    full_tune=True):
+    """Times one lattice configuration: tuner choice, the timed benchmark
+    steps (graph replay of lbm_step(10) with in-loop diagnostics every 10
+    steps), and the per-step time of plain steps (graph replay, no
+    diagnostics), from which the fused step's launch time follows."""
+    import torch.distributed as dist
+    dev = precision.endswith("dev")
+    if args.no_tune:
+        choice = dict(pattern=patterns[-1], block=(128, 2, 1), occupancy=0, fused=int(args.fused),
+                      fused_fz=args.fused_fz, fused_group=args.fused_group)
+    elif full_tune:
+        choice = autotune.tune_lattice(w.nx, w.ny, w.nz, precision=precision, patterns=patterns,
+                                       blocks=((128, 2, 1), (64, 4, 1), (32, 8, 1)), occupancies=(2, 3),
+                                       tau=w.tau, G=w.G, steps=10, use_cache=False)
+    else:
+        # variants: the fused step's launch shapes where it applies (A-B),
+        # two block shapes of the two-kernel step otherwise
+        choice = autotune.tune_lattice(w.nx, w.ny, w.nz, precision=precision, patterns=patterns,
+                                       blocks=((128, 2, 1), (64, 4, 1)) if patterns == ("aa",) else
+                                       ((128, 2, 1),),
+                                       occupancies=(2, 3), tau=w.tau, G=w.G, steps=10, use_cache=False,
+                                       fused_runs=(8, 12, 16), fused_groups=(1, 4), reps=2)
+    pattern = choice["pattern"]
+    lat = L.Lattice(w.nx, w.ny, w.nz, w.tau, w.G, precision=precision, pattern=pattern,
+                    rho_ref=rho_v if dev else 0.0)
+    try:
+        autotune.apply(lat, choice)
+        fused = bool(lat.get_option("fused"))
+        lat.init_ligament(w.R0, w.lam, w.eps, w.phase, rho_l, rho_v, w.width)
+        lat.set_option("diag_interval", LBM_PER_STEP)
+        stream = torch.cuda.current_stream()
+        for _ in range(args.warmup):
+            lat.step(LBM_PER_STEP)
+        lat.sync()
+        lat.diag_history()
+        t0, t1 = _events(torch)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks is not None:
+            clocks.__enter__()
+        t0.record(stream)
+        for _ in range(args.steps):
+            lat.step(LBM_PER_STEP)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        if clocks is not None:
+            clocks.__exit__(None, None, None)
+        if world > 1:
+            dist.barrier()
+        ms = t0.elapsed_time(t1)
+        lat.sync()
+        hist = lat.diag_history()
+        # plain steps (no in-loop diagnostics): every lattice step is one
+        # launch of the fused kernel, or psi pass + collide-stream
+        lat.set_option("diag_interval", 0)
+        lat.step(LBM_PER_STEP)
+        torch.cuda.synchronize()
+        p0, p1 = _events(torch)
+        p0.record(stream)
+        for _ in range(args.steps):
+            lat.step(LBM_PER_STEP)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        ms_plain = p0.elapsed_time(p1)
+        lat.sync()
+        fz_used = int(lat.get_option("fused_fz_used")) if fused else 0
+        grp_used = int(lat.get_option("fused_group_used")) if fused else 0
+        out = dict(lat=None, choice=choice, pattern=pattern, fused=fused, ms=ms, ms_plain=ms_plain,
+                   hist=hist, fz_used=fz_used, grp_used=grp_used)
+        if args.keep_lattice:
+            out["lat"] = lat
+            lat = None
+        return out
+    finally:
+        if lat is not None:
+            lat.close()
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
-    from paper_1904_11792_gb300 import build, lbm as L
+    from paper_1904_11792_gb300 import autotune, build, lbm as L
 
     world, rank, local = dist_env()
     if world > 1:
@@ -196,148 +291,149 @@ def run_ours(args):
     torch.cuda.set_device(local)
     build.build()
     L.load()
-    w = lbm_inputs.GRID_1024 if args.workload == "grid1024" else WORKLOAD
-    if args.workload == "grid1024":
-        # 40.8 GB of FP32 populations: no host-buffer end-to-end leg and no
-        # CPU oracle sample at this size
-        args.no_extras = True
+    w = WORKLOADS[args.workload]
     N = w.nodes
     if args.rho_l and args.rho_v:
         rho_l, rho_v = args.rho_l, args.rho_v
     else:
         rho_l, rho_v = coexistence_densities(w.G, w.tau)
-    # streaming pattern, block shape and register budget from the autotuner
-    # (timed on this GPU before the measured region)
-    from paper_1904_11792_gb300 import autotune
     patterns = ("ab", "aa") if args.pattern == "auto" else (args.pattern,)
-    if args.no_tune:
-        choice = dict(pattern=patterns[-1], block=(128, 2, 1), occupancy=0, fused=int(args.fused),
-                      fused_fz=args.fused_fz, fused_group=args.fused_group)
-    else:
-        choice = autotune.tune_lattice(w.nx, w.ny, w.nz, precision=args.precision,
-                                       patterns=patterns,
-                                       blocks=((128, 2, 1), (64, 4, 1), (32, 8, 1)),
-                                       occupancies=(2, 3), tau=w.tau, G=w.G, steps=10,
-                                       use_cache=False)
-    pattern = choice["pattern"]
-    lat = L.Lattice(w.nx, w.ny, w.nz, w.tau, w.G, precision=args.precision, pattern=pattern,
-                    rho_ref=rho_v if args.precision.endswith("dev") else 0.0)
-    autotune.apply(lat, choice)
-    fused = bool(lat.get_option("fused"))
-    lat.init_ligament(w.R0, w.lam, w.eps, w.phase, rho_l, rho_v, w.width)
-    # diagnostics inside the time loop: the psi pass of every 10th step also
-    # reduces mass, momentum, liquid volume and the neck area (FP64)
-    lat.set_option("diag_interval", LBM_PER_STEP)
-    stream = torch.cuda.current_stream()
-
-    def bench_step():
-        lat.step(LBM_PER_STEP)
-
-    for _ in range(args.warmup):
-        bench_step()
-    lat.sync()
-    lat.diag_history()
-    # ---- timed region: whole steps as a user runs them (each benchmark step
-    # is one replay of the captured 10-step graph), device time by events on
-    # the library's stream ----
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        t0.record(stream)
-        for _ in range(args.steps):
-            bench_step()
-        t1.record(stream)
-        torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    ms = t0.elapsed_time(t1)
-    lat.sync()
-    hist = lat.diag_history()
-    # ---- per-kernel device time: the same number of steps again, with an
-    # event pair around every kernel (eager launches) ----
-    lat.set_option("kernel_timing", 1)
-    torch.cuda.synchronize()
-    for _ in range(args.steps):
-        bench_step()
-    torch.cuda.synchronize()
-    n_psi, ms_psi = L.lbm_kernel_time(lat.h, 0)
-    n_k2, ms_k2 = L.lbm_kernel_time(lat.h, 1)
-    n_fu, ms_fu = L.lbm_kernel_time(lat.h, 2)
-    lat.set_option("kernel_timing", 0)
-    lat.sync()
-    lat.diag_history()
-    d = hist[-1]
-    ms = max_over_ranks(ms, world, device="cuda")
+    peak, peak_kind = peaks()
+    clk = Clocks(local)
+    args.keep_lattice = not args.no_extras
+    m = measure_lattice(torch, L, autotune, w, args.precision, patterns, args, rho_l, rho_v, world, clk)
+    lat = m["lat"]
+    ms = max_over_ranks(m["ms"], world, device="cuda")
     lbm_steps = args.steps * LBM_PER_STEP
     value = job_value(N, lbm_steps, ms, world)
-    # ---- end to end through the C ABI with pinned host buffers ----
-    e2e = None if args.no_extras else run_e2e(args, lat, L, torch, N)
-    peak, peak_kind = peaks()
-    k2_avg = ms_k2 / max(n_k2, 1)
-    fu_avg = ms_fu / max(n_fu, 1)
-    # the dominant kernel: the fused step when it runs, else collide-stream
+    ms_step = ms / args.steps
+    plain_step_ms = m["ms_plain"] / lbm_steps
+    fused = m["fused"]
+    # the dominant kernel: the fused step when it runs (one launch per plain
+    # step), else collide-stream (its share of the plain step from the
+    # eager per-kernel timing below)
     if fused:
-        kname, bpl, avg, launches = "fused_step", FUSED_BYTES_PER_LU[args.precision], fu_avg, n_fu
-        # every step fused; the diagnostic step's variant also writes the
-        # partials that two small kernels reduce
+        kname, bpl, avg = "fused_step", FUSED_BYTES_PER_LU[args.precision], plain_step_ms
+        avg_from = ("graph replay of %d plain steps (no in-loop diagnostics), one fused launch per step, "
+                    "CUDA events on the library stream" % lbm_steps)
         step_model = bpl
         launches_per_step = LBM_PER_STEP + 2
     else:
-        kname, bpl, avg, launches = "collide_stream", K2_BYTES_PER_LU[args.precision], k2_avg, n_k2
+        kname, bpl = "collide_stream", K2_BYTES_PER_LU[args.precision]
+        n_k2, ms_k2 = 0, 0.0
+        if lat is not None:
+            lat.set_option("kernel_timing", 1)
+            lat.step(LBM_PER_STEP * 4)
+            n_k2, ms_k2 = L.lbm_kernel_time(lat.h, 1)
+            lat.set_option("kernel_timing", 0)
+            lat.sync()
+        avg = ms_k2 / n_k2 if n_k2 else plain_step_ms
+        avg_from = "events around each collide-stream launch (eager steps)"
         step_model = STEP_BYTES_PER_LU[args.precision]
         launches_per_step = 2 * (LBM_PER_STEP - 1) + 4
     achieved = bpl * N / (avg * 1e-3) / 1e9
-    fz_used = int(lat.get_option("fused_fz_used")) if fused else 0
-    grp_used = int(lat.get_option("fused_group_used")) if fused else 0
-    traffic = ncu_traffic(args.workload, args.precision, pattern, fused, fz_used, grp_used)
-    clocks = clk.summary()
+    traffic = ncu_traffic(args.workload, args.precision, m["pattern"], fused, m["fz_used"], m["grp_used"])
+    d = m["hist"][-1] if m["hist"] else {}
+    e2e = None
+    if lat is not None:
+        e2e = run_e2e(args, lat, L, torch, N)
+        lat.close()
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision == "f32" else args.precision,
+        "dtype": "f32" if args.precision in ("f32", "f16dev", "bf16dev") else args.precision,
         "data": "synthetic (seeded ligament initial condition, no dataset)",
         "config": {
             "workload": "ligament %dx%dx%d R0=%g lambda=%g eps=%g tau=%g G=%g, %s storage, %s "
                         "streaming" % (w.nx, w.ny, w.nz, w.R0, w.lam, w.eps, w.tau, w.G,
-                                       args.precision, pattern.upper()),
-            "tuned": {"pattern": pattern, "fused": fused, "fused_fz": choice.get("fused_fz", 0),
-                      "fused_group": choice.get("fused_group", 0), "fused_launch": [fz_used, grp_used],
-                      "block": choice["block"],
-                      "occupancy": choice["occupancy"], "vector": True},
+                                       args.precision, m["pattern"].upper()),
+            "tuned": {"pattern": m["pattern"], "fused": fused, "fused_fz": m["choice"].get("fused_fz", 0),
+                      "fused_group": m["choice"].get("fused_group", 0),
+                      "fused_launch": [m["fz_used"], m["grp_used"]], "block": m["choice"]["block"],
+                      "occupancy": m["choice"]["occupancy"], "vector": True},
             "nodes": N, "lattice_steps_per_step": LBM_PER_STEP, "diagnostics_every": LBM_PER_STEP,
             "parallelism": "replicas" if world > 1 else "single GPU",
-            "l2": "no flush: populations %.0f MB > 129 MB L2" % (
-                (2 if pattern == "ab" else 1) * 19 * N
-                * (4 if args.precision == "f32" else 8 if args.precision == "f64" else 2) / 1e6),
+            "l2": "no flush: populations %.1f GB > 129 MB L2" % (
+                (2 if m["pattern"] == "ab" else 1) * 19 * N * ELEM[args.precision] / 1e9),
             "rho_l": round(rho_l, 6), "rho_v": round(rho_v, 6),
-            "step_model_bytes_per_lu": round(step_model, 1),
+            "step_model_bytes_per_lu": step_model,
             "hbm_frac_step_model": round(value / world * step_model / peak, 4),
         },
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "peak_source": peak_kind,
-                     "traffic": traffic, "bytes_per_lu": bpl,
-                     "avg_launch_ms": round(avg, 5), "launches": launches,
-                     "avg_launch_from": "events around every kernel in a second pass of the same "
-                                        "number of steps",
-                     "collide_stream_avg_ms": round(k2_avg, 5), "collide_stream_launches": n_k2,
-                     "psi_pass_avg_ms": round(ms_psi / max(n_psi, 1), 5)},
+                     "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs, STREAM-style copy)",
+                     "traffic": traffic, "bytes_per_lu": bpl, "avg_launch_ms": round(avg, 5),
+                     "avg_launch_from": avg_from,
+                     "kernel_time_check": {"ten_launches_ms": round(10 * avg, 4),
+                                           "ms_per_step": round(ms_step, 4),
+                                           "ok": bool(10 * avg <= ms_step * 1.001)}},
         "e2e": e2e,
         "gpu_launches": int(args.steps * launches_per_step),
-        "clocks": clocks,
-        "diag_last": {"mass": d["mass"], "neck_radius": round(d["neck_radius"], 4),
-                      "step": d["step"], "records_in_timed_region": len(hist)},
+        "clocks": clk.summary(),
+        "diag_last": {"mass": d.get("mass"), "neck_radius": round(d.get("neck_radius", 0.0), 4),
+                      "step": d.get("step"), "records_in_timed_region": len(m["hist"])},
     }
+    if not args.no_variants and args.precision == "f32":
+        line["variants"] = run_variants(args, torch, L, autotune, w, rho_l, rho_v, value / world, peak, world)
     if rank == 0 and world == 1 and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline(w, rho_l, rho_v)
-    lat.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_variants(args, torch, L, autotune, w, rho_l, rho_v, fp32_glups, peak, world):
+    """FP16/BF16 deviation storage and AA in-place streaming on the same
+    workload, and the batched sweep, each timed like the headline."""
+    out = {}
+    keep = args.keep_lattice
+    args.keep_lattice = False
+    N = w.nodes
+    for name, prec, pattern in VARIANTS:
+        m = measure_lattice(torch, L, autotune, w, prec, (pattern,), args, rho_l, rho_v, world, full_tune=False)
+        ms = max_over_ranks(m["ms"], world, device="cuda")
+        v = N * args.steps * LBM_PER_STEP / (ms * 1e-3) / 1e9
+        bpl = FUSED_BYTES_PER_LU[prec] if m["fused"] else STEP_BYTES_PER_LU[prec]
+        plain = m["ms_plain"] / (args.steps * LBM_PER_STEP)
+        e = {"precision": prec, "pattern": pattern, "step_form": "fused" if m["fused"] else "two-kernel",
+             "value": round(v, 4), "ms_per_step": round(ms / args.steps, 4), "vs_fp32": round(v / fp32_glups, 4),
+             "bytes_per_lu": bpl, "hbm_frac_step_model": round(v * bpl / peak, 4),
+             "plain_step_ms": round(plain, 5),
+             "plain_step_hbm_frac": round(bpl * N / (plain * 1e-3) / 1e9 / peak, 4),
+             "fused_launch": [m["fz_used"], m["grp_used"]] if m["fused"] else None,
+             "numeric_ok": all(h["numeric_ok"] == 1 for h in m["hist"])}
+        if m["fused"]:
+            e["traffic"] = ncu_traffic(args.workload, prec, pattern, True, m["fz_used"], m["grp_used"])
+        out[name] = e
+    out["batched_sweep48"] = batch_sweep(args, torch, L, autotune, rho_l, rho_v)
+    args.keep_lattice = keep
+    return out
+
+
+def host_memory_available() -> int:
+    """Bytes of host memory this process may still take: MemAvailable,
+    bounded by the cgroup's limit less its current use where one is set."""
+    avail = None
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    try:
+        with open("/sys/fs/cgroup/memory.max") as fh:
+            lim = fh.read().strip()
+        with open("/sys/fs/cgroup/memory.current") as fh:
+            cur = int(fh.read().strip())
+        if lim != "max":
+            room = int(lim) - cur
+            avail = room if avail is None else min(avail, room)
+    except (OSError, ValueError):
+        pass
+    return avail if avail is not None else 0
 
 
 def run_e2e(args, lat, L, torch, N):
@@ -346,9 +442,14 @@ def run_e2e(args, lat, L, torch, N):
     benchmark step, and the final density field is read back."""
     lib = L.load()
     nbytes = L.lbm_state_bytes(lat.h)
+    need = nbytes + 8 * N
+    if 2 * need > host_memory_available():
+        return {"value": None, "unit": UNIT, "h2d_bytes_per_step": int(nbytes // args.steps),
+                "d2h_bytes_per_step": int(8 * N // args.steps),
+                "note": "not run: the pinned host buffers (%.1f GB) need more than half of the host memory "
+                        "available (%.1f GB)" % (need / 1e9, host_memory_available() / 1e9)}
     host_state = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-    rc = lib.lbm_save_state(lat.h, ctypes.c_void_p(host_state.data_ptr()), nbytes)
-    L.check(rc)
+    L.check(lib.lbm_save_state(lat.h, ctypes.c_void_p(host_state.data_ptr()), nbytes))
     host_rho = torch.empty(N, dtype=torch.float64, pin_memory=True)
     diag = (L.lbm_diag * 4)()
     got = ctypes.c_int()
@@ -365,26 +466,39 @@ def run_e2e(args, lat, L, torch, N):
     return {"value": round(N * steps / (t1 - t0) / 1e9, 4), "unit": UNIT,
             "h2d_bytes_per_step": int(nbytes // args.steps),
             "d2h_bytes_per_step": int(ctypes.sizeof(L.lbm_diag) + 8 * N // args.steps),
-            "note": "host wall clock around the C ABI calls: state upload, graph-replayed steps "
-                    "with a diagnostics read-back each benchmark step, density download"}
+            "note": "host wall clock around the C ABI calls: state upload from pinned memory (%.1f GB), "
+                    "graph-replayed steps with a diagnostics read-back each benchmark step, density "
+                    "download (%.1f GB); transfers amortised per benchmark step" % (nbytes / 1e9, 8 * N / 1e9)}
+
+
+def oracle_sample(w, rho_l, rho_v):
+    """The oracle's state for a bounded sample of workload w: the lattice
+    itself when its FP64 A-B state is small, else a slab of SLAB_NZ z planes
+    of the same x-y cross-section (the same per-node work)."""
+    import oracle
+    nz = w.nz if w.nodes <= (1 << 23) else SLAB_NZ
+    f = oracle.init_ligament(w.nx, w.ny, nz, w.R0, w.lam, w.eps, w.phase, rho_l, rho_v, w.width)
+    what = ("the %dx%dx%d ligament" % (w.nx, w.ny, w.nz) if nz == w.nz else
+            "a %dx%dx%d periodic slab of the %dx%dx%d ligament's cross-section (the full FP64 A-B state "
+            "needs %.0f GB of host memory)" % (w.nx, w.ny, nz, w.nx, w.ny, w.nz, 2 * 19 * 8 * w.nodes / 1e9))
+    return f, w.nx * w.ny * nz, what
 
 
 def cpu_baseline(w, rho_l, rho_v, budget_s: float = 12.0):
-    """The oracle, as it stands, on this machine's cores: FP64 A-B steps of the
-    same 256x128x128 ligament, as many as fit in about budget_s seconds."""
+    """The oracle, as it stands, on this machine's cores: FP64 A-B steps of a
+    bounded sample of the workload, as many as fit in about budget_s seconds."""
     import oracle
-    f = oracle.init_ligament(w.nx, w.ny, w.nz, w.R0, w.lam, w.eps, w.phase, rho_l, rho_v, w.width)
+    f, n_nodes, what = oracle_sample(w, rho_l, rho_v)
     f = oracle.step(f, w.tau, w.G, 1)          # first touch of the buffers, untimed
     n, el = 0, 0.0
     t = time.perf_counter()
-    while el < budget_s and n < 5000:           # blocks of 8 steps until the budget is spent
-        f = oracle.step(f, w.tau, w.G, 8)
-        n += 8
+    while el < budget_s and n < 5000:           # blocks of 4 steps until the budget is spent
+        f = oracle.step(f, w.tau, w.G, 4)
+        n += 4
         el = time.perf_counter() - t
-    return {"value": round(w.nodes * n / el / 1e9, 6), "unit": UNIT,
+    return {"value": round(n_nodes * n / el / 1e9, 6), "unit": UNIT,
             "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "%d FP64 A-B steps of the %dx%dx%d ligament (%.1f s)" % (
-                n, w.nx, w.ny, w.nz, el)}
+            "sample": "%d FP64 A-B steps of %s (%.1f s)" % (n, what, el)}
 
 
 def run_reference(args):
@@ -392,23 +506,23 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    w = WORKLOAD
+    w = WORKLOADS.get(args.workload, lbm_inputs.GRID_1024)
     rc = oracle.coexistence(w.tau, w.G, n=64, tol=1e-10, rho_l0=2.6, rho_v0=0.07)
-    f = oracle.init_ligament(w.nx, w.ny, w.nz, w.R0, w.lam, w.eps, w.phase, rc["rho_l"],
-                             rc["rho_v"], w.width)
-    # a benchmark step is up to LBM_PER_STEP lattice steps, as in the GPU
-    # arm, fewer when that keeps the whole run within about two minutes of
-    # host time (about 0.07 s per lattice step on 16 cores)
-    per = max(1, min(LBM_PER_STEP, 1700 // max(1, args.steps + args.warmup)))
+    f, n_nodes, what = oracle_sample(w, rc["rho_l"], rc["rho_v"])
+    # a benchmark step is up to LBM_PER_STEP lattice steps of the sample, as
+    # in the GPU arm, fewer when that keeps the whole run within about two
+    # minutes of host time (about 0.07 s per lattice step of 4 M nodes on 16
+    # cores)
+    budget = 1700 * (1 << 22) // n_nodes
+    per = max(1, min(LBM_PER_STEP, budget // max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         f = oracle.step(f, w.tau, w.G, per)
     t = time.perf_counter()
     for _ in range(args.steps):
         f = oracle.step(f, w.tau, w.G, per)
     el = time.perf_counter() - t
-    value = w.nodes * args.steps * per / el / 1e9
-    sample = "%d FP64 A-B lattice steps of the %dx%dx%d ligament, %d per benchmark step" % (
-        args.steps * per, w.nx, w.ny, w.nz, per)
+    value = n_nodes * args.steps * per / el / 1e9
+    sample = "%d FP64 A-B lattice steps of %s, %d per benchmark step" % (args.steps * per, what, per)
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -417,7 +531,7 @@ def run_reference(args):
         "data": "synthetic (seeded ligament initial condition, no dataset)",
         "config": {"workload": "ligament %dx%dx%d R0=%g lambda=%g eps=%g tau=%g G=%g, CPU FP64 "
                                "oracle" % (w.nx, w.ny, w.nz, w.R0, w.lam, w.eps, w.tau, w.G),
-                   "nodes": w.nodes},
+                   "nodes": w.nodes, "sample_nodes": n_nodes},
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": oracle.num_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -426,46 +540,51 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
+def batch_sweep(args, torch, L, autotune, rho_l, rho_v, precision="f32"):
     """The batched sweep: 48 periodic ligaments of uneven size (R0 in
-    {8..24}, box lambda x 4R0 x 4R0, tau in [0.6, 1]), FP32, stepped as one
-    graph-replayed pair of launches per step for the whole batch (block size
-    and register budget from the autotuner), against the same steps as
-    48 x 2 launches per step, each instance launched as a standalone lattice
-    of its size runs by default."""
-    import torch
-    from paper_1904_11792_gb300 import autotune, build, lbm as L
-    torch.cuda.set_device(dist_env()[2])
-    build.build()
-    L.load()
-    rho_l, rho_v = (args.rho_l, args.rho_v) if (args.rho_l and args.rho_v) else \
-        coexistence_densities(-6.0, 1.0)
+    {8..24}, box lambda x 4R0 x 4R0), stepped as one graph-replayed pair of
+    launches per step for the whole batch (block size and register budget
+    from the autotuner), against the same steps as 48 x 2 launches per step,
+    each instance launched as a standalone lattice of its size.  Timed on
+    the sweep with tau lifted to >= 0.8, where every instance stays finite
+    (reading R15); the instances of the drawn tau in [0.6, 1] that go
+    non-finite are listed from a separate untimed run."""
     sweep = lbm_inputs.batched_sweep(48)
-    insts = [dict(nx=i.nx, ny=i.ny, nz=i.nz, tau=i.tau, G=i.G, R0=i.R0, lam=i.lam, eps=i.eps,
-                  phase=i.phase, rho_l=rho_l, rho_v=rho_v, width=i.width) for i in sweep]
-    total = sum(d["nx"] * d["ny"] * d["nz"] for d in insts)
+
+    def insts(lift):
+        return [dict(nx=i.nx, ny=i.ny, nz=i.nz, tau=max(i.tau, 0.8) if lift else i.tau, G=i.G, R0=i.R0,
+                     lam=i.lam, eps=i.eps, phase=i.phase, rho_l=rho_l, rho_v=rho_v, width=i.width)
+                for i in sweep]
+
+    stable = insts(True)
+    total = sum(d["nx"] * d["ny"] * d["nz"] for d in stable)
     stream = torch.cuda.current_stream()
-    with L.Batch(insts, precision=args.precision) as b:
+    with L.Batch(stable, precision=precision) as b:
         b.init()
         tuned = autotune.tune_batch(b, blocks=((256, 1, 1), (128, 1, 1)), occupancies=(2, 3, 4), steps=10)
-        b.init()
 
-        def timed(fn, nsteps):
+        def timed(fn):
+            b.init()                       # each arm from the same initial state
             for _ in range(args.warmup):
                 fn(LBM_PER_STEP)
             torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0, e1 = _events(torch)
             e0.record(stream)
-            for _ in range(nsteps):
+            for _ in range(args.steps):
                 fn(LBM_PER_STEP)
             e1.record(stream)
             torch.cuda.synchronize()
-            return e0.elapsed_time(e1)
+            ok = [b.diagnostics(k)["numeric_ok"] == 1 for k in range(len(stable))]
+            return e0.elapsed_time(e1), all(ok)
 
-        with Clocks(dist_env()[2]) as clk:
-            ms_b = timed(b.step, args.steps)
-        ms_s = timed(b.step_sequential, args.steps)
-        unstable = [k for k in range(len(insts)) if b.diagnostics(k)["numeric_ok"] != 1]
+        ms_b, ok_b = timed(b.step)
+        ms_s, ok_s = timed(b.step_sequential)
+        b.sync()
+    unstable = []
+    with L.Batch(insts(False), precision=precision) as b:
+        b.init()
+        b.step(200)
+        unstable = [k for k in range(len(sweep)) if b.diagnostics(k)["numeric_ok"] != 1]
         try:
             b.sync()
         except L.LbmError:
@@ -474,23 +593,36 @@ def run_batch(args):
     value = total * steps / (ms_b * 1e-3) / 1e9
     seq = total * steps / (ms_s * 1e-3) / 1e9
     peak, _ = peaks()
+    return {"value": round(value, 4), "unit": UNIT, "ms_per_step": round(ms_b / args.steps, 4),
+            "sequential_value": round(seq, 4), "speedup_vs_sequential": round(value / seq, 3),
+            "total_nodes": total, "precision": precision, "tuned": tuned,
+            "bytes_per_lu": STEP_BYTES_PER_LU[precision],
+            "hbm_frac_step_model": round(value * STEP_BYTES_PER_LU[precision] / peak, 4),
+            "hbm_frac_floor_160": round(value * 160 / peak, 4),
+            "numeric_ok_batched": ok_b, "numeric_ok_sequential": ok_s,
+            "sweep": "48 periodic ligaments, R0 in {8,12,16,20,24}, lambda/R0 in [4.5,12], eps=0.05, G=-6, "
+                     "box lambda x 4R0 x 4R0, tau drawn in [0.6,1.0] and lifted to >= 0.8 for the timing",
+            "unstable_at_drawn_tau": unstable,
+            "mode": "one psi + one collide launch per step for all instances, graph replay"}
+
+
+def run_batch(args):
+    import torch
+    from paper_1904_11792_gb300 import autotune, build, lbm as L
+    torch.cuda.set_device(dist_env()[2])
+    build.build()
+    L.load()
+    rho_l, rho_v = (args.rho_l, args.rho_v) if (args.rho_l and args.rho_v) else \
+        coexistence_densities(-6.0, 1.0)
+    with Clocks(dist_env()[2]) as clk:
+        r = batch_sweep(args, torch, L, autotune, rho_l, rho_v, args.precision)
     line = {
-        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_b / args.steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded ligament sweep, no dataset)",
-        "config": {"workload": "batched sweep: 48 periodic ligaments, R0 in {8,12,16,20,24}, "
-                               "lambda/R0 in [4.5,12], tau in [0.6,1.0], G=-6, eps=0.05, box "
-                               "lambda x 4R0 x 4R0, %s A-B" % args.precision,
-                   "total_nodes": total, "lattice_steps_per_step": LBM_PER_STEP,
-                   "mode": "one psi + one collide launch per step for all instances, graph",
-                   "tuned": tuned,
-                   "sequential_glups": round(seq, 4),
-                   "speedup_vs_sequential": round(value / seq, 3),
-                   "hbm_frac_step_model": round(value * STEP_BYTES_PER_LU[args.precision] / peak, 4),
-                   "unstable_instances": unstable,
-                   "note": "instances with tau < ~0.75 go non-finite from the tanh start "
-                           "(G=-6 SRT stability limit); their launches still run in full"},
+        "config": dict({"workload": "batched sweep: " + r["sweep"]}, **{k: v for k, v in r.items()
+                                                                        if k not in ("value", "unit")}),
         "clocks": clk.summary(),
         "gpu_launches": int(args.steps * LBM_PER_STEP * 2),
     }
@@ -500,12 +632,12 @@ def run_batch(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("grid256", "grid1024", "batch48"), default="grid256",
-                    help="grid256: the headline ligament; grid1024: the 1024x512x512 ligament "
-                         "(268 M nodes; device legs only); batch48: the batched sweep")
+    ap.add_argument("--workload", choices=("grid1024", "grid256", "batch48"), default="grid1024",
+                    help="grid1024: the 1024x512x512 ligament (268 M nodes), the headline; grid256: the "
+                         "256x128x128 grid-convergence ligament; batch48: the batched sweep alone")
     ap.add_argument("--precision", choices=("f32", "f64", "f16dev", "bf16dev"), default="f32")
     ap.add_argument("--pattern", choices=("auto", "ab", "aa"), default="auto",
                     help="streaming pattern; auto = the autotuner's choice")
@@ -513,8 +645,7 @@ def main():
                     help="liquid density (with --rho-v: skip the flat-interface run)")
     ap.add_argument("--rho-v", type=float, default=None)
     ap.add_argument("--fused", action="store_true",
-                    help="with --no-tune: the single-pass fused step on non-diagnostic A-B steps "
-                         "(the autotuner otherwise chooses)")
+                    help="with --no-tune: the single-pass fused step (the autotuner otherwise chooses)")
     ap.add_argument("--fused-fz", type=int, default=0,
                     help="with --no-tune --fused: z planes per block (0 = automatic)")
     ap.add_argument("--fused-group", type=int, default=0,
@@ -523,6 +654,8 @@ def main():
                     help="skip the autotuner (default launch configuration; profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the end-to-end and CPU-baseline legs (profiling runs)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP16/BF16/AA/batched comparisons (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

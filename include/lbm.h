@@ -156,9 +156,10 @@ int lbm_set_stream(lbm_handle h, void *stream);
  * the default: 2 for the two-node kernel, 3 for the one-node kernel),
  * "vector" (0/1, default 1: when nx is even each thread updates two
  * neighbouring nodes with 2-element vector loads and stores; block_x then
- * counts node pairs), "fused" (0/1, default 1: A-B steps without in-loop
- * diagnostics run as one single-pass kernel that computes psi per tile in
- * shared memory, reading the populations once per step; applies to FP32,
+ * counts node pairs), "fused" (0/1, default 1: A-B steps run as one
+ * single-pass kernel that computes psi per tile in shared memory, reading
+ * the populations once per step, with a variant that also reduces the
+ * in-loop diagnostics on diagnostic steps; applies to FP32,
  * FP16-dev and BF16-dev storage when nx % 64 == 0 and ny % 4 == 0, other
  * lattices take the two-kernel step; results equal the two-kernel step
  * bitwise; lbm_get_option answers whether it applies), "fused_fz" (z planes
@@ -212,8 +213,16 @@ int lbm_init_ligament(lbm_handle h, double R0, double lambda, double eps, double
 int lbm_init_profile(lbm_handle h, double R0, double lambda, double eps, double phase,
                      const double *prof, int n, double d0, double dd);
 
-/* Enqueues n >= 0 time steps (psi pass, then fused force + collision +
- * streaming) on the handle's stream and returns without waiting. */
+/* Enqueues n >= 0 time steps on the handle's stream and returns without
+ * waiting.  Each step computes psi (definition after Eq. 5), the force of
+ * Eq. 5, the velocity shift of Eq. 6, the equilibrium of Eq. 2, the BGK
+ * relaxation of Eq. 3 and streaming.  Where option "fused" applies (A-B
+ * streaming, FP32 or 2-byte storage, nx % 64 == 0, ny % 4 == 0; the
+ * default) a step is one single-pass kernel that computes psi per tile in
+ * shared memory (its diagnostic-step variant also reduces the in-loop
+ * diagnostics); otherwise it is a psi pass followed by one kernel of force,
+ * collision and streaming.  Steps are replayed from captured CUDA graphs
+ * unless option "kernel_timing" is on. */
 int lbm_step(lbm_handle h, int n);
 
 /* Diagnostics recorded inside lbm_step (option "diag_interval"), oldest

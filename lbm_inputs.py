@@ -108,9 +108,9 @@ PRECISION_512 = Ligament("ligament 512x256x256 R0=48", 512, 256, 256, 48.0, 512.
 # Large single ligament: 1024x512x512, R0 = 96, lambda = 1024, eps 0.01, tau 0.7.
 LARGE_1024 = Ligament("ligament 1024x512x512 R0=96", 1024, 512, 512, 96.0, 1024.0, 0.01, 0.7,
                       steps=5000)
-# The large lattice at the grid-convergence ligament's tau = 1 (tau = 0.7 is
-# unstable for the SRT collision at G = -6): throughput at 268 M nodes.
-GRID_1024 = Ligament("ligament 1024x512x512 R0=96 tau=1", 1024, 512, 512, 96.0, 1024.0, 0.02, 1.0,
+# The large ligament at tau = 1 instead of 0.7 (tau = 0.7 is unstable for the
+# SRT collision at G = -6 from either start): throughput at 268 M nodes.
+GRID_1024 = Ligament("ligament 1024x512x512 R0=96 tau=1", 1024, 512, 512, 96.0, 1024.0, 0.01, 1.0,
                      steps=5000)
 
 

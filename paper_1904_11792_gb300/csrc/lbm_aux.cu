@@ -165,11 +165,16 @@ int diag_row_blocks(const Geom& g) {
   return (int)rb;
 }
 
-// Per-thread sums run in the compute precision (FP32 except in FP64 mode:
-// GB300's FP64 units are slow) over the thread's rows, then every block
-// reduces them in FP64 in a fixed order.
+// Each node's momentum and liquid fraction are computed in the compute
+// precision (FP32 except in FP64 mode), its density as that sum plus its
+// rounding error (rho_of_x), and all are converted to FP64 before the first
+// add: the per-thread sums over the thread's rows, the warp
+// shuffle tree and the block sums of mass, momentum and the weighted liquid
+// volume are all FP64, so the totals carry no reduction error above FP64
+// rounding, whatever the storage precision.  Counts, extrema and the
+// numeric flag are exact in any precision.
 template <int P, bool WRITE_PSI, int LAYOUT>
-__global__ void __launch_bounds__(DX* DY) diag_partial_kernel(Geom g, Phys ph,
+__global__ void __launch_bounds__(DX* DY, 2) diag_partial_kernel(Geom g, Phys ph,
                                                               const typename Prec<P>::T* f,
                                                               double rho_l, double rho_v,
                                                               double* slices, double* blocks,
@@ -179,8 +184,8 @@ __global__ void __launch_bounds__(DX* DY) diag_partial_kernel(Geom g, Phys ph,
   const int x = blockIdx.x * DX + tx;
   const long long rows = (long long)g.ny * g.nz;
   const C thr = (C)(0.5 * (rho_l + rho_v)), inv = (C)(1.0 / (rho_l - rho_v)), rv = (C)rho_v;
-  C s_mass = 0, s_jx = 0, s_jy = 0, s_jz = 0, s_vol = 0, umax = 0;
-  C rmin = (C)3.0e38, rmax = (C)-3.0e38;
+  double s_mass = 0.0, s_jx = 0.0, s_jy = 0.0, s_jz = 0.0, s_vol = 0.0;
+  C umax = 0, rmin = (C)3.0e38, rmax = (C)-3.0e38;
   int cnt = 0;
   bool bad = false;
   const C s0 = (C)shift_d<P>(0, ph.rho_ref);
@@ -203,17 +208,18 @@ __global__ void __launch_bounds__(DX* DY) diag_partial_kernel(Geom g, Phys ph,
           fv[a] = Prec<P>::load(f + (long long)opp(a) * g.N + nb.idx(-cx(a), -cy(a), -cz(a)),
                                 a == 0 ? s0 : (a <= 6 ? s1 : s2));
       }
-      const C rho = rho_of<C>(fv);
+      C rho_lo;
+      const C rho = rho_of_x(fv, rho_lo);   // rho_of bitwise, plus its rounding error
       C jx, jy, jz;
       mom_of<C>(fv, jx, jy, jz);
       if constexpr (WRITE_PSI) psi[i] = psi_of<C>(rho, ph);
-      s_mass += rho;
-      s_jx += jx;
-      s_jy += jy;
-      s_jz += jz;
+      s_mass += (double)rho + (double)rho_lo;
+      s_jx += (double)jx;
+      s_jy += (double)jy;
+      s_jz += (double)jz;
       C phi = (rho - rv) * inv;
       phi = phi < (C)0 ? (C)0 : (phi > (C)1 ? (C)1 : phi);
-      s_vol += phi;
+      s_vol += (double)phi;
       cnt += rho > thr;
       const C u = sqrt(xfma(jz, jz, xfma(jy, jy, xmul(jx, jx)))) / rho;
       umax = u > umax ? u : umax;
@@ -225,11 +231,11 @@ __global__ void __launch_bounds__(DX* DY) diag_partial_kernel(Geom g, Phys ph,
   if constexpr (WRITE_PSI) raise_flag(bad, flag);
   // per-slice sums over the block's 8 row groups (FP64, fixed order)
   __shared__ double sh_s[2][DY][DX];
-  sh_s[0][ty][tx] = (double)s_vol;
+  sh_s[0][ty][tx] = s_vol;
   sh_s[1][ty][tx] = (double)cnt;
-  // block totals: a fixed shuffle tree within each warp (in the compute
-  // precision), then the 8 warp results in FP64 in warp order
-  C v[6] = {s_mass, s_jx, s_jy, s_jz, s_vol, (C)0};
+  // block totals: a fixed FP64 shuffle tree within each warp, then the 8
+  // warp results in FP64 in warp order
+  double v[5] = {s_mass, s_jx, s_jy, s_jz, s_vol};
   float c_f = (float)cnt;  // exact below 2^24 nodes per warp
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -246,11 +252,11 @@ __global__ void __launch_bounds__(DX* DY) diag_partial_kernel(Geom g, Phys ph,
   const int anybad = __any_sync(0xffffffffu, bad);
   __shared__ double sh_w[NG][DY];
   if (tx == 0) {
-    sh_w[0][ty] = (double)v[0];
-    sh_w[1][ty] = (double)v[1];
-    sh_w[2][ty] = (double)v[2];
-    sh_w[3][ty] = (double)v[3];
-    sh_w[4][ty] = (double)v[4];
+    sh_w[0][ty] = v[0];
+    sh_w[1][ty] = v[1];
+    sh_w[2][ty] = v[2];
+    sh_w[3][ty] = v[3];
+    sh_w[4][ty] = v[4];
     sh_w[5][ty] = (double)c_f;
     sh_w[6][ty] = (double)umax;
     sh_w[7][ty] = (double)rmin;

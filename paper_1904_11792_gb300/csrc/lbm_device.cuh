@@ -133,6 +133,40 @@ __device__ __forceinline__ C rho_of(const C f[Q]) {
           s11 = f[11] + f[12], s13 = f[13] + f[14], s15 = f[15] + f[16], s17 = f[17] + f[18];
   return ((f[0] + s1) + (s3 + s5)) + (((s7 + s9) + (s11 + s13)) + (s15 + s17));
 }
+// Density with its rounding error, for the FP64 mass diagnostics: the same
+// tree as rho_of, each add done as Knuth's error-free TwoSum (s = a + b
+// rounded, e = (a - (s - (s - a))) + (b - (s - a)) exactly, in round to
+// nearest), so hi equals rho_of bitwise and hi + lo is the exact sum of the
+// 19 values to within the FP32 rounding of the 18 small error terms (about
+// 2^-44 of rho).  The mass of FP32 and 2-byte states then reaches the FP64
+// reduction without the per-node rounding of rho, which in a uniform
+// region is the same at every node and does not average out.  FP64
+// storage: lo = 0.
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+  return s;
+}
+__device__ __forceinline__ float rho_of_x(const float f[Q], float& lo) {
+  float e[18];
+  const float s1 = two_sum(f[1], f[2], e[0]), s3 = two_sum(f[3], f[4], e[1]), s5 = two_sum(f[5], f[6], e[2]),
+              s7 = two_sum(f[7], f[8], e[3]), s9 = two_sum(f[9], f[10], e[4]), s11 = two_sum(f[11], f[12], e[5]),
+              s13 = two_sum(f[13], f[14], e[6]), s15 = two_sum(f[15], f[16], e[7]),
+              s17 = two_sum(f[17], f[18], e[8]);
+  const float a = two_sum(two_sum(f[0], s1, e[9]), two_sum(s3, s5, e[10]), e[11]);
+  const float b = two_sum(two_sum(s7, s9, e[12]), two_sum(s11, s13, e[13]), e[14]);
+  const float c = two_sum(b, two_sum(s15, s17, e[15]), e[16]);
+  const float hi = two_sum(a, c, e[17]);
+  lo = (((e[0] + e[1]) + (e[2] + e[3])) + ((e[4] + e[5]) + (e[6] + e[7]))) +
+       (((e[8] + e[9]) + (e[10] + e[11])) + ((e[12] + e[13]) + (e[14] + e[15])) + (e[16] + e[17]));
+  return hi;
+}
+__device__ __forceinline__ double rho_of_x(const double f[Q], double& lo) {
+  lo = 0.0;
+  return rho_of<double>(f);
+}
 template <typename C>
 __device__ __forceinline__ void mom_of(const C f[Q], C& jx, C& jy, C& jz) {
   const C d1 = f[1] - f[2], d3 = f[3] - f[4], d5 = f[5] - f[6], d7 = f[7] - f[8], d9 = f[9] - f[10],

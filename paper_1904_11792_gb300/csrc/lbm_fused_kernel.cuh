@@ -192,10 +192,13 @@ __device__ __forceinline__ void issue_plane(unsigned char* smem, const Maps& m, 
 }
 
 // Diagnostics of the step's starting state, reduced in the same pass (DIAG):
-// every thread sums, in the compute precision, the nodes of the planes its
-// block owns (the run z0 .. z1 - 1, not the two halo planes), and the block
-// writes FP64 partials in the layout the diagnostics reduction reads: slice
-// sums [row block][x][2] with one row block per (tile row, z run), and block
+// every thread sums the nodes of the planes its block owns (the run z0 ..
+// z1 - 1, not the two halo planes), each node's momentum, liquid fraction
+// and density (with its rounding error, rho_of_x) converted to FP64 before
+// the first add (the sums, the warp
+// shuffle tree and the block sums are FP64), and the block writes FP64
+// partials in the layout the diagnostics reduction reads: slice sums
+// [row block][x][2] with one row block per (tile row, z run), and block
 // totals [block][DIAG_NG].
 struct DiagOut {
   double rho_l, rho_v;
@@ -305,9 +308,9 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
   const unsigned salt = (Prec<P>::dev && ph.sr) ? salt_of(ph) : 0u;
   V prev[Q];   // stored populations of this thread's two nodes, previous plane
   // diagnostics sums (DIAG): block totals and the two x columns of the thread
-  C d_mass = 0, d_jx = 0, d_jy = 0, d_jz = 0, d_vol = 0, d_umax = 0;
-  C d_rmin = (C)3.0e38, d_rmax = (C)-3.0e38;
-  C col_w[2] = {0, 0}, col_n[2] = {0, 0};
+  double d_mass = 0.0, d_jx = 0.0, d_jy = 0.0, d_jz = 0.0, d_vol = 0.0, col_w[2] = {0.0, 0.0};
+  C d_umax = 0, d_rmin = (C)3.0e38, d_rmax = (C)-3.0e38;
+  C col_n[2] = {0, 0};
   bool d_bad = false;
   const C d_thr = (C)(0.5 * (dg.rho_l + dg.rho_v)), d_inv = (C)(1.0 / (dg.rho_l - dg.rho_v)),
           d_rv = (C)dg.rho_v;
@@ -333,22 +336,26 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
     if constexpr (DIAG) {
       // momentum of the two nodes (the summation order of the two-kernel
       // diagnostics)
-      C jv[2][3];
+      C jv[2][3], lo[2];
       mom_of<C>(f0, jv[0][0], jv[0][1], jv[0][2]);
       mom_of<C>(f1, jv[1][0], jv[1][1], jv[1][2]);
       if (k >= 1 && k <= np - 2) {
+        // the rounding error of each density (rho_of_x's high part is r0, r1)
+        rho_of_x(f0, lo[0]);
+        rho_of_x(f1, lo[1]);
 #pragma unroll
         for (int n = 0; n < 2; ++n) {
           const C rho = n ? r1 : r0;
           const C jx = jv[n][0], jy = jv[n][1], jz = jv[n][2];
-          d_mass += rho;
-          d_jx += jx;
-          d_jy += jy;
-          d_jz += jz;
+          d_mass += (double)rho + (double)lo[n];
+          d_jx += (double)jx;
+          d_jy += (double)jy;
+          d_jz += (double)jz;
           C phi = (rho - d_rv) * d_inv;
           phi = phi < (C)0 ? (C)0 : (phi > (C)1 ? (C)1 : phi);
-          d_vol += phi;
-          col_w[n] += phi;
+          const double phd = (double)phi;
+          d_vol += phd;
+          col_w[n] += phd;
           col_n[n] += rho > d_thr ? (C)1 : (C)0;
           const C um = sqrt(xfma(jz, jz, xfma(jy, jy, xmul(jx, jx)))) / rho;
           d_umax = um > d_umax ? um : d_umax;
@@ -504,11 +511,11 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
     double* sh_w = sh_col + 2 * TY * TX;
 #pragma unroll
     for (int n = 0; n < 2; ++n) {
-      sh_col[(ty * TX + 2 * lane + n) * 2 + 0] = (double)col_w[n];
+      sh_col[(ty * TX + 2 * lane + n) * 2 + 0] = col_w[n];
       sh_col[(ty * TX + 2 * lane + n) * 2 + 1] = (double)col_n[n];
     }
-    // warp totals: a fixed shuffle tree in the compute precision
-    C v[5] = {d_mass, d_jx, d_jy, d_jz, d_vol};
+    // warp totals: a fixed FP64 shuffle tree
+    double v[5] = {d_mass, d_jx, d_jy, d_jz, d_vol};
     float c_f = 0.0f;
 #pragma unroll
     for (int n = 0; n < 2; ++n) c_f += (float)col_n[n];
@@ -526,11 +533,11 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
     }
     const int anybad = __any_sync(0xffffffffu, d_bad);
     if (lane == 0) {
-      sh_w[0 * TY + ty] = (double)v[0];
-      sh_w[1 * TY + ty] = (double)v[1];
-      sh_w[2 * TY + ty] = (double)v[2];
-      sh_w[3 * TY + ty] = (double)v[3];
-      sh_w[4 * TY + ty] = (double)v[4];
+      sh_w[0 * TY + ty] = v[0];
+      sh_w[1 * TY + ty] = v[1];
+      sh_w[2 * TY + ty] = v[2];
+      sh_w[3 * TY + ty] = v[3];
+      sh_w[4 * TY + ty] = v[4];
       sh_w[5 * TY + ty] = (double)c_f;
       sh_w[6 * TY + ty] = (double)d_umax;
       sh_w[7 * TY + ty] = (double)d_rmin;

@@ -22,7 +22,8 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
     assert line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 3 and line["n_gpus"] == 1
     assert line["higher_is_better"] is True and line["vs_baseline"] is None and line["dtype"] == "f64"
-    assert "256x128x128" in line["config"]["workload"]
+    assert "1024x512x512" in line["config"]["workload"]
+    assert "1024x512x8" in line["cpu_baseline"]["sample"] and line["config"]["sample_nodes"] == 1024 * 512 * 8
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
     e = line["e2e"]
