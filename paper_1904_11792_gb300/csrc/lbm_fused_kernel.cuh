@@ -25,7 +25,7 @@
 // write p + 1), so one block barrier per plane suffices.  Populations leave
 // DRAM once per step (halo boxes and the two boundary planes of a run are
 // read by neighbouring blocks at about the same time and mostly hit L2),
-// psi never goes to DRAM.  The arithmetic is psi_math and collide_math of
+// psi never goes to DRAM.  The arithmetic is psi_of and collide_math of
 // lbm_node.cuh and the stores are those of collide_pair, so the results
 // equal the two-kernel step bitwise.  A-B streaming, 4- and 2-byte storage,
 // lattices with nx % 64 == 0 and ny % 4 == 0.
@@ -262,8 +262,10 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
   // every warp makes one pass.  h_off: element offset in a plane buffer (-1:
   // no cell), h_str: stride between directions (scalar cells), h_ring: ring
   // position.
+  // (the instruction count of the pass is per warp whatever its active
+  // lanes, so the scalar cells all go to one warp)
   constexpr int SC = 4 + 2 * TY;                      // scalar halo cells
-  constexpr int SPW = (SC + TY - 3) / (TY - 2);       // scalar cells per warp
+  constexpr int SPW = SC;                             // scalar cells per warp (warp 2 takes all)
   static_assert(TY >= 3 && SPW <= 32, "halo split needs two row warps and room for the cells");
   int h_off = -1, h_str = 0, h_ring = 0;
   if (ty < 2) {
@@ -306,7 +308,12 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
       issue_plane<P>(smem, maps, k, x0, y0, xl, xr, ym, yp, zplane(k), full + k);
 
   const unsigned salt = (Prec<P>::dev && ph.sr) ? salt_of(ph) : 0u;
+  // a non-positive or non-finite density met by this thread's psi
+  // evaluations (raised on the flag once, after the run: the host reads the
+  // flag only after the kernel)
+  bool nbad = false;
   V prev[Q];   // stored populations of this thread's two nodes, previous plane
+  C prho[2];   // their densities (rho_of of the unpacked values, from the psi step)
   // diagnostics sums (DIAG): block totals and the two x columns of the thread
   double d_mass = 0.0, d_jx = 0.0, d_jy = 0.0, d_jz = 0.0, d_vol = 0.0, col_w[2] = {0.0, 0.0};
   C d_umax = 0, d_rmin = (C)3.0e38, d_rmax = (C)-3.0e38;
@@ -329,10 +336,9 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
       cur[a] = *reinterpret_cast<const V*>(buf + (a * TY + ty) * TX + 2 * lane);
       unpack_shifted<P>(cur[a], a == 0 ? s0 : (a <= 6 ? s1 : s2), f0[a], f1[a]);
     }
-    C p0, p1;
     const C r0 = rho_of<C>(f0), r1 = rho_of<C>(f1);
-    psi_math<C>(ph, r0, &p0, flag);
-    psi_math<C>(ph, r1, &p1, flag);
+    const C p0 = psi_of<C>(r0, ph), p1 = psi_of<C>(r1, ph);
+    nbad |= bad_rho(r0) | bad_rho(r1);
     if constexpr (DIAG) {
       // momentum of the two nodes (the summation order of the two-kernel
       // diagnostics)
@@ -377,9 +383,9 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
         unpack_shifted<P>(*reinterpret_cast<const V*>(buf + h_off + a * TX), a == 0 ? s0 : (a <= 6 ? s1 : s2),
                           fa[a], fb[a]);
       }
-      C pa, pb;
-      psi_math<C>(ph, rho_of<C>(fa), &pa, flag);
-      psi_math<C>(ph, rho_of<C>(fb), &pb, flag);
+      const C ra = rho_of<C>(fa), rb = rho_of<C>(fb);
+      const C pa = psi_of<C>(ra, ph), pb = psi_of<C>(rb, ph);
+      nbad |= bad_rho(ra) | bad_rho(rb);
       if constexpr (sizeof(C) == 4)
         *reinterpret_cast<float2*>(slot + h_ring) = make_float2(pa, pb);
       else
@@ -389,7 +395,9 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
 #pragma unroll
       for (int a = 0; a < Q; ++a)
         fv[a] = load_shifted<P>(buf + h_off + a * h_str, a == 0 ? s0 : (a <= 6 ? s1 : s2));
-      psi_math<C>(ph, rho_of<C>(fv), slot + h_ring, flag);
+      const C rv = rho_of<C>(fv);
+      slot[h_ring] = psi_of<C>(rv, ph);
+      nbad |= bad_rho(rv);
     }
     // every psi of plane zplane(k) is in the ring and buffer b is read out
     if (__syncthreads_or(!ok)) break;
@@ -443,8 +451,8 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
         collide_math_mrt<C>(ph, g0, q[1][1][1], pn0, fs0);
         collide_math_mrt<C>(ph, g1, q[1][1][2], pn1, fs1);
       } else {
-        collide_math<C>(ph, g0, q[1][1][1], pn0, fs0);
-        collide_math<C>(ph, g1, q[1][1][2], pn1, fs1);
+        collide_math_r<C>(ph, g0, prho[0], q[1][1][1], pn0, fs0);
+        collide_math_r<C>(ph, g1, prho[1], q[1][1][2], pn1, fs1);
       }
       const int i0 = x + g.nx * (y + g.ny * z);
       const bool sr = Prec<P>::dev && ph.sr;
@@ -494,7 +502,10 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
     }
 #pragma unroll
     for (int a = 0; a < Q; ++a) prev[a] = cur[a];
+    prho[0] = r0;
+    prho[1] = r1;
   }
+  raise_flag(nbad, flag);
   if (k < np) {
     // a wait gave up: record it, and let the copies already issued land
     // before the block's shared memory is released

@@ -130,13 +130,36 @@ __device__ __forceinline__ void store_pop(const Phys& ph, typename Prec<P>::T* p
 // arithmetic of one node
 // ---------------------------------------------------------------------------
 
-// Post-collision populations fs of a node with populations f, psi(x) = pc
+// Correctly rounded reciprocal: the bits of 1 / x (IEEE division) without
+// the division's general path.
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
+// c_a . u for odd a, whose first nonzero velocity component is +1: sums of
+// the velocity components only (no 0 + u_x, which the compiler must keep
+// for a -0 operand).
+static_assert(cx(9) == 1 && cx(13) == 1 && cy(17) == 1 && cy(15) == 1 && cx(1) == 1 && cy(3) == 1 &&
+                  cz(5) == 1 && cx(7) == 1 && cx(11) == 1,
+              "odd directions lead with a +1 component");
+template <typename C>
+__device__ __forceinline__ C cdotu(int a, C ux, C uy, C uz) {
+  if (cx(a)) {
+    C cu = ux;
+    if (cy(a)) cu = cy(a) > 0 ? cu + uy : cu - uy;
+    if (cz(a)) cu = cz(a) > 0 ? cu + uz : cu - uz;
+    return cu;
+  }
+  if (cy(a)) return cz(a) ? (cz(a) > 0 ? uy + uz : uy - uz) : uy;
+  return uz;
+}
+
+// Post-collision populations fs of a node with populations f, density rho
+// (= rho_of(f), passed in where the caller has it already), psi(x) = pc
 // and neighbour values pn[a] = psi(x + c_a) (a = 1..18).
 template <typename C>
-__device__ __forceinline__ void collide_math(const Phys& ph, const C f[Q], C pc, const C pn[Q],
-                                             C fs[Q]) {
-  // Eq. 4
-  const C rho = rho_of<C>(f);
+__device__ __forceinline__ void collide_math_r(const Phys& ph, const C f[Q], C rho, C pc, const C pn[Q],
+                                               C fs[Q]) {
+  // Eq. 4 (the momentum; rho from the caller)
   C jx, jy, jz;
   mom_of<C>(f, jx, jy, jz);
   // Eq. 5: sum_a w_a psi(x + c_a) c_a, split by weight class
@@ -152,46 +175,59 @@ __device__ __forceinline__ void collide_math(const Phys& ph, const C f[Q], C pc,
   const C Fz = xmul(gp, xfma(w1, az, xmul(w2, dz)));
   // Eq. 6
   const C tau = (C)ph.tau;
-  const C inv_rho = (C)1 / rho;
+  const C inv_rho = rcp_rn(rho);
   const C ux = xmul(xfma(tau, Fx, jx), inv_rho);
   const C uy = xmul(xfma(tau, Fy, jy), inv_rho);
   const C uz = xmul(xfma(tau, Fz, jz), inv_rho);
   const C usq = xmul((C)1.5, xfma(uz, uz, xfma(uy, uy, xmul(ux, ux))));
+  // Eq. 2 and Eq. 3 as f* = (1 - omega) f + omega f_eq.  For the pair a, b =
+  // opp(a) of weight w, with q = omega w rho and cu = c_a . u':
+  //   omega f_eq_a = A + B,  omega f_eq_b = A - B,
+  //   A = q (1 - 3/2 u'.u') + (9/2) q cu^2,  B = 3 q cu,
+  // and q, 9/2 q, 3 q of the diagonal class are exactly half those of the
+  // axis class (w2 = w1 / 2).  The rest population takes omega f_eq_0 =
+  // omega rho - 2 sum_pairs A, which equals Eq. 2's omega w_0 rho (1 - 3/2
+  // u'.u') for the exact weights (sum_{a>=1} w_a = 2/3, sum_{a>=1} w_a
+  // (c_a.u')^2 = u'.u'/3) and keeps sum_a f* = rho up to unbiased rounding
+  // (with weights rounded to the arithmetic's precision the direct form of
+  // Eq. 2 creates mass of relative order 1e-8 per FP32 collision in one
+  // direction).
   const C omega = (C)1 / tau;
-  // Eq. 2 and Eq. 3.  The moving populations a = 1..18 take f_eq from Eq. 2
-  // directly; the rest population takes f_eq_0 = rho - sum_{a>=1} f_eq_a,
-  // which equals Eq. 2's w_0 rho (1 - 3/2 u.u) for the exact weights
-  // (sum_{a>=1} w_a = 2/3, sum_{a>=1} w_a (c_a.u)^2 = u.u/3).  With weights
-  // rounded to the arithmetic's precision the direct form makes every
-  // collision create mass of relative order 1e-8 (FP32) in one direction;
-  // this form conserves mass up to unbiased rounding.
-  C feq_sum = 0;
-  const C one_m_usq = (C)1 - usq;
+  const C om1 = (C)1 - omega;
+  const C orho = xmul(omega, rho);
+  const C q1 = xmul(orho, w1);
+  const C E1 = xmul(q1, (C)1 - usq), M1 = xmul((C)4.5, q1), T1 = xmul((C)3, q1);
+  const C E2 = (C)0.5 * E1, M2 = (C)0.5 * M1, T2 = (C)0.5 * T1;
+  C sumA = 0;
 #pragma unroll
   for (int a = 1; a < Q; a += 2) {
     const int b = a + 1;  // opp(a)
-    // c_a . u with c_a components in {-1, 0, 1}: sums only
-    C cu = 0;
-    if (cx(a)) cu = cx(a) > 0 ? cu + ux : cu - ux;
-    if (cy(a)) cu = cy(a) > 0 ? cu + uy : cu - uy;
-    if (cz(a)) cu = cz(a) > 0 ? cu + uz : cu - uz;
-    const C wr = xmul((C)wgt(a), rho);
-    const C even = xfma(xmul((C)4.5, cu), cu, one_m_usq);
-    const C feq_a = xmul(wr, xfma((C)3, cu, even));
-    const C feq_b = xmul(wr, xfma((C)-3, cu, even));
-    feq_sum += feq_a + feq_b;
-    fs[a] = xfma(-omega, f[a] - feq_a, f[a]);
-    fs[b] = xfma(-omega, f[b] - feq_b, f[b]);
+    const bool axis = a <= 6;
+    const C cu = cdotu<C>(a, ux, uy, uz);
+    const C A = xfma(xmul(axis ? M1 : M2, cu), cu, axis ? E1 : E2);
+    const C B = xmul(axis ? T1 : T2, cu);
+    sumA = a == 1 ? A : sumA + A;
+    fs[a] = xfma(om1, f[a], A + B);
+    fs[b] = xfma(om1, f[b], A - B);
   }
-  const C feq_0 = rho - feq_sum;
-  fs[0] = xfma(-omega, f[0] - feq_0, f[0]);
+  fs[0] = xfma(om1, f[0], xfma((C)-2, sumA, orho));
+}
+
+template <typename C>
+__device__ __forceinline__ void collide_math(const Phys& ph, const C f[Q], C pc, const C pn[Q], C fs[Q]) {
+  collide_math_r<C>(ph, f, rho_of<C>(f), pc, pn, fs);
+}
+
+// A non-positive, NaN or infinite density (the numeric flag's condition).
+template <typename C>
+__device__ __forceinline__ bool bad_rho(C rho) {
+  return !(rho > (C)0) || !(rho <= (C)3.0e38);
 }
 
 template <typename C>
 __device__ __forceinline__ void psi_math(const Phys& ph, C rho, C* out, int* flag) {
   *out = psi_of<C>(rho, ph);
-  // non-positive, NaN or infinite density
-  raise_flag(!(rho > (C)0) || !(rho <= (C)3.0e38), flag);
+  raise_flag(bad_rho(rho), flag);
 }
 
 // ---------------------------------------------------------------------------

@@ -124,8 +124,13 @@ def test_breakup_step_neck_and_droplets_match_oracle(L, orc_run, precision):
         lat.close()
 
 
-@pytest.mark.parametrize("precision", ["f16dev", "bf16dev"])
-def test_reduced_precision_breakup_within_one_percent(L, orc_run, precision):
+# Mass at break-up against the FP64 run: stochastic rounding is unbiased, so
+# the stored mass does a random walk of one storage rounding per value and
+# step; with the liquid's deviations of order f (rho_ref = rho_v) its size at
+# break-up is about 1.2e-4 for BF16 (8-bit significand, measured 3.3e-4) and
+# eight times less for FP16 (11 bits).
+@pytest.mark.parametrize("precision,drift", [("f16dev", 1e-4), ("bf16dev", 1e-3)])
+def test_reduced_precision_breakup_within_one_percent(L, orc_run, precision, drift):
     rl, rv = orc_run["rl"], orc_run["rv"]
     t64, _, lat64 = _gpu_breakup(L, "f64", rl, rv, 1)
     m64 = lat64.diagnostics()["mass"]
@@ -136,7 +141,7 @@ def test_reduced_precision_breakup_within_one_percent(L, orc_run, precision):
         d = lat.diagnostics(ccl=True)
         assert d["droplets"] == orc_run["drops"][0][0]
         # mass of the stored deviations at break-up against the FP64 run's
-        assert abs(d["mass"] / m64 - 1) <= 1e-4
+        assert abs(d["mass"] / m64 - 1) <= drift
     finally:
         lat.close()
 

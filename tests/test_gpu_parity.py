@@ -227,9 +227,12 @@ def test_moments_match_oracle(L, coex):
 # the mass is the FP64 sum of each node's exact density (its FP32 sum plus
 # the rounding error of that sum), so it equals the oracle's FP64 sum of the
 # same stored state to FP64 rounding plus the 2^-40 relative bound of the
-# error term's own FP32 sum; momentum and the liquid fractions are per node
-# FP32 values (exact zero where opposite populations are equal) summed in
-# FP64, 1e-10 of the mass.
+# error term's own FP32 sum; the momentum is per node FP32 (exact zero where
+# opposite populations are equal) summed in FP64, 1e-10 of the mass (measured
+# 1e-13).  The liquid fraction phi = clamp((rho - rho_v)/(rho_l - rho_v)) is
+# an FP32 value per node (exact 0 or 1 outside the interface): at each
+# interface node its error is at most about 20 roundings of rho_l, relative
+# to rho_l - rho_v, which bounds the FP64 sums of phi.
 @pytest.mark.parametrize("precision", ["f64", "f32", "f16dev", "bf16dev"])
 def test_diagnostics_and_droplets_match_oracle(L, coex, precision):
     rl, rv = coex
@@ -248,8 +251,11 @@ def test_diagnostics_and_droplets_match_oracle(L, coex, precision):
     for k in range(3):
         dj = d["mom"][k] - (o["mom_x"], o["mom_y"], o["mom_z"])[k]
         assert abs(dj) <= tol_j * o["mass"], (k, dj / o["mass"])
-    assert abs(d["liquid_volume_w"] - o["liquid_volume_w"]) <= tol_j * o["liquid_volume_w"]
-    assert abs(d["min_slice_area_w"] - o["min_slice_area_w"]) <= tol_j * max(1.0, o["min_slice_area_w"])
+    rho_o = f.sum(axis=0)
+    n_if = int(((rho_o > rv) & (rho_o < rl)).sum())
+    tol_phi = 1e-12 if precision == "f64" else 20 * 2.0 ** -24 * rho_o.max() / (rl - rv)
+    assert abs(d["liquid_volume_w"] - o["liquid_volume_w"]) <= n_if * tol_phi + 1e-12 * o["liquid_volume_w"]
+    assert abs(d["min_slice_area_w"] - o["min_slice_area_w"]) <= n_if * tol_phi + 1e-12
     # integer decisions on the GPU's own rho: compare with the oracle on the same field
     liq = rho > 0.5 * (rl + rv)
     assert d["liquid_count"] == int(liq.sum())
@@ -490,11 +496,14 @@ def test_grid1024_fused_conserves_mass_and_momentum(L, coex):
         lat.sync()
         d1 = lat.diagnostics()
     assert d0["numeric_ok"] == 1 and d1["numeric_ok"] == 1
-    # unbiased rounding of 19 stores per node: drift of order 1e-10 here,
-    # resolved by the FP64 sums
-    assert abs(d1["mass"] / d0["mass"] - 1) < 1e-8
+    # FP32 storage: the density sum and the stored values round to nearest,
+    # and in the uniform liquid and vapour every node rounds the same way, so
+    # the mass moves by a coherent rounding each step (measured 1.1e-7 over
+    # these 20 steps, resolved by the FP64 sums); momentum is exactly zero in
+    # uniform regions and moves only by interface roundings
+    assert abs(d1["mass"] / d0["mass"] - 1) < 1e-6
     for k in range(3):
-        assert abs(d1["mom"][k] - d0["mom"][k]) < 1e-8 * d0["mass"]
+        assert abs(d1["mom"][k] - d0["mom"][k]) < 1e-7 * d0["mass"]
     assert d1["liquid_count"] > 0 and d1["rho_max"] < 1.2 * rl
 
 
