@@ -364,8 +364,12 @@ int lbm_batch_diagnostics(lbm_batch b, int k, lbm_diag *out, int want_ccl);
  *   stream:  cudaStream_t the kernels run on (NULL = the legacy default stream).
  * Asynchronous: out holds the results once the stream reaches them.  The
  * first call on a device looks up the device address of the static array
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call shares the array and leaves its last
+ * (cudaGetSymbolAddress, with that device current) and keeps it for later
+ * calls; make that first call before any stream capture.  A device reset
+ * (cudaDeviceReset) between calls ends the context that held the array, and
+ * the kept address with it: the first call after it fails with
+ * LBM_ERR_CUDA and forgets the address, and the next call looks it up
+ * again.  Every call shares the array and leaves its last
  * contents there (nothing in it needs to start at zero: the kernels write
  * every partial before reading it); calls that overlap on the GPU (streams
  * without an ordering between them) race and give wrong results.  A lattice

@@ -167,10 +167,10 @@ int diag_row_blocks(const Geom& g) {
 
 // Each node's momentum and liquid fraction are computed in the compute
 // precision (FP32 except in FP64 mode), its density as that sum plus its
-// rounding error (rho_of_x), and all are converted to FP64 before the first
-// add: the per-thread sums over the thread's rows, the warp
+// rounding error (rho_of_x); the per-thread sums over the thread's rows are
+// DSum accumulators (an error-free FP32 pair, exact to FP64 level), the warp
 // shuffle tree and the block sums of mass, momentum and the weighted liquid
-// volume are all FP64, so the totals carry no reduction error above FP64
+// volume are FP64, so the totals carry no reduction error above FP64
 // rounding, whatever the storage precision.  Counts, extrema and the
 // numeric flag are exact in any precision.
 template <int P, bool WRITE_PSI, int LAYOUT>
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(DX* DY, 2) diag_partial_kernel(Geom g, Phys ph
   const int x = blockIdx.x * DX + tx;
   const long long rows = (long long)g.ny * g.nz;
   const C thr = (C)(0.5 * (rho_l + rho_v)), inv = (C)(1.0 / (rho_l - rho_v)), rv = (C)rho_v;
-  double s_mass = 0.0, s_jx = 0.0, s_jy = 0.0, s_jz = 0.0, s_vol = 0.0;
+  DSum<C> s_mass, s_jx, s_jy, s_jz, s_vol;
   C umax = 0, rmin = (C)3.0e38, rmax = (C)-3.0e38;
   int cnt = 0;
   bool bad = false;
@@ -213,13 +213,13 @@ __global__ void __launch_bounds__(DX* DY, 2) diag_partial_kernel(Geom g, Phys ph
       C jx, jy, jz;
       mom_of<C>(fv, jx, jy, jz);
       if constexpr (WRITE_PSI) psi[i] = psi_of<C>(rho, ph);
-      s_mass += (double)rho + (double)rho_lo;
-      s_jx += (double)jx;
-      s_jy += (double)jy;
-      s_jz += (double)jz;
+      s_mass.add(rho, rho_lo);
+      s_jx.add(jx);
+      s_jy.add(jy);
+      s_jz.add(jz);
       C phi = (rho - rv) * inv;
       phi = phi < (C)0 ? (C)0 : (phi > (C)1 ? (C)1 : phi);
-      s_vol += (double)phi;
+      s_vol.add(phi);
       cnt += rho > thr;
       const C u = sqrt(xfma(jz, jz, xfma(jy, jy, xmul(jx, jx)))) / rho;
       umax = u > umax ? u : umax;
@@ -231,11 +231,11 @@ __global__ void __launch_bounds__(DX* DY, 2) diag_partial_kernel(Geom g, Phys ph
   if constexpr (WRITE_PSI) raise_flag(bad, flag);
   // per-slice sums over the block's 8 row groups (FP64, fixed order)
   __shared__ double sh_s[2][DY][DX];
-  sh_s[0][ty][tx] = s_vol;
+  sh_s[0][ty][tx] = s_vol.value();
   sh_s[1][ty][tx] = (double)cnt;
   // block totals: a fixed FP64 shuffle tree within each warp, then the 8
   // warp results in FP64 in warp order
-  double v[5] = {s_mass, s_jx, s_jy, s_jz, s_vol};
+  double v[5] = {s_mass.value(), s_jx.value(), s_jy.value(), s_jz.value(), s_vol.value()};
   float c_f = (float)cnt;  // exact below 2^24 nodes per warp
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

@@ -167,6 +167,39 @@ __device__ __forceinline__ double rho_of_x(const double f[Q], double& lo) {
   lo = 0.0;
   return rho_of<double>(f);
 }
+
+// Per-thread accumulator of the FP64 diagnostics sums.  For FP32
+// arithmetic it is an unevaluated FP32 pair hi + lo: each added value goes
+// through TwoSum into hi, the rounding error into lo, so after n adds hi + lo
+// is the exact sum to about n 2^-48 (lo's own rounding), as close as an FP64
+// sum; value() hands it to the FP64 warp and block stages.  GB300's FP64
+// pipe runs at about 1/64 of the FP32 rate: an FP64 conversion and add per
+// value of every node made the diagnostic step of the 1024x512x512 lattice
+// 6.5 ms (100 %) longer, the pair costs FP32 operations only.  FP64
+// arithmetic: a plain double.
+template <typename C> struct DSum;
+template <> struct DSum<float> {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    float e;
+    hi = two_sum(hi, x, e);
+    lo = __fadd_rn(lo, e);
+  }
+  // x plus a small correction (the rounding error of x itself)
+  __device__ __forceinline__ void add(float x, float xlo) {
+    float e;
+    hi = two_sum(hi, x, e);
+    lo = __fadd_rn(lo, __fadd_rn(e, xlo));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <> struct DSum<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void add(double x, double xlo) { v += x + xlo; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+
 template <typename C>
 __device__ __forceinline__ void mom_of(const C f[Q], C& jx, C& jy, C& jz) {
   const C d1 = f[1] - f[2], d3 = f[3] - f[4], d5 = f[5] - f[6], d7 = f[7] - f[8], d9 = f[9] - f[10],

@@ -105,29 +105,46 @@ int choose_fz(const Geom& g, long long tiles, long long slots, bool cap) {
   return best;
 }
 
-// Grid of the fused step: z run length, runs per tile column, blocks.  The
-// first call per storage type sets the kernels' shared-memory limit and
-// reads the occupancy of the step kernel.
+// Per device and storage type: the kernels' shared-memory limit is set and
+// the SM count and resident blocks per SM of the step kernel are read on
+// the first call with that device current (under a lock: several threads,
+// or several devices, may make their first calls at once).
 template <int P>
-cudaError_t fused_grid(const Geom& g, int fz_req, int grp_req, int* fz, int* nchunks, int* grp,
-                       long long* blocks) {
+cudaError_t fused_device_info(int* slots_per_sm, int* sms) {
   using S = FusedShape<P>;
-  static int slots_per_sm = 0, sms = 0;
-  if (!slots_per_sm) {
-    cudaError_t e = cudaSuccess;
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static int slots_of[kMaxDev] = {}, sms_of[kMaxDev] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!slots_of[dev]) {
     for (const void* k : {(const void*)fused_kernel<P, false, COLL_SRT>, (const void*)fused_kernel<P, true, COLL_SRT>,
                           (const void*)fused_kernel<P, false, COLL_MRT>, (const void*)fused_kernel<P, true, COLL_MRT>})
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
-    int dev = 0;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int slots = 0;
+    int n_sm = 0, slots = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&slots, fused_kernel<P, false, COLL_SRT>, NT, S::smem);
     if (e != cudaSuccess) return e;
     if (slots < 1) return cudaErrorInvalidConfiguration;
-    slots_per_sm = slots;
+    sms_of[dev] = n_sm;
+    slots_of[dev] = slots;
   }
+  *slots_per_sm = slots_of[dev];
+  *sms = sms_of[dev];
+  return cudaSuccess;
+}
+
+// Grid of the fused step: z run length, runs per tile column, blocks.
+template <int P>
+cudaError_t fused_grid(const Geom& g, int fz_req, int grp_req, int* fz, int* nchunks, int* grp,
+                       long long* blocks) {
+  int slots_per_sm = 0, sms = 0;
+  cudaError_t e = fused_device_info<P>(&slots_per_sm, &sms);
+  if (e != cudaSuccess) return e;
   const long long tiles = (long long)(g.nx / TX) * (g.ny / TY);
   *fz = fz_req > 0 ? std::min(fz_req, g.nz) : choose_fz(g, tiles, (long long)slots_per_sm * sms, !Prec<P>::dev);
   *nchunks = (g.nz + *fz - 1) / *fz;

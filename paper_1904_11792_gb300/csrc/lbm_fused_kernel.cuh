@@ -193,13 +193,12 @@ __device__ __forceinline__ void issue_plane(unsigned char* smem, const Maps& m, 
 
 // Diagnostics of the step's starting state, reduced in the same pass (DIAG):
 // every thread sums the nodes of the planes its block owns (the run z0 ..
-// z1 - 1, not the two halo planes), each node's momentum, liquid fraction
-// and density (with its rounding error, rho_of_x) converted to FP64 before
-// the first add (the sums, the warp
-// shuffle tree and the block sums are FP64), and the block writes FP64
-// partials in the layout the diagnostics reduction reads: slice sums
-// [row block][x][2] with one row block per (tile row, z run), and block
-// totals [block][DIAG_NG].
+// z1 - 1, not the two halo planes): each node's momentum, liquid fraction
+// and density (with its rounding error, rho_of_x) into DSum accumulators
+// (exact to FP64 level), then an FP64 warp shuffle tree and FP64 block
+// sums; the block writes FP64 partials in the layout the diagnostics
+// reduction reads: slice sums [row block][x][2] with one row block per
+// (tile row, z run), and block totals [block][DIAG_NG].
 struct DiagOut {
   double rho_l, rho_v;
   double* slices;
@@ -315,7 +314,7 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
   V prev[Q];   // stored populations of this thread's two nodes, previous plane
   C prho[2];   // their densities (rho_of of the unpacked values, from the psi step)
   // diagnostics sums (DIAG): block totals and the two x columns of the thread
-  double d_mass = 0.0, d_jx = 0.0, d_jy = 0.0, d_jz = 0.0, d_vol = 0.0, col_w[2] = {0.0, 0.0};
+  DSum<C> d_mass, d_jx, d_jy, d_jz, d_vol, col_w[2];
   C d_umax = 0, d_rmin = (C)3.0e38, d_rmax = (C)-3.0e38;
   C col_n[2] = {0, 0};
   bool d_bad = false;
@@ -353,15 +352,14 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
         for (int n = 0; n < 2; ++n) {
           const C rho = n ? r1 : r0;
           const C jx = jv[n][0], jy = jv[n][1], jz = jv[n][2];
-          d_mass += (double)rho + (double)lo[n];
-          d_jx += (double)jx;
-          d_jy += (double)jy;
-          d_jz += (double)jz;
+          d_mass.add(rho, lo[n]);
+          d_jx.add(jx);
+          d_jy.add(jy);
+          d_jz.add(jz);
           C phi = (rho - d_rv) * d_inv;
           phi = phi < (C)0 ? (C)0 : (phi > (C)1 ? (C)1 : phi);
-          const double phd = (double)phi;
-          d_vol += phd;
-          col_w[n] += phd;
+          d_vol.add(phi);
+          col_w[n].add(phi);
           col_n[n] += rho > d_thr ? (C)1 : (C)0;
           const C um = sqrt(xfma(jz, jz, xfma(jy, jy, xmul(jx, jx)))) / rho;
           d_umax = um > d_umax ? um : d_umax;
@@ -522,11 +520,11 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
     double* sh_w = sh_col + 2 * TY * TX;
 #pragma unroll
     for (int n = 0; n < 2; ++n) {
-      sh_col[(ty * TX + 2 * lane + n) * 2 + 0] = col_w[n];
+      sh_col[(ty * TX + 2 * lane + n) * 2 + 0] = col_w[n].value();
       sh_col[(ty * TX + 2 * lane + n) * 2 + 1] = (double)col_n[n];
     }
     // warp totals: a fixed FP64 shuffle tree
-    double v[5] = {d_mass, d_jx, d_jy, d_jz, d_vol};
+    double v[5] = {d_mass.value(), d_jx.value(), d_jy.value(), d_jz.value(), d_vol.value()};
     float c_f = 0.0f;
 #pragma unroll
     for (int n = 0; n < 2; ++n) c_f += (float)col_n[n];

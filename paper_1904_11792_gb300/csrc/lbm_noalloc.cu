@@ -78,7 +78,13 @@ int lbm_diagnostics_noalloc(const void* f, int nx, int ny, int nz, int precision
   ph.inv_rho0 = 1.0;
   e = launch_diagnostics(precision, LAYOUT_LOCAL, g, ph, f, rho_l, rho_v, scratch, out, nullptr,
                          nullptr, nullptr, 0, (cudaStream_t)stream);
-  if (e != cudaSuccess) return nfail(LBM_ERR_CUDA, std::string("diagnostics launch: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    // the cached address may belong to a context that no longer exists (a
+    // device reset): look it up again on the next call
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_scratch_ptr[dev] = nullptr;
+    return nfail(LBM_ERR_CUDA, std::string("diagnostics launch: ") + cudaGetErrorString(e));
+  }
   return LBM_OK;
 }
 

@@ -29,28 +29,34 @@ def _lib():
     return lbm, lib
 
 
-def _noalloc(lib, lat, shape, precision, out, stream):
+def _noalloc(lib, lat, shape, precision, rho_ref, out, stream):
     nx, ny, nz = shape
     rc = lib.lbm_diagnostics_noalloc(ctypes.c_void_p(lat._buffers[0].data_ptr()), nx, ny, nz,
-                                     precision, 0.0, RL, RV, ctypes.c_void_p(out.data_ptr()),
+                                     precision, rho_ref, RL, RV, ctypes.c_void_p(out.data_ptr()),
                                      ctypes.c_void_p(stream))
     assert rc == 0, lib.lbm_noalloc_last_error().decode()
 
 
-def test_noalloc_diagnostics_equal_handle_diagnostics_two_calls():
+# Two calls in a row on different lattices (they share the static scratch),
+# for each storage precision; the *DEV forms pass the lattice's rho_ref, from
+# which the entry point rebuilds the deviation shifts, and one lattice of each
+# pair streams in place (AA) after an even number of steps, whose array is
+# then in the canonical layout the entry point reads.
+@pytest.mark.parametrize("precision", ["f32", "f64", "f16dev", "bf16dev"])
+def test_noalloc_diagnostics_equal_handle_diagnostics_two_calls(precision):
     import torch
     L, lib = _lib()
     stream = torch.cuda.current_stream().cuda_stream or 1
+    rho_ref = RV if precision.endswith("dev") else 0.0
     cases = []
-    for shape, R0 in (((64, 32, 32), 8.0), ((40, 24, 20), 5.0)):
-        lat = L.Lattice(*shape, 1.0, -6.0, precision="f32")
+    for shape, R0, pattern in (((64, 32, 32), 8.0, "ab"), ((40, 24, 20), 5.0, "aa")):
+        lat = L.Lattice(*shape, 1.0, -6.0, precision=precision, pattern=pattern, rho_ref=rho_ref)
         lat.init_ligament(R0, float(shape[0]), 0.1, 0.0, RL, RV, 2.0)
         lat.step(12)            # even step count: the current array is the first one
         cases.append((shape, lat, lat.diagnostics()))
     outs = [torch.full((13,), float("nan"), dtype=torch.float64, device="cuda") for _ in cases]
-    # two calls in a row on different lattices share the static scratch
     for (shape, lat, _), out in zip(cases, outs):
-        _noalloc(lib, lat, shape, L.LBM_F32, out, stream)
+        _noalloc(lib, lat, shape, L.PRECISIONS[precision], rho_ref, out, stream)
     torch.cuda.synchronize()
     for (shape, lat, want), out in zip(cases, outs):
         r = out.cpu().numpy()
