@@ -292,9 +292,10 @@ int lbm_kernel_time(lbm_handle h, int k, long long *launches, double *ms);
 
 /* ---- batched form ---------------------------------------------------------
  * A batch advances many independent periodic lattices of uneven size (e.g.
- * a sweep of ligaments) together: every time step is one psi-pass launch and
- * one collide-stream launch for the whole batch (blocks find their lattice
- * in a tile table), replayed from a captured CUDA graph.  The per-node
+ * a sweep of ligaments) together: every time step is one single-pass launch
+ * for the whole batch (option "fused", the default; or one psi-pass launch
+ * and one collide-stream launch), whose blocks find their lattice in a tile
+ * table, replayed from a captured CUDA graph.  The per-node
  * arithmetic is that of a single lattice, so each instance evolves bitwise
  * as it would alone.  A-B streaming; all instances share the precision. */
 typedef struct lbm_batch_ctx *lbm_batch;
@@ -314,8 +315,15 @@ lbm_batch lbm_batch_create(const lbm_instance *inst, int count, int precision, i
 void lbm_batch_destroy(lbm_batch b);
 const char *lbm_batch_last_error(void);
 int lbm_batch_set_stream(lbm_batch b, void *stream);
-/* "graph" (0/1), "stochastic_rounding" (0/1, as lbm_set_option),
- * "occupancy" (2, 3, 4; default 2), "vector" (0/1, default 1:
+/* "fused" (0/1, default 1: every step of the whole batch is one
+ * single-pass kernel - blocks own 32 x 8 tiles of an instance's x-y plane,
+ * cut short at its edges, march through a run of z planes and compute psi
+ * of the tile and its one-node ring in shared memory, so the populations
+ * are read once per step (Eqs. 2-6 as in lbm_step; instances of any size);
+ * 0: a psi pass and a collide-stream kernel per step), "fused_fz" (z planes
+ * per block of the single-pass step, default 16), "graph" (0/1),
+ * "stochastic_rounding" (0/1, as lbm_set_option), and for the two-kernel
+ * step "occupancy" (2, 3, 4; default 2), "vector" (0/1, default 1:
  * instances with even nx update two nodes per thread), "block_x",
  * "block_y", "block_z" (<= 256 threads in all: the batched collide-stream
  * kernel runs block_x * block_y * block_z threads per block over that many

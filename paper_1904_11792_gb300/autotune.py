@@ -163,34 +163,45 @@ def apply(lat: "L.Lattice", choice: dict) -> None:
 
 
 def tune_batch(batch: "L.Batch", blocks=((256, 1, 1), (128, 1, 1), (64, 1, 1)), occupancies=(2, 3, 4),
-               steps=20, verbose=False) -> dict:
-    """Times the batched step for each block size / occupancy and leaves the
+               steps=20, verbose=False, fused_runs=(8, 16, 32)) -> dict:
+    """Times the batched step - the single-pass form for each z run length,
+    and the two-kernel form for each block size / occupancy - and leaves the
     batch configured with the fastest; returns the choice."""
     import torch
     best = None
-    for occ in occupancies:
-        for b in blocks:
-            for k, v in zip(("block_x", "block_y", "block_z"), (1, 1, 1)):
-                batch.set_option(k, v)
-            for k, v in zip(("block_x", "block_y", "block_z"), b):
-                batch.set_option(k, v)
-            batch.set_option("occupancy", occ)
-            batch.step(2)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            batch.step(steps)
-            e1.record()
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / steps
-            t = dict(block=list(b), occupancy=occ, step_ms=ms)
-            if verbose:
-                print(json.dumps(t))
-            if best is None or ms < best["step_ms"]:
-                best = t
+
+    def timed():
+        batch.step(2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        batch.step(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    cands = [dict(fused=1, fused_fz=fz, block=[0, 0, 0], occupancy=0) for fz in fused_runs]
+    cands += [dict(fused=0, fused_fz=0, block=list(b), occupancy=occ) for occ in occupancies for b in blocks]
+    for c in cands:
+        apply_batch(batch, c)
+        t = dict(c, step_ms=timed())
+        if verbose:
+            print(json.dumps(t))
+        if best is None or t["step_ms"] < best["step_ms"]:
+            best = t
+    apply_batch(batch, best)
+    return best
+
+
+def apply_batch(batch: "L.Batch", choice: dict) -> None:
+    """Applies a tuned batch choice (single-pass with its run length, or the
+    two-kernel step with its block shape and occupancy)."""
+    batch.set_option("fused", int(choice.get("fused", 0)))
+    if choice.get("fused"):
+        batch.set_option("fused_fz", int(choice["fused_fz"]))
+        return
     for k, v in zip(("block_x", "block_y", "block_z"), (1, 1, 1)):
         batch.set_option(k, v)
-    for k, v in zip(("block_x", "block_y", "block_z"), best["block"]):
+    for k, v in zip(("block_x", "block_y", "block_z"), choice["block"]):
         batch.set_option(k, v)
-    batch.set_option("occupancy", best["occupancy"])
-    return best
+    batch.set_option("occupancy", choice["occupancy"])

@@ -6,6 +6,7 @@
 // single-lattice kernels run (lbm_node.cuh), so each instance evolves
 // bitwise as it would alone.  lbm_batch_step_sequential is the plain
 // alternative: per instance, its own two launches per step.
+#include <algorithm>
 #include <type_traits>
 #include <cmath>
 #include <cstring>
@@ -13,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "lbm_gfused.cuh"
 #include "lbm_node.cuh"
 
 namespace lbm {
@@ -129,6 +131,43 @@ cudaError_t batch_launch_t(const BatchInst* d_inst, int count, int psi_blocks, i
   return cudaGetLastError();
 }
 
+// The single-pass step's kernels may take more than 48 KB of dynamic shared
+// memory; set once per layout (on the current device, outside any capture).
+cudaError_t batch_fused_prepare(int precision) {
+  switch (precision) {
+    case LBM_F64:
+      return cudaFuncSetAttribute(gfused_kernel<LBM_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)GShape<LBM_F64>::smem);
+    case LBM_F32:
+      return cudaFuncSetAttribute(gfused_kernel<LBM_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)GShape<LBM_F32>::smem);
+    default:
+      return cudaSuccess;   // 2-byte storage: the psi ring only, under 48 KB
+  }
+}
+
+// The single-pass step of the whole batch: one launch.
+cudaError_t batch_fused_launch(int precision, const GInst* d_ginst, int count, int blocks, void* pool_f, int cur,
+                               int* flag, cudaStream_t s) {
+  switch (precision) {
+    case LBM_F64:
+      gfused_kernel<LBM_F64><<<blocks, GNT, GShape<LBM_F64>::smem, s>>>(d_ginst, count, (double*)pool_f, cur, flag);
+      break;
+    case LBM_F32:
+      gfused_kernel<LBM_F32><<<blocks, GNT, GShape<LBM_F32>::smem, s>>>(d_ginst, count, (float*)pool_f, cur, flag);
+      break;
+    case LBM_F16DEV:
+      gfused_kernel<LBM_F16DEV><<<blocks, GNT, GShape<LBM_F16DEV>::smem, s>>>(d_ginst, count, (__half*)pool_f,
+                                                                              cur, flag);
+      break;
+    default:
+      gfused_kernel<LBM_BF16DEV><<<blocks, GNT, GShape<LBM_BF16DEV>::smem, s>>>(
+          d_ginst, count, (__nv_bfloat16*)pool_f, cur, flag);
+      break;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t batch_launch(int precision, const BatchInst* d_inst, int count, int psi_blocks, int tiles,
                          void* pool_f, int cur, void* pool_psi, int* flag, dim3 block, int minb,
                          cudaStream_t s) {
@@ -156,6 +195,10 @@ struct lbm_batch_ctx {
   std::vector<lbm_instance> spec;
   std::vector<BatchInst> inst;
   BatchInst* d_inst = nullptr;
+  GInst* d_ginst = nullptr;        // single-pass step: per-instance tile table
+  int gblocks = 0;
+  bool fused = true;               // option "fused": the single-pass step
+  int gfz = 16;                    // its z run length (option "fused_fz")
   void* pool_f = nullptr;
   size_t pool_f_bytes = 0;
   void* pool_psi = nullptr;
@@ -216,6 +259,27 @@ int layout_tiles(lbm_batch_ctx* b) {
   if (tiles > 0x7fffffffLL || psi_blocks > 0x7fffffffLL) return bfail(LBM_ERR_ARG, "batch too large for one grid");
   b->tiles = (int)tiles;
   b->psi_blocks = (int)psi_blocks;
+  // the single-pass step: GX x GY tiles in x-y, z runs of gfz planes
+  std::vector<GInst> gi(b->count);
+  long long gblocks = 0;
+  for (int k = 0; k < b->count; ++k) {
+    const BatchInst& I = b->inst[k];
+    GInst& G = gi[k];
+    std::memset(&G, 0, sizeof(G));
+    G.g = I.g;
+    G.ph = I.ph;
+    G.off_f = I.off_f;
+    G.ntx = (I.g.nx + GX - 1) / GX;
+    G.nty = (I.g.ny + GY - 1) / GY;
+    G.fz = std::min(b->gfz, I.g.nz);
+    G.nchunks = (I.g.nz + G.fz - 1) / G.fz;
+    G.block0 = (int)gblocks;
+    gblocks += (long long)G.ntx * G.nty * G.nchunks;
+  }
+  if (gblocks > 0x7fffffffLL) return bfail(LBM_ERR_ARG, "batch too large for one grid");
+  b->gblocks = (int)gblocks;
+  BCK(batch_fused_prepare(b->precision));
+  BCK(cudaMemcpyAsync(b->d_ginst, gi.data(), sizeof(GInst) * b->count, cudaMemcpyHostToDevice, b->stream));
   BCK(cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(BatchInst) * b->count, cudaMemcpyHostToDevice,
                       b->stream));
   BCK(cudaStreamSynchronize(b->stream));
@@ -228,8 +292,11 @@ bool batch_sr(const lbm_batch_ctx* b) {
 }
 
 int enqueue_batch_step(lbm_batch_ctx* b, cudaStream_t s, int cur) {
-  BCK(batch_launch(b->precision, b->d_inst, b->count, b->psi_blocks, b->tiles, b->pool_f, cur, b->pool_psi,
-                   b->d_flag, b->block, b->minb, s));
+  if (b->fused)
+    BCK(batch_fused_launch(b->precision, b->d_ginst, b->count, b->gblocks, b->pool_f, cur, b->d_flag, s));
+  else
+    BCK(batch_launch(b->precision, b->d_inst, b->count, b->psi_blocks, b->tiles, b->pool_f, cur, b->pool_psi,
+                     b->d_flag, b->block, b->minb, s));
   if (batch_sr(b)) BCK(launch_salt((unsigned*)(b->d_flag + 2), false, 0u, s));
   return LBM_OK;
 }
@@ -302,6 +369,7 @@ void lbm_batch_destroy(lbm_batch b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   drop_graphs(b);
   cudaFree(b->d_inst);
+  cudaFree(b->d_ginst);
   cudaFree(b->pool_f);
   cudaFree(b->pool_psi);
   cudaFree(b->d_flag);
@@ -350,8 +418,11 @@ lbm_batch lbm_batch_create(const lbm_instance* inst, int count, int precision, i
     I.ph.inv_rho0 = 1.0 / rho0;
     I.off_f = off_f;
     I.off_psi = off_psi;
-    off_f += 2 * (long long)Q * N;
-    off_psi += N;
+    // every instance's arrays start on a multiple of 8 elements (64 bytes in
+    // FP64): the vector kernels move node pairs (and four-node groups) as one
+    // 2- or 4-element access, which an odd N before them would misalign
+    off_f += (2 * (long long)Q * N + 7) / 8 * 8;
+    off_psi += (N + 7) / 8 * 8;
     b->inst.push_back(I);
     b->max_nodes = N > b->max_nodes ? N : b->max_nodes;
     b->total_nodes += N;
@@ -367,6 +438,7 @@ lbm_batch lbm_batch_create(const lbm_instance* inst, int count, int precision, i
     b->stream = b->own_stream;
   }
   if (err == cudaSuccess) err = cudaMalloc(&b->d_inst, sizeof(BatchInst) * count);
+  if (err == cudaSuccess) err = cudaMalloc(&b->d_ginst, sizeof(GInst) * count);
   if (err == cudaSuccess) err = cudaMalloc(&b->pool_f, b->pool_f_bytes);
   if (err == cudaSuccess) err = cudaMalloc(&b->pool_psi, b->pool_psi_bytes);
   if (err == cudaSuccess) err = cudaMalloc(&b->d_flag, sizeof(int) * 4);
@@ -412,6 +484,17 @@ int lbm_batch_set_option(lbm_batch b, const char* key, double v) {
   }
   if (k == "vector") {
     b->vec = v != 0.0;
+    return layout_tiles(b);
+  }
+  if (k == "fused") {
+    b->fused = v != 0.0;
+    drop_graphs(b);
+    return LBM_OK;
+  }
+  if (k == "fused_fz") {
+    const long long n = (long long)v;
+    if (n < 1 || n > 1 << 20 || (double)n != v) return bfail(LBM_ERR_ARG, "fused_fz must be a positive integer");
+    b->gfz = (int)n;
     return layout_tiles(b);
   }
   if (k == "occupancy") {

@@ -83,8 +83,9 @@ cudaError_t maps_for(int precision, const Geom& g, const void* base, Maps* out) 
 // than that (measured on GB300, 1024x512x512 in groups of runs: 12-, 16-,
 // 19-, 24- and 32-plane runs take 6.5, 6.4-7.8, 7.0, 7.7 and 8.2 ms per
 // step: the longer a block lives, the further apart in time neighbouring
-// tiles read the rows they share), so on lattices with more tiles than
-// resident blocks runs stop at 12 planes (cap); small grids (256x128x128:
+// tiles read the rows they share; with the current kernel, 8-plane runs in
+// groups of 4 take 6.44 ms and 12-plane runs 6.99 ms), so on lattices with
+// more tiles than resident blocks runs stop at 8 planes (cap); small grids (256x128x128:
 // 1.96 waves of 19-plane runs, 0.114 ms, against 0.126 ms for 16-plane runs
 // in 2.25 waves) keep the wave count low instead.  2-byte storage, bound by
 // instruction issue and with half the bytes per plane in L2, has no cap
@@ -95,7 +96,7 @@ int choose_fz(const Geom& g, long long tiles, long long slots, bool cap) {
   for (int fz = 4; fz <= g.nz; ++fz) {
     const long long chunks = (g.nz + fz - 1) / fz;
     const long long waves = (tiles * chunks + slots - 1) / slots;
-    if (cap && fz > 12 && tiles > slots) continue;
+    if (cap && fz > 8 && tiles > slots) continue;
     const double cost = (double)waves * (fz + 2) * (1.0 + fz / 256.0);
     if (best_cost < 0.0 || cost < best_cost) {
       best_cost = cost;

@@ -1,0 +1,251 @@
+// Single-pass time step for lattices of any size (the batched sweep).
+//
+// The TMA fused step (lbm_fused_kernel.cuh) needs rows of a 16-byte multiple
+// and nx % 64 == 0; the ligaments of a sweep have arbitrary lengths.  This
+// kernel does the same single pass with plain coalesced loads: a block owns
+// a GX x GY tile of (x, y), one node per thread (a warp per row), possibly
+// cut short at the lattice's edge, and marches through a run of z planes:
+//
+//   iteration k, plane p = z0 - 1 + k (periodic; odd runs march downwards):
+//     load the 19 populations of the thread's node of plane p, rho and psi
+//     -> centre of psi ring slot k % 4; threads 0 .. RINGN - 1 load one node
+//     each of the tile's one-node ring of plane p -> ring
+//     barrier
+//     collide + stream plane p - 1 from the populations kept in registers
+//     since the last iteration and psi of planes p - 2 .. p
+//
+// Populations leave DRAM once per step (the ring nodes and the two planes
+// around a run are read by the neighbouring blocks about when they read
+// them, and hit L2), psi never goes to DRAM.  The arithmetic is psi_of,
+// rho_of, collide_math_r and the stores of collide_node, so every instance
+// evolves bitwise as a standalone lattice of its size.  A-B streaming, the
+// paper's SRT collision, any storage precision.
+#pragma once
+
+#include "lbm_node.cuh"
+
+namespace lbm {
+
+constexpr int GX = 32;                          // tile along x: one node per lane
+constexpr int GY = 8;                           // tile along y: one warp per row
+constexpr int GNT = GX * GY;
+constexpr int GRX = GX + 2, GRY = GY + 2;       // tile with its one-node ring
+constexpr int RINGN = 2 * GRX + 2 * GY;         // ring nodes of a plane
+constexpr int GNR = 4;                          // psi ring slots
+static_assert(RINGN <= GNT, "one thread per ring node");
+
+// One lattice as the single-pass batched kernel sees it (a trivial
+// aggregate: kernels copy it).
+struct GInst {
+  Geom g;
+  Phys ph;
+  long long off_f;    // element offset of the instance's first array in the pool
+  int block0;         // first block of the instance
+  int ntx, nty;       // tiles along x and y
+  int nchunks, fz;    // z runs and their length
+};
+
+template <int P> constexpr int gfused_minb() { return P == LBM_F64 ? 1 : 2; }
+
+// Populations of 4 and 8 bytes reach shared memory by per-thread cp.async
+// copies issued two planes ahead (each thread later reads only the slots it
+// copied, so no barrier guards them); 2-byte populations (no 2-byte
+// cp.async) are plain loads at the plane's turn.
+template <int P> struct GShape {
+  using T = typename Prec<P>::T;
+  using C = typename Prec<P>::C;
+  static constexpr bool async = sizeof(T) >= 4;
+  static constexpr int NBUF = 3;                   // own populations: planes k - 1, k, k + 1
+  static constexpr int RPAD = (RINGN + 31) / 32 * 32;
+  static constexpr size_t own_bytes = async ? (size_t)NBUF * Q * GNT * sizeof(T) : 0;
+  static constexpr size_t ring_pop_bytes = async ? (size_t)2 * Q * RPAD * sizeof(T) : 0;
+  static constexpr size_t psi_bytes = (size_t)GNR * GRY * GRX * sizeof(C);
+  static constexpr size_t smem = own_bytes + ring_pop_bytes + psi_bytes;
+};
+
+__device__ __forceinline__ unsigned gsmem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+template <int B>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  static_assert(B == 4 || B == 8, "cp.async of 4 or 8 bytes");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(gsmem_addr(dst)), "l"(src), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Instance of a block: largest k with block0[k] <= b.
+__device__ __forceinline__ int gfind(const GInst* __restrict__ inst, int count, int b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (inst[mid].block0 <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int P>
+__global__ void __launch_bounds__(GNT, gfused_minb<P>())
+    gfused_kernel(const GInst* __restrict__ inst, int count, typename Prec<P>::T* pool_f, int cur, int* flag) {
+  using T = typename Prec<P>::T;
+  using C = typename Prec<P>::C;
+  using S = GShape<P>;
+  extern __shared__ __align__(16) unsigned char gsm[];
+  T* own = reinterpret_cast<T*>(gsm);                                  // [NBUF][Q][GNT]
+  T* rpop = reinterpret_cast<T*>(gsm + S::own_bytes);                  // [2][Q][RPAD]
+  C(*ring)[GRY][GRX] = reinterpret_cast<C(*)[GRY][GRX]>(gsm + S::own_bytes + S::ring_pop_bytes);
+
+  const GInst& I = inst[gfind(inst, count, blockIdx.x)];
+  const Geom g = I.g;
+  const Phys ph = I.ph;
+  const long long N = g.N;
+  const T* src = pool_f + I.off_f + (long long)cur * Q * N;
+  T* dst = pool_f + I.off_f + (long long)(cur ^ 1) * Q * N;
+  // block -> (z run, tile x, tile y), the run fastest: the runs of a tile and
+  // the tiles of a row of tiles are launched together and share planes and
+  // ring rows in L2
+  const int u = blockIdx.x - I.block0;
+  const int chunk = u % I.nchunks, xy = u / I.nchunks;
+  const int x0 = (xy % I.ntx) * GX, y0 = (xy / I.ntx) * GY;
+  const int w = min(GX, g.nx - x0), h = min(GY, g.ny - y0);   // tile extent (cut at the edge)
+  const int z0 = chunk * I.fz, z1 = min(z0 + I.fz, g.nz);
+  const int np = (z1 - z0) + 2;
+  const int dir = (chunk & 1) ? -1 : 1;
+  const int tid = threadIdx.x, lane = tid & 31, wy = tid >> 5;
+  auto zwrap = [&](int p) { return p < 0 ? p + g.nz : (p >= g.nz ? p - g.nz : p); };
+  auto zplane = [&](int k) { return zwrap(dir > 0 ? z0 - 1 + k : z1 - k); };
+  auto xwrap = [&](int x) { return x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x); };
+  auto ywrap = [&](int y) { return y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y); };
+
+  // this thread's node (interior) and ring node
+  const bool act = lane < w && wy < h;
+  const int x = x0 + lane, y = y0 + wy;
+  int rx = -1, ry = -1;
+  if (tid < 2 * GRX) {                         // the rows y0 - 1 and y0 + h
+    rx = tid % GRX;
+    ry = tid < GRX ? 0 : h + 1;
+    if (rx > w + 1) rx = -1;
+  } else if (tid < RINGN) {                    // the columns x0 - 1 and x0 + w
+    const int r = tid - 2 * GRX;
+    ry = 1 + r % GY;
+    rx = r < GY ? 0 : w + 1;
+    if (ry > h) rx = -1;
+  }
+  const bool ract = rx >= 0;
+  const int rxg = ract ? xwrap(x0 - 1 + rx) : 0, ryg = ract ? ywrap(y0 - 1 + ry) : 0;
+  const int rrow = rxg + g.nx * ryg;           // in-plane index of the ring node, less the plane
+  const int orow = x + g.nx * y;               // in-plane index of the own node, less the plane
+  const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x + 1 == g.nx ? 0 : x + 1;
+  const int yv[3] = {y == 0 ? g.ny - 1 : y - 1, y, y + 1 == g.ny ? 0 : y + 1};
+  const int xs[3] = {xm, x, xp};
+
+  const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref), s2 = shift_of<P>(7, ph.rho_ref);
+  auto shift = [&](int a) { return a == 0 ? s0 : (a <= 6 ? s1 : s2); };
+  const unsigned salt = (Prec<P>::dev && ph.sr) ? salt_of(ph) : 0u;
+  const long long plane_n = (long long)g.nx * g.ny;
+
+  // copies of plane zplane(k) (own node into buffer k % 3, ring node into
+  // ring buffer k % 2), one commit group per plane, empty past the run
+  auto issue = [&](int k) {
+    if constexpr (S::async) {
+      if (k < np) {
+        const long long zo = plane_n * zplane(k);
+        if (act) {
+          T* d = own + (size_t)(k % S::NBUF) * Q * GNT + tid;
+#pragma unroll
+          for (int a = 0; a < Q; ++a) cp_async<sizeof(T)>(d + a * GNT, src + (long long)a * N + zo + orow);
+        }
+        if (ract) {
+          T* d = rpop + (size_t)(k % 2) * Q * S::RPAD + tid;
+#pragma unroll
+          for (int a = 0; a < Q; ++a) cp_async<sizeof(T)>(d + a * S::RPAD, src + (long long)a * N + zo + rrow);
+        }
+      }
+      cp_async_commit();
+    }
+  };
+  issue(0);
+  issue(1);
+
+  bool nbad = false;
+  C prev[S::async ? 1 : Q], prho = 0;
+  for (int k = 0; k < np; ++k) {
+    const int zk = zplane(k);
+    C(*slot)[GRX] = ring[k % GNR];
+    C f[Q];
+    C rho = 0;
+    if constexpr (S::async) cp_async_wait_one();   // this thread's copies of plane k have landed
+    if (act) {
+      if constexpr (S::async) {
+        const T* o = own + (size_t)(k % S::NBUF) * Q * GNT + tid;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) f[a] = (C)o[a * GNT];
+      } else {
+        const long long i = orow + plane_n * zk;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) f[a] = Prec<P>::load(src + (long long)a * N + i, shift(a));
+      }
+      rho = rho_of<C>(f);
+      nbad |= bad_rho(rho);
+      slot[wy + 1][lane + 1] = psi_of<C>(rho, ph);
+    }
+    if (ract) {
+      C fr[Q];
+      if constexpr (S::async) {
+        const T* o = rpop + (size_t)(k % 2) * Q * S::RPAD + tid;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) fr[a] = (C)o[a * S::RPAD];
+      } else {
+        const long long i = rrow + plane_n * zk;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) fr[a] = Prec<P>::load(src + (long long)a * N + i, shift(a));
+      }
+      const C rr = rho_of<C>(fr);
+      nbad |= bad_rho(rr);
+      slot[ry][rx] = psi_of<C>(rr, ph);
+    }
+    // every psi of plane zk is in the ring
+    __syncthreads();
+    if (k >= 2 && act) {
+      // collide + stream this thread's node of plane z = zplane(k - 1); plane
+      // z + dz sits in ring slot (k - 1 + dir dz) % 4
+      const int z = zplane(k - 1);
+      const int zv[3] = {z == 0 ? g.nz - 1 : z - 1, z, z + 1 == g.nz ? 0 : z + 1};
+      C fp[Q];
+      if constexpr (S::async) {
+        const T* o = own + (size_t)((k - 1) % S::NBUF) * Q * GNT + tid;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) fp[a] = (C)o[a * GNT];
+      } else {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) fp[a] = prev[a];
+      }
+      C pn[Q];
+      pn[0] = 0;
+#pragma unroll
+      for (int a = 1; a < Q; ++a) pn[a] = ring[(k - 1 + dir * cz(a) + GNR) % GNR][wy + 1 + cy(a)][lane + 1 + cx(a)];
+      const C pc = ring[(k - 1) % GNR][wy + 1][lane + 1];
+      C fs[Q];
+      collide_math_r<C>(ph, fp, prho, pc, pn, fs);
+      const int i = x + g.nx * (y + g.ny * z);
+      const unsigned seed = (Prec<P>::dev && ph.sr) ? sr_seed(i, fs[0], salt) : 0u;
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const int d = xs[1 + cx(a)] + g.nx * (yv[1 + cy(a)] + g.ny * zv[1 + cz(a)]);
+        store_pop<P>(ph, dst + (long long)a * N + d, fs[a], shift(a), seed, a);
+      }
+    }
+    // the buffers of plane k - 1 (own) and k (ring) are read out by this
+    // thread: plane k + 2 goes there
+    issue(k + 2);
+    if (act) {
+      if constexpr (!S::async) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) prev[a] = f[a];
+      }
+      prho = rho;
+    }
+  }
+  raise_flag(nbad, flag);
+}
+
+}  // namespace lbm

@@ -1,5 +1,7 @@
-"""Batched form (many uneven ligaments, two launches per step for the whole
-batch) against standalone lattices and the oracle: bitwise per instance."""
+"""Batched form (many uneven ligaments advanced together: by default one
+single-pass launch per step for the whole batch, or the two-kernel step with
+option fused = 0) against standalone lattices and the oracle: bitwise per
+instance."""
 import numpy as np
 import pytest
 
@@ -65,6 +67,7 @@ def test_sequential_equals_batched_and_block_shapes(L):
                         ("batched", (32, 4, 1)), ("batched", (96, 1, 1))):
         with L.Batch(insts) as b:
             if block:
+                b.set_option("fused", 0)          # block shapes of the two-kernel step
                 for key, v in zip(("block_x", "block_y", "block_z"), (1, 1, 1)):
                     b.set_option(key, v)
                 for key, v in zip(("block_x", "block_y", "block_z"), block):
@@ -106,3 +109,35 @@ def test_full_sweep_builds_and_runs(L):
         m1 = [b.diagnostics(k)["mass"] for k in (0, 17, 47)]
     for a, c in zip(m0, m1):
         assert abs(a - c) <= 1e-6 * a
+
+
+# The single-pass batched step against the two-kernel batched step, bitwise,
+# on instances the tiles of 32 x 8 nodes and z runs cut in every way: odd and
+# short x extents, y not a multiple of 8, a z extent shorter than a run,
+# several runs with a short last one, the minimum lattice 3 x 3 x 3; every
+# storage precision; an odd number of steps (the A-B array parity) and a
+# second call that continues the first.
+SHAPES = ((37, 12, 9), (3, 3, 3), (70, 20, 37), (33, 8, 16), (5, 11, 3), (64, 16, 40))
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16dev", "bf16dev"])
+def test_fused_batch_equals_two_kernel_batch(L, precision):
+    insts = []
+    for k, (nx, ny, nz) in enumerate(SHAPES):
+        R0 = max(1.0, min(ny, nz) / 4.0)
+        insts.append(dict(nx=nx, ny=ny, nz=nz, tau=0.8 + 0.05 * k, G=-5.5, R0=R0, lam=float(nx), eps=0.1,
+                          phase=0.3 * k, rho_l=2.5, rho_v=0.15, width=2.0))
+    res = []
+    for fused, fz in ((0, 0), (1, 0), (1, 7)):
+        with L.Batch(insts, precision=precision) as b:
+            b.set_option("fused", fused)
+            if fz:
+                b.set_option("fused_fz", fz)
+            b.init()
+            b.step(5)
+            b.step(6)
+            b.sync()
+            res.append([b.populations(k) for k in range(len(insts))])
+    for r in res[1:]:
+        for k, (a, c) in enumerate(zip(res[0], r)):
+            np.testing.assert_array_equal(a, c, err_msg=str(SHAPES[k]))
