@@ -329,7 +329,47 @@ __global__ void __launch_bounds__(256) diag_slices_kernel(Geom g, int row_blocks
 // Writes the DIAG_OUT results to out, or, with a ring counter, to record
 // slot (counter++ mod ring_cap) of the ring at out (DIAG_STRIDE doubles per
 // record).
-__global__ void __launch_bounds__(FT) diag_final_kernel(Geom g, int nblocks,
+// First stage for many block partials (the fused step writes one per block):
+// block j folds the records [j chunk, (j + 1) chunk) into record j chunk, in
+// a fixed order, so the final kernel reads nblocks / chunk records.
+__global__ void __launch_bounds__(FT) diag_blocks_kernel(int nblocks, int chunk, double* blocks) {
+  __shared__ double sg[NG][FT];
+  const int t = threadIdx.x;
+  const long long b0 = (long long)blockIdx.x * chunk;
+  const long long b1 = min((long long)nblocks, b0 + chunk);
+  double acc[NG];
+#pragma unroll
+  for (int k = 0; k < NG; ++k) acc[k] = 0.0;
+  acc[7] = 1e300;
+  acc[8] = -1e300;
+  for (long long b = b0 + t; b < b1; b += FT) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] += blocks[b * NG + k];
+    acc[6] = fmax(acc[6], blocks[b * NG + 6]);
+    acc[7] = fmin(acc[7], blocks[b * NG + 7]);
+    acc[8] = fmax(acc[8], blocks[b * NG + 8]);
+    acc[9] = fmax(acc[9], blocks[b * NG + 9]);
+  }
+#pragma unroll
+  for (int k = 0; k < NG; ++k) sg[k][t] = acc[k];
+  __syncthreads();
+  for (int s = FT / 2; s > 0; s >>= 1) {
+    if (t < s) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) sg[k][t] += sg[k][t + s];
+      sg[6][t] = fmax(sg[6][t], sg[6][t + s]);
+      sg[7][t] = fmin(sg[7][t], sg[7][t + s]);
+      sg[8][t] = fmax(sg[8][t], sg[8][t + s]);
+      sg[9][t] = fmax(sg[9][t], sg[9][t + s]);
+    }
+    __syncthreads();
+  }
+  if (t < NG) blocks[b0 * NG + t] = t < 10 ? sg[t][0] : 0.0;
+}
+
+// Final reduction: the nblocks block records, stride records apart, and the
+// slice totals.
+__global__ void __launch_bounds__(FT) diag_final_kernel(Geom g, int nblocks, int stride,
                                                        const double* slice_tot, const double* blocks,
                                                        double* out, unsigned long long* ring_count,
                                                        int ring_cap) {
@@ -344,12 +384,13 @@ __global__ void __launch_bounds__(FT) diag_final_kernel(Geom g, int nblocks,
   acc[8] = -1e300;
 #pragma unroll 4
   for (int b = t; b < nblocks; b += FT) {
+    const double* r = blocks + (long long)b * stride * NG;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) acc[k] += blocks[(long long)b * NG + k];
-    acc[6] = fmax(acc[6], blocks[(long long)b * NG + 6]);
-    acc[7] = fmin(acc[7], blocks[(long long)b * NG + 7]);
-    acc[8] = fmax(acc[8], blocks[(long long)b * NG + 8]);
-    acc[9] = fmax(acc[9], blocks[(long long)b * NG + 9]);
+    for (int k = 0; k < 6; ++k) acc[k] += r[k];
+    acc[6] = fmax(acc[6], r[6]);
+    acc[7] = fmin(acc[7], r[7]);
+    acc[8] = fmax(acc[8], r[8]);
+    acc[9] = fmax(acc[9], r[9]);
   }
   // minima over the slice totals (first x on ties)
   double mw = 1e300, mn = 1e300;
@@ -641,7 +682,7 @@ cudaError_t diag_t(int layout, const Geom& g, const Phys& ph, const void* f, dou
   diag_slices_kernel<<<(g.nx + 7) / 8, 256, 0, s>>>(g, rb, slices, slice_tot);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  diag_final_kernel<<<1, FT, 0, s>>>(g, gx * rb, slice_tot, blocks, out, ring_count, ring_cap);
+  diag_final_kernel<<<1, FT, 0, s>>>(g, gx * rb, 1, slice_tot, blocks, out, ring_count, ring_cap);
   return cudaGetLastError();
 }
 template <int P>
@@ -686,12 +727,24 @@ cudaError_t launch_salt(unsigned* salt, bool set, unsigned value, cudaStream_t s
 }
 
 cudaError_t launch_diag_reduce(const Geom& g, int row_blocks, int nblocks, const double* slices,
-                               const double* blocks, double* slice_tot, double* out,
+                               double* blocks, double* slice_tot, double* out,
                                unsigned long long* ring_count, int ring_cap, cudaStream_t s) {
   diag_slices_kernel<<<(g.nx + 7) / 8, 256, 0, s>>>(g, row_blocks, slices, slice_tot);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  diag_final_kernel<<<1, FT, 0, s>>>(g, nblocks, slice_tot, blocks, out, ring_count, ring_cap);
+  // many records (one per block of the fused step): a parallel first stage
+  // folds runs of kChunk records in place (a single block reading 131072
+  // records of the 1024x512x512 lattice took 0.44 ms)
+  constexpr int kChunk = 256;
+  int stride = 1, n = nblocks;
+  if (nblocks > 4 * kChunk) {
+    n = (nblocks + kChunk - 1) / kChunk;
+    diag_blocks_kernel<<<n, FT, 0, s>>>(nblocks, kChunk, blocks);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    stride = kChunk;
+  }
+  diag_final_kernel<<<1, FT, 0, s>>>(g, n, stride, slice_tot, blocks, out, ring_count, ring_cap);
   return cudaGetLastError();
 }
 

@@ -50,7 +50,11 @@ template <int P> constexpr int gfused_minb() { return P == LBM_F64 ? 1 : 2; }
 // Populations of 4 and 8 bytes reach shared memory by per-thread cp.async
 // copies issued two planes ahead (each thread later reads only the slots it
 // copied, so no barrier guards them); 2-byte populations (no 2-byte
-// cp.async) are plain loads at the plane's turn.
+// cp.async) are plain loads at the plane's turn.  Either way a thread keeps
+// its node's populations in registers from the psi step to the collision
+// in the next iteration (re-reading them from shared memory instead was 4 %
+// slower on the 48-ligament sweep: the shared-memory queue is the kernel's
+// top stall).
 template <int P> struct GShape {
   using T = typename Prec<P>::T;
   using C = typename Prec<P>::C;
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(GNT, gfused_minb<P>())
   issue(1);
 
   bool nbad = false;
-  C prev[S::async ? 1 : Q], prho = 0;
+  C prev[Q], prho = 0;
   for (int k = 0; k < np; ++k) {
     const int zk = zplane(k);
     C(*slot)[GRX] = ring[k % GNR];
@@ -211,14 +215,8 @@ __global__ void __launch_bounds__(GNT, gfused_minb<P>())
       const int z = zplane(k - 1);
       const int zv[3] = {z == 0 ? g.nz - 1 : z - 1, z, z + 1 == g.nz ? 0 : z + 1};
       C fp[Q];
-      if constexpr (S::async) {
-        const T* o = own + (size_t)((k - 1) % S::NBUF) * Q * GNT + tid;
 #pragma unroll
-        for (int a = 0; a < Q; ++a) fp[a] = (C)o[a * GNT];
-      } else {
-#pragma unroll
-        for (int a = 0; a < Q; ++a) fp[a] = prev[a];
-      }
+      for (int a = 0; a < Q; ++a) fp[a] = prev[a];
       C pn[Q];
       pn[0] = 0;
 #pragma unroll
@@ -238,10 +236,8 @@ __global__ void __launch_bounds__(GNT, gfused_minb<P>())
     // thread: plane k + 2 goes there
     issue(k + 2);
     if (act) {
-      if constexpr (!S::async) {
 #pragma unroll
-        for (int a = 0; a < Q; ++a) prev[a] = f[a];
-      }
+      for (int a = 0; a < Q; ++a) prev[a] = f[a];
       prho = rho;
     }
   }

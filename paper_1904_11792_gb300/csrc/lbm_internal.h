@@ -119,9 +119,10 @@ cudaError_t launch_salt(unsigned* salt, bool set, unsigned value, cudaStream_t s
 
 // Second and third stage of the diagnostics reduction from partials
 // slices[row_blocks][nx][2] and blocks[nblocks][DIAG_NG] (slice_tot: 2 nx
-// doubles of scratch); arguments after slice_tot as launch_diagnostics.
+// doubles of scratch; with many block records they are folded in place, so
+// blocks is overwritten); arguments after slice_tot as launch_diagnostics.
 cudaError_t launch_diag_reduce(const Geom& g, int row_blocks, int nblocks, const double* slices,
-                               const double* blocks, double* slice_tot, double* out,
+                               double* blocks, double* slice_tot, double* out,
                                unsigned long long* ring_count, int ring_cap, cudaStream_t s);
 
 // Connected components of the liquid mask.  labels: N ints; sizes: N ints;
