@@ -559,7 +559,7 @@ def batch_sweep(args, torch, L, autotune, rho_l, rho_v, precision="f32"):
     arms are timed, each from the same initial state, on the sweep with tau
     raised to the smallest floor (0.8, 0.9 or 1) at which every instance
     stays finite through all the steps the timing takes."""
-    sweep = lbm_inputs.batched_sweep(48)
+    sweep = lbm_inputs.batched_sweep(48)[:args.batch_size]
     n_steps = (args.warmup + args.steps) * LBM_PER_STEP + 40
 
     def insts(floor):
@@ -578,12 +578,16 @@ def batch_sweep(args, torch, L, autotune, rho_l, rho_v, precision="f32"):
                 pass
         return bad
 
-    unstable_drawn = unstable_after(0.0)
-    floor = None
-    for fl in (0.8, 0.9, 1.0):
-        if not unstable_after(fl):
-            floor = fl
-            break
+    if args.no_tune:
+        # profiling runs: the floor measured on GB300, no stability scan
+        unstable_drawn, floor = None, 0.9
+    else:
+        unstable_drawn = unstable_after(0.0)
+        floor = None
+        for fl in (0.8, 0.9, 1.0):
+            if not unstable_after(fl):
+                floor = fl
+                break
     if floor is None:
         return {"error": "no tau floor up to 1 keeps all 48 instances finite for %d steps" % n_steps,
                 "unstable_at_drawn_tau": unstable_drawn}
@@ -592,12 +596,16 @@ def batch_sweep(args, torch, L, autotune, rho_l, rho_v, precision="f32"):
     stream = torch.cuda.current_stream()
     with L.Batch(stable, precision=precision) as b:
         b.init()
-        tuned = autotune.tune_batch(b, blocks=((256, 1, 1), (128, 1, 1)), occupancies=(2, 3, 4), steps=10)
-        # the other step form, for the record: the best two-kernel shape
-        # when the single-pass form won, else the single-pass form
-        other = autotune.tune_batch(b, blocks=((256, 1, 1), (128, 1, 1)), occupancies=(2, 3, 4), steps=10,
-                                    fused_runs=()) if tuned.get("fused") else \
-            autotune.tune_batch(b, blocks=(), occupancies=(), steps=10)
+        if args.no_tune:
+            tuned = dict(fused=1, fused_fz=16, block=[0, 0, 0], occupancy=0)
+            other = dict(fused=0, fused_fz=0, block=[128, 1, 1], occupancy=3)
+        else:
+            tuned = autotune.tune_batch(b, blocks=((256, 1, 1), (128, 1, 1)), occupancies=(2, 3, 4), steps=10)
+            # the other step form, for the record: the best two-kernel shape
+            # when the single-pass form won, else the single-pass form
+            other = autotune.tune_batch(b, blocks=((256, 1, 1), (128, 1, 1)), occupancies=(2, 3, 4), steps=10,
+                                        fused_runs=()) if tuned.get("fused") else \
+                autotune.tune_batch(b, blocks=(), occupancies=(), steps=10)
         autotune.apply_batch(b, tuned)
 
         def timed(fn):
@@ -636,8 +644,8 @@ def batch_sweep(args, torch, L, autotune, rho_l, rho_v, precision="f32"):
             "bytes_per_lu": bpl, "hbm_frac_step_model": round(value * bpl / peak, 4),
             "hbm_frac_floor_160": round(value * 160 / peak, 4),
             "numeric_ok_batched": ok_b and ok_o, "numeric_ok_sequential": ok_s,
-            "sweep": "48 periodic ligaments, R0 in {8,12,16,20,24}, lambda/R0 in [4.5,12], eps=0.05, G=-6, "
-                     "box lambda x 4R0 x 4R0, tau drawn in [0.6,1.0]",
+            "sweep": "%d periodic ligaments, R0 in {8,12,16,20,24}, lambda/R0 in [4.5,12], eps=0.05, G=-6, "
+                     "box lambda x 4R0 x 4R0, tau drawn in [0.6,1.0]" % len(sweep),
             "timed_tau_floor": floor,
             "unstable_at_drawn_tau": unstable_drawn,
             "mode": "one launch per step (single-pass) or one psi + one collide launch per step (two-kernel) for "
@@ -659,7 +667,7 @@ def run_batch(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r.get("ms_per_step"),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded ligament sweep, no dataset)",
-        "config": dict({"workload": "batched sweep: " + r["sweep"]}, **{k: v for k, v in r.items()
+        "config": dict({"workload": "batched sweep: " + r.get("sweep", "")}, **{k: v for k, v in r.items()
                                                                         if k not in ("value", "unit")}),
         "clocks": clk.summary(),
         "gpu_launches": int(args.steps * LBM_PER_STEP * 2),
@@ -694,6 +702,8 @@ def main():
                     help="skip the end-to-end and CPU-baseline legs (profiling runs)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP16/BF16/AA/batched comparisons (profiling runs)")
+    ap.add_argument("--batch-size", type=int, default=48,
+                    help="batch48: the first K instances of the sweep (profiling runs on a smaller batch)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
