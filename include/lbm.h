@@ -160,7 +160,8 @@ int lbm_set_stream(lbm_handle h, void *stream);
  * single-pass kernel that computes psi per tile in shared memory, reading
  * the populations once per step, with a variant that also reduces the
  * in-loop diagnostics on diagnostic steps; applies to FP32,
- * FP16-dev and BF16-dev storage when nx % 64 == 0 and ny % 4 == 0, other
+ * FP16-dev and BF16-dev storage when nx % 64 == 0 and ny % 4 == 0 (FP32) or
+ * ny % 8 == 0 (2-byte storage), other
  * lattices take the two-kernel step; results equal the two-kernel step
  * bitwise; lbm_get_option answers whether it applies), "fused_fz" (z planes
  * each block of the fused step marches through; 0 = chosen from the lattice
@@ -217,7 +218,8 @@ int lbm_init_profile(lbm_handle h, double R0, double lambda, double eps, double 
  * waiting.  Each step computes psi (definition after Eq. 5), the force of
  * Eq. 5, the velocity shift of Eq. 6, the equilibrium of Eq. 2, the BGK
  * relaxation of Eq. 3 and streaming.  Where option "fused" applies (A-B
- * streaming, FP32 or 2-byte storage, nx % 64 == 0, ny % 4 == 0; the
+ * streaming, FP32 or 2-byte storage, nx % 64 == 0, ny % 4 == 0 for FP32 or
+ * ny % 8 == 0 for 2-byte storage; the
  * default) a step is one single-pass kernel that computes psi per tile in
  * shared memory (its diagnostic-step variant also reduces the in-loop
  * diagnostics); otherwise it is a psi pass followed by one kernel of force,

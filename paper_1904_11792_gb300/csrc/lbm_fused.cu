@@ -15,6 +15,12 @@ namespace lbm {
 
 namespace {
 
+// Tile rows of the fused step for a storage precision (FusedShape<P>::TY).
+int fused_tile_rows(int precision) {
+  return precision == LBM_F16DEV ? FusedShape<LBM_F16DEV>::TY
+                                 : (precision == LBM_BF16DEV ? FusedShape<LBM_BF16DEV>::TY : FusedShape<LBM_F32>::TY);
+}
+
 // ---- tensor maps ------------------------------------------------------------
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -65,9 +71,10 @@ cudaError_t maps_for(int precision, const Geom& g, const void* base, Maps* out) 
   if (it == cache.end()) {
     const int cw = 16 / (int)elem_size(precision);
     Maps m;
-    cudaError_t e = make_map(&m.interior, precision, g, base, TX, TY);
+    const int ty = fused_tile_rows(precision);
+    cudaError_t e = make_map(&m.interior, precision, g, base, TX, ty);
     if (e == cudaSuccess) e = make_map(&m.row, precision, g, base, TX, 1);
-    if (e == cudaSuccess) e = make_map(&m.col, precision, g, base, cw, TY);
+    if (e == cudaSuccess) e = make_map(&m.col, precision, g, base, cw, ty);
     if (e == cudaSuccess) e = make_map(&m.cor, precision, g, base, cw, 1);
     if (e != cudaSuccess) return e;
     it = cache.emplace(key, m).first;
@@ -128,7 +135,7 @@ cudaError_t fused_device_info(int* slots_per_sm, int* sms) {
     int n_sm = 0, slots = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&slots, fused_kernel<P, false, COLL_SRT>, NT, S::smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&slots, fused_kernel<P, false, COLL_SRT>, S::NT, S::smem);
     if (e != cudaSuccess) return e;
     if (slots < 1) return cudaErrorInvalidConfiguration;
     sms_of[dev] = n_sm;
@@ -146,7 +153,7 @@ cudaError_t fused_grid(const Geom& g, int fz_req, int grp_req, int* fz, int* nch
   int slots_per_sm = 0, sms = 0;
   cudaError_t e = fused_device_info<P>(&slots_per_sm, &sms);
   if (e != cudaSuccess) return e;
-  const long long tiles = (long long)(g.nx / TX) * (g.ny / TY);
+  const long long tiles = (long long)(g.nx / TX) * (g.ny / FusedShape<P>::TY);
   *fz = fz_req > 0 ? std::min(fz_req, g.nz) : choose_fz(g, tiles, (long long)slots_per_sm * sms, !Prec<P>::dev);
   *nchunks = (g.nz + *fz - 1) / *fz;
   *blocks = tiles * *nchunks;
@@ -179,14 +186,14 @@ cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, i
   if (!diag) {
     const DiagOut none{0.0, 0.0, nullptr, nullptr, stall_ns};
     if (ph.coll == COLL_MRT)
-      fused_kernel<P, false, COLL_MRT><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
+      fused_kernel<P, false, COLL_MRT><<<(unsigned)blocks, S::NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
                                                                              fz, grp, none);
     else
-      fused_kernel<P, false, COLL_SRT><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
+      fused_kernel<P, false, COLL_SRT><<<(unsigned)blocks, S::NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
                                                                              fz, grp, none);
     return cudaGetLastError();
   }
-  const long long row_blocks = (long long)(g.ny / TY) * nchunks;
+  const long long row_blocks = (long long)(g.ny / S::TY) * nchunks;
   const size_t need = (size_t)row_blocks * g.nx * 2 + (size_t)blocks * DIAG_NG + (size_t)g.nx * 2;
   if (need > diag->scratch_doubles) return cudaErrorInvalidValue;
   double* slices = diag->scratch;
@@ -194,10 +201,10 @@ cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, i
   double* slice_tot = bl + (size_t)blocks * DIAG_NG;
   const DiagOut dg{diag->rho_l, diag->rho_v, slices, bl, stall_ns};
   if (ph.coll == COLL_MRT)
-    fused_kernel<P, true, COLL_MRT><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
+    fused_kernel<P, true, COLL_MRT><<<(unsigned)blocks, S::NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
                                                                           fz, grp, dg);
   else
-    fused_kernel<P, true, COLL_SRT><<<(unsigned)blocks, NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
+    fused_kernel<P, true, COLL_SRT><<<(unsigned)blocks, S::NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
                                                                           fz, grp, dg);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -210,7 +217,7 @@ size_t fused_scratch_t(const Geom& g, int fz_req) {
   int fz = 0, nchunks = 0, grp = 0;
   long long blocks = 0;
   if (fused_grid<P>(g, fz_req, 0, &fz, &nchunks, &grp, &blocks) != cudaSuccess) return 0;
-  return (size_t)(g.ny / TY) * nchunks * g.nx * 2 + (size_t)blocks * DIAG_NG + (size_t)g.nx * 2;
+  return (size_t)(g.ny / FusedShape<P>::TY) * nchunks * g.nx * 2 + (size_t)blocks * DIAG_NG + (size_t)g.nx * 2;
 }
 
 }  // namespace
@@ -227,7 +234,7 @@ cudaError_t fused_launch_shape(int precision, const Geom& g, int fz_req, int grp
 }
 
 bool fused_applicable(const Geom& g, int precision) {
-  return precision != LBM_F64 && g.nx % TX == 0 && g.ny % TY == 0 && g.nz >= 3;
+  return precision != LBM_F64 && g.nx % TX == 0 && g.ny % fused_tile_rows(precision) == 0 && g.nz >= 3;
 }
 
 cudaError_t launch_fused(int precision, const Geom& g, const Phys& ph, const void* src, void* dst, int* flag,

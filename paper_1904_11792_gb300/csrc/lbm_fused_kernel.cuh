@@ -44,19 +44,25 @@ namespace lbm {
 namespace {
 
 constexpr int TX = 64;   // tile along x: 32 lanes x 2 nodes
-constexpr int TY = 4;    // tile along y: one warp per row
-constexpr int NT = 32 * TY;
 constexpr int NB = 2;    // plane buffers
 constexpr int NR = 4;    // psi ring slots
 constexpr int RW = TX + 4;   // ring row: position x - x0 + 2 (pairs start 8-byte aligned)
-constexpr int RH = TY + 2;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // a wait on a plane gives up after 2 s
 
 __host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) & ~size_t(127); }
 
+// Tile rows (one warp each): 4 for 4-byte storage, 8 for 2-byte storage,
+// whose smaller plane buffers leave room for the taller tile (less halo psi
+// per node: the ring of a 64 x 8 tile is 148 nodes for 512, of a 64 x 4 tile
+// 140 for 256; and its halo cells spread one node per lane over five of the
+// eight warps instead of two node-pair passes and one scalar pass on three
+// of four, which the per-plane barrier waited for).
 template <int P> struct FusedShape {
   using T = typename Prec<P>::T;
   using C = typename Prec<P>::C;
+  static constexpr int TY = Prec<P>::dev ? 8 : 4;  // tile along y: one warp per row
+  static constexpr int NT = 32 * TY;
+  static constexpr int RH = TY + 2;                 // psi ring rows
   static constexpr int E = sizeof(T);
   static constexpr int CW = 16 / E;                               // one 16-byte TMA unit along x
   static constexpr size_t int_bytes = (size_t)Q * TY * TX * E;    // box (64, TY, 1, 19)
@@ -208,22 +214,26 @@ struct DiagOut {
   unsigned long long stall_test_ns;
 };
 
-// Blocks per SM the register budget must allow: 3 for 4-byte storage (its
-// 73 KB of shared memory allow no more), 4 for 2-byte storage (44 KB), the
-// diagnostic variants included (no spills at 168 and 128 registers).
+// Blocks per SM the register budget must allow: 3 of 128 threads for 4-byte
+// storage (its 73 KB of shared memory allow no more), 2 of 256 threads for
+// 2-byte storage (71 KB each), the diagnostic variants included (no spills
+// at 168 and 128 registers).
 template <int P, bool DIAG, int COLL = COLL_SRT>
 constexpr int fused_minb() {
-  return Prec<P>::dev ? 4 : 3;
+  return Prec<P>::dev ? 2 : 3;
 }
 
 template <int P, bool DIAG, int COLL>
-__global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
+__global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>())
     fused_kernel(const __grid_constant__ Maps maps, Geom g, Phys ph, typename Prec<P>::T* dst, int* flag, int ntx,
                  int nchunks, int fz, int grp, DiagOut dg) {
   using T = typename Prec<P>::T;
   using C = typename Prec<P>::C;
   using V = typename Pair<P>::V;
   using S = FusedShape<P>;
+  constexpr int TY = S::TY, RH = S::RH;
+  static_assert(2 * TY * TX * sizeof(double) + 10 * TY * sizeof(double) <= S::ring_bytes,
+                "the diagnostics reduction reuses the psi ring");
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + S::off_bar);
   C* ring = reinterpret_cast<C*>(smem + S::off_ring);
@@ -255,23 +265,29 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
   auto zwrap = [&](int p) { return p < 0 ? p + g.nz : (p >= g.nz ? p - g.nz : p); };
   auto zplane = [&](int k) { return zwrap(dir > 0 ? z0 - 1 + k : z1 - k); };   // plane of march index k
 
-  // psi of the halo ring of a plane: warps 0 and 1 take the rows y0 - 1 and
-  // y0 + TY over x0 .. x0 + TX - 1 as x pairs (like the interior), warps
-  // 2 .. TY - 1 the four corners and the 2 TY column cells, one per lane, so
-  // every warp makes one pass.  h_off: element offset in a plane buffer (-1:
-  // no cell), h_str: stride between directions (scalar cells), h_ring: ring
-  // position.
-  // (the instruction count of the pass is per warp whatever its active
-  // lanes, so the scalar cells all go to one warp)
-  constexpr int SC = 4 + 2 * TY;                      // scalar halo cells
-  constexpr int SPW = SC;                             // scalar cells per warp (warp 2 takes all)
-  static_assert(TY >= 3 && SPW <= 32, "halo split needs two row warps and room for the cells");
+  // psi of the halo ring of a plane.  4-row tiles: warps 0 and 1 take the
+  // rows y0 - 1 and y0 + TY over x0 .. x0 + TX - 1 as x pairs (like the
+  // interior), warp 2 the four corners and the 2 TY column cells, one per
+  // lane.  8-row tiles: warps 0 and 1 take row y0 - 1, warps 2 and 3 row
+  // y0 + TY, one node per lane, and warp 4 the corners and column cells.  A
+  // pass costs a warp the same instructions whatever its active lanes.
+  // h_off: element offset in a plane buffer (-1: no cell), h_str: stride
+  // between directions (one-node cells), h_ring: ring position.
+  constexpr bool PAIR_ROWS = TY == 4;
+  constexpr int SC = 4 + 2 * TY;                      // corner and column cells
+  constexpr int SW = PAIR_ROWS ? 2 : 4;               // the warp that takes them
+  static_assert((TY == 4 || TY == 8) && SC <= 32, "halo split for 4- or 8-row tiles");
   int h_off = -1, h_str = 0, h_ring = 0;
-  if (ty < 2) {
+  if (PAIR_ROWS && ty < 2) {
     h_off = (int)((ty ? S::off_bot : S::off_top) / S::E) + 2 * lane;
     h_ring = (ty ? TY + 1 : 0) * RW + 2 * lane + 2;
-  } else if (lane < SPW && (ty - 2) * SPW + lane < SC) {
-    const int h = (ty - 2) * SPW + lane;
+  } else if (!PAIR_ROWS && ty < 4) {
+    const int side = ty >> 1, xo = (ty & 1) * 32 + lane;
+    h_off = (int)((side ? S::off_bot : S::off_top) / S::E) + xo;
+    h_str = TX;
+    h_ring = (side ? TY + 1 : 0) * RW + xo + 2;
+  } else if (ty == SW && lane < SC) {
+    const int h = lane;
     if (h < 4) {
       const int side = h >> 1, right = h & 1;   // corners in the copy order of issue_plane
       h_off = (int)((S::off_cor + h * S::cor_stride) / S::E) + (right ? 0 : S::CW - 1);
@@ -374,7 +390,7 @@ __global__ void __launch_bounds__(NT, fused_minb<P, DIAG, COLL>())
     else
       *reinterpret_cast<double2*>(slot + (ty + 1) * RW + 2 * lane + 2) = make_double2(p0, p1);
     // psi of this thread's halo cells
-    if (ty < 2) {
+    if (PAIR_ROWS && ty < 2) {
       C fa[Q], fb[Q];
 #pragma unroll
       for (int a = 0; a < Q; ++a) {

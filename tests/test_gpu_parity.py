@@ -697,10 +697,14 @@ def test_fp64_vector_path_parity(L, shape):
 # ---------------------------------------------------------------------------
 
 # shapes: several z runs per tile column; a run of one plane (nz = 17); one
-# tile row and the shortest periodic z (64 x 4 x 3); three tile rows
+# tile row and the shortest periodic z (64 x 4 x 3; 2-byte storage, whose
+# tiles have 8 rows: 64 x 8 x 3); three tile rows (4-byte: 192 x 12 x 17,
+# 2-byte: 192 x 24 x 17)
 @pytest.mark.parametrize("precision", ["f32", "f16dev", "bf16dev"])
 @pytest.mark.parametrize("shape", [(64, 16, 12), (128, 8, 5), (192, 12, 17), (64, 4, 3)])
 def test_fused_equals_two_pass_bitwise(L, precision, shape):
+    if precision != "f32" and shape[1] % 8:
+        shape = (shape[0], 2 * shape[1], shape[2])
     f0 = lbm_inputs.random_populations(*shape, seed=51)
     out = []
     for fused in (1, 0):
@@ -717,9 +721,11 @@ def test_fused_equals_two_pass_bitwise(L, precision, shape):
 
 @pytest.mark.parametrize("shape", [(64, 16, 12), (64, 8, 8)])
 def test_fused_not_applicable_runs_two_pass(L, shape):
-    # FP64 storage, and nx not a multiple of 64, take the two-kernel step
+    # FP64 storage, nx not a multiple of 64, and ny not a multiple of the
+    # tile rows (4 for 4-byte, 8 for 2-byte storage) take the two-kernel step
     nx, ny, nz = shape
-    for precision, sh in (("f64", shape), ("f32", (nx + 32, ny, nz)), ("f32", (nx, ny + 2, nz))):
+    for precision, sh in (("f64", shape), ("f32", (nx + 32, ny, nz)), ("f32", (nx, ny + 2, nz)),
+                          ("f16dev", (nx, ny + 4, nz))):
         with make(L, sh, 0.9, -5.5, precision, "ab") as lat:
             lat.set_option("fused", 1)
             assert lat.get_option("fused") == 0
@@ -835,12 +841,14 @@ def test_fused_wait_timeout_is_reported_and_recoverable(L):
 # diagnostics it reduces in the same pass agree exactly.
 @pytest.mark.parametrize("precision", ["f32", "f16dev"])
 def test_fused_group_order_is_bitwise_neutral(L, precision):
-    shape = (192, 12, 20)          # 3 x 3 tiles of 64 x 4; 5-plane runs: 4 runs
+    # 3 x 3 tiles (64 x 4, or 64 x 8 for 2-byte storage); 5-plane runs: 4 runs
+    shape = (192, 12, 20) if precision == "f32" else (192, 24, 20)
     f0 = lbm_inputs.random_populations(*shape, seed=61)
     out = {}
     for fused, grp in ((0, 0), (1, 0), (1, 1), (1, 3), (1, 4), (1, 64)):
         with make(L, shape, 0.9, -5.5, precision, "ab", rho_ref=0.1) as lat:
             lat.set_option("fused", fused)
+            assert lat.get_option("fused") == fused
             lat.set_option("fused_fz", 5)
             lat.set_option("fused_group", grp)
             assert lat.get_option("fused_group") == grp
