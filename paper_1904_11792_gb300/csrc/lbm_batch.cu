@@ -131,11 +131,7 @@ cudaError_t batch_launch_t(const BatchInst* d_inst, int count, int psi_blocks, i
   return cudaGetLastError();
 }
 
-// The single-pass step: the bulk-copy kernel for 4- and 2-byte storage, the
-// per-element-copy kernel for FP64 (bound by its FP64 arithmetic).
-bool batch_uses_bulk(int precision) { return precision != LBM_F64; }
-
-// The single-pass step's kernels take more than 48 KB of dynamic shared
+// The single-pass step's kernels may take more than 48 KB of dynamic shared
 // memory; set once per layout (on the current device, outside any capture).
 cudaError_t batch_fused_prepare(int precision) {
   switch (precision) {
@@ -143,14 +139,10 @@ cudaError_t batch_fused_prepare(int precision) {
       return cudaFuncSetAttribute(gfused_kernel<LBM_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)GShape<LBM_F64>::smem);
     case LBM_F32:
-      return cudaFuncSetAttribute(gbulk_kernel<LBM_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)BShape<LBM_F32>::smem);
-    case LBM_F16DEV:
-      return cudaFuncSetAttribute(gbulk_kernel<LBM_F16DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)BShape<LBM_F16DEV>::smem);
+      return cudaFuncSetAttribute(gfused_kernel<LBM_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)GShape<LBM_F32>::smem);
     default:
-      return cudaFuncSetAttribute(gbulk_kernel<LBM_BF16DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)BShape<LBM_BF16DEV>::smem);
+      return cudaSuccess;   // 2-byte storage: the psi ring only, under 48 KB
   }
 }
 
@@ -162,14 +154,14 @@ cudaError_t batch_fused_launch(int precision, const GInst* d_ginst, int count, i
       gfused_kernel<LBM_F64><<<blocks, GNT, GShape<LBM_F64>::smem, s>>>(d_ginst, count, (double*)pool_f, cur, flag);
       break;
     case LBM_F32:
-      gbulk_kernel<LBM_F32><<<blocks, BNT, BShape<LBM_F32>::smem, s>>>(d_ginst, count, (float*)pool_f, cur, flag);
+      gfused_kernel<LBM_F32><<<blocks, GNT, GShape<LBM_F32>::smem, s>>>(d_ginst, count, (float*)pool_f, cur, flag);
       break;
     case LBM_F16DEV:
-      gbulk_kernel<LBM_F16DEV><<<blocks, BNT, BShape<LBM_F16DEV>::smem, s>>>(d_ginst, count, (__half*)pool_f, cur,
-                                                                            flag);
+      gfused_kernel<LBM_F16DEV><<<blocks, GNT, GShape<LBM_F16DEV>::smem, s>>>(d_ginst, count, (__half*)pool_f,
+                                                                              cur, flag);
       break;
     default:
-      gbulk_kernel<LBM_BF16DEV><<<blocks, BNT, BShape<LBM_BF16DEV>::smem, s>>>(
+      gfused_kernel<LBM_BF16DEV><<<blocks, GNT, GShape<LBM_BF16DEV>::smem, s>>>(
           d_ginst, count, (__nv_bfloat16*)pool_f, cur, flag);
       break;
   }
@@ -277,9 +269,8 @@ int layout_tiles(lbm_batch_ctx* b) {
     G.g = I.g;
     G.ph = I.ph;
     G.off_f = I.off_f;
-    const int tx = batch_uses_bulk(b->precision) ? BX : GX, ty = batch_uses_bulk(b->precision) ? BY : GY;
-    G.ntx = (I.g.nx + tx - 1) / tx;
-    G.nty = (I.g.ny + ty - 1) / ty;
+    G.ntx = (I.g.nx + GX - 1) / GX;
+    G.nty = (I.g.ny + GY - 1) / GY;
     G.fz = std::min(b->gfz, I.g.nz);
     G.nchunks = (I.g.nz + G.fz - 1) / G.fz;
     G.block0 = (int)gblocks;
@@ -409,10 +400,7 @@ lbm_batch lbm_batch_create(const lbm_instance* inst, int count, int precision, i
   b->count = count;
   b->precision = precision;
   b->spec.assign(inst, inst + count);
-  // kBulkPad elements before the first array and after the last: the bulk
-  // copies of the single-pass step start at the 16-byte boundary at or below
-  // a row's element x0 - 1 and run a fixed length past its end
-  long long off_f = kBulkPad, off_psi = 0;
+  long long off_f = 0, off_psi = 0;
   for (int k = 0; k < count; ++k) {
     const lbm_instance& s = inst[k];
     const long long N = (long long)s.nx * s.ny * s.nz;
@@ -440,7 +428,7 @@ lbm_batch lbm_batch_create(const lbm_instance* inst, int count, int precision, i
     b->total_nodes += N;
   }
   const size_t e = elem_size(precision);
-  b->pool_f_bytes = (size_t)(off_f + kBulkPad) * e;
+  b->pool_f_bytes = (size_t)off_f * e;
   b->pool_psi_bytes = (size_t)off_psi * (precision == LBM_F64 ? 8 : 4);
   cudaError_t err = cudaSuccess;
   if (stream) {
@@ -609,7 +597,6 @@ int lbm_batch_sync(lbm_batch b) {
   if (flag) {
     BCK(cudaMemsetAsync(b->d_flag, 0, sizeof(int), b->stream));
     BCK(cudaStreamSynchronize(b->stream));
-    if (flag & 2) return bfail(LBM_ERR_TIMEOUT, "a bounded wait of the single-pass step gave up; the steps since are void");
     return bfail(LBM_ERR_NUMERIC, "a density became non-positive or non-finite");
   }
   return LBM_OK;
