@@ -440,6 +440,51 @@ def test_grid1024_sampled_one_step(L, coex):
     assert rel(got, want) <= 1e-5
 
 
+# The benchmark's FP16 / BF16 variants at their full size (1024x512x512,
+# fused step, its launch shape): one step on sampled nodes against the
+# oracle stepping each node's 5x5x5 neighbourhood of the decoded stored state
+# (deviation + the shift w_a rho_ref rounded to the storage format), within
+# one storage ulp of the stored deviation plus the FP32 arithmetic, as the
+# 256x128x128 case below.
+@pytest.mark.parametrize("precision,eps", [("f16dev", 2.0 ** -10), ("bf16dev", 2.0 ** -7)])
+def test_grid1024_sampled_one_step_deviation_storage(L, coex, precision, eps):
+    import torch
+    rl, rv = coex
+    w = lbm_inputs.GRID_1024
+    N = w.nx * w.ny * w.nz
+    wts = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    if precision == "f16dev":
+        shift = (wts * rv).astype(np.float32).astype(np.float16).astype(np.float64)
+        tdt = torch.float16
+    else:   # BF16: the top 16 bits of the FP32 value, rounded to nearest even
+        b = (wts * rv).astype(np.float32).view(np.uint32).astype(np.uint64)
+        b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+        shift = b.astype(np.uint32).view(np.float32).astype(np.float64)
+        tdt = torch.bfloat16
+    with make(L, (w.nx, w.ny, w.nz), w.tau, w.G, precision, rho_ref=rv) as lat:
+        assert lat.get_option("fused") == 1 and lat.get_option("stochastic_rounding") == 1
+        lat.init_ligament(w.R0, w.lam, w.eps, w.phase, rl, rv, w.width)
+        lat.step(20)
+        lat.sync()
+        state = lat._buffers[0].view(tdt)
+        u = lbm_inputs.uniform(4245, 300)
+        c = (w.ny // 2) * w.nx + (w.nz // 2) * w.nx * w.ny
+        nodes = np.unique(np.concatenate([
+            (u * N).astype(np.int64), [0, N - 1, w.nx - 1, w.nx * w.ny - 1, c + 17],
+            [x + w.nx * (w.ny // 2 + int(w.R0)) + w.nx * w.ny * (w.nz // 2) for x in (0, 255, 511, 1023)]]))
+        before = _patches(state[:19 * N], N, w.nx, w.ny, nodes) + shift[None, :, None, None, None]
+        lat.step(1)
+        lat.sync()
+        after = state[19 * N:2 * 19 * N]
+        got = after[torch.arange(19, device="cuda")[:, None] * N
+                    + torch.as_tensor(nodes, device="cuda")[None, :]].double().cpu().numpy().T + shift[None, :]
+    want = np.stack([oracle.step(p, w.tau, w.G, 1)[:, 2, 2, 2] for p in before])
+    dev = np.abs(want - shift[None, :])
+    tol = 1.01 * (eps * dev + 2.0 ** -24) + 4e-7 * np.abs(want)
+    err = np.abs(got - want)
+    assert (err <= tol).all(), float((err / tol).max())
+
+
 # The same full-size sampled step with FP16 / BF16 deviation storage (the
 # fused step with stochastic rounding, as the benchmark runs it): the oracle
 # steps the decoded stored state; the GPU result, computed in FP32, is stored
