@@ -119,6 +119,33 @@ __device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ float xfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double xfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// Two FP32 lanes in one value (the nodes x and x + 1 of a thread of the
+// single-pass step).  Blackwell's paired FP32 instructions (add / mul / fma
+// .f32x2) compute both lanes in one issue slot, each lane rounded to nearest
+// exactly like the scalar instruction, so the node arithmetic below, written
+// once over C = float, double or float2, gives per lane the bits of the
+// scalar form.  vadd / vsub are the plain operators on scalars (what the
+// kernels always wrote); the paired difference is fma(b, -1, a), which is a
+// - b rounded once.
+__device__ __forceinline__ float2 xmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 xfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ double vadd(double a, double b) { return a + b; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
+__device__ __forceinline__ double vsub(double a, double b) { return a - b; }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+// lane type, and a lane value in every lane
+template <typename C> struct Lane { using S = C; };
+template <> struct Lane<float2> { using S = float; };
+template <typename C>
+__device__ __forceinline__ C splat(typename Lane<C>::S x) {
+  if constexpr (sizeof(C) == 2 * sizeof(typename Lane<C>::S))
+    return make_float2(x, x);
+  else
+    return x;
+}
+
 // Moments of one node's populations, and the link sums of the force, in one
 // fixed order shared by every kernel: opposite populations a, a + 1 (a odd)
 // are combined first, then short trees, so the dependency chains are 5 adds
@@ -129,9 +156,11 @@ static_assert(cx(1) == 1 && cx(7) == 1 && cy(7) == 1 && cx(9) == 1 && cy(9) == -
               "direction order of the moment sums");
 template <typename C>
 __device__ __forceinline__ C rho_of(const C f[Q]) {
-  const C s1 = f[1] + f[2], s3 = f[3] + f[4], s5 = f[5] + f[6], s7 = f[7] + f[8], s9 = f[9] + f[10],
-          s11 = f[11] + f[12], s13 = f[13] + f[14], s15 = f[15] + f[16], s17 = f[17] + f[18];
-  return ((f[0] + s1) + (s3 + s5)) + (((s7 + s9) + (s11 + s13)) + (s15 + s17));
+  const C s1 = vadd(f[1], f[2]), s3 = vadd(f[3], f[4]), s5 = vadd(f[5], f[6]), s7 = vadd(f[7], f[8]),
+          s9 = vadd(f[9], f[10]), s11 = vadd(f[11], f[12]), s13 = vadd(f[13], f[14]), s15 = vadd(f[15], f[16]),
+          s17 = vadd(f[17], f[18]);
+  return vadd(vadd(vadd(f[0], s1), vadd(s3, s5)),
+              vadd(vadd(vadd(s7, s9), vadd(s11, s13)), vadd(s15, s17)));
 }
 // Density with its rounding error, for the FP64 mass diagnostics: the same
 // tree as rho_of, each add done as Knuth's error-free TwoSum (s = a + b
@@ -202,24 +231,35 @@ template <> struct DSum<double> {
 
 template <typename C>
 __device__ __forceinline__ void mom_of(const C f[Q], C& jx, C& jy, C& jz) {
-  const C d1 = f[1] - f[2], d3 = f[3] - f[4], d5 = f[5] - f[6], d7 = f[7] - f[8], d9 = f[9] - f[10],
-          d11 = f[11] - f[12], d13 = f[13] - f[14], d15 = f[15] - f[16], d17 = f[17] - f[18];
-  jx = (d1 + (d7 + d9)) + (d11 + d13);
-  jy = (d3 + (d7 - d9)) + (d15 + d17);
-  jz = (d5 + (d11 - d13)) + (d15 - d17);
+  const C d1 = vsub(f[1], f[2]), d3 = vsub(f[3], f[4]), d5 = vsub(f[5], f[6]), d7 = vsub(f[7], f[8]),
+          d9 = vsub(f[9], f[10]), d11 = vsub(f[11], f[12]), d13 = vsub(f[13], f[14]), d15 = vsub(f[15], f[16]),
+          d17 = vsub(f[17], f[18]);
+  jx = vadd(vadd(d1, vadd(d7, d9)), vadd(d11, d13));
+  jy = vadd(vadd(d3, vsub(d7, d9)), vadd(d15, d17));
+  jz = vadd(vadd(d5, vsub(d11, d13)), vsub(d15, d17));
 }
 // sum over the axis links of p(x + c_a) c_a (a, b, c) and over the diagonal
-// links (d, e, f), from the neighbour values p[1..18]
+// links (d, e, f): from the link differences e_a = p[a] - p[a + 1] (a odd) of
+// the neighbour values p[1..18], and from those values
+template <typename C>
+__device__ __forceinline__ void link_combine(const C e[Q], C& ax, C& ay, C& az, C& dx, C& dy, C& dz) {
+  ax = e[1];
+  ay = e[3];
+  az = e[5];
+  dx = vadd(vadd(e[7], e[9]), vadd(e[11], e[13]));
+  dy = vadd(vsub(e[7], e[9]), vadd(e[15], e[17]));
+  dz = vadd(vsub(e[11], e[13]), vsub(e[15], e[17]));
+}
 template <typename C>
 __device__ __forceinline__ void link_sums(const C p[Q], C& ax, C& ay, C& az, C& dx, C& dy, C& dz) {
-  ax = p[1] - p[2];
-  ay = p[3] - p[4];
-  az = p[5] - p[6];
-  const C e7 = p[7] - p[8], e9 = p[9] - p[10], e11 = p[11] - p[12], e13 = p[13] - p[14], e15 = p[15] - p[16],
-          e17 = p[17] - p[18];
-  dx = (e7 + e9) + (e11 + e13);
-  dy = (e7 - e9) + (e15 + e17);
-  dz = (e11 - e13) + (e15 - e17);
+  ax = vsub(p[1], p[2]);
+  ay = vsub(p[3], p[4]);
+  az = vsub(p[5], p[6]);
+  const C e7 = vsub(p[7], p[8]), e9 = vsub(p[9], p[10]), e11 = vsub(p[11], p[12]), e13 = vsub(p[13], p[14]),
+          e15 = vsub(p[15], p[16]), e17 = vsub(p[17], p[18]);
+  dx = vadd(vadd(e7, e9), vadd(e11, e13));
+  dy = vadd(vsub(e7, e9), vadd(e15, e17));
+  dz = vadd(vsub(e11, e13), vsub(e15, e17));
 }
 
 // Storage traits.  T = stored type, C = compute type.  The *DEV forms store
@@ -381,8 +421,18 @@ __device__ __forceinline__ C psi_of(C rho, const Phys& ph) {
   if constexpr (sizeof(C) == 8) {
     return ph.rho0 * (1.0 - exp(-rho / ph.rho0));
   } else {
-    return (float)ph.rho0 * (1.0f - expf(-rho * (float)ph.inv_rho0));
+    // products and the difference through the non-contracted forms: the
+    // bits of psi_of2 below (a product fused into 1 - e would differ)
+    return __fmul_rn((float)ph.rho0, __fsub_rn(1.0f, expf(__fmul_rn(rho, -(float)ph.inv_rho0))));
   }
+}
+// psi of two FP32 lanes: per lane the bits of psi_of<float> ((-rho) c is rho
+// (-c), 1 - e is fma(e, -1, 1) rounded once)
+__device__ __forceinline__ float2 psi_of2(float2 rho, const Phys& ph) {
+  if (ph.psi_form == LBM_PSI_RHO) return rho;
+  const float2 t = xmul(rho, splat<float2>(-(float)ph.inv_rho0));
+  const float2 e = make_float2(expf(t.x), expf(t.y));
+  return xmul(splat<float2>((float)ph.rho0), vsub(splat<float2>(1.0f), e));
 }
 
 }  // namespace lbm

@@ -26,8 +26,10 @@
 // DRAM once per step (halo boxes and the two boundary planes of a run are
 // read by neighbouring blocks at about the same time and mostly hit L2),
 // psi never goes to DRAM.  The arithmetic is psi_of and collide_math of
-// lbm_node.cuh and the stores are those of collide_pair, so the results
-// equal the two-kernel step bitwise.  A-B streaming, 4- and 2-byte storage,
+// lbm_node.cuh, computed for the thread's two nodes at once in paired FP32
+// instructions (float2 lanes, each rounded like the scalar instruction), and
+// the stores are those of collide_pair, so the results equal the two-kernel
+// step bitwise.  A-B streaming, 4- and 2-byte storage,
 // lattices with nx % 64 == 0 and ny % 4 == 0.
 //
 // This header holds the kernel and its device helpers; lbm_fused.cu holds
@@ -343,25 +345,33 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
     if (k == 0 && dg.stall_test_ns) ok = ok && mbar_wait_bounded(full + NB, 0u, dg.stall_test_ns);
     const T* buf = reinterpret_cast<const T*>(smem + (size_t)b * S::plane);
     C* slot = ring + (k % NR) * RH * RW;
-    // psi of this thread's two nodes of plane zplane(k)
+    // psi of this thread's two nodes of plane zplane(k), the two nodes as the
+    // lanes of one float2 (paired FP32 arithmetic, the bits of the scalar
+    // form per lane)
     V cur[Q];
-    C f0[Q], f1[Q];
+    float2 fp[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
       cur[a] = *reinterpret_cast<const V*>(buf + (a * TY + ty) * TX + 2 * lane);
-      unpack_shifted<P>(cur[a], a == 0 ? s0 : (a <= 6 ? s1 : s2), f0[a], f1[a]);
+      unpack_shifted<P>(cur[a], a == 0 ? s0 : (a <= 6 ? s1 : s2), fp[a].x, fp[a].y);
     }
-    const C r0 = rho_of<C>(f0), r1 = rho_of<C>(f1);
-    const C p0 = psi_of<C>(r0, ph), p1 = psi_of<C>(r1, ph);
+    const float2 rr = rho_of<float2>(fp);
+    const float2 pp = psi_of2(rr, ph);
+    const C r0 = rr.x, r1 = rr.y, p0 = pp.x, p1 = pp.y;
     nbad |= bad_rho(r0) | bad_rho(r1);
     if constexpr (DIAG) {
       // momentum of the two nodes (the summation order of the two-kernel
       // diagnostics)
       C jv[2][3], lo[2];
-      mom_of<C>(f0, jv[0][0], jv[0][1], jv[0][2]);
-      mom_of<C>(f1, jv[1][0], jv[1][1], jv[1][2]);
+      float2 jx2, jy2, jz2;
+      mom_of<float2>(fp, jx2, jy2, jz2);
+      jv[0][0] = jx2.x, jv[0][1] = jy2.x, jv[0][2] = jz2.x;
+      jv[1][0] = jx2.y, jv[1][1] = jy2.y, jv[1][2] = jz2.y;
       if (k >= 1 && k <= np - 2) {
         // the rounding error of each density (rho_of_x's high part is r0, r1)
+        C f0[Q], f1[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) f0[a] = fp[a].x, f1[a] = fp[a].y;
         rho_of_x(f0, lo[0]);
         rho_of_x(f1, lo[1]);
 #pragma unroll
@@ -449,24 +459,46 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
             q[dy + 1][dz + 1][3] = 0;
           }
         }
-      C g0[Q], g1[Q], pn0[Q], pn1[Q];
+      float2 g2[Q];
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
-        unpack_shifted<P>(prev[a], a == 0 ? s0 : (a <= 6 ? s1 : s2), g0[a], g1[a]);
-      }
-      pn0[0] = pn1[0] = 0;
-#pragma unroll
-      for (int a = 1; a < Q; ++a) {
-        pn0[a] = q[cy(a) + 1][cz(a) + 1][1 + cx(a)];
-        pn1[a] = q[cy(a) + 1][cz(a) + 1][2 + cx(a)];
+        unpack_shifted<P>(prev[a], a == 0 ? s0 : (a <= 6 ? s1 : s2), g2[a].x, g2[a].y);
       }
       C fs0[Q], fs1[Q];
       if constexpr (COLL == COLL_MRT) {
+        C g0[Q], g1[Q], pn0[Q], pn1[Q];
+        pn0[0] = pn1[0] = 0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) g0[a] = g2[a].x, g1[a] = g2[a].y;
+#pragma unroll
+        for (int a = 1; a < Q; ++a) {
+          pn0[a] = q[cy(a) + 1][cz(a) + 1][1 + cx(a)];
+          pn1[a] = q[cy(a) + 1][cz(a) + 1][2 + cx(a)];
+        }
         collide_math_mrt<C>(ph, g0, q[1][1][1], pn0, fs0);
         collide_math_mrt<C>(ph, g1, q[1][1][2], pn1, fs1);
       } else {
-        collide_math_r<C>(ph, g0, prho[0], q[1][1][1], pn0, fs0);
-        collide_math_r<C>(ph, g1, prho[1], q[1][1][2], pn1, fs1);
+        // the link differences p[a] - p[a + 1] of the two nodes as pairs:
+        // one paired difference where both neighbours lie in the thread's own
+        // x columns (the two values of one ring load), two scalar ones where
+        // a neighbour is shifted along x (their results pair up freely)
+        float2 e[Q];
+#pragma unroll
+        for (int a = 1; a < Q; a += 2) {
+          const int b = a + 1;
+          const C* qa = q[cy(a) + 1][cz(a) + 1];
+          const C* qb = q[cy(b) + 1][cz(b) + 1];
+          if (cx(a) == 0)
+            e[a] = vsub(make_float2(qa[1], qa[2]), make_float2(qb[1], qb[2]));
+          else
+            e[a] = make_float2(qa[1 + cx(a)] - qb[1 + cx(b)], qa[2 + cx(a)] - qb[2 + cx(b)]);
+        }
+        float2 ax, ay, az, dx, dy, dz, fs2[Q];
+        link_combine<float2>(e, ax, ay, az, dx, dy, dz);
+        collide_math_ls<float2>(ph, g2, make_float2(prho[0], prho[1]), make_float2(q[1][1][1], q[1][1][2]), ax,
+                                ay, az, dx, dy, dz, fs2);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) fs0[a] = fs2[a].x, fs1[a] = fs2[a].y;
       }
       const int i0 = x + g.nx * (y + g.ny * z);
       const bool sr = Prec<P>::dev && ph.sr;
@@ -477,11 +509,16 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
         const int row = g.nx * (yv[1 + cy(a)] + g.ny * zv[1 + cz(a)]);
         if constexpr (Prec<P>::dev) {
           T* const base = s_dir[a];
+          // the shift comes off both nodes in one paired difference
+          const float2 sh2 = splat<float2>(sh);
           if (cx(a) == 0) {
-            if (sr)
-              store_pair_sr<P>(base + (row + x), fs0[a], fs1[a], sh, sr_bits(seed0, a), sr_bits(seed1, a));
-            else
+            if (sr) {
+              const float2 d = vsub(make_float2(fs0[a], fs1[a]), sh2);   // node x low, x + 1 high
+              *reinterpret_cast<unsigned*>(base + (row + x)) =
+                  cvt_pair_sr<P>(d.y, d.x, (sr_bits(seed1, a) << 16) | (sr_bits(seed0, a) & 0xFFFFu));
+            } else {
               store_pair<P>(base + (row + x), fs0[a], fs1[a], sh);
+            }
           } else if (!sr) {
             store_pop<P>(ph, base + (row + (cx(a) > 0 ? x + 1 : xm)), fs0[a], sh, seed0, a);
             store_pop<P>(ph, base + (row + (cx(a) > 0 ? xp : x)), fs1[a], sh, seed1, a);
@@ -493,8 +530,10 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
             T* const base_b = s_dir[a + 1];
             const int row_b = g.nx * (yv[1 + cy(a + 1)] + g.ny * zv[1 + cz(a + 1)]);
             const unsigned j = (unsigned)(a + 1) >> 1;
-            const unsigned d0 = cvt_pair_sr<P>(fs0[a] - sh, fs0[a + 1] - sh, sr_word(seed0, j));
-            const unsigned d1 = cvt_pair_sr<P>(fs1[a] - sh, fs1[a + 1] - sh, sr_word(seed1, j));
+            const float2 da = vsub(make_float2(fs0[a], fs1[a]), sh2);
+            const float2 db = vsub(make_float2(fs0[a + 1], fs1[a + 1]), sh2);
+            const unsigned d0 = cvt_pair_sr<P>(da.x, db.x, sr_word(seed0, j));
+            const unsigned d1 = cvt_pair_sr<P>(da.y, db.y, sr_word(seed1, j));
             unsigned short* const pa = reinterpret_cast<unsigned short*>(base + row);
             unsigned short* const pb = reinterpret_cast<unsigned short*>(base_b + row_b);
             pa[cx(a) > 0 ? x + 1 : xm] = (unsigned short)(d0 >> 16);

@@ -135,6 +135,9 @@ __device__ __forceinline__ void store_pop(const Phys& ph, typename Prec<P>::T* p
 __device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
 
+// Lane-wise correctly rounded reciprocal of a pair.
+__device__ __forceinline__ float2 rcp_rn(float2 x) { return make_float2(__frcp_rn(x.x), __frcp_rn(x.y)); }
+
 // c_a . u for odd a, whose first nonzero velocity component is +1: sums of
 // the velocity components only (no 0 + u_x, which the compiler must keep
 // for a -0 operand).
@@ -145,41 +148,42 @@ template <typename C>
 __device__ __forceinline__ C cdotu(int a, C ux, C uy, C uz) {
   if (cx(a)) {
     C cu = ux;
-    if (cy(a)) cu = cy(a) > 0 ? cu + uy : cu - uy;
-    if (cz(a)) cu = cz(a) > 0 ? cu + uz : cu - uz;
+    if (cy(a)) cu = cy(a) > 0 ? vadd(cu, uy) : vsub(cu, uy);
+    if (cz(a)) cu = cz(a) > 0 ? vadd(cu, uz) : vsub(cu, uz);
     return cu;
   }
-  if (cy(a)) return cz(a) ? (cz(a) > 0 ? uy + uz : uy - uz) : uy;
+  if (cy(a)) return cz(a) ? (cz(a) > 0 ? vadd(uy, uz) : vsub(uy, uz)) : uy;
   return uz;
 }
 
 // Post-collision populations fs of a node with populations f, density rho
 // (= rho_of(f), passed in where the caller has it already), psi(x) = pc
-// and neighbour values pn[a] = psi(x + c_a) (a = 1..18).
+// and the link sums of its neighbour values (link_sums).  C = float2
+// computes two nodes, lane by lane with the bits of C = float.
 template <typename C>
-__device__ __forceinline__ void collide_math_r(const Phys& ph, const C f[Q], C rho, C pc, const C pn[Q],
-                                               C fs[Q]) {
+__device__ __forceinline__ void collide_math_ls(const Phys& ph, const C f[Q], C rho, C pc, C ax, C ay, C az, C dx,
+                                                C dy, C dz, C fs[Q]) {
+  using S = typename Lane<C>::S;
   // Eq. 4 (the momentum; rho from the caller)
   C jx, jy, jz;
   mom_of<C>(f, jx, jy, jz);
-  // Eq. 5: sum_a w_a psi(x + c_a) c_a, split by weight class
-  C ax, ay, az, dx, dy, dz;
-  link_sums<C>(pn, ax, ay, az, dx, dy, dz);
-  // Products and sums below go through xmul / xfma (round to nearest, fused
+  // Eq. 5: sum_a w_a psi(x + c_a) c_a, split by weight class.  Products and
+  // sums below go through xmul / xfma / vadd / vsub (round to nearest, fused
   // only where written), so every kernel that inlines this function computes
   // the same bits whatever the compiler's contraction choices around it.
-  const C w1 = (C)(1.0 / 18.0), w2 = (C)(1.0 / 36.0);
-  const C gp = xmul(-(C)ph.G, pc);
+  const C w1 = splat<C>((S)(1.0 / 18.0)), w2 = splat<C>((S)(1.0 / 36.0));
+  const C gp = xmul(splat<C>(-(S)ph.G), pc);
   const C Fx = xmul(gp, xfma(w1, ax, xmul(w2, dx)));
   const C Fy = xmul(gp, xfma(w1, ay, xmul(w2, dy)));
   const C Fz = xmul(gp, xfma(w1, az, xmul(w2, dz)));
   // Eq. 6
-  const C tau = (C)ph.tau;
+  const S tau_s = (S)ph.tau;
+  const C tau = splat<C>(tau_s);
   const C inv_rho = rcp_rn(rho);
   const C ux = xmul(xfma(tau, Fx, jx), inv_rho);
   const C uy = xmul(xfma(tau, Fy, jy), inv_rho);
   const C uz = xmul(xfma(tau, Fz, jz), inv_rho);
-  const C usq = xmul((C)1.5, xfma(uz, uz, xfma(uy, uy, xmul(ux, ux))));
+  const C usq = xmul(splat<C>((S)1.5), xfma(uz, uz, xfma(uy, uy, xmul(ux, ux))));
   // Eq. 2 and Eq. 3 as f* = (1 - omega) f + omega f_eq.  For the pair a, b =
   // opp(a) of weight w, with q = omega w rho and cu = c_a . u':
   //   omega f_eq_a = A + B,  omega f_eq_b = A - B,
@@ -192,13 +196,15 @@ __device__ __forceinline__ void collide_math_r(const Phys& ph, const C f[Q], C r
   // (with weights rounded to the arithmetic's precision the direct form of
   // Eq. 2 creates mass of relative order 1e-8 per FP32 collision in one
   // direction).
-  const C omega = (C)1 / tau;
-  const C om1 = (C)1 - omega;
-  const C orho = xmul(omega, rho);
+  const S omega_s = (S)1 / tau_s;
+  const C om1 = splat<C>((S)1 - omega_s);
+  const C orho = xmul(splat<C>(omega_s), rho);
   const C q1 = xmul(orho, w1);
-  const C E1 = xmul(q1, (C)1 - usq), M1 = xmul((C)4.5, q1), T1 = xmul((C)3, q1);
-  const C E2 = (C)0.5 * E1, M2 = (C)0.5 * M1, T2 = (C)0.5 * T1;
-  C sumA = 0;
+  const C E1 = xmul(q1, vsub(splat<C>((S)1), usq)), M1 = xmul(splat<C>((S)4.5), q1),
+          T1 = xmul(splat<C>((S)3), q1);
+  const C half = splat<C>((S)0.5);
+  const C E2 = xmul(half, E1), M2 = xmul(half, M1), T2 = xmul(half, T1);
+  C sumA = splat<C>((S)0);
 #pragma unroll
   for (int a = 1; a < Q; a += 2) {
     const int b = a + 1;  // opp(a)
@@ -206,11 +212,20 @@ __device__ __forceinline__ void collide_math_r(const Phys& ph, const C f[Q], C r
     const C cu = cdotu<C>(a, ux, uy, uz);
     const C A = xfma(xmul(axis ? M1 : M2, cu), cu, axis ? E1 : E2);
     const C B = xmul(axis ? T1 : T2, cu);
-    sumA = a == 1 ? A : sumA + A;
-    fs[a] = xfma(om1, f[a], A + B);
-    fs[b] = xfma(om1, f[b], A - B);
+    sumA = a == 1 ? A : vadd(sumA, A);
+    fs[a] = xfma(om1, f[a], vadd(A, B));
+    fs[b] = xfma(om1, f[b], vsub(A, B));
   }
-  fs[0] = xfma(om1, f[0], xfma((C)-2, sumA, orho));
+  fs[0] = xfma(om1, f[0], xfma(splat<C>((S)-2), sumA, orho));
+}
+
+// The same from the neighbour values pn[a] = psi(x + c_a) (a = 1..18).
+template <typename C>
+__device__ __forceinline__ void collide_math_r(const Phys& ph, const C f[Q], C rho, C pc, const C pn[Q],
+                                               C fs[Q]) {
+  C ax, ay, az, dx, dy, dz;
+  link_sums<C>(pn, ax, ay, az, dx, dy, dz);
+  collide_math_ls<C>(ph, f, rho, pc, ax, ay, az, dx, dy, dz, fs);
 }
 
 template <typename C>
