@@ -135,50 +135,6 @@ struct Maps {
   CUtensorMap interior, row, col, cor;
 };
 
-// Stored value to compute precision plus the deviation shift.  For 2-byte
-// storage one widening add (add.rn.f32.f16 / .bf16, sm_100 and later) does
-// both: the conversion is exact, so the result is the FP32 sum of the
-// converted value and the shift rounded once to nearest, the bits of the
-// conversion-then-add of the two-kernel step.
-__device__ __forceinline__ float add_wide(__half h, float c) {
-  float d;
-  asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(__half_as_ushort(h)), "f"(c));
-  return d;
-}
-__device__ __forceinline__ float add_wide(__nv_bfloat16 h, float c) {
-  float d;
-  asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(__bfloat16_as_ushort(h)), "f"(c));
-  return d;
-}
-template <int P>
-__device__ __forceinline__ void unpack_shifted(typename Pair<P>::V v, float sh, float& a, float& b) {
-  if constexpr (P == LBM_F16DEV) {
-    a = add_wide(__low2half(v), sh);
-    b = add_wide(__high2half(v), sh);
-  } else if constexpr (P == LBM_BF16DEV) {
-    a = add_wide(__low2bfloat16(v), sh);
-    b = add_wide(__high2bfloat16(v), sh);
-  } else {
-    Pair<P>::unpack(v, a, b);   // full precision: no shift
-  }
-}
-// Two FP32 values to a packed 2-byte pair with stochastic rounding: hi takes
-// the random bits rbits[31:16], lo rbits[15:0].
-template <int P>
-__device__ __forceinline__ unsigned cvt_pair_sr(float hi, float lo, unsigned rbits) {
-  if constexpr (P == LBM_BF16DEV)
-    return cvt_rs_bf16x2(hi, lo, rbits);
-  else
-    return cvt_rs_f16x2(hi, lo, rbits);
-}
-template <int P>
-__device__ __forceinline__ float load_shifted(const typename Prec<P>::T* p, float sh) {
-  if constexpr (Prec<P>::dev)
-    return add_wide(*p, sh);
-  else
-    return *p;
-}
-
 // Issues the nine copies of plane zz into buffer b (one thread).
 template <int P>
 __device__ __forceinline__ void issue_plane(unsigned char* smem, const Maps& m, int b, int x0, int y0, int xl,
@@ -493,10 +449,11 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
           else
             e[a] = make_float2(qa[1 + cx(a)] - qb[1 + cx(b)], qa[2 + cx(a)] - qb[2 + cx(b)]);
         }
-        float2 ax, ay, az, dx, dy, dz, fs2[Q];
+        float2 ax, ay, az, dx, dy, dz, jx, jy, jz, fs2[Q];
         link_combine<float2>(e, ax, ay, az, dx, dy, dz);
-        collide_math_ls<float2>(ph, g2, make_float2(prho[0], prho[1]), make_float2(q[1][1][1], q[1][1][2]), ax,
-                                ay, az, dx, dy, dz, fs2);
+        mom_of<float2>(g2, jx, jy, jz);
+        collide_math_ls<float2>(ph, g2, make_float2(prho[0], prho[1]), jx, jy, jz,
+                                make_float2(q[1][1][1], q[1][1][2]), ax, ay, az, dx, dy, dz, fs2);
 #pragma unroll
         for (int a = 0; a < Q; ++a) fs0[a] = fs2[a].x, fs1[a] = fs2[a].y;
       }

@@ -223,7 +223,17 @@ __global__ void __launch_bounds__(GNT, gfused_minb<P>())
       for (int a = 1; a < Q; ++a) pn[a] = ring[(k - 1 + dir * cz(a) + GNR) % GNR][wy + 1 + cy(a)][lane + 1 + cx(a)];
       const C pc = ring[(k - 1) % GNR][wy + 1][lane + 1];
       C fs[Q];
-      collide_math_r<C>(ph, fp, prho, pc, pn, fs);
+      if constexpr (Prec<P>::dev) {
+        // collide_math_r with the momentum before the link sums: that order
+        // keeps the 2-byte forms of this kernel within 128 registers (the
+        // other order spills; for FP32 it is 1.8 % faster)
+        C jx, jy, jz, ax, ay, az, dx, dy, dz;
+        mom_of<C>(fp, jx, jy, jz);
+        link_sums<C>(pn, ax, ay, az, dx, dy, dz);
+        collide_math_ls<C>(ph, fp, prho, jx, jy, jz, pc, ax, ay, az, dx, dy, dz, fs);
+      } else {
+        collide_math_r<C>(ph, fp, prho, pc, pn, fs);
+      }
       const int i = x + g.nx * (y + g.ny * z);
       const unsigned seed = (Prec<P>::dev && ph.sr) ? sr_seed(i, fs[0], salt) : 0u;
 #pragma unroll

@@ -79,6 +79,50 @@ template <> struct Pair<LBM_BF16DEV> {
   }
 };
 
+// Stored value to compute precision plus the deviation shift.  For 2-byte
+// storage one widening add (add.rn.f32.f16 / .bf16, sm_100 and later) does
+// both: the conversion is exact, so the result is the FP32 sum of the
+// converted value and the shift rounded once to nearest, the bits of the
+// conversion-then-add of the two-kernel step.
+__device__ __forceinline__ float add_wide(__half h, float c) {
+  float d;
+  asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(__half_as_ushort(h)), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float add_wide(__nv_bfloat16 h, float c) {
+  float d;
+  asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(__bfloat16_as_ushort(h)), "f"(c));
+  return d;
+}
+template <int P>
+__device__ __forceinline__ void unpack_shifted(typename Pair<P>::V v, float sh, float& a, float& b) {
+  if constexpr (P == LBM_F16DEV) {
+    a = add_wide(__low2half(v), sh);
+    b = add_wide(__high2half(v), sh);
+  } else if constexpr (P == LBM_BF16DEV) {
+    a = add_wide(__low2bfloat16(v), sh);
+    b = add_wide(__high2bfloat16(v), sh);
+  } else {
+    Pair<P>::unpack(v, a, b);   // full precision: no shift
+  }
+}
+// Two FP32 values to a packed 2-byte pair with stochastic rounding: hi takes
+// the random bits rbits[31:16], lo rbits[15:0].
+template <int P>
+__device__ __forceinline__ unsigned cvt_pair_sr(float hi, float lo, unsigned rbits) {
+  if constexpr (P == LBM_BF16DEV)
+    return cvt_rs_bf16x2(hi, lo, rbits);
+  else
+    return cvt_rs_f16x2(hi, lo, rbits);
+}
+template <int P>
+__device__ __forceinline__ float load_shifted(const typename Prec<P>::T* p, float sh) {
+  if constexpr (Prec<P>::dev)
+    return add_wide(*p, sh);
+  else
+    return *p;
+}
+
 // Loads populations x and x + 1 (RO: read-only path; else a plain load for
 // in-place updates) and adds the deviation shift.  Full-precision storage has
 // no shift and skips the add (x + 0 is not x for x = -0, so the compiler
@@ -157,16 +201,14 @@ __device__ __forceinline__ C cdotu(int a, C ux, C uy, C uz) {
 }
 
 // Post-collision populations fs of a node with populations f, density rho
-// (= rho_of(f), passed in where the caller has it already), psi(x) = pc
-// and the link sums of its neighbour values (link_sums).  C = float2
-// computes two nodes, lane by lane with the bits of C = float.
+// (= rho_of(f), passed in where the caller has it already), momentum (jx,
+// jy, jz) = mom_of(f) (Eq. 4), psi(x) = pc and the link sums of its
+// neighbour values (link_sums).  C = float2 computes two nodes, lane by lane
+// with the bits of C = float.
 template <typename C>
-__device__ __forceinline__ void collide_math_ls(const Phys& ph, const C f[Q], C rho, C pc, C ax, C ay, C az, C dx,
-                                                C dy, C dz, C fs[Q]) {
+__device__ __forceinline__ void collide_math_ls(const Phys& ph, const C f[Q], C rho, C jx, C jy, C jz, C pc, C ax,
+                                                C ay, C az, C dx, C dy, C dz, C fs[Q]) {
   using S = typename Lane<C>::S;
-  // Eq. 4 (the momentum; rho from the caller)
-  C jx, jy, jz;
-  mom_of<C>(f, jx, jy, jz);
   // Eq. 5: sum_a w_a psi(x + c_a) c_a, split by weight class.  Products and
   // sums below go through xmul / xfma / vadd / vsub (round to nearest, fused
   // only where written), so every kernel that inlines this function computes
@@ -223,9 +265,12 @@ __device__ __forceinline__ void collide_math_ls(const Phys& ph, const C f[Q], C 
 template <typename C>
 __device__ __forceinline__ void collide_math_r(const Phys& ph, const C f[Q], C rho, C pc, const C pn[Q],
                                                C fs[Q]) {
-  C ax, ay, az, dx, dy, dz;
+  // (the link sums first: with the momentum first the batched collide-stream
+  // kernel, compiled to 64 - 80 registers, ran 6 % slower)
+  C jx, jy, jz, ax, ay, az, dx, dy, dz;
   link_sums<C>(pn, ax, ay, az, dx, dy, dz);
-  collide_math_ls<C>(ph, f, rho, pc, ax, ay, az, dx, dy, dz, fs);
+  mom_of<C>(f, jx, jy, jz);
+  collide_math_ls<C>(ph, f, rho, jx, jy, jz, pc, ax, ay, az, dx, dy, dz, fs);
 }
 
 template <typename C>
