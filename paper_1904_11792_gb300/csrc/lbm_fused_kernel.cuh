@@ -434,26 +434,8 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
         collide_math_mrt<C>(ph, g0, q[1][1][1], pn0, fs0);
         collide_math_mrt<C>(ph, g1, q[1][1][2], pn1, fs1);
       } else {
-        // the link differences p[a] - p[a + 1] of the two nodes as pairs:
-        // one paired difference where both neighbours lie in the thread's own
-        // x columns (the two values of one ring load), two scalar ones where
-        // a neighbour is shifted along x (their results pair up freely)
-        float2 e[Q];
-#pragma unroll
-        for (int a = 1; a < Q; a += 2) {
-          const int b = a + 1;
-          const C* qa = q[cy(a) + 1][cz(a) + 1];
-          const C* qb = q[cy(b) + 1][cz(b) + 1];
-          if (cx(a) == 0)
-            e[a] = vsub(make_float2(qa[1], qa[2]), make_float2(qb[1], qb[2]));
-          else
-            e[a] = make_float2(qa[1 + cx(a)] - qb[1 + cx(b)], qa[2 + cx(a)] - qb[2 + cx(b)]);
-        }
-        float2 ax, ay, az, dx, dy, dz, jx, jy, jz, fs2[Q];
-        link_combine<float2>(e, ax, ay, az, dx, dy, dz);
-        mom_of<float2>(g2, jx, jy, jz);
-        collide_math_ls<float2>(ph, g2, make_float2(prho[0], prho[1]), jx, jy, jz,
-                                make_float2(q[1][1][1], q[1][1][2]), ax, ay, az, dx, dy, dz, fs2);
+        float2 fs2[Q];
+        collide_pair_math(ph, g2, make_float2(prho[0], prho[1]), q, fs2);
 #pragma unroll
         for (int a = 0; a < Q; ++a) fs0[a] = fs2[a].x, fs1[a] = fs2[a].y;
       }

@@ -278,6 +278,31 @@ __device__ __forceinline__ void collide_math(const Phys& ph, const C f[Q], C pc,
   collide_math_r<C>(ph, f, rho_of<C>(f), pc, pn, fs);
 }
 
+// The collision of two x-adjacent nodes (x, x + 1) as the lanes of float2,
+// with the bits of collide_math_r<float> per node: f their populations,
+// rho their densities, q[dy + 1][dz + 1][i] psi at x - 1 + i of the row (y +
+// dy, z + dz).  The link differences of the directions with c_x = 0 are one
+// paired difference of the pair's own two values, those of the x-shifted
+// directions two scalar differences (their results pair up freely).
+__device__ __forceinline__ void collide_pair_math(const Phys& ph, const float2 f[Q], float2 rho,
+                                                  const float (&q)[3][3][4], float2 fs[Q]) {
+  float2 e[Q];
+#pragma unroll
+  for (int a = 1; a < Q; a += 2) {
+    const int b = a + 1;
+    const float* qa = q[cy(a) + 1][cz(a) + 1];
+    const float* qb = q[cy(b) + 1][cz(b) + 1];
+    if (cx(a) == 0)
+      e[a] = vsub(make_float2(qa[1], qa[2]), make_float2(qb[1], qb[2]));
+    else
+      e[a] = make_float2(qa[1 + cx(a)] - qb[1 + cx(b)], qa[2 + cx(a)] - qb[2 + cx(b)]);
+  }
+  float2 ax, ay, az, dx, dy, dz, jx, jy, jz;
+  link_combine<float2>(e, ax, ay, az, dx, dy, dz);
+  mom_of<float2>(f, jx, jy, jz);
+  collide_math_ls<float2>(ph, f, rho, jx, jy, jz, make_float2(q[1][1][1], q[1][1][2]), ax, ay, az, dx, dy, dz, fs);
+}
+
 // A non-positive, NaN or infinite density (the numeric flag's condition).
 template <typename C>
 __device__ __forceinline__ bool bad_rho(C rho) {
@@ -363,12 +388,19 @@ __device__ __forceinline__ void psi_pair(const Geom& g, const Phys& ph, const ty
       }
     }
   }
-  C p0, p1;
-  psi_math<C>(ph, rho_of<C>(f0), &p0, flag);
-  psi_math<C>(ph, rho_of<C>(f1), &p1, flag);
   if constexpr (sizeof(C) == 4) {
-    *reinterpret_cast<float2*>(psi + i) = make_float2(p0, p1);
+    // the two nodes as float2 lanes (paired FP32 instructions, the bits of
+    // the scalar form)
+    float2 fp[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) fp[a] = make_float2(f0[a], f1[a]);
+    const float2 rho = rho_of<float2>(fp);
+    raise_flag(bad_rho(rho.x) | bad_rho(rho.y), flag);
+    *reinterpret_cast<float2*>(psi + i) = psi_of2(rho, ph);
   } else {
+    C p0, p1;
+    psi_math<C>(ph, rho_of<C>(f0), &p0, flag);
+    psi_math<C>(ph, rho_of<C>(f1), &p1, flag);
     *reinterpret_cast<double2*>(psi + i) = make_double2(p0, p1);
   }
 }
@@ -406,10 +438,15 @@ __device__ __forceinline__ void psi_quad(const Geom& g, const Phys& ph, const ty
       fv[3][a] += sh;
     }
   }
-  float ps[4];
+  // nodes (0, 1) and (2, 3) as float2 lanes (paired FP32 instructions, the
+  // bits of the scalar form)
+  float2 pa[Q], pb[Q];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) psi_math<float>(ph, rho_of<float>(fv[k]), &ps[k], flag);
-  *reinterpret_cast<float4*>(psi + i) = make_float4(ps[0], ps[1], ps[2], ps[3]);
+  for (int a = 0; a < Q; ++a) pa[a] = make_float2(fv[0][a], fv[1][a]), pb[a] = make_float2(fv[2][a], fv[3][a]);
+  const float2 ra = rho_of<float2>(pa), rb = rho_of<float2>(pb);
+  raise_flag(bad_rho(ra.x) | bad_rho(ra.y) | bad_rho(rb.x) | bad_rho(rb.y), flag);
+  const float2 qa = psi_of2(ra, ph), qb = psi_of2(rb, ph);
+  *reinterpret_cast<float4*>(psi + i) = make_float4(qa.x, qa.y, qb.x, qb.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -553,6 +590,13 @@ __device__ __forceinline__ void collide_pair(const Geom& g, const Phys& ph,
   if constexpr (COLL == COLL_MRT) {
     collide_math_mrt<C>(ph, f0, q[1][1][1], pn0, fs0);
     collide_math_mrt<C>(ph, f1, q[1][1][2], pn1, fs1);
+  } else if constexpr (sizeof(C) == 4) {
+    float2 fp[Q], fs[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) fp[a] = make_float2(f0[a], f1[a]);
+    collide_pair_math(ph, fp, rho_of<float2>(fp), q, fs);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) fs0[a] = fs[a].x, fs1[a] = fs[a].y;
   } else {
     collide_math<C>(ph, f0, q[1][1][1], pn0, fs0);
     collide_math<C>(ph, f1, q[1][1][2], pn1, fs1);
