@@ -153,7 +153,10 @@ int lbm_set_stream(lbm_handle h, void *stream);
  * disables graphs), "block_x", "block_y", "block_z" (collide-stream block
  * shape, at most 256 threads), "occupancy" (2, 3 or 4: 256-thread blocks
  * per SM the collide-stream kernel's register budget allows; 0 = auto,
- * the default: 2 for the two-node kernel, 3 for the one-node kernel),
+ * the default: 3 for the one-node kernel and the AA even step's two-node
+ * kernel, 3 for the AA odd step's with 2-byte storage and 2 otherwise, 2
+ * for the A-B step's two-node kernel; get answers the odd step's (AA) or
+ * the A-B step's value),
  * "vector" (0/1, default 1: when nx is even each thread updates two
  * neighbouring nodes with 2-element vector loads and stores; block_x then
  * counts node pairs), "fused" (0/1, default 1: A-B steps run as one

@@ -140,6 +140,20 @@ int salt_word(const lbm_ctx* h, long long step, int cur) {
   return h->cfg.pattern == LBM_AA ? (int)(step & 1) : (cur & 1);
 }
 
+// Default register budget of the collide-stream kernel (blocks of 256
+// threads per SM), as measured on the 1024x512x512 lattice: 3 for the
+// one-node kernel and for the AA even step's two-node kernel (local loads
+// and stores: no spills at 80 registers); for the AA odd step's two-node
+// kernel 3 with 2-byte storage (6.93 ms per FP16 AA step against 7.65 with
+// 2, although it spills a little at 80 registers) and 2 otherwise (FP32:
+// 9.11 ms against 9.84); 2 for the A-B step's two-node kernel (no spills at
+// <= 128 registers).
+int auto_minb(bool vec, int mode, int precision) {
+  if (!vec || mode == MODE_AA_EVEN) return 3;
+  if (mode == MODE_AA_ODD && (precision == LBM_F16DEV || precision == LBM_BF16DEV)) return 3;
+  return 2;
+}
+
 // Enqueues one time step on stream s.  `phase` is the step parity (AA) or
 // the index of the current array (A-B).  With timing on, each kernel is
 // bracketed by events on s.
@@ -210,10 +224,8 @@ int enqueue_step(lbm_ctx* h, cudaStream_t s, long long step, int cur, bool timed
     CK(launch_psi(prec, layout, h->vec, h->g, h->ph, src, h->psi, h->d_flag, s));
   }
   if (timed) CK(cudaEventRecord(e1, s));
-  // default register budget: 2 blocks/SM for the two-node kernel (no
-  // spills at <= 128 registers), 3 for the one-node kernel
   const bool vec = h->vec && (h->g.nx % 2 == 0);
-  const int minb = h->minb ? h->minb : (vec ? 2 : 3);
+  const int minb = h->minb ? h->minb : auto_minb(vec, mode, prec);
   if (h->ph.coll == COLL_MRT)
     CK(launch_collide_mrt(prec, mode, vec, h->g, ph, src, dst, h->psi, h->block, s));
   else
@@ -665,7 +677,10 @@ int lbm_get_option(lbm_handle h, const char* key, double* v) {
   else if (k == "graph") *v = h->use_graph;
   else if (k == "diag_interval") *v = h->diag_interval;
   else if (k == "diag_ccl") *v = h->diag_ccl;
-  else if (k == "occupancy") *v = h->minb ? h->minb : ((h->vec && h->g.nx % 2 == 0) ? 2 : 3);
+  else if (k == "occupancy")
+    *v = h->minb ? h->minb
+                 : auto_minb(h->vec && h->g.nx % 2 == 0, h->cfg.pattern == LBM_AA ? MODE_AA_ODD : MODE_AB,
+                             h->cfg.precision);
   else if (k == "vector") *v = h->vec && (h->g.nx % 2 == 0);
   else if (k == "stochastic_rounding") *v = h->ph.sr;
   else if (k == "fused")
