@@ -324,8 +324,9 @@ int lbm_batch_set_stream(lbm_batch b, void *stream);
  * single-pass kernel - blocks own 32 x 8 tiles of an instance's x-y plane,
  * cut short at its edges, march through a run of z planes and compute psi
  * of the tile and its one-node ring in shared memory, so the populations
- * are read once per step (Eqs. 2-6 as in lbm_step; instances of any size);
- * 0: a psi pass and a collide-stream kernel per step), "fused_fz" (z planes
+ * are read once per step (Eqs. 2-6 as in lbm_step; instances of any size
+ * up to 113 M nodes, larger ones take the two kernels); 0: a psi pass and a
+ * collide-stream kernel per step), "fused_fz" (z planes
  * per block of the single-pass step, default 16), "graph" (0/1),
  * "stochastic_rounding" (0/1, as lbm_set_option), and for the two-kernel
  * step "occupancy" (2, 3, 4; default 2), "vector" (0/1, default 1:

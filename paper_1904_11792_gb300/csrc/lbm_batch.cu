@@ -292,7 +292,10 @@ bool batch_sr(const lbm_batch_ctx* b) {
 }
 
 int enqueue_batch_step(lbm_batch_ctx* b, cudaStream_t s, int cur) {
-  if (b->fused)
+  // the single-pass kernel addresses an instance's populations by 32-bit
+  // offsets: instances of 113 M nodes or more take the two kernels
+  const bool fused_fits = 19LL * b->max_nodes <= 0x7fffffffLL;
+  if (b->fused && fused_fits)
     BCK(batch_fused_launch(b->precision, b->d_ginst, b->count, b->gblocks, b->pool_f, cur, b->d_flag, s));
   else
     BCK(batch_launch(b->precision, b->d_inst, b->count, b->psi_blocks, b->tiles, b->pool_f, cur, b->pool_psi,

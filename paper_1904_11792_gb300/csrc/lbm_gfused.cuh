@@ -101,7 +101,9 @@ __global__ void __launch_bounds__(GNT, gfused_minb<P>())
   const GInst& I = inst[gfind(inst, count, blockIdx.x)];
   const Geom g = I.g;
   const Phys ph = I.ph;
-  const long long N = g.N;
+  // element offsets within an instance are 32-bit: 19 N < 2^31 (the host
+  // sends larger instances to the two-kernel step)
+  const int N = (int)g.N;
   const T* src = pool_f + I.off_f + (long long)cur * Q * N;
   T* dst = pool_f + I.off_f + (long long)(cur ^ 1) * Q * N;
   // block -> (z run, tile x, tile y), the run fastest: the runs of a tile and
@@ -145,23 +147,23 @@ __global__ void __launch_bounds__(GNT, gfused_minb<P>())
   const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref), s2 = shift_of<P>(7, ph.rho_ref);
   auto shift = [&](int a) { return a == 0 ? s0 : (a <= 6 ? s1 : s2); };
   const unsigned salt = (Prec<P>::dev && ph.sr) ? salt_of(ph) : 0u;
-  const long long plane_n = (long long)g.nx * g.ny;
+  const int plane_n = g.nx * g.ny;
 
   // copies of plane zplane(k) (own node into buffer k % 3, ring node into
   // ring buffer k % 2), one commit group per plane, empty past the run
   auto issue = [&](int k) {
     if constexpr (S::async) {
       if (k < np) {
-        const long long zo = plane_n * zplane(k);
+        const int zo = plane_n * zplane(k);
         if (act) {
           T* d = own + (size_t)(k % S::NBUF) * Q * GNT + tid;
 #pragma unroll
-          for (int a = 0; a < Q; ++a) cp_async<sizeof(T)>(d + a * GNT, src + (long long)a * N + zo + orow);
+          for (int a = 0; a < Q; ++a) cp_async<sizeof(T)>(d + a * GNT, src + (a * N + zo + orow));
         }
         if (ract) {
           T* d = rpop + (size_t)(k % 2) * Q * S::RPAD + tid;
 #pragma unroll
-          for (int a = 0; a < Q; ++a) cp_async<sizeof(T)>(d + a * S::RPAD, src + (long long)a * N + zo + rrow);
+          for (int a = 0; a < Q; ++a) cp_async<sizeof(T)>(d + a * S::RPAD, src + (a * N + zo + rrow));
         }
       }
       cp_async_commit();
@@ -184,9 +186,9 @@ __global__ void __launch_bounds__(GNT, gfused_minb<P>())
 #pragma unroll
         for (int a = 0; a < Q; ++a) f[a] = (C)o[a * GNT];
       } else {
-        const long long i = orow + plane_n * zk;
+        const int i = orow + plane_n * zk;
 #pragma unroll
-        for (int a = 0; a < Q; ++a) f[a] = Prec<P>::load(src + (long long)a * N + i, shift(a));
+        for (int a = 0; a < Q; ++a) f[a] = Prec<P>::load(src + (a * N + i), shift(a));
       }
       rho = rho_of<C>(f);
       nbad |= bad_rho(rho);
@@ -199,9 +201,9 @@ __global__ void __launch_bounds__(GNT, gfused_minb<P>())
 #pragma unroll
         for (int a = 0; a < Q; ++a) fr[a] = (C)o[a * S::RPAD];
       } else {
-        const long long i = rrow + plane_n * zk;
+        const int i = rrow + plane_n * zk;
 #pragma unroll
-        for (int a = 0; a < Q; ++a) fr[a] = Prec<P>::load(src + (long long)a * N + i, shift(a));
+        for (int a = 0; a < Q; ++a) fr[a] = Prec<P>::load(src + (a * N + i), shift(a));
       }
       const C rr = rho_of<C>(fr);
       nbad |= bad_rho(rr);
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(GNT, gfused_minb<P>())
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
         const int d = xs[1 + cx(a)] + g.nx * (yv[1 + cy(a)] + g.ny * zv[1 + cz(a)]);
-        store_pop<P>(ph, dst + (long long)a * N + d, fs[a], shift(a), seed, a);
+        store_pop<P>(ph, dst + (a * N + d), fs[a], shift(a), seed, a);
       }
     }
     // the buffers of plane k - 1 (own) and k (ring) are read out by this
