@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(GNT, gfused_minb<P>())
   const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x + 1 == g.nx ? 0 : x + 1;
   const int yv[3] = {y == 0 ? g.ny - 1 : y - 1, y, y + 1 == g.ny ? 0 : y + 1};
   const int xs[3] = {xm, x, xp};
+  const int yrow[3] = {g.nx * yv[0], g.nx * yv[1], g.nx * yv[2]};   // row offsets of y - 1, y, y + 1
 
   const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref), s2 = shift_of<P>(7, ph.rho_ref);
   auto shift = [&](int a) { return a == 0 ? s0 : (a <= 6 ? s1 : s2); };
@@ -238,9 +239,11 @@ __global__ void __launch_bounds__(GNT, gfused_minb<P>())
       }
       const int i = x + g.nx * (y + g.ny * z);
       const unsigned seed = (Prec<P>::dev && ph.sr) ? sr_seed(i, fs[0], salt) : 0u;
+      // destination offsets: x + row of y + plane of z, and a N
+      const int pz[3] = {plane_n * zv[0], plane_n * zv[1], plane_n * zv[2]};
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
-        const int d = xs[1 + cx(a)] + g.nx * (yv[1 + cy(a)] + g.ny * zv[1 + cz(a)]);
+        const int d = xs[1 + cx(a)] + yrow[1 + cy(a)] + pz[1 + cz(a)];
         store_pop<P>(ph, dst + (a * N + d), fs[a], shift(a), seed, a);
       }
     }
