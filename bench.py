@@ -628,22 +628,33 @@ def batch_sweep(args, torch, L, autotune, rho_l, rho_v, precision="f32"):
 
         ms_b, ok_b = timed(b.step)
         ms_s, ok_s = timed(b.step_sequential)
+        # the single-pass form as one persistent cooperative launch per
+        # benchmark step (10 lattice steps, grid barriers between them)
+        ms_p, ok_p = None, True
+        if tuned.get("fused"):
+            b.set_option("persistent", 1)
+            ms_p, ok_p = timed(b.step)
+            b.set_option("persistent", 0)
         autotune.apply_batch(b, other)
         ms_o, ok_o = timed(b.step)
     steps = args.steps * LBM_PER_STEP
     value = total * steps / (ms_b * 1e-3) / 1e9
     seq = total * steps / (ms_s * 1e-3) / 1e9
     oth = total * steps / (ms_o * 1e-3) / 1e9
+    pers = total * steps / (ms_p * 1e-3) / 1e9 if ms_p else None
     peak, _ = peaks()
     bpl = FUSED_BYTES_PER_LU[precision] if tuned.get("fused") else STEP_BYTES_PER_LU[precision]
     return {"value": round(value, 4), "unit": UNIT, "ms_per_step": round(ms_b / args.steps, 4),
             "step_form": "single-pass (one launch per step)" if tuned.get("fused") else "two-kernel",
             "sequential_value": round(seq, 4), "speedup_vs_sequential": round(value / seq, 3),
             "other_form_value": round(oth, 4), "other_form": other,
+            "persistent_value": round(pers, 4) if pers else None,
+            "persistent_form": "the same single-pass step, %d steps per cooperative launch of persistent blocks "
+                               "with grid barriers between the steps" % LBM_PER_STEP,
             "total_nodes": total, "precision": precision, "tuned": tuned,
             "bytes_per_lu": bpl, "hbm_frac_step_model": round(value * bpl / peak, 4),
             "hbm_frac_floor_160": round(value * 160 / peak, 4),
-            "numeric_ok_batched": ok_b and ok_o, "numeric_ok_sequential": ok_s,
+            "numeric_ok_batched": ok_b and ok_o and ok_p, "numeric_ok_sequential": ok_s,
             "sweep": "%d periodic ligaments, R0 in {8,12,16,20,24}, lambda/R0 in [4.5,12], eps=0.05, G=-6, "
                      "box lambda x 4R0 x 4R0, tau drawn in [0.6,1.0]" % len(sweep),
             "timed_tau_floor": floor,

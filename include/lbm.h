@@ -326,7 +326,15 @@ int lbm_batch_set_stream(lbm_batch b, void *stream);
  * of the tile and its one-node ring in shared memory, so the populations
  * are read once per step (Eqs. 2-6 as in lbm_step; instances of any size
  * up to 113 M nodes, larger ones take the two kernels); 0: a psi pass and a
- * collide-stream kernel per step), "fused_fz" (z planes
+ * collide-stream kernel per step), "persistent" (0/1, default 0: with the
+ * single-pass step, every lbm_batch_step call runs its n steps as one
+ * cooperative launch of persistent blocks - as many as the GPU holds at once,
+ * each taking several tiles and z runs per step - separated by grid-wide
+ * barriers; the same results as one launch per step, no graph; a barrier
+ * that waits more than 2 s gives up, the launch returns and lbm_batch_sync
+ * reports LBM_ERR_TIMEOUT with the state void), "persistent_stall_test" (a
+ * test hook of that failure path, in ms, 0..10: one block skips the first
+ * barrier and the others give up after this long), "fused_fz" (z planes
  * per block of the single-pass step, default 16), "graph" (0/1),
  * "stochastic_rounding" (0/1, as lbm_set_option), and for the two-kernel
  * step "occupancy" (2, 3, 4; default 2), "vector" (0/1, default 1:
@@ -346,7 +354,9 @@ int lbm_batch_step(lbm_batch b, int n);
 /* n steps, each instance with its own two launches per step (the plain
  * per-lattice path, for comparison). */
 int lbm_batch_step_sequential(lbm_batch b, int n);
-/* Waits; LBM_ERR_NUMERIC if a density of any instance went bad. */
+/* Waits; LBM_ERR_NUMERIC if a density of any instance went bad,
+ * LBM_ERR_TIMEOUT if a grid barrier of the persistent step gave up (the
+ * state is then void: re-initialise).  Clears the flag it reports. */
 int lbm_batch_sync(lbm_batch b);
 /* Canonical FP64 populations of instance k (19 * N_k doubles). */
 int lbm_batch_get_populations(lbm_batch b, int k, double *host);

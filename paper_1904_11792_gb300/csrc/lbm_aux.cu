@@ -717,12 +717,20 @@ cudaError_t droplets_t(int layout, const Geom& g, const Phys& ph, const void* f,
 
 }  // namespace
 
-// Stochastic-rounding step salt: set it, or advance it by one (after each
-// time step's collision).
-__global__ void salt_kernel(unsigned* salt, int set, unsigned value) { *salt = set ? value : *salt + 1u; }
+// Stochastic-rounding step salt: set it (mode 1), advance it by one (mode
+// 0, after each time step's collision) or by `value` (mode 2, after a launch
+// that ran `value` steps).
+__global__ void salt_kernel(unsigned* salt, int mode, unsigned value) {
+  *salt = mode == 1 ? value : *salt + (mode == 2 ? value : 1u);
+}
 
 cudaError_t launch_salt(unsigned* salt, bool set, unsigned value, cudaStream_t s) {
   salt_kernel<<<1, 1, 0, s>>>(salt, set ? 1 : 0, value);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_salt_add(unsigned* salt, unsigned n, cudaStream_t s) {
+  salt_kernel<<<1, 1, 0, s>>>(salt, 2, n);
   return cudaGetLastError();
 }
 

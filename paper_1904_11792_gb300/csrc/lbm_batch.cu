@@ -133,16 +133,65 @@ cudaError_t batch_launch_t(const BatchInst* d_inst, int count, int psi_blocks, i
 
 // The single-pass step's kernels may take more than 48 KB of dynamic shared
 // memory; set once per layout (on the current device, outside any capture).
+template <int P>
+cudaError_t batch_fused_prepare_p() {
+  cudaError_t e = cudaFuncSetAttribute(gfused_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)GShape<P>::smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gpersist_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)GShape<P>::smem);
+  return e;
+}
 cudaError_t batch_fused_prepare(int precision) {
   switch (precision) {
+    case LBM_F64: return batch_fused_prepare_p<LBM_F64>();
+    case LBM_F32: return batch_fused_prepare_p<LBM_F32>();
+    case LBM_F16DEV: return batch_fused_prepare_p<LBM_F16DEV>();
+    default: return batch_fused_prepare_p<LBM_BF16DEV>();
+  }
+}
+
+// nsteps single-pass steps of the whole batch as one cooperative launch of
+// persistent blocks (as many as fit on the GPU at once, at most one per work
+// item), grid barriers on *bar between the steps.
+template <int P>
+cudaError_t batch_persist_launch_p(const GInst* d_ginst, int count, int items, void* pool_f, int cur, int nsteps,
+                                   unsigned* bar, unsigned* tickets, int* flag, unsigned long long stall_ns,
+                                   cudaStream_t s) {
+  using T = typename Prec<P>::T;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gpersist_kernel<P>, GNT, GShape<P>::smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  const int grid = std::min(items, per_sm * sms);
+  e = cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tickets, 0, sizeof(unsigned) * (size_t)nsteps, s);
+  if (e != cudaSuccess) return e;
+  T* pf = (T*)pool_f;
+  void* args[] = {(void*)&d_ginst, (void*)&count, (void*)&pf, (void*)&cur, (void*)&nsteps,
+                  (void*)&items, (void*)&bar, (void*)&tickets, (void*)&flag, (void*)&stall_ns};
+  return cudaLaunchCooperativeKernel((const void*)gpersist_kernel<P>, dim3(grid), dim3(GNT), args,
+                                     GShape<P>::smem, s);
+}
+cudaError_t batch_persist_launch(int precision, const GInst* d_ginst, int count, int items, void* pool_f, int cur,
+                                 int nsteps, unsigned* bar, unsigned* tickets, int* flag,
+                                 unsigned long long stall_ns, cudaStream_t s) {
+  switch (precision) {
     case LBM_F64:
-      return cudaFuncSetAttribute(gfused_kernel<LBM_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)GShape<LBM_F64>::smem);
+      return batch_persist_launch_p<LBM_F64>(d_ginst, count, items, pool_f, cur, nsteps, bar, tickets, flag,
+                                             stall_ns, s);
     case LBM_F32:
-      return cudaFuncSetAttribute(gfused_kernel<LBM_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)GShape<LBM_F32>::smem);
+      return batch_persist_launch_p<LBM_F32>(d_ginst, count, items, pool_f, cur, nsteps, bar, tickets, flag,
+                                             stall_ns, s);
+    case LBM_F16DEV:
+      return batch_persist_launch_p<LBM_F16DEV>(d_ginst, count, items, pool_f, cur, nsteps, bar, tickets, flag,
+                                                stall_ns, s);
     default:
-      return cudaSuccess;   // 2-byte storage: the psi ring only, under 48 KB
+      return batch_persist_launch_p<LBM_BF16DEV>(d_ginst, count, items, pool_f, cur, nsteps, bar, tickets, flag,
+                                                 stall_ns, s);
   }
 }
 
@@ -199,6 +248,10 @@ struct lbm_batch_ctx {
   int gblocks = 0;
   bool fused = true;               // option "fused": the single-pass step
   int gfz = 16;                    // its z run length (option "fused_fz")
+  bool persistent = false;         // option "persistent": n steps per cooperative launch
+  unsigned* d_tickets = nullptr;   // its per-step work-item counters
+  int tickets_n = 0;
+  double persist_stall_ms = 0.0;   // option "persistent_stall_test" (test hook)
   void* pool_f = nullptr;
   size_t pool_f_bytes = 0;
   void* pool_psi = nullptr;
@@ -376,6 +429,7 @@ void lbm_batch_destroy(lbm_batch b) {
   cudaFree(b->pool_f);
   cudaFree(b->pool_psi);
   cudaFree(b->d_flag);
+  cudaFree(b->d_tickets);
   cudaFree(b->d_small);
   cudaFree(b->d_scratch);
   cudaFree(b->d_labels);
@@ -444,9 +498,11 @@ lbm_batch lbm_batch_create(const lbm_instance* inst, int count, int precision, i
   if (err == cudaSuccess) err = cudaMalloc(&b->d_ginst, sizeof(GInst) * count);
   if (err == cudaSuccess) err = cudaMalloc(&b->pool_f, b->pool_f_bytes);
   if (err == cudaSuccess) err = cudaMalloc(&b->pool_psi, b->pool_psi_bytes);
-  if (err == cudaSuccess) err = cudaMalloc(&b->d_flag, sizeof(int) * 4);
+  // d_flag[0] the numeric flag, [2] the stochastic-rounding salt, [4] the
+  // grid-barrier counter of the persistent step
+  if (err == cudaSuccess) err = cudaMalloc(&b->d_flag, sizeof(int) * 8);
   if (err == cudaSuccess) err = cudaMalloc(&b->d_small, sizeof(double) * 64);
-  if (err == cudaSuccess) err = cudaMemsetAsync(b->d_flag, 0, sizeof(int) * 4, b->stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(b->d_flag, 0, sizeof(int) * 8, b->stream);
   // d_flag[2] is the stochastic-rounding step salt of every instance
   if (err == cudaSuccess)
     for (auto& I : b->inst) I.ph.salt = (const unsigned*)(b->d_flag + 2);
@@ -492,6 +548,15 @@ int lbm_batch_set_option(lbm_batch b, const char* key, double v) {
   if (k == "fused") {
     b->fused = v != 0.0;
     drop_graphs(b);
+    return LBM_OK;
+  }
+  if (k == "persistent") {
+    b->persistent = v != 0.0;
+    return LBM_OK;
+  }
+  if (k == "persistent_stall_test") {
+    if (!(v >= 0.0 && v <= 10.0)) return bfail(LBM_ERR_ARG, "persistent_stall_test must be in 0..10 ms");
+    b->persist_stall_ms = v;
     return LBM_OK;
   }
   if (k == "fused_fz") {
@@ -551,6 +616,22 @@ int lbm_batch_init(lbm_batch b) {
 int lbm_batch_step(lbm_batch b, int n) {
   if (!b || n < 0) return bfail(LBM_ERR_ARG, "null batch or negative step count");
   if (!b->initialized) return bfail(LBM_ERR_STATE, "batch not initialised");
+  while (n > 0 && b->persistent && b->fused && 19LL * b->max_nodes <= 0x7fffffffLL) {
+    // up to kPersistSteps steps in one cooperative launch of persistent blocks
+    constexpr int kPersistSteps = 1024;
+    const int m = std::min(n, kPersistSteps);
+    if (!b->d_tickets) {
+      BCK(cudaMalloc(&b->d_tickets, sizeof(unsigned) * kPersistSteps));
+      b->tickets_n = kPersistSteps;
+    }
+    const unsigned long long stall_ns = (unsigned long long)(b->persist_stall_ms * 1e6);
+    BCK(batch_persist_launch(b->precision, b->d_ginst, b->count, b->gblocks, b->pool_f, b->cur, m,
+                             (unsigned*)(b->d_flag + 4), b->d_tickets, b->d_flag, stall_ns, b->stream));
+    if (batch_sr(b)) BCK(launch_salt_add((unsigned*)(b->d_flag + 2), (unsigned)m, b->stream));
+    b->cur ^= m & 1;
+    b->step += m;
+    n -= m;
+  }
   while (n > 0) {
     if (b->use_graph && n >= 2) {
       if (!b->graph[b->cur]) {
@@ -600,6 +681,7 @@ int lbm_batch_sync(lbm_batch b) {
   if (flag) {
     BCK(cudaMemsetAsync(b->d_flag, 0, sizeof(int), b->stream));
     BCK(cudaStreamSynchronize(b->stream));
+    if (flag & 2) return bfail(LBM_ERR_TIMEOUT, "a grid barrier of the persistent step gave up; the state is void");
     return bfail(LBM_ERR_NUMERIC, "a density became non-positive or non-finite");
   }
   return LBM_OK;

@@ -87,18 +87,21 @@ __device__ __forceinline__ int gfind(const GInst* __restrict__ inst, int count, 
   return lo;
 }
 
+// One work item of the step: block index blk of the tile table (a tile and
+// z run of one instance), A-B arrays cur -> cur ^ 1, stochastic-rounding salt
+// `salt` (read by the caller), shared memory gsm of GShape<P>::smem bytes.
 template <int P>
-__global__ void __launch_bounds__(GNT, gfused_minb<P>())
-    gfused_kernel(const GInst* __restrict__ inst, int count, typename Prec<P>::T* pool_f, int cur, int* flag) {
+__device__ __forceinline__ void gfused_item(const GInst* __restrict__ inst, int count,
+                                            typename Prec<P>::T* pool_f, int cur, int* flag, int blk,
+                                            unsigned salt, unsigned char* gsm) {
   using T = typename Prec<P>::T;
   using C = typename Prec<P>::C;
   using S = GShape<P>;
-  extern __shared__ __align__(16) unsigned char gsm[];
   T* own = reinterpret_cast<T*>(gsm);                                  // [NBUF][Q][GNT]
   T* rpop = reinterpret_cast<T*>(gsm + S::own_bytes);                  // [2][Q][RPAD]
   C(*ring)[GRY][GRX] = reinterpret_cast<C(*)[GRY][GRX]>(gsm + S::own_bytes + S::ring_pop_bytes);
 
-  const GInst& I = inst[gfind(inst, count, blockIdx.x)];
+  const GInst& I = inst[gfind(inst, count, blk)];
   const Geom g = I.g;
   const Phys ph = I.ph;
   // element offsets within an instance are 32-bit: 19 N < 2^31 (the host
@@ -109,7 +112,7 @@ __global__ void __launch_bounds__(GNT, gfused_minb<P>())
   // block -> (z run, tile x, tile y), the run fastest: the runs of a tile and
   // the tiles of a row of tiles are launched together and share planes and
   // ring rows in L2
-  const int u = blockIdx.x - I.block0;
+  const int u = blk - I.block0;
   const int chunk = u % I.nchunks, xy = u / I.nchunks;
   const int x0 = (xy % I.ntx) * GX, y0 = (xy / I.ntx) * GY;
   const int w = min(GX, g.nx - x0), h = min(GY, g.ny - y0);   // tile extent (cut at the edge)
@@ -147,7 +150,6 @@ __global__ void __launch_bounds__(GNT, gfused_minb<P>())
 
   const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref), s2 = shift_of<P>(7, ph.rho_ref);
   auto shift = [&](int a) { return a == 0 ? s0 : (a <= 6 ? s1 : s2); };
-  const unsigned salt = (Prec<P>::dev && ph.sr) ? salt_of(ph) : 0u;
   const int plane_n = g.nx * g.ny;
 
   // copies of plane zplane(k) (own node into buffer k % 3, ring node into
@@ -257,6 +259,98 @@ __global__ void __launch_bounds__(GNT, gfused_minb<P>())
     }
   }
   raise_flag(nbad, flag);
+}
+
+// The step of the whole batch: one block per work item.
+template <int P>
+__global__ void __launch_bounds__(GNT, gfused_minb<P>())
+    gfused_kernel(const GInst* __restrict__ inst, int count, typename Prec<P>::T* pool_f, int cur, int* flag) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  const Phys& ph = inst[0].ph;   // every instance shares the salt word
+  const unsigned salt = (Prec<P>::dev && ph.sr) ? salt_of(ph) : 0u;
+  gfused_item<P>(inst, count, pool_f, cur, flag, blockIdx.x, salt, gsm);
+}
+
+// Grid-wide barrier of a cooperative launch: counter ctr (zero before the
+// launch) reaches `target` = gridDim.x per barrier passed.  Thread 0 of each
+// block releases the block's writes, arrives and polls with acquire loads,
+// for at most kGridWaitNs of wall time (then it raises bit 2 of the flag and
+// the barrier reports failure); the block barrier and an acquire fence in
+// every thread then order all later loads of the block, through L1
+// included, after every block's writes before the barrier.
+constexpr unsigned long long kGridWaitNs = 2000000000ull;
+__device__ __forceinline__ unsigned long long gsm_global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int* flag,
+                                             unsigned long long limit_ns) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    atomicAdd(ctr, 1u);
+    const unsigned long long t0 = gsm_global_ns();
+    for (;;) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+      if (v >= target) break;
+      if (gsm_global_ns() - t0 > limit_ns) {
+        atomicOr(flag, 2);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  ok = __syncthreads_and(ok);
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  return ok != 0;
+}
+
+// nsteps steps of the whole batch in one cooperative launch of persistent
+// blocks (each takes the next work item of the step until none is left:
+// tickets[s], zero before the launch, hands them out), the steps separated
+// by grid barriers on *bar.  Step s runs
+// arrays cur0 ^ (s & 1) -> the other with salt salt0 + s, salt0 the value of
+// the salt word at the launch (the host advances the word by nsteps after
+// it), so the results are those of nsteps launches of gfused_kernel.  A block
+// returns at once if bit 2 of the flag is set (a barrier of this launch or
+// an earlier one gave up).  stall_test_ns > 0 (a test hook of the failure
+// path): block 0 does not arrive at the first barrier, every other block
+// gives up on it after stall_test_ns.
+template <int P>
+__global__ void __launch_bounds__(GNT, gfused_minb<P>())
+    gpersist_kernel(const GInst* __restrict__ inst, int count, typename Prec<P>::T* pool_f, int cur0, int nsteps,
+                    int items, unsigned* bar, unsigned* tickets, int* flag, unsigned long long stall_test_ns) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  __shared__ int s_item;
+  const Phys& ph = inst[0].ph;
+  unsigned salt0 = 0u;
+  if (Prec<P>::dev && ph.sr) salt0 = *(const volatile unsigned*)ph.salt;
+  const unsigned long long limit = stall_test_ns ? stall_test_ns : kGridWaitNs;
+  for (int s = 0; s < nsteps; ++s) {
+    // one read of the flag for the whole block: every thread returns or none
+    if (__syncthreads_or(threadIdx.x == 0 && (*(volatile int*)flag & 2) != 0)) return;
+    const int cur = cur0 ^ (s & 1);
+    // work items in launch order, each to the next block that asks
+    // (tickets[s] counts the items handed out in step s; asking for the next
+    // one while working on the current one was 7 % slower: a block then holds
+    // an item that idle blocks could take at the end of the step)
+    for (;;) {
+      if (threadIdx.x == 0) s_item = (int)atomicAdd(tickets + s, 1u);
+      __syncthreads();
+      const int w = s_item;
+      if (w >= items) break;
+      gfused_item<P>(inst, count, pool_f, cur, flag, w, salt0 + (unsigned)s, gsm);
+      __syncthreads();   // the item's shared memory and s_item are read out before the next item
+    }
+    if (s + 1 < nsteps) {
+      if (stall_test_ns && s == 0 && blockIdx.x == 0) return;
+      if (!grid_barrier(bar, (unsigned)(s + 1) * gridDim.x, flag, limit)) return;
+    }
+  }
 }
 
 }  // namespace lbm

@@ -116,6 +116,8 @@ cudaError_t launch_diagnostics(int precision, int layout, const Geom& g, const P
 
 // Stochastic-rounding step salt (Phys::salt): set to value, or advance by one.
 cudaError_t launch_salt(unsigned* salt, bool set, unsigned value, cudaStream_t s);
+// Advances the salt word by n (after a launch that ran n steps).
+cudaError_t launch_salt_add(unsigned* salt, unsigned n, cudaStream_t s);
 
 // Second and third stage of the diagnostics reduction from partials
 // slices[row_blocks][nx][2] and blocks[nblocks][DIAG_NG] (slice_tot: 2 nx

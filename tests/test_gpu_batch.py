@@ -141,3 +141,59 @@ def test_fused_batch_equals_two_kernel_batch(L, precision):
     for r in res[1:]:
         for k, (a, c) in enumerate(zip(res[0], r)):
             np.testing.assert_array_equal(a, c, err_msg=str(SHAPES[k]))
+
+
+# The persistent form (option persistent: all n steps of a call in one
+# cooperative launch, grid barriers between the steps) against one launch
+# per step, bitwise: every precision (the stochastic-rounding salt advances
+# the same), the instance shapes above, odd step counts and calls that
+# continue one another, and fewer persistent blocks than work items (each
+# block takes several tiles and z runs per step).
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16dev", "bf16dev"])
+def test_persistent_batch_equals_per_step_launches(L, precision):
+    insts = []
+    for k, (nx, ny, nz) in enumerate(SHAPES + ((130, 64, 96),)):
+        R0 = max(1.0, min(ny, nz) / 4.0)
+        insts.append(dict(nx=nx, ny=ny, nz=nz, tau=0.8 + 0.05 * k, G=-5.5, R0=R0, lam=float(nx), eps=0.1,
+                          phase=0.3 * k, rho_l=2.5, rho_v=0.15, width=2.0))
+    res = []
+    for persistent in (0, 1):
+        with L.Batch(insts, precision=precision) as b:
+            b.set_option("persistent", persistent)
+            b.set_option("fused_fz", 4)
+            b.init()
+            b.step(1)
+            b.step(5)
+            b.step(6)
+            b.sync()
+            res.append([b.populations(k) for k in range(len(insts))])
+    for k in range(len(insts)):
+        np.testing.assert_array_equal(res[1][k], res[0][k])
+
+
+# The failure path of the persistent form's grid barrier, without a fault: a
+# test hook keeps one block from arriving at the first barrier; every other
+# block gives up on it after 5 ms, raises the timeout bit and returns.  The
+# host reads LBM_ERR_TIMEOUT, and the batch steps correctly afterwards.
+def test_persistent_batch_barrier_timeout(L):
+    insts = [dict(nx=nx, ny=ny, nz=nz, tau=0.9, G=-5.5, R0=max(1.0, min(ny, nz) / 4.0), lam=float(nx), eps=0.1,
+                  phase=0.0, rho_l=2.5, rho_v=0.15, width=2.0) for nx, ny, nz in SHAPES]
+    with L.Batch(insts) as b:
+        b.set_option("persistent", 1)
+        b.set_option("persistent_stall_test", 5.0)
+        b.init()
+        b.step(3)
+        with pytest.raises(L.LbmError) as ei:
+            b.sync()
+        assert ei.value.status == L.LBM_ERR_TIMEOUT
+        b.set_option("persistent_stall_test", 0)
+        b.init()
+        b.step(4)
+        b.sync()
+        got = [b.populations(k) for k in range(len(insts))]
+    with L.Batch(insts) as b:
+        b.init()
+        b.step(4)
+        want = [b.populations(k) for k in range(len(insts))]
+    for g, w in zip(got, want):
+        np.testing.assert_array_equal(g, w)
