@@ -597,15 +597,17 @@ def batch_sweep(args, torch, L, autotune, rho_l, rho_v, precision="f32"):
     with L.Batch(stable, precision=precision) as b:
         b.init()
         if args.no_tune:
-            tuned = dict(fused=1, fused_fz=16, block=[0, 0, 0], occupancy=0)
+            tuned = dict(fused=args.batch_fused, fused_fz=16, block=[0, 0, 0], occupancy=0)
+            per_elem = dict(fused=1, fused_fz=16, block=[0, 0, 0], occupancy=0)
             other = dict(fused=0, fused_fz=0, block=[128, 1, 1], occupancy=3)
         else:
             tuned = autotune.tune_batch(b, blocks=((256, 1, 1), (128, 1, 1)), occupancies=(2, 3, 4), steps=10)
-            # the other step form, for the record: the best two-kernel shape
-            # when the single-pass form won, else the single-pass form
+            # the other step forms, for the record: the per-element single
+            # pass (form 1, which the persistent launch uses) and the best
+            # two-kernel shape
+            per_elem = autotune.tune_batch(b, blocks=(), occupancies=(), steps=10, fused_forms=(1,))
             other = autotune.tune_batch(b, blocks=((256, 1, 1), (128, 1, 1)), occupancies=(2, 3, 4), steps=10,
-                                        fused_runs=()) if tuned.get("fused") else \
-                autotune.tune_batch(b, blocks=(), occupancies=(), steps=10)
+                                        fused_runs=())
         autotune.apply_batch(b, tuned)
 
         def timed(fn):
@@ -628,33 +630,35 @@ def batch_sweep(args, torch, L, autotune, rho_l, rho_v, precision="f32"):
 
         ms_b, ok_b = timed(b.step)
         ms_s, ok_s = timed(b.step_sequential)
-        # the single-pass form as one persistent cooperative launch per
-        # benchmark step (10 lattice steps, grid barriers between them)
-        ms_p, ok_p = None, True
-        if tuned.get("fused"):
-            b.set_option("persistent", 1)
-            ms_p, ok_p = timed(b.step)
-            b.set_option("persistent", 0)
+        # the per-element single pass, one launch per step and as one
+        # persistent cooperative launch per benchmark step (10 lattice
+        # steps, grid barriers between them)
+        autotune.apply_batch(b, per_elem)
+        ms_e, ok_e = timed(b.step)
+        b.set_option("persistent", 1)
+        ms_p, ok_p = timed(b.step)
+        b.set_option("persistent", 0)
         autotune.apply_batch(b, other)
         ms_o, ok_o = timed(b.step)
     steps = args.steps * LBM_PER_STEP
-    value = total * steps / (ms_b * 1e-3) / 1e9
-    seq = total * steps / (ms_s * 1e-3) / 1e9
-    oth = total * steps / (ms_o * 1e-3) / 1e9
-    pers = total * steps / (ms_p * 1e-3) / 1e9 if ms_p else None
+    glups = lambda ms: total * steps / (ms * 1e-3) / 1e9
+    value, seq, oth, elem, pers = glups(ms_b), glups(ms_s), glups(ms_o), glups(ms_e), glups(ms_p)
     peak, _ = peaks()
     bpl = FUSED_BYTES_PER_LU[precision] if tuned.get("fused") else STEP_BYTES_PER_LU[precision]
+    forms = {0: "two-kernel", 1: "single-pass, per-element copies (one launch per step)",
+             2: "single-pass, TMA on padded rows (one launch per step)"}
     return {"value": round(value, 4), "unit": UNIT, "ms_per_step": round(ms_b / args.steps, 4),
-            "step_form": "single-pass (one launch per step)" if tuned.get("fused") else "two-kernel",
+            "step_form": forms[int(tuned.get("fused", 0))],
             "sequential_value": round(seq, 4), "speedup_vs_sequential": round(value / seq, 3),
             "other_form_value": round(oth, 4), "other_form": other,
-            "persistent_value": round(pers, 4) if pers else None,
-            "persistent_form": "the same single-pass step, %d steps per cooperative launch of persistent blocks "
-                               "with grid barriers between the steps" % LBM_PER_STEP,
+            "per_element_value": round(elem, 4), "per_element_form": per_elem,
+            "persistent_value": round(pers, 4),
+            "persistent_form": "the per-element single pass, %d steps per cooperative launch of persistent "
+                               "blocks with grid barriers between the steps" % LBM_PER_STEP,
             "total_nodes": total, "precision": precision, "tuned": tuned,
             "bytes_per_lu": bpl, "hbm_frac_step_model": round(value * bpl / peak, 4),
             "hbm_frac_floor_160": round(value * 160 / peak, 4),
-            "numeric_ok_batched": ok_b and ok_o and ok_p, "numeric_ok_sequential": ok_s,
+            "numeric_ok_batched": ok_b and ok_o and ok_p and ok_e, "numeric_ok_sequential": ok_s,
             "sweep": "%d periodic ligaments, R0 in {8,12,16,20,24}, lambda/R0 in [4.5,12], eps=0.05, G=-6, "
                      "box lambda x 4R0 x 4R0, tau drawn in [0.6,1.0]" % len(sweep),
             "timed_tau_floor": floor,
@@ -713,6 +717,9 @@ def main():
                     help="skip the end-to-end and CPU-baseline legs (profiling runs)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP16/BF16/AA/batched comparisons (profiling runs)")
+    ap.add_argument("--batch-fused", type=int, choices=(0, 1, 2), default=2,
+                    help="with --no-tune: the batched step form timed first (2: TMA single pass on padded rows, "
+                         "1: per-element single pass, 0: two kernels)")
     ap.add_argument("--batch-size", type=int, default=48,
                     help="batch48: the first K instances of the sweep (profiling runs on a smaller batch)")
     args = ap.parse_args()

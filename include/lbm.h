@@ -320,14 +320,20 @@ lbm_batch lbm_batch_create(const lbm_instance *inst, int count, int precision, i
 void lbm_batch_destroy(lbm_batch b);
 const char *lbm_batch_last_error(void);
 int lbm_batch_set_stream(lbm_batch b, void *stream);
-/* "fused" (0/1, default 1: every step of the whole batch is one
- * single-pass kernel - blocks own 32 x 8 tiles of an instance's x-y plane,
- * cut short at its edges, march through a run of z planes and compute psi
- * of the tile and its one-node ring in shared memory, so the populations
- * are read once per step (Eqs. 2-6 as in lbm_step; instances of any size
- * up to 113 M nodes, larger ones take the two kernels); 0: a psi pass and a
- * collide-stream kernel per step), "persistent" (0/1, default 0: with the
- * single-pass step, every lbm_batch_step call runs its n steps as one
+/* "fused" (0, 1 or 2; default 2: every step of the whole batch is one
+ * single-pass kernel - blocks own tiles of an instance's x-y plane, cut
+ * short at its edges, march through a run of z planes and compute psi of
+ * the tile and its one-node ring in shared memory, so the populations are
+ * read once per step (Eqs. 2-6 as in lbm_step).  2: the TMA-staged step of
+ * lbm_step on 64 x 4 (FP32) or 64 x 8 (2-byte) tiles, for which the batch
+ * keeps a second pool with every row padded to a 16-byte multiple and moves
+ * the state there and back by 2-D copies when the step form changes or
+ * another call reads it; FP64 and instances whose padded planes pass 2^31
+ * elements take form 1.  1: blocks of 32 x 8 nodes, one per thread, copying
+ * the populations element by element (instances up to 113 M nodes, larger
+ * ones take the two kernels).  0: a psi pass and a collide-stream kernel per
+ * step), "persistent" (0/1, default 0: with the
+ * single-pass step of form 1, every lbm_batch_step call runs its n steps as one
  * cooperative launch of persistent blocks - as many as the GPU holds at once,
  * each taking several tiles and z runs per step - separated by grid-wide
  * barriers; the same results as one launch per step, no graph; a barrier

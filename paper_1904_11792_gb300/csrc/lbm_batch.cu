@@ -248,6 +248,16 @@ struct lbm_batch_ctx {
   int gblocks = 0;
   bool fused = true;               // option "fused": the single-pass step
   int gfz = 16;                    // its z run length (option "fused_fz")
+  bool tma = true;                 // option "fused" = 2 (the default): the single pass on padded rows (TMA)
+  // its own pool, rows padded to 16 bytes, which holds the state while that
+  // form steps (the state moves between the pools by 2-D copies)
+  void* pool_p = nullptr;
+  std::vector<long long> off_p;
+  std::vector<int> px;
+  void* d_ttable = nullptr;        // its tensor maps and block table
+  int tblocks = 0;
+  bool ttable_ok = false;
+  bool padded = false;             // the current state lives in pool_p
   bool persistent = false;         // option "persistent": n steps per cooperative launch
   unsigned* d_tickets = nullptr;   // its per-step work-item counters
   int tickets_n = 0;
@@ -331,6 +341,7 @@ int layout_tiles(lbm_batch_ctx* b) {
   }
   if (gblocks > 0x7fffffffLL) return bfail(LBM_ERR_ARG, "batch too large for one grid");
   b->gblocks = (int)gblocks;
+  b->ttable_ok = false;
   BCK(batch_fused_prepare(b->precision));
   BCK(cudaMemcpyAsync(b->d_ginst, gi.data(), sizeof(GInst) * b->count, cudaMemcpyHostToDevice, b->stream));
   BCK(cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(BatchInst) * b->count, cudaMemcpyHostToDevice,
@@ -338,6 +349,73 @@ int layout_tiles(lbm_batch_ctx* b) {
   BCK(cudaStreamSynchronize(b->stream));
   drop_graphs(b);
   return LBM_OK;
+}
+
+// The single pass on padded rows applies to 4- and 2-byte storage whose
+// padded instances keep 32-bit in-plane offsets.
+bool tma_applicable(const lbm_batch_ctx* b) {
+  if (b->precision == LBM_F64) return false;
+  const int al = batch_tma_row_align(b->precision);
+  for (const auto& I : b->inst)
+    if ((long long)((I.g.nx + al - 1) / al * al) * I.g.ny * I.g.nz > 0x7fffffffLL) return false;
+  return true;
+}
+
+bool tma_form(const lbm_batch_ctx* b) { return b->fused && b->tma && tma_applicable(b); }
+
+// Copies the current array of every instance between the pools.
+int convert_state(lbm_batch_ctx* b, bool to_padded) {
+  const size_t e = elem_size(b->precision);
+  for (int k = 0; k < b->count; ++k) {
+    const BatchInst& I = b->inst[k];
+    const size_t w = (size_t)I.g.nx * e, rows = (size_t)Q * I.g.ny * I.g.nz;
+    char* c = (char*)b->pool_f + (size_t)(I.off_f + (long long)b->cur * Q * I.g.N) * e;
+    char* p = (char*)b->pool_p +
+              (size_t)(b->off_p[k] + (long long)b->cur * Q * b->px[k] * I.g.ny * I.g.nz) * e;
+    const size_t pp = (size_t)b->px[k] * e;
+    if (to_padded)
+      BCK(cudaMemcpy2DAsync(p, pp, c, w, w, rows, cudaMemcpyDeviceToDevice, b->stream));
+    else
+      BCK(cudaMemcpy2DAsync(c, w, p, pp, w, rows, cudaMemcpyDeviceToDevice, b->stream));
+  }
+  b->padded = to_padded;
+  return LBM_OK;
+}
+
+// The state in the unpadded pool (every path but the padded single pass).
+int ensure_contig(lbm_batch_ctx* b) { return b->padded ? convert_state(b, false) : LBM_OK; }
+
+// The padded pool, its tensor maps and block table, and the state in it.
+int ensure_padded(lbm_batch_ctx* b) {
+  const size_t e = elem_size(b->precision);
+  if (!b->pool_p) {
+    const int al = batch_tma_row_align(b->precision);
+    long long off = 0;
+    b->off_p.resize(b->count);
+    b->px.resize(b->count);
+    for (int k = 0; k < b->count; ++k) {
+      const Geom& g = b->inst[k].g;
+      b->px[k] = (g.nx + al - 1) / al * al;
+      b->off_p[k] = off;
+      off += 2LL * Q * b->px[k] * g.ny * g.nz;   // a multiple of al: every instance starts on 16 bytes
+    }
+    BCK(cudaMalloc(&b->pool_p, (size_t)off * e));
+    BCK(cudaMalloc(&b->d_ttable, batch_tma_table_bytes(b->count)));
+    b->ttable_ok = false;
+  }
+  if (!b->ttable_ok) {
+    std::vector<BatchTmaInst> t(b->count);
+    for (int k = 0; k < b->count; ++k) {
+      t[k].g = b->inst[k].g;
+      t[k].ph = b->inst[k].ph;
+      t[k].off_f = b->off_p[k];
+      t[k].px = b->px[k];
+    }
+    BCK(batch_tma_build(b->precision, t.data(), b->count, b->gfz, b->pool_p, b->d_ttable, &b->tblocks,
+                        b->stream));
+    b->ttable_ok = true;
+  }
+  return b->padded ? LBM_OK : convert_state(b, true);
 }
 
 bool batch_sr(const lbm_batch_ctx* b) {
@@ -348,7 +426,9 @@ int enqueue_batch_step(lbm_batch_ctx* b, cudaStream_t s, int cur) {
   // the single-pass kernel addresses an instance's populations by 32-bit
   // offsets: instances of 113 M nodes or more take the two kernels
   const bool fused_fits = 19LL * b->max_nodes <= 0x7fffffffLL;
-  if (b->fused && fused_fits)
+  if (tma_form(b))
+    BCK(batch_tma_launch(b->precision, b->d_ttable, b->count, b->tblocks, b->pool_p, cur, b->d_flag, s));
+  else if (b->fused && fused_fits)
     BCK(batch_fused_launch(b->precision, b->d_ginst, b->count, b->gblocks, b->pool_f, cur, b->d_flag, s));
   else
     BCK(batch_launch(b->precision, b->d_inst, b->count, b->psi_blocks, b->tiles, b->pool_f, cur, b->pool_psi,
@@ -430,6 +510,8 @@ void lbm_batch_destroy(lbm_batch b) {
   cudaFree(b->pool_psi);
   cudaFree(b->d_flag);
   cudaFree(b->d_tickets);
+  cudaFree(b->pool_p);
+  cudaFree(b->d_ttable);
   cudaFree(b->d_small);
   cudaFree(b->d_scratch);
   cudaFree(b->d_labels);
@@ -546,7 +628,9 @@ int lbm_batch_set_option(lbm_batch b, const char* key, double v) {
     return layout_tiles(b);
   }
   if (k == "fused") {
+    if (v != 0.0 && v != 1.0 && v != 2.0) return bfail(LBM_ERR_ARG, "fused must be 0, 1 or 2");
     b->fused = v != 0.0;
+    b->tma = v == 2.0;
     drop_graphs(b);
     return LBM_OK;
   }
@@ -601,6 +685,7 @@ int lbm_batch_init(lbm_batch b) {
   if (!b) return bfail(LBM_ERR_ARG, "null batch");
   b->cur = 0;
   b->step = 0;
+  b->padded = false;   // the initial condition goes to the unpadded pool
   BCK(launch_salt((unsigned*)(b->d_flag + 2), true, 0u, b->stream));
   for (int k = 0; k < b->count; ++k) {
     const lbm_instance& s = b->spec[k];
@@ -616,7 +701,11 @@ int lbm_batch_init(lbm_batch b) {
 int lbm_batch_step(lbm_batch b, int n) {
   if (!b || n < 0) return bfail(LBM_ERR_ARG, "null batch or negative step count");
   if (!b->initialized) return bfail(LBM_ERR_STATE, "batch not initialised");
-  while (n > 0 && b->persistent && b->fused && 19LL * b->max_nodes <= 0x7fffffffLL) {
+  if (n > 0) {
+    const int rc = tma_form(b) ? ensure_padded(b) : ensure_contig(b);
+    if (rc) return rc;
+  }
+  while (n > 0 && b->persistent && b->fused && !tma_form(b) && 19LL * b->max_nodes <= 0x7fffffffLL) {
     // up to kPersistSteps steps in one cooperative launch of persistent blocks
     constexpr int kPersistSteps = 1024;
     const int m = std::min(n, kPersistSteps);
@@ -655,6 +744,7 @@ int lbm_batch_step(lbm_batch b, int n) {
 int lbm_batch_step_sequential(lbm_batch b, int n) {
   if (!b || n < 0) return bfail(LBM_ERR_ARG, "null batch or negative step count");
   if (!b->initialized) return bfail(LBM_ERR_STATE, "batch not initialised");
+  if (int rc = ensure_contig(b)) return rc;
   const size_t e = elem_size(b->precision);
   for (int s = 0; s < n; ++s) {
     for (int k = 0; k < b->count; ++k) {
@@ -689,6 +779,7 @@ int lbm_batch_sync(lbm_batch b) {
 
 int lbm_batch_get_populations(lbm_batch b, int k, double* host) {
   if (!b || !host || k < 0 || k >= b->count) return bfail(LBM_ERR_ARG, "bad batch, instance or buffer");
+  if (int rc = ensure_contig(b)) return rc;
   if (!b->d_plane) BCK(cudaMalloc(&b->d_plane, sizeof(double) * b->max_nodes));
   View v = view_of(b, k);
   for (int a = 0; a < Q; ++a) {
@@ -702,6 +793,7 @@ int lbm_batch_get_populations(lbm_batch b, int k, double* host) {
 
 int lbm_batch_diagnostics(lbm_batch b, int k, lbm_diag* out, int want_ccl) {
   if (!b || !out || k < 0 || k >= b->count) return bfail(LBM_ERR_ARG, "bad batch, instance or output");
+  if (int rc = ensure_contig(b)) return rc;
   View v = view_of(b, k);
   const size_t need = diag_scratch_doubles(v.g);
   if (need > b->scratch_doubles) {

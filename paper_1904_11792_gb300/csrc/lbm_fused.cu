@@ -5,9 +5,11 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 #include "lbm_fused_kernel.cuh"
 
@@ -46,13 +48,15 @@ CUtensorMapDataType tma_type(int precision) {
   }
 }
 
-// The 4-D view [19][nz][ny][nx] of a population array with box (bx, by, 1, 19).
-cudaError_t make_map(CUtensorMap* tm, int precision, const Geom& g, const void* base, int bx, int by) {
+// The 4-D view [19][nz][ny][nx] of a population array with box (bx, by, 1, 19),
+// rows px elements apart (px = nx, or nx padded for the batched step).
+cudaError_t make_map(CUtensorMap* tm, int precision, const Geom& g, const void* base, int bx, int by, int px = 0) {
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   const size_t e = elem_size(precision);
+  const cuuint64_t p = px > 0 ? (cuuint64_t)px : (cuuint64_t)g.nx;
   const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)Q};
-  const cuuint64_t strides[3] = {(cuuint64_t)g.nx * e, (cuuint64_t)g.nx * g.ny * e, (cuuint64_t)g.N * e};
+  const cuuint64_t strides[3] = {p * e, p * g.ny * e, p * g.ny * g.nz * e};
   const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1u, (cuuint32_t)Q};
   const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
   const CUresult r = fn(tm, tma_type(precision), 4, const_cast<void*>(base), dims, strides, box, estr,
@@ -130,7 +134,8 @@ cudaError_t fused_device_info(int* slots_per_sm, int* sms) {
   std::lock_guard<std::mutex> lock(mu);
   if (!slots_of[dev]) {
     for (const void* k : {(const void*)fused_kernel<P, false, COLL_SRT>, (const void*)fused_kernel<P, true, COLL_SRT>,
-                          (const void*)fused_kernel<P, false, COLL_MRT>, (const void*)fused_kernel<P, true, COLL_MRT>})
+                          (const void*)fused_kernel<P, false, COLL_MRT>, (const void*)fused_kernel<P, true, COLL_MRT>,
+                          (const void*)bfused_kernel<P>})
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
     int n_sm = 0, slots = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -246,6 +251,100 @@ cudaError_t launch_fused(int precision, const Geom& g, const Phys& ph, const voi
     case LBM_BF16DEV: return fused_t<LBM_BF16DEV>(g, ph, src, dst, flag, fz, grp, diag, stall_ns, s);
   }
   return cudaErrorInvalidValue;
+}
+
+// ---- batched single-pass step on padded rows --------------------------------
+
+namespace {
+
+template <int P>
+cudaError_t batch_tma_build_t(const BatchTmaInst* in, int count, int fz_req, const void* pool, void* d_table,
+                              int* blocks_out, cudaStream_t s) {
+  using S = FusedShape<P>;
+  int slots_per_sm = 0, sms = 0;
+  cudaError_t e = fused_device_info<P>(&slots_per_sm, &sms);   // the kernels' shared-memory limit
+  if (e != cudaSuccess) return e;
+  const size_t es = elem_size(P);
+  const size_t inst_bytes = align128(sizeof(BTInst) * (size_t)count);
+  std::vector<unsigned char> host(inst_bytes + sizeof(Maps) * 2 * (size_t)count);
+  BTInst* ti = reinterpret_cast<BTInst*>(host.data());
+  Maps* tm = reinterpret_cast<Maps*>(host.data() + inst_bytes);
+  const Maps* d_maps = reinterpret_cast<const Maps*>((const unsigned char*)d_table + inst_bytes);
+  const int cw = 16 / (int)es;
+  long long blocks = 0;
+  for (int k = 0; k < count; ++k) {
+    const BatchTmaInst& b = in[k];
+    if (b.px % cw || b.off_f % cw || b.px < b.g.nx) return cudaErrorInvalidValue;
+    BTInst& t = ti[k];
+    std::memset(&t, 0, sizeof(t));
+    t.g = b.g;
+    t.ph = b.ph;
+    t.off_f = b.off_f;
+    t.px = b.px;
+    t.dstride = (long long)b.px * b.g.ny * b.g.nz;
+    t.maps = d_maps + 2 * k;
+    t.ntx = (b.g.nx + TX - 1) / TX;
+    const int nty = (b.g.ny + S::TY - 1) / S::TY;
+    t.fz = std::min(fz_req > 0 ? fz_req : 16, b.g.nz);
+    t.nchunks = (b.g.nz + t.fz - 1) / t.fz;
+    t.grp = t.nchunks;   // a tile's z runs one after another in the launch order
+    t.block0 = (int)blocks;
+    blocks += (long long)t.ntx * nty * t.nchunks;
+    for (int arr = 0; arr < 2; ++arr) {
+      const void* base = (const unsigned char*)pool + (size_t)(b.off_f + (long long)arr * Q * t.dstride) * es;
+      Maps& m = tm[2 * k + arr];
+      e = make_map(&m.interior, P, b.g, base, TX, S::TY, b.px);
+      if (e == cudaSuccess) e = make_map(&m.row, P, b.g, base, TX, 1, b.px);
+      if (e == cudaSuccess) e = make_map(&m.col, P, b.g, base, cw, S::TY, b.px);
+      if (e == cudaSuccess) e = make_map(&m.cor, P, b.g, base, cw, 1, b.px);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  *blocks_out = (int)blocks;
+  e = cudaMemcpyAsync(d_table, host.data(), host.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host table goes out of scope
+  return e;
+}
+
+}  // namespace
+
+size_t batch_tma_table_bytes(int count) {
+  return align128(sizeof(BTInst) * (size_t)count) + sizeof(Maps) * 2 * (size_t)count;
+}
+
+int batch_tma_row_align(int precision) { return 16 / (int)elem_size(precision); }
+
+cudaError_t batch_tma_build(int precision, const BatchTmaInst* insts, int count, int fz, const void* pool,
+                            void* d_table, int* blocks, cudaStream_t s) {
+  switch (precision) {
+    case LBM_F32: return batch_tma_build_t<LBM_F32>(insts, count, fz, pool, d_table, blocks, s);
+    case LBM_F16DEV: return batch_tma_build_t<LBM_F16DEV>(insts, count, fz, pool, d_table, blocks, s);
+    case LBM_BF16DEV: return batch_tma_build_t<LBM_BF16DEV>(insts, count, fz, pool, d_table, blocks, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t batch_tma_launch(int precision, const void* d_table, int count, int blocks, void* pool, int cur,
+                             int* flag, cudaStream_t s) {
+  const BTInst* t = reinterpret_cast<const BTInst*>(d_table);
+  switch (precision) {
+    case LBM_F32:
+      bfused_kernel<LBM_F32><<<blocks, FusedShape<LBM_F32>::NT, FusedShape<LBM_F32>::smem, s>>>(t, count,
+                                                                                             (float*)pool, cur, flag);
+      break;
+    case LBM_F16DEV:
+      bfused_kernel<LBM_F16DEV><<<blocks, FusedShape<LBM_F16DEV>::NT, FusedShape<LBM_F16DEV>::smem, s>>>(
+          t, count, (__half*)pool, cur, flag);
+      break;
+    case LBM_BF16DEV:
+      bfused_kernel<LBM_BF16DEV><<<blocks, FusedShape<LBM_BF16DEV>::NT, FusedShape<LBM_BF16DEV>::smem, s>>>(
+          t, count, (__nv_bfloat16*)pool, cur, flag);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 size_t fused_diag_scratch_doubles(const Geom& g, int precision, int fz) {

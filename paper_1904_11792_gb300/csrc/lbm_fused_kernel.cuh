@@ -180,10 +180,17 @@ constexpr int fused_minb() {
   return Prec<P>::dev ? 2 : 3;
 }
 
-template <int P, bool DIAG, int COLL>
-__global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>())
-    fused_kernel(const __grid_constant__ Maps maps, Geom g, Phys ph, typename Prec<P>::T* dst, int* flag, int ntx,
-                 int nchunks, int fz, int grp, DiagOut dg) {
+// The step of one block: work item u of a lattice (a tile and z run), tensor
+// maps `maps` of its source array, destination array dst with rows of px
+// elements and dstride elements per direction.  BATCH: the lattice is an
+// instance of the batched sweep of any size - tiles are cut at its x and y
+// edges (the tensor maps read zeros past them, and nodes there neither
+// store nor write psi), its rows are padded to a 16-byte multiple, and the
+// halo column at x = nx - 1 comes from the 16-byte box that contains it.
+template <int P, bool DIAG, int COLL, bool BATCH>
+__device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, const Phys& ph,
+                                           typename Prec<P>::T* dst, int* flag, int ntx, int nchunks, int fz,
+                                           int grp, const DiagOut& dg, int u, int px, long long dstride) {
   using T = typename Prec<P>::T;
   using C = typename Prec<P>::C;
   using V = typename Pair<P>::V;
@@ -191,22 +198,24 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
   constexpr int TY = S::TY, RH = S::RH;
   static_assert(2 * TY * TX * sizeof(double) + 10 * TY * sizeof(double) <= S::ring_bytes,
                 "the diagnostics reduction reuses the psi ring");
+  static_assert(!(BATCH && (DIAG || COLL != COLL_SRT)), "the batched step is the plain SRT step");
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + S::off_bar);
   C* ring = reinterpret_cast<C*>(smem + S::off_ring);
 
   advance_salt(ph);
-  const int u = blockIdx.x;
   // Block order: z runs in groups of grp consecutive runs; inside a group
   // the run index varies fastest, then the tile x, then the tile y.  Blocks
   // that share planes (the two runs either side of a run boundary, x- and
   // y-neighbour tiles) are then launched close together, so the planes and
   // halo rows they share are still in L2 when the second one reads them.
-  const int tiles = ntx * (g.ny / TY);
+  const int tiles = ntx * (BATCH ? (g.ny + TY - 1) / TY : g.ny / TY);
   const int zg = u / (grp * tiles), r = u - zg * grp * tiles;
   const int gs = min(grp, nchunks - zg * grp);   // runs in this group
   const int chunk = zg * grp + r % gs, xy = r / gs;
   const int x0 = (xy % ntx) * TX, y0 = (xy / ntx) * TY;
+  // tile extent (BATCH: cut at the lattice's edges)
+  const int w = BATCH ? min(TX, g.nx - x0) : TX, h = BATCH ? min(TY, g.ny - y0) : TY;
   const int z0 = chunk * fz, z1 = min(z0 + fz, g.nz);
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
   const int np = (z1 - z0) + 2;        // planes z0 - 1 .. z1, march index k in buffer k % NB
@@ -214,9 +223,13 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
   // two neighbouring runs share is read by both near the same time (at the
   // start of both, or at the end of both) and the second read hits L2.
   const int dir = (chunk & 1) ? -1 : 1;
-  const long long N = g.N;
-  const int ym = y0 == 0 ? g.ny - 1 : y0 - 1, yp = y0 + TY == g.ny ? 0 : y0 + TY;
-  const int xl = x0 == 0 ? g.nx - S::CW : x0 - S::CW, xr = x0 + TX == g.nx ? 0 : x0 + TX;
+  const long long N = dstride;
+  const int ym = y0 == 0 ? g.ny - 1 : y0 - 1, yp = y0 + h == g.ny ? 0 : y0 + h;
+  // the left halo column x0 - 1 (nx - 1 for the first tile) is element lofs
+  // of the 16-byte box at xl; the right one, x0 + w, starts a box
+  const int xl = x0 == 0 ? (BATCH ? (g.nx - 1) / S::CW * S::CW : g.nx - S::CW) : x0 - S::CW;
+  const int lofs = BATCH && x0 == 0 ? g.nx - 1 - xl : S::CW - 1;
+  const int xr = x0 + w == g.nx ? 0 : x0 + TX;
   const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
           s2 = shift_of<P>(7, ph.rho_ref);
   auto zwrap = [&](int p) { return p < 0 ? p + g.nz : (p >= g.nz ? p - g.nz : p); };
@@ -237,21 +250,28 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
   int h_off = -1, h_str = 0, h_ring = 0;
   if (ty < 2) {
     h_off = (int)((ty ? S::off_bot : S::off_top) / S::E) + 2 * lane;
-    h_ring = (ty ? TY + 1 : 0) * RW + 2 * lane + 2;
+    h_ring = (ty ? h + 1 : 0) * RW + 2 * lane + 2;
   } else if (ty == SW && lane < SC) {
-    const int h = lane;
-    if (h < 4) {
-      const int side = h >> 1, right = h & 1;   // corners in the copy order of issue_plane
-      h_off = (int)((S::off_cor + h * S::cor_stride) / S::E) + (right ? 0 : S::CW - 1);
+    const int c = lane;
+    if (c < 4) {
+      const int side = c >> 1, right = c & 1;   // corners in the copy order of issue_plane
+      h_off = (int)((S::off_cor + c * S::cor_stride) / S::E) + (right ? 0 : lofs);
       h_str = S::CW;
-      h_ring = (side ? TY + 1 : 0) * RW + (right ? TX + 2 : 1);
+      h_ring = (side ? h + 1 : 0) * RW + (right ? w + 2 : 1);
     } else {
-      const int i = h - 4, side = i >= TY, r = i - side * TY;   // side 0: column x0 - 1, 1: x0 + TX
-      h_off = (int)((side ? S::off_rgt : S::off_lft) / S::E) + r * S::CW + (side ? 0 : S::CW - 1);
+      const int i = c - 4, side = i >= TY, r = i - side * TY;   // side 0: column x0 - 1, 1: x0 + w
+      h_off = (int)((side ? S::off_rgt : S::off_lft) / S::E) + r * S::CW + (side ? 0 : lofs);
       h_str = TY * S::CW;
-      h_ring = (r + 1) * RW + (side ? TX + 2 : 1);
+      h_ring = (r + 1) * RW + (side ? w + 2 : 1);
+      if (BATCH && r >= h) h_off = -1;   // below the lattice's last row
     }
   }
+  // BATCH: this thread's nodes x0 + 2 lane (+1) of row y0 + ty lie in the
+  // lattice (act: the first, act1: both)
+  const bool act = !BATCH || (ty < h && 2 * lane < w);
+  const bool act1 = !BATCH || (ty < h && 2 * lane + 1 < w);
+  // the halo row cells x0 + 2 lane (+1) of rows y0 - 1 and y0 + h
+  const bool hact = !BATCH || 2 * lane < w, hact1 = !BATCH || 2 * lane + 1 < w;
 
   // dst + a N, the start of direction a in the destination array: with
   // 2-byte storage (bound by instruction issue) the stores address a
@@ -308,7 +328,7 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
     const float2 rr = rho_of<float2>(fp);
     const float2 pp = psi_of2(rr, ph);
     const C r0 = rr.x, r1 = rr.y, p0 = pp.x, p1 = pp.y;
-    nbad |= bad_rho(r0) | bad_rho(r1);
+    nbad |= (act && bad_rho(r0)) | (act1 && bad_rho(r1));
     if constexpr (DIAG) {
       // momentum of the two nodes (the summation order of the two-kernel
       // diagnostics)
@@ -345,10 +365,16 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
         }
       }
     }
-    if constexpr (sizeof(C) == 4)
+    if constexpr (BATCH) {
+      if (act1)
+        *reinterpret_cast<float2*>(slot + (ty + 1) * RW + 2 * lane + 2) = make_float2(p0, p1);
+      else if (act)
+        slot[(ty + 1) * RW + 2 * lane + 2] = p0;   // the right halo column follows
+    } else if constexpr (sizeof(C) == 4) {
       *reinterpret_cast<float2*>(slot + (ty + 1) * RW + 2 * lane + 2) = make_float2(p0, p1);
-    else
+    } else {
       *reinterpret_cast<double2*>(slot + (ty + 1) * RW + 2 * lane + 2) = make_double2(p0, p1);
+    }
     // psi of this thread's halo cells
     if (ty < 2) {
       float2 fh[Q];
@@ -358,8 +384,12 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
                           fh[a].x, fh[a].y);
       }
       const float2 rh = rho_of<float2>(fh);
-      nbad |= bad_rho(rh.x) | bad_rho(rh.y);
-      *reinterpret_cast<float2*>(slot + h_ring) = psi_of2(rh, ph);
+      nbad |= (hact && bad_rho(rh.x)) | (hact1 && bad_rho(rh.y));
+      const float2 ph2 = psi_of2(rh, ph);
+      if (!BATCH || hact1)
+        *reinterpret_cast<float2*>(slot + h_ring) = ph2;
+      else if (hact)
+        slot[h_ring] = ph2.x;
     } else if (h_off >= 0) {
       C fv[Q];
 #pragma unroll
@@ -374,12 +404,15 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
     if (tid == 0 && k + NB < np)
       issue_plane<P>(smem, maps, b, x0, y0, xl, xr, ym, yp, zplane(k + NB), full + b);
 
-    if (k >= 2) {
+    if (k >= 2 && act) {
       // collide + stream the two nodes (x0 + 2 lane, y0 + ty) of plane z =
       // zplane(k - 1); plane z + dz has march index k - 1 + dir dz
       const int z = zplane(k - 1);
       const int x = x0 + 2 * lane, y = y0 + ty;
       const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x + 2 == g.nx ? 0 : x + 2;
+      // right of node 0 (BATCH: x + 1 may be past the lattice's last column)
+      const int xr0 = BATCH ? (x + 1 == g.nx ? 0 : x + 1) : x + 1;
+      const int rowp = BATCH ? px : g.nx;   // elements per stored row
       const int yv[3] = {y == 0 ? g.ny - 1 : y - 1, y, y == g.ny - 1 ? 0 : y + 1};
       const int zv[3] = {z == 0 ? g.nz - 1 : z - 1, z, z == g.nz - 1 ? 0 : z + 1};
       C q[3][3][4];
@@ -435,13 +468,15 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
         const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
-        const int row = g.nx * (yv[1 + cy(a)] + g.ny * zv[1 + cz(a)]);
+        const int row = rowp * (yv[1 + cy(a)] + g.ny * zv[1 + cz(a)]);
         if constexpr (Prec<P>::dev) {
           T* const base = s_dir[a];
           // the shift comes off both nodes in one paired difference
           const float2 sh2 = splat<float2>(sh);
           if (cx(a) == 0) {
-            if (sr) {
+            if (BATCH && !act1) {
+              store_pop<P>(ph, base + (row + x), fs0[a], sh, seed0, a);   // alone: its bits as in the pair
+            } else if (sr) {
               const float2 d = vsub(make_float2(fs0[a], fs1[a]), sh2);   // node x low, x + 1 high
               *reinterpret_cast<unsigned*>(base + (row + x)) =
                   cvt_pair_sr<P>(d.y, d.x, (sr_bits(seed1, a) << 16) | (sr_bits(seed0, a) & 0xFFFFu));
@@ -449,15 +484,15 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
               store_pair<P>(base + (row + x), fs0[a], fs1[a], sh);
             }
           } else if (!sr) {
-            store_pop<P>(ph, base + (row + (cx(a) > 0 ? x + 1 : xm)), fs0[a], sh, seed0, a);
-            store_pop<P>(ph, base + (row + (cx(a) > 0 ? xp : x)), fs1[a], sh, seed1, a);
+            store_pop<P>(ph, base + (row + (cx(a) > 0 ? xr0 : xm)), fs0[a], sh, seed0, a);
+            if (act1) store_pop<P>(ph, base + (row + (cx(a) > 0 ? xp : x)), fs1[a], sh, seed1, a);
           } else if (a & 1) {
             // a and its opposite a + 1 (c_x != 0, the same weight and shift):
             // one conversion per node rounds both with the bits sr_bits gives
             // them (the high half a, the low half a + 1), so the stored values
             // equal those of the one-value conversions of the two-kernel step
             T* const base_b = s_dir[a + 1];
-            const int row_b = g.nx * (yv[1 + cy(a + 1)] + g.ny * zv[1 + cz(a + 1)]);
+            const int row_b = rowp * (yv[1 + cy(a + 1)] + g.ny * zv[1 + cz(a + 1)]);
             const unsigned j = (unsigned)(a + 1) >> 1;
             const float2 da = vsub(make_float2(fs0[a], fs1[a]), sh2);
             const float2 db = vsub(make_float2(fs0[a + 1], fs1[a + 1]), sh2);
@@ -465,19 +500,24 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
             const unsigned d1 = cvt_pair_sr<P>(da.y, db.y, sr_word(seed1, j));
             unsigned short* const pa = reinterpret_cast<unsigned short*>(base + row);
             unsigned short* const pb = reinterpret_cast<unsigned short*>(base_b + row_b);
-            pa[cx(a) > 0 ? x + 1 : xm] = (unsigned short)(d0 >> 16);
-            pa[cx(a) > 0 ? xp : x] = (unsigned short)(d1 >> 16);
-            pb[cx(a + 1) > 0 ? x + 1 : xm] = (unsigned short)d0;
-            pb[cx(a + 1) > 0 ? xp : x] = (unsigned short)d1;
+            pa[cx(a) > 0 ? xr0 : xm] = (unsigned short)(d0 >> 16);
+            pb[cx(a + 1) > 0 ? xr0 : xm] = (unsigned short)d0;
+            if (act1) {
+              pa[cx(a) > 0 ? xp : x] = (unsigned short)(d1 >> 16);
+              pb[cx(a + 1) > 0 ? xp : x] = (unsigned short)d1;
+            }
           }
           // even a with c_x != 0 under stochastic rounding: stored with a - 1
         } else {
           T* base = dst + (long long)a * N + row;
           if (cx(a) == 0) {
-            store_pair<P>(base + x, fs0[a], fs1[a], sh);
+            if (act1)
+              store_pair<P>(base + x, fs0[a], fs1[a], sh);
+            else
+              store_pop<P>(ph, base + x, fs0[a], sh, seed0, a);
           } else {
-            store_pop<P>(ph, base + (cx(a) > 0 ? x + 1 : xm), fs0[a], sh, seed0, a);
-            store_pop<P>(ph, base + (cx(a) > 0 ? xp : x), fs1[a], sh, seed1, a);
+            store_pop<P>(ph, base + (cx(a) > 0 ? xr0 : xm), fs0[a], sh, seed0, a);
+            if (act1) store_pop<P>(ph, base + (cx(a) > 0 ? xp : x), fs1[a], sh, seed1, a);
           }
         }
       }
@@ -565,6 +605,53 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>()
       dg.blocks[(long long)blockIdx.x * DIAG_NG + i] = r;
     }
   }
+}
+
+template <int P, bool DIAG, int COLL>
+__global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>())
+    fused_kernel(const __grid_constant__ Maps maps, Geom g, Phys ph, typename Prec<P>::T* dst, int* flag, int ntx,
+                 int nchunks, int fz, int grp, DiagOut dg) {
+  fused_body<P, DIAG, COLL, false>(maps, g, ph, dst, flag, ntx, nchunks, fz, grp, dg, blockIdx.x, g.nx, g.N);
+}
+
+// One instance of the batched TMA step (device table built by the host).
+struct BTInst {
+  Geom g;
+  Phys ph;
+  long long off_f;     // element offset of the instance's array 0 in the padded pool
+  long long dstride;   // elements per direction: px ny nz
+  const Maps* maps;    // tensor maps of its arrays 0 and 1 (device memory, 64-byte aligned)
+  int px;              // elements per row (nx padded to a 16-byte multiple)
+  int block0;          // first block of the instance
+  int ntx, nchunks, fz, grp;
+};
+
+// The single-pass step of a batch of lattices of any size, their rows
+// padded to 16-byte multiples: one launch, each block finds its instance
+// (the largest block0 <= blockIdx.x) and runs fused_body on it with that
+// instance's tensor maps, which live in global memory (ordered before their
+// use by the tensor-map proxy fence).
+template <int P>
+__global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, false, COLL_SRT>())
+    bfused_kernel(const BTInst* __restrict__ inst, int count, typename Prec<P>::T* pool, int cur, int* flag) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (inst[mid].block0 <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const BTInst& I = inst[lo];
+  const Maps& m = I.maps[cur];
+  if (threadIdx.x == 0) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.interior) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.row) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.col) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.cor) : "memory");
+  }
+  typename Prec<P>::T* dst = pool + I.off_f + (long long)(cur ^ 1) * Q * I.dstride;
+  const DiagOut none{0.0, 0.0, nullptr, nullptr, 0ull};
+  fused_body<P, false, COLL_SRT, true>(m, I.g, I.ph, dst, flag, I.ntx, I.nchunks, I.fz, I.grp, none,
+                                       (int)blockIdx.x - I.block0, I.px, I.dstride);
 }
 
 }  // namespace

@@ -150,6 +150,29 @@ cudaError_t launch_droplets(int precision, int layout, const Geom& g, const Phys
                             double rho_l, double rho_v, const int* labels, int* sizes, double* rec,
                             unsigned* xbits, unsigned* nslot, int cap, cudaStream_t s);
 
+
+// ---- batched single-pass step on padded rows (lbm_fused.cu) ----------------
+// One instance: geometry, physics, element offset of its array 0 in the
+// padded pool (arrays 0 and 1 are Q px ny nz elements each) and its row
+// pitch px (nx rounded up to batch_tma_row_align elements, 16 bytes).
+struct BatchTmaInst {
+  Geom g;
+  Phys ph;
+  long long off_f;
+  int px;
+};
+int batch_tma_row_align(int precision);
+// Bytes of the device table (instance records and their tensor maps).
+size_t batch_tma_table_bytes(int count);
+// Encodes the tensor maps, builds the block table for z runs of fz planes
+// and copies it to d_table (device, batch_tma_table_bytes); *blocks = blocks
+// of one launch.  FP32, FP16-dev, BF16-dev.  Synchronises s.
+cudaError_t batch_tma_build(int precision, const BatchTmaInst* insts, int count, int fz, const void* pool,
+                            void* d_table, int* blocks, cudaStream_t s);
+// One step of every instance: padded pool arrays cur -> cur ^ 1.
+cudaError_t batch_tma_launch(int precision, const void* d_table, int count, int blocks, void* pool, int cur,
+                             int* flag, cudaStream_t s);
+
 }  // namespace lbm
 
 // ---- the handle -------------------------------------------------------------

@@ -143,9 +143,9 @@ def test_fused_batch_equals_two_kernel_batch(L, precision):
             np.testing.assert_array_equal(a, c, err_msg=str(SHAPES[k]))
 
 
-# The persistent form (option persistent: all n steps of a call in one
-# cooperative launch, grid barriers between the steps) against one launch
-# per step, bitwise: every precision (the stochastic-rounding salt advances
+# The persistent form (option persistent with the per-element single pass,
+# fused = 1: all n steps of a call in one cooperative launch, grid barriers
+# between the steps) against one launch per step, bitwise: every precision (the stochastic-rounding salt advances
 # the same), the instance shapes above, odd step counts and calls that
 # continue one another, and fewer persistent blocks than work items (each
 # block takes several tiles and z runs per step).
@@ -159,6 +159,7 @@ def test_persistent_batch_equals_per_step_launches(L, precision):
     res = []
     for persistent in (0, 1):
         with L.Batch(insts, precision=precision) as b:
+            b.set_option("fused", 1)
             b.set_option("persistent", persistent)
             b.set_option("fused_fz", 4)
             b.init()
@@ -179,6 +180,7 @@ def test_persistent_batch_barrier_timeout(L):
     insts = [dict(nx=nx, ny=ny, nz=nz, tau=0.9, G=-5.5, R0=max(1.0, min(ny, nz) / 4.0), lam=float(nx), eps=0.1,
                   phase=0.0, rho_l=2.5, rho_v=0.15, width=2.0) for nx, ny, nz in SHAPES]
     with L.Batch(insts) as b:
+        b.set_option("fused", 1)
         b.set_option("persistent", 1)
         b.set_option("persistent_stall_test", 5.0)
         b.init()
@@ -197,3 +199,35 @@ def test_persistent_batch_barrier_timeout(L):
         want = [b.populations(k) for k in range(len(insts))]
     for g, w in zip(got, want):
         np.testing.assert_array_equal(g, w)
+
+
+# The single pass on padded rows (option fused = 2: per-instance tensor maps,
+# tiles of 64 x 4 (64 x 8 for 2-byte storage) cut at the instance's edges)
+# against the per-element single pass (fused = 1), bitwise: the shapes above
+# plus x extents around the 64-node tile (63, 64, 65, 130) and y extents that
+# leave a partial tile row; an odd number of steps over two calls, and a run
+# that switches form in the middle (the state moves between the pools).
+TMA_SHAPES = SHAPES + ((63, 9, 7), (64, 8, 5), (65, 13, 6), (130, 20, 37))
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16dev", "bf16dev"])
+def test_padded_tma_batch_equals_per_element_batch(L, precision):
+    insts = []
+    for k, (nx, ny, nz) in enumerate(TMA_SHAPES):
+        R0 = max(1.0, min(ny, nz) / 4.0)
+        insts.append(dict(nx=nx, ny=ny, nz=nz, tau=0.8 + 0.04 * k, G=-5.5, R0=R0, lam=float(nx), eps=0.1,
+                          phase=0.3 * k, rho_l=2.5, rho_v=0.15, width=2.0))
+    res = []
+    for forms in ((1, 1), (2, 2), (2, 1), (1, 2)):
+        with L.Batch(insts, precision=precision) as b:
+            b.set_option("fused_fz", 4)
+            b.init()
+            b.set_option("fused", forms[0])
+            b.step(5)
+            b.set_option("fused", forms[1])
+            b.step(6)
+            b.sync()
+            res.append([b.populations(k) for k in range(len(insts))])
+    for r in res[1:]:
+        for k in range(len(insts)):
+            np.testing.assert_array_equal(r[k], res[0][k])
