@@ -501,11 +501,9 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
             unsigned short* const pa = reinterpret_cast<unsigned short*>(base + row);
             unsigned short* const pb = reinterpret_cast<unsigned short*>(base_b + row_b);
             pa[cx(a) > 0 ? xr0 : xm] = (unsigned short)(d0 >> 16);
+            if (act1) pa[cx(a) > 0 ? xp : x] = (unsigned short)(d1 >> 16);
             pb[cx(a + 1) > 0 ? xr0 : xm] = (unsigned short)d0;
-            if (act1) {
-              pa[cx(a) > 0 ? xp : x] = (unsigned short)(d1 >> 16);
-              pb[cx(a + 1) > 0 ? xp : x] = (unsigned short)d1;
-            }
+            if (act1) pb[cx(a + 1) > 0 ? xp : x] = (unsigned short)d1;
           }
           // even a with c_x != 0 under stochastic rounding: stored with a - 1
         } else {
