@@ -39,6 +39,7 @@ import ctypes
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -100,15 +101,29 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_digest(fused: bool = False) -> str:
-    """sha256 over the sources of the time-step kernels (two-kernel step, or
-    the single-pass fused step)."""
+def source_code_bytes(text: str) -> bytes:
+    """A source file without its comments and blank lines: what the compiler
+    sees of it (so that the digest below changes with the code, not with the
+    text around it)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln.strip()).encode()
+
+
+def kernel_digest(fused: bool = False, read=None) -> str:
+    """sha256 over the code (comments stripped) of the time-step kernels'
+    sources (two-kernel step, or the single-pass fused step); `read` maps a
+    file name to its text (default: the files of this tree)."""
     h = hashlib.sha256()
     names = ("lbm_node.cuh", "lbm_fused_kernel.cuh", "lbm_device.cuh") if fused else (
         "lbm_node.cuh", "lbm_step.cu", "lbm_device.cuh")
     for name in names:
-        with open(os.path.join(ROOT, "paper_1904_11792_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        if read is None:
+            with open(os.path.join(ROOT, "paper_1904_11792_gb300", "csrc", name)) as fh:
+                text = fh.read()
+        else:
+            text = read(name)
+        h.update(source_code_bytes(text))
     return h.hexdigest()
 
 

@@ -29,8 +29,10 @@
 // lbm_node.cuh, computed for the thread's two nodes at once in paired FP32
 // instructions (float2 lanes, each rounded like the scalar instruction), and
 // the stores are those of collide_pair, so the results equal the two-kernel
-// step bitwise.  A-B streaming, 4- and 2-byte storage,
-// lattices with nx % 64 == 0 and ny % 4 == 0.
+// step bitwise.  A-B streaming, 4- and 2-byte storage, lattices with
+// nx % 64 == 0 and ny % 4 == 0 (8 for 2-byte storage); bfused_kernel runs
+// the same body over the instances of a batch, of any size, whose rows the
+// batch pads to 16-byte multiples.
 //
 // This header holds the kernel and its device helpers; lbm_fused.cu holds
 // the host side (tensor maps, launch shape, launches).  Include it from one

@@ -1,7 +1,9 @@
-// Single-pass time step for lattices of any size (the batched sweep).
+// Single-pass time step for lattices of any size, on the batch's unpadded
+// pool (the batched sweep's per-element form: FP64, instances too large for
+// the padded TMA form of lbm_fused_kernel.cuh, and the persistent launch).
 //
-// The TMA fused step (lbm_fused_kernel.cuh) needs rows of a 16-byte multiple
-// and nx % 64 == 0; the ligaments of a sweep have arbitrary lengths.  This
+// The TMA fused step needs rows of a 16-byte multiple, which the ligaments
+// of a sweep (arbitrary lengths) have only in the batch's padded pool.  This
 // kernel does the same single pass with plain coalesced loads: a block owns
 // a GX x GY tile of (x, y), one node per thread (a warp per row), possibly
 // cut short at the lattice's edge, and marches through a run of z planes:
