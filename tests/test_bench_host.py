@@ -68,3 +68,14 @@ def test_committed_traffic_records_are_well_formed():
             if r["kernel_source_sha256"] == bench.kernel_digest(key.endswith("/fused")):
                 ratio = r["dram_bytes_per_launch_full_size"] / r["algorithmic_bytes_per_launch"]
                 assert 0.8 <= ratio <= 1.2, (key, ratio)
+
+
+def test_kernel_digest_follows_the_code_not_the_comments():
+    import bench
+    base = {"lbm_node.cuh": "int a; // one\n", "lbm_fused_kernel.cuh": "/* two\n lines */ int b;\n",
+            "lbm_device.cuh": "int c;\n\n"}
+    d0 = bench.kernel_digest(True, read=base.get)
+    commented = dict(base, **{"lbm_node.cuh": "// a new comment\nint a;   // other words\n\n"})
+    assert bench.kernel_digest(True, read=commented.get) == d0
+    changed = dict(base, **{"lbm_device.cuh": "int c = 1;\n"})
+    assert bench.kernel_digest(True, read=changed.get) != d0
