@@ -332,8 +332,8 @@ int lbm_batch_set_stream(lbm_batch b, void *stream);
  * elements take form 1.  1: blocks of 32 x 8 nodes, one per thread, copying
  * the populations element by element (instances up to 113 M nodes, larger
  * ones take the two kernels).  0: a psi pass and a collide-stream kernel per
- * step), "persistent" (0/1, default 0: with the
- * single-pass step of form 1, every lbm_batch_step call runs its n steps as one
+ * step), "persistent" (0/1, default 0: with a single-pass form (1 or 2),
+ * every lbm_batch_step call runs its n steps as one
  * cooperative launch of persistent blocks - as many as the GPU holds at once,
  * each taking several tiles and z runs per step - separated by grid-wide
  * barriers; the same results as one launch per step, no graph; a barrier

@@ -705,7 +705,7 @@ int lbm_batch_step(lbm_batch b, int n) {
     const int rc = tma_form(b) ? ensure_padded(b) : ensure_contig(b);
     if (rc) return rc;
   }
-  while (n > 0 && b->persistent && b->fused && !tma_form(b) && 19LL * b->max_nodes <= 0x7fffffffLL) {
+  while (n > 0 && b->persistent && b->fused && (tma_form(b) || 19LL * b->max_nodes <= 0x7fffffffLL)) {
     // up to kPersistSteps steps in one cooperative launch of persistent blocks
     constexpr int kPersistSteps = 1024;
     const int m = std::min(n, kPersistSteps);
@@ -714,8 +714,12 @@ int lbm_batch_step(lbm_batch b, int n) {
       b->tickets_n = kPersistSteps;
     }
     const unsigned long long stall_ns = (unsigned long long)(b->persist_stall_ms * 1e6);
-    BCK(batch_persist_launch(b->precision, b->d_ginst, b->count, b->gblocks, b->pool_f, b->cur, m,
-                             (unsigned*)(b->d_flag + 4), b->d_tickets, b->d_flag, stall_ns, b->stream));
+    if (tma_form(b))
+      BCK(batch_tma_persist_launch(b->precision, b->d_ttable, b->count, b->tblocks, b->pool_p, b->cur, m,
+                                   (unsigned*)(b->d_flag + 4), b->d_tickets, b->d_flag, stall_ns, b->stream));
+    else
+      BCK(batch_persist_launch(b->precision, b->d_ginst, b->count, b->gblocks, b->pool_f, b->cur, m,
+                               (unsigned*)(b->d_flag + 4), b->d_tickets, b->d_flag, stall_ns, b->stream));
     if (batch_sr(b)) BCK(launch_salt_add((unsigned*)(b->d_flag + 2), (unsigned)m, b->stream));
     b->cur ^= m & 1;
     b->step += m;

@@ -135,7 +135,7 @@ cudaError_t fused_device_info(int* slots_per_sm, int* sms) {
   if (!slots_of[dev]) {
     for (const void* k : {(const void*)fused_kernel<P, false, COLL_SRT>, (const void*)fused_kernel<P, true, COLL_SRT>,
                           (const void*)fused_kernel<P, false, COLL_MRT>, (const void*)fused_kernel<P, true, COLL_MRT>,
-                          (const void*)bfused_kernel<P>})
+                          (const void*)bfused_kernel<P>, (const void*)bpersist_kernel<P>})
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
     int n_sm = 0, slots = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -345,6 +345,49 @@ cudaError_t batch_tma_launch(int precision, const void* d_table, int count, int 
       return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+namespace {
+
+template <int P>
+cudaError_t batch_tma_persist_t(const void* d_table, int count, int items, void* pool, int cur, int nsteps,
+                                unsigned* bar, unsigned* tickets, int* flag, unsigned long long stall_ns,
+                                cudaStream_t s) {
+  using S = FusedShape<P>;
+  using T = typename Prec<P>::T;
+  int slots_per_sm = 0, sms = 0, per_sm = 0;
+  cudaError_t e = fused_device_info<P>(&slots_per_sm, &sms);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bpersist_kernel<P>, S::NT, S::smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  const int grid = std::min(items, per_sm * sms);
+  e = cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tickets, 0, sizeof(unsigned) * (size_t)nsteps, s);
+  if (e != cudaSuccess) return e;
+  const BTInst* t = reinterpret_cast<const BTInst*>(d_table);
+  T* pf = (T*)pool;
+  void* args[] = {(void*)&t, (void*)&count, (void*)&pf, (void*)&cur, (void*)&nsteps,
+                  (void*)&items, (void*)&bar, (void*)&tickets, (void*)&flag, (void*)&stall_ns};
+  return cudaLaunchCooperativeKernel((const void*)bpersist_kernel<P>, dim3(grid), dim3(S::NT), args, S::smem, s);
+}
+
+}  // namespace
+
+cudaError_t batch_tma_persist_launch(int precision, const void* d_table, int count, int items, void* pool,
+                                     int cur, int nsteps, unsigned* bar, unsigned* tickets, int* flag,
+                                     unsigned long long stall_ns, cudaStream_t s) {
+  switch (precision) {
+    case LBM_F32:
+      return batch_tma_persist_t<LBM_F32>(d_table, count, items, pool, cur, nsteps, bar, tickets, flag, stall_ns, s);
+    case LBM_F16DEV:
+      return batch_tma_persist_t<LBM_F16DEV>(d_table, count, items, pool, cur, nsteps, bar, tickets, flag, stall_ns,
+                                             s);
+    case LBM_BF16DEV:
+      return batch_tma_persist_t<LBM_BF16DEV>(d_table, count, items, pool, cur, nsteps, bar, tickets, flag,
+                                              stall_ns, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 size_t fused_diag_scratch_doubles(const Geom& g, int precision, int fz) {

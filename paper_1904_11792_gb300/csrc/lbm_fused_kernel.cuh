@@ -189,10 +189,11 @@ constexpr int fused_minb() {
 // edges (the tensor maps read zeros past them, and nodes there neither
 // store nor write psi), its rows are padded to a 16-byte multiple, and the
 // halo column at x = nx - 1 comes from the 16-byte box that contains it.
-template <int P, bool DIAG, int COLL, bool BATCH>
+template <int P, bool DIAG, int COLL, bool BATCH, bool SALT_GIVEN = false>
 __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, const Phys& ph,
                                            typename Prec<P>::T* dst, int* flag, int ntx, int nchunks, int fz,
-                                           int grp, const DiagOut& dg, int u, int px, long long dstride) {
+                                           int grp, const DiagOut& dg, int u, int px, long long dstride,
+                                           unsigned salt_given = 0u) {
   using T = typename Prec<P>::T;
   using C = typename Prec<P>::C;
   using V = typename Pair<P>::V;
@@ -296,7 +297,9 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
     for (int k = 0; k < NB && k < np; ++k)
       issue_plane<P>(smem, maps, k, x0, y0, xl, xr, ym, yp, zplane(k), full + k);
 
-  const unsigned salt = (Prec<P>::dev && ph.sr) ? salt_of(ph) : 0u;
+  // the step's stochastic-rounding salt (SALT_GIVEN: by the caller, which
+  // runs several steps in one launch)
+  const unsigned salt = (Prec<P>::dev && ph.sr) ? (SALT_GIVEN ? salt_given : salt_of(ph)) : 0u;
   // a non-positive or non-finite density met by this thread's psi
   // evaluations (raised on the flag once, after the run: the host reads the
   // flag only after the kernel)
@@ -652,6 +655,69 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, false, COLL_S
   const DiagOut none{0.0, 0.0, nullptr, nullptr, 0ull};
   fused_body<P, false, COLL_SRT, true>(m, I.g, I.ph, dst, flag, I.ntx, I.nchunks, I.fz, I.grp, none,
                                        (int)blockIdx.x - I.block0, I.px, I.dstride);
+}
+
+// nsteps steps of the batched TMA step in one cooperative launch of
+// persistent blocks: in each step a block takes the next work item (from
+// tickets[s], zero before the launch) until none is left and runs fused_body
+// on it (its mbarriers invalidated after each item, the next item
+// initialises them again); grid barriers on *bar separate the steps (bounded:
+// a barrier that waits too long raises the timeout bit and the block
+// returns).  Step s runs arrays cur0 ^ (s & 1) -> the other with salt
+// salt0 + s, salt0 the salt word at the launch (the host advances the word
+// by nsteps after it): the results of nsteps launches of bfused_kernel.
+// stall_test_ns > 0 (a test hook of the failure path): block 0 skips the
+// first barrier, the others give up on it after stall_test_ns.
+template <int P>
+__global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, false, COLL_SRT>())
+    bpersist_kernel(const BTInst* __restrict__ inst, int count, typename Prec<P>::T* pool, int cur0, int nsteps,
+                    int items, unsigned* bar, unsigned* tickets, int* flag, unsigned long long stall_test_ns) {
+  using S = FusedShape<P>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + S::off_bar);
+  __shared__ int s_item;
+  const Phys& ph0 = inst[0].ph;   // every instance shares the salt word
+  unsigned salt0 = 0u;
+  if (Prec<P>::dev && ph0.sr) salt0 = *(const volatile unsigned*)ph0.salt;
+  const unsigned long long limit = stall_test_ns ? stall_test_ns : kGridWaitNs;
+  const DiagOut none{0.0, 0.0, nullptr, nullptr, 0ull};
+  for (int s = 0; s < nsteps; ++s) {
+    // one read of the flag for the whole block: every thread returns or none
+    if (__syncthreads_or(threadIdx.x == 0 && (*(volatile int*)flag & 2) != 0)) return;
+    const int cur = cur0 ^ (s & 1);
+    for (;;) {
+      if (threadIdx.x == 0) s_item = (int)atomicAdd(tickets + s, 1u);
+      __syncthreads();
+      const int w = s_item;
+      if (w >= items) break;
+      int lo = 0, hi = count - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (inst[mid].block0 <= w) lo = mid;
+        else hi = mid - 1;
+      }
+      const BTInst& I = inst[lo];
+      const Maps& m = I.maps[cur];
+      if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.interior) : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.row) : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.col) : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.cor) : "memory");
+      }
+      typename Prec<P>::T* dst = pool + I.off_f + (long long)(cur ^ 1) * Q * I.dstride;
+      fused_body<P, false, COLL_SRT, true, true>(m, I.g, I.ph, dst, flag, I.ntx, I.nchunks, I.fz, I.grp, none,
+                                                 w - I.block0, I.px, I.dstride, salt0 + (unsigned)s);
+      __syncthreads();   // the item's shared memory, barriers and s_item are done with
+      if (threadIdx.x == 0)
+        for (int b = 0; b < NB + 1; ++b)
+          asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(full + b)) : "memory");
+      __syncthreads();
+    }
+    if (s + 1 < nsteps) {
+      if (stall_test_ns && s == 0 && blockIdx.x == 0) return;
+      if (!grid_barrier(bar, (unsigned)(s + 1) * gridDim.x, flag, limit)) return;
+    }
+  }
 }
 
 }  // namespace

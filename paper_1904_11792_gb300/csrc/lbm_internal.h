@@ -172,6 +172,12 @@ cudaError_t batch_tma_build(int precision, const BatchTmaInst* insts, int count,
 // One step of every instance: padded pool arrays cur -> cur ^ 1.
 cudaError_t batch_tma_launch(int precision, const void* d_table, int count, int blocks, void* pool, int cur,
                              int* flag, cudaStream_t s);
+// nsteps such steps in one cooperative launch of persistent blocks: grid
+// barriers on *bar (zeroed here), per-step work tickets tickets[nsteps]
+// (zeroed here); stall_ns > 0 is the barrier-timeout test hook.
+cudaError_t batch_tma_persist_launch(int precision, const void* d_table, int count, int items, void* pool,
+                                     int cur, int nsteps, unsigned* bar, unsigned* tickets, int* flag,
+                                     unsigned long long stall_ns, cudaStream_t s);
 
 }  // namespace lbm
 

@@ -629,4 +629,42 @@ __device__ __forceinline__ void collide_pair(const Geom& g, const Phys& ph,
   }
 }
 
+// Grid-wide barrier of a cooperative launch: counter ctr (zero before the
+// launch) reaches `target` = gridDim.x per barrier passed.  Thread 0 of each
+// block releases the block's writes, arrives and polls with acquire loads,
+// for at most kGridWaitNs of wall time (then it raises bit 2 of the flag and
+// the barrier reports failure); the block barrier and an acquire fence in
+// every thread then order all later loads of the block, through L1
+// included, after every block's writes before the barrier.
+constexpr unsigned long long kGridWaitNs = 2000000000ull;
+__device__ __forceinline__ unsigned long long gsm_global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int* flag,
+                                             unsigned long long limit_ns) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    atomicAdd(ctr, 1u);
+    const unsigned long long t0 = gsm_global_ns();
+    for (;;) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+      if (v >= target) break;
+      if (gsm_global_ns() - t0 > limit_ns) {
+        atomicOr(flag, 2);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  ok = __syncthreads_and(ok);
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  return ok != 0;
+}
+
 }  // namespace lbm

@@ -143,14 +143,15 @@ def test_fused_batch_equals_two_kernel_batch(L, precision):
             np.testing.assert_array_equal(a, c, err_msg=str(SHAPES[k]))
 
 
-# The persistent form (option persistent with the per-element single pass,
-# fused = 1: all n steps of a call in one cooperative launch, grid barriers
-# between the steps) against one launch per step, bitwise: every precision (the stochastic-rounding salt advances
+# The persistent form (option persistent, with either single-pass form: all
+# n steps of a call in one cooperative launch, grid barriers between the
+# steps) against one launch per step, bitwise: every precision (the stochastic-rounding salt advances
 # the same), the instance shapes above, odd step counts and calls that
 # continue one another, and fewer persistent blocks than work items (each
 # block takes several tiles and z runs per step).
-@pytest.mark.parametrize("precision", ["f64", "f32", "f16dev", "bf16dev"])
-def test_persistent_batch_equals_per_step_launches(L, precision):
+@pytest.mark.parametrize("precision,form", [("f64", 1), ("f32", 1), ("f16dev", 1), ("bf16dev", 1),
+                                            ("f32", 2), ("f16dev", 2), ("bf16dev", 2)])
+def test_persistent_batch_equals_per_step_launches(L, precision, form):
     insts = []
     for k, (nx, ny, nz) in enumerate(SHAPES + ((130, 64, 96),)):
         R0 = max(1.0, min(ny, nz) / 4.0)
@@ -159,7 +160,7 @@ def test_persistent_batch_equals_per_step_launches(L, precision):
     res = []
     for persistent in (0, 1):
         with L.Batch(insts, precision=precision) as b:
-            b.set_option("fused", 1)
+            b.set_option("fused", form)
             b.set_option("persistent", persistent)
             b.set_option("fused_fz", 4)
             b.init()
@@ -176,11 +177,12 @@ def test_persistent_batch_equals_per_step_launches(L, precision):
 # test hook keeps one block from arriving at the first barrier; every other
 # block gives up on it after 5 ms, raises the timeout bit and returns.  The
 # host reads LBM_ERR_TIMEOUT, and the batch steps correctly afterwards.
-def test_persistent_batch_barrier_timeout(L):
+@pytest.mark.parametrize("form", [1, 2])
+def test_persistent_batch_barrier_timeout(L, form):
     insts = [dict(nx=nx, ny=ny, nz=nz, tau=0.9, G=-5.5, R0=max(1.0, min(ny, nz) / 4.0), lam=float(nx), eps=0.1,
                   phase=0.0, rho_l=2.5, rho_v=0.15, width=2.0) for nx, ny, nz in SHAPES]
     with L.Batch(insts) as b:
-        b.set_option("fused", 1)
+        b.set_option("fused", form)
         b.set_option("persistent", 1)
         b.set_option("persistent_stall_test", 5.0)
         b.init()
