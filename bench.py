@@ -612,7 +612,7 @@ def batch_sweep(args, torch, L, autotune, rho_l, rho_v, precision="f32"):
     with L.Batch(stable, precision=precision) as b:
         b.init()
         if args.no_tune:
-            tuned = dict(fused=args.batch_fused, fused_fz=16, block=[0, 0, 0], occupancy=0)
+            tuned = dict(fused=args.batch_fused, fused_fz=16, fused_group=0, block=[0, 0, 0], occupancy=0)
             per_elem = dict(fused=1, fused_fz=16, block=[0, 0, 0], occupancy=0)
             other = dict(fused=0, fused_fz=0, block=[128, 1, 1], occupancy=3)
         else:

@@ -341,7 +341,9 @@ int lbm_batch_set_stream(lbm_batch b, void *stream);
  * reports LBM_ERR_TIMEOUT with the state void), "persistent_stall_test" (a
  * test hook of that failure path, in ms, 0..10: one block skips the first
  * barrier and the others give up after this long), "fused_fz" (z planes
- * per block of the single-pass step, default 16), "graph" (0/1),
+ * per block of the single-pass step, default 16), "fused_group" (form 2:
+ * z runs per block-order group, as lbm_set_option's; 0, the default: all
+ * runs of a tile one after another), "graph" (0/1),
  * "stochastic_rounding" (0/1, as lbm_set_option), and for the two-kernel
  * step "occupancy" (2, 3, 4; default 2), "vector" (0/1, default 1:
  * instances with even nx update two nodes per thread), "block_x",

@@ -248,6 +248,7 @@ struct lbm_batch_ctx {
   int gblocks = 0;
   bool fused = true;               // option "fused": the single-pass step
   int gfz = 16;                    // its z run length (option "fused_fz")
+  int ggrp = 0;                    // runs per block-order group of the padded form (option "fused_group")
   bool tma = true;                 // option "fused" = 2 (the default): the single pass on padded rows (TMA)
   // its own pool, rows padded to 16 bytes, which holds the state while that
   // form steps (the state moves between the pools by 2-D copies)
@@ -411,7 +412,7 @@ int ensure_padded(lbm_batch_ctx* b) {
       t[k].off_f = b->off_p[k];
       t[k].px = b->px[k];
     }
-    BCK(batch_tma_build(b->precision, t.data(), b->count, b->gfz, b->pool_p, b->d_ttable, &b->tblocks,
+    BCK(batch_tma_build(b->precision, t.data(), b->count, b->gfz, b->ggrp, b->pool_p, b->d_ttable, &b->tblocks,
                         b->stream));
     b->ttable_ok = true;
   }
@@ -642,6 +643,12 @@ int lbm_batch_set_option(lbm_batch b, const char* key, double v) {
     if (!(v >= 0.0 && v <= 10.0)) return bfail(LBM_ERR_ARG, "persistent_stall_test must be in 0..10 ms");
     b->persist_stall_ms = v;
     return LBM_OK;
+  }
+  if (k == "fused_group") {
+    const long long n = (long long)v;
+    if (n < 0 || n > 1 << 20 || (double)n != v) return bfail(LBM_ERR_ARG, "fused_group must be a non-negative integer");
+    b->ggrp = (int)n;
+    return layout_tiles(b);
   }
   if (k == "fused_fz") {
     const long long n = (long long)v;

@@ -258,8 +258,8 @@ cudaError_t launch_fused(int precision, const Geom& g, const Phys& ph, const voi
 namespace {
 
 template <int P>
-cudaError_t batch_tma_build_t(const BatchTmaInst* in, int count, int fz_req, const void* pool, void* d_table,
-                              int* blocks_out, cudaStream_t s) {
+cudaError_t batch_tma_build_t(const BatchTmaInst* in, int count, int fz_req, int grp_req, const void* pool,
+                              void* d_table, int* blocks_out, cudaStream_t s) {
   using S = FusedShape<P>;
   int slots_per_sm = 0, sms = 0;
   cudaError_t e = fused_device_info<P>(&slots_per_sm, &sms);   // the kernels' shared-memory limit
@@ -287,7 +287,8 @@ cudaError_t batch_tma_build_t(const BatchTmaInst* in, int count, int fz_req, con
     const int nty = (b.g.ny + S::TY - 1) / S::TY;
     t.fz = std::min(fz_req > 0 ? fz_req : 16, b.g.nz);
     t.nchunks = (b.g.nz + t.fz - 1) / t.fz;
-    t.grp = t.nchunks;   // a tile's z runs one after another in the launch order
+    // runs per block-order group (0: a tile's z runs one after another)
+    t.grp = grp_req > 0 ? std::min(grp_req, t.nchunks) : t.nchunks;
     t.block0 = (int)blocks;
     blocks += (long long)t.ntx * nty * t.nchunks;
     for (int arr = 0; arr < 2; ++arr) {
@@ -315,12 +316,12 @@ size_t batch_tma_table_bytes(int count) {
 
 int batch_tma_row_align(int precision) { return 16 / (int)elem_size(precision); }
 
-cudaError_t batch_tma_build(int precision, const BatchTmaInst* insts, int count, int fz, const void* pool,
-                            void* d_table, int* blocks, cudaStream_t s) {
+cudaError_t batch_tma_build(int precision, const BatchTmaInst* insts, int count, int fz, int grp,
+                            const void* pool, void* d_table, int* blocks, cudaStream_t s) {
   switch (precision) {
-    case LBM_F32: return batch_tma_build_t<LBM_F32>(insts, count, fz, pool, d_table, blocks, s);
-    case LBM_F16DEV: return batch_tma_build_t<LBM_F16DEV>(insts, count, fz, pool, d_table, blocks, s);
-    case LBM_BF16DEV: return batch_tma_build_t<LBM_BF16DEV>(insts, count, fz, pool, d_table, blocks, s);
+    case LBM_F32: return batch_tma_build_t<LBM_F32>(insts, count, fz, grp, pool, d_table, blocks, s);
+    case LBM_F16DEV: return batch_tma_build_t<LBM_F16DEV>(insts, count, fz, grp, pool, d_table, blocks, s);
+    case LBM_BF16DEV: return batch_tma_build_t<LBM_BF16DEV>(insts, count, fz, grp, pool, d_table, blocks, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -165,10 +165,11 @@ int batch_tma_row_align(int precision);
 // Bytes of the device table (instance records and their tensor maps).
 size_t batch_tma_table_bytes(int count);
 // Encodes the tensor maps, builds the block table for z runs of fz planes
-// and copies it to d_table (device, batch_tma_table_bytes); *blocks = blocks
+// in groups of grp runs (0: all runs of a tile one after another) and
+// copies it to d_table (device, batch_tma_table_bytes); *blocks = blocks
 // of one launch.  FP32, FP16-dev, BF16-dev.  Synchronises s.
-cudaError_t batch_tma_build(int precision, const BatchTmaInst* insts, int count, int fz, const void* pool,
-                            void* d_table, int* blocks, cudaStream_t s);
+cudaError_t batch_tma_build(int precision, const BatchTmaInst* insts, int count, int fz, int grp,
+                            const void* pool, void* d_table, int* blocks, cudaStream_t s);
 // One step of every instance: padded pool arrays cur -> cur ^ 1.
 cudaError_t batch_tma_launch(int precision, const void* d_table, int count, int blocks, void* pool, int cur,
                              int* flag, cudaStream_t s);

@@ -212,8 +212,8 @@ def test_persistent_batch_barrier_timeout(L, form):
 TMA_SHAPES = SHAPES + ((63, 9, 7), (64, 8, 5), (65, 13, 6), (130, 20, 37))
 
 
-@pytest.mark.parametrize("precision", ["f32", "f16dev", "bf16dev"])
-def test_padded_tma_batch_equals_per_element_batch(L, precision):
+@pytest.mark.parametrize("precision,sr", [("f32", 1), ("f16dev", 1), ("bf16dev", 1), ("f16dev", 0), ("bf16dev", 0)])
+def test_padded_tma_batch_equals_per_element_batch(L, precision, sr):
     insts = []
     for k, (nx, ny, nz) in enumerate(TMA_SHAPES):
         R0 = max(1.0, min(ny, nz) / 4.0)
@@ -223,6 +223,7 @@ def test_padded_tma_batch_equals_per_element_batch(L, precision):
     for forms in ((1, 1), (2, 2), (2, 1), (1, 2)):
         with L.Batch(insts, precision=precision) as b:
             b.set_option("fused_fz", 4)
+            b.set_option("stochastic_rounding", sr)
             b.init()
             b.set_option("fused", forms[0])
             b.step(5)
