@@ -401,6 +401,9 @@ int ensure_padded(lbm_batch_ctx* b) {
       off += 2LL * Q * b->px[k] * g.ny * g.nz;   // a multiple of al: every instance starts on 16 bytes
     }
     BCK(cudaMalloc(&b->pool_p, (size_t)off * e));
+    b->ttable_ok = false;
+  }
+  if (!b->d_ttable) {
     BCK(cudaMalloc(&b->d_ttable, batch_tma_table_bytes(b->count)));
     b->ttable_ok = false;
   }
