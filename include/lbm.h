@@ -327,8 +327,9 @@ int lbm_batch_set_stream(lbm_batch b, void *stream);
  * read once per step (Eqs. 2-6 as in lbm_step).  2: the TMA-staged step of
  * lbm_step on 64 x 4 (FP32) or 64 x 8 (2-byte) tiles, for which the batch
  * keeps a second pool with every row padded to a 16-byte multiple and moves
- * the state there and back by 2-D copies when the step form changes or
- * another call reads it; FP64 and instances whose padded planes pass 2^31
+ * the state there and back by 2-D copies when the step form changes (a
+ * read of one instance - diagnostics, populations - copies that instance
+ * out, and the padded pool stays current); FP64 and instances whose padded planes pass 2^31
  * elements take form 1.  1: blocks of 32 x 8 nodes, one per thread, copying
  * the populations element by element (instances up to 113 M nodes, larger
  * ones take the two kernels).  0: a psi pass and a collide-stream kernel per

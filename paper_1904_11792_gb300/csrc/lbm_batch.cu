@@ -259,6 +259,7 @@ struct lbm_batch_ctx {
   int tblocks = 0;
   bool ttable_ok = false;
   bool padded = false;             // the current state lives in pool_p
+  std::vector<char> contig_ok;     // while padded: instance k's unpadded copy is current too
   bool persistent = false;         // option "persistent": n steps per cooperative launch
   unsigned* d_tickets = nullptr;   // its per-step work-item counters
   int tickets_n = 0;
@@ -364,27 +365,39 @@ bool tma_applicable(const lbm_batch_ctx* b) {
 
 bool tma_form(const lbm_batch_ctx* b) { return b->fused && b->tma && tma_applicable(b); }
 
-// Copies the current array of every instance between the pools.
-int convert_state(lbm_batch_ctx* b, bool to_padded) {
+// Copies the current array of instance k between the pools.
+int copy_instance(lbm_batch_ctx* b, int k, bool to_padded) {
   const size_t e = elem_size(b->precision);
-  for (int k = 0; k < b->count; ++k) {
-    const BatchInst& I = b->inst[k];
-    const size_t w = (size_t)I.g.nx * e, rows = (size_t)Q * I.g.ny * I.g.nz;
-    char* c = (char*)b->pool_f + (size_t)(I.off_f + (long long)b->cur * Q * I.g.N) * e;
-    char* p = (char*)b->pool_p +
-              (size_t)(b->off_p[k] + (long long)b->cur * Q * b->px[k] * I.g.ny * I.g.nz) * e;
-    const size_t pp = (size_t)b->px[k] * e;
-    if (to_padded)
-      BCK(cudaMemcpy2DAsync(p, pp, c, w, w, rows, cudaMemcpyDeviceToDevice, b->stream));
-    else
-      BCK(cudaMemcpy2DAsync(c, w, p, pp, w, rows, cudaMemcpyDeviceToDevice, b->stream));
-  }
-  b->padded = to_padded;
+  const BatchInst& I = b->inst[k];
+  const size_t w = (size_t)I.g.nx * e, rows = (size_t)Q * I.g.ny * I.g.nz;
+  char* c = (char*)b->pool_f + (size_t)(I.off_f + (long long)b->cur * Q * I.g.N) * e;
+  char* p = (char*)b->pool_p + (size_t)(b->off_p[k] + (long long)b->cur * Q * b->px[k] * I.g.ny * I.g.nz) * e;
+  const size_t pp = (size_t)b->px[k] * e;
+  if (to_padded)
+    BCK(cudaMemcpy2DAsync(p, pp, c, w, w, rows, cudaMemcpyDeviceToDevice, b->stream));
+  else
+    BCK(cudaMemcpy2DAsync(c, w, p, pp, w, rows, cudaMemcpyDeviceToDevice, b->stream));
   return LBM_OK;
 }
 
-// The state in the unpadded pool (every path but the padded single pass).
-int ensure_contig(lbm_batch_ctx* b) { return b->padded ? convert_state(b, false) : LBM_OK; }
+// Instance k's current state in the unpadded pool, for a call that reads
+// it (diagnostics, populations); the padded pool stays the state's home.
+int ensure_contig_instance(lbm_batch_ctx* b, int k) {
+  if (!b->padded || b->contig_ok[k]) return LBM_OK;
+  if (int rc = copy_instance(b, k, false)) return rc;
+  b->contig_ok[k] = 1;
+  return LBM_OK;
+}
+
+// The state back in the unpadded pool (every step form but the padded
+// single pass).
+int ensure_contig(lbm_batch_ctx* b) {
+  if (!b->padded) return LBM_OK;
+  for (int k = 0; k < b->count; ++k)
+    if (int rc = ensure_contig_instance(b, k)) return rc;
+  b->padded = false;
+  return LBM_OK;
+}
 
 // The padded pool, its tensor maps and block table, and the state in it.
 int ensure_padded(lbm_batch_ctx* b) {
@@ -419,7 +432,13 @@ int ensure_padded(lbm_batch_ctx* b) {
                         b->stream));
     b->ttable_ok = true;
   }
-  return b->padded ? LBM_OK : convert_state(b, true);
+  if (!b->padded) {
+    for (int k = 0; k < b->count; ++k)
+      if (int rc = copy_instance(b, k, true)) return rc;
+    b->padded = true;
+    b->contig_ok.assign(b->count, 1);   // both copies current until the next step
+  }
+  return LBM_OK;
 }
 
 bool batch_sr(const lbm_batch_ctx* b) {
@@ -432,6 +451,7 @@ int enqueue_batch_step(lbm_batch_ctx* b, cudaStream_t s, int cur) {
   const bool fused_fits = 19LL * b->max_nodes <= 0x7fffffffLL;
   if (tma_form(b))
     BCK(batch_tma_launch(b->precision, b->d_ttable, b->count, b->tblocks, b->pool_p, cur, b->d_flag, s));
+  // (the caller marks the unpadded copies stale: lbm_batch_step)
   else if (b->fused && fused_fits)
     BCK(batch_fused_launch(b->precision, b->d_ginst, b->count, b->gblocks, b->pool_f, cur, b->d_flag, s));
   else
@@ -714,6 +734,7 @@ int lbm_batch_step(lbm_batch b, int n) {
   if (n > 0) {
     const int rc = tma_form(b) ? ensure_padded(b) : ensure_contig(b);
     if (rc) return rc;
+    if (b->padded) b->contig_ok.assign(b->count, 0);   // the steps below change the padded state
   }
   while (n > 0 && b->persistent && b->fused && (tma_form(b) || 19LL * b->max_nodes <= 0x7fffffffLL)) {
     // up to kPersistSteps steps in one cooperative launch of persistent blocks
@@ -793,7 +814,7 @@ int lbm_batch_sync(lbm_batch b) {
 
 int lbm_batch_get_populations(lbm_batch b, int k, double* host) {
   if (!b || !host || k < 0 || k >= b->count) return bfail(LBM_ERR_ARG, "bad batch, instance or buffer");
-  if (int rc = ensure_contig(b)) return rc;
+  if (int rc = ensure_contig_instance(b, k)) return rc;
   if (!b->d_plane) BCK(cudaMalloc(&b->d_plane, sizeof(double) * b->max_nodes));
   View v = view_of(b, k);
   for (int a = 0; a < Q; ++a) {
@@ -807,7 +828,7 @@ int lbm_batch_get_populations(lbm_batch b, int k, double* host) {
 
 int lbm_batch_diagnostics(lbm_batch b, int k, lbm_diag* out, int want_ccl) {
   if (!b || !out || k < 0 || k >= b->count) return bfail(LBM_ERR_ARG, "bad batch, instance or output");
-  if (int rc = ensure_contig(b)) return rc;
+  if (int rc = ensure_contig_instance(b, k)) return rc;
   View v = view_of(b, k);
   const size_t need = diag_scratch_doubles(v.g);
   if (need > b->scratch_doubles) {

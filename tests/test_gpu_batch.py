@@ -207,8 +207,9 @@ def test_persistent_batch_barrier_timeout(L, form):
 # tiles of 64 x 4 (64 x 8 for 2-byte storage) cut at the instance's edges)
 # against the per-element single pass (fused = 1), bitwise: the shapes above
 # plus x extents around the 64-node tile (63, 64, 65, 130) and y extents that
-# leave a partial tile row; an odd number of steps over two calls, and a run
-# that switches form in the middle (the state moves between the pools).
+# leave a partial tile row; an odd number of steps over two calls, a run
+# that switches form in the middle (the state moves between the pools) and
+# diagnostics read in the middle.
 TMA_SHAPES = SHAPES + ((63, 9, 7), (64, 8, 5), (65, 13, 6), (130, 20, 37))
 
 
@@ -227,10 +228,14 @@ def test_padded_tma_batch_equals_per_element_batch(L, precision, sr):
             b.init()
             b.set_option("fused", forms[0])
             b.step(5)
+            # a read of two instances in the middle (from the padded form:
+            # their states are copied out, the padded pool stays current)
+            mid = [b.diagnostics(k)["mass"] for k in (1, len(insts) - 1)]
             b.set_option("fused", forms[1])
             b.step(6)
             b.sync()
-            res.append([b.populations(k) for k in range(len(insts))])
-    for r in res[1:]:
+            res.append(([b.populations(k) for k in range(len(insts))], mid))
+    for r, m in res[1:]:
+        assert m == res[0][1]
         for k in range(len(insts)):
-            np.testing.assert_array_equal(r[k], res[0][k])
+            np.testing.assert_array_equal(r[k], res[0][0][k])
