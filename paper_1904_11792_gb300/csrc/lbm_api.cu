@@ -1084,3 +1084,13 @@ int lbm_kernel_time(lbm_handle h, int k, long long* launches, double* ms) {
 }
 
 }  // extern "C"
+
+namespace lbm {
+// The allocation cap of LBM_ALLOC_CAP_BYTES for one request of `bytes`
+// (the batched form's pools; the single lattice also counts what it holds).
+bool alloc_over_cap(size_t bytes) {
+  const char* cap = std::getenv("LBM_ALLOC_CAP_BYTES");
+  return cap && *cap && bytes > std::strtoull(cap, nullptr, 10);
+}
+}  // namespace lbm
+

@@ -413,6 +413,7 @@ int ensure_padded(lbm_batch_ctx* b) {
       b->off_p[k] = off;
       off += 2LL * Q * b->px[k] * g.ny * g.nz;   // a multiple of al: every instance starts on 16 bytes
     }
+    if (alloc_over_cap((size_t)off * e)) return bfail(LBM_ERR_OOM, "the padded pool exceeds LBM_ALLOC_CAP_BYTES");
     BCK(cudaMalloc(&b->pool_p, (size_t)off * e));
     b->ttable_ok = false;
   }
@@ -602,6 +603,11 @@ lbm_batch lbm_batch_create(const lbm_instance* inst, int count, int precision, i
   }
   if (err == cudaSuccess) err = cudaMalloc(&b->d_inst, sizeof(BatchInst) * count);
   if (err == cudaSuccess) err = cudaMalloc(&b->d_ginst, sizeof(GInst) * count);
+  if (err == cudaSuccess && alloc_over_cap(b->pool_f_bytes + b->pool_psi_bytes)) {
+    bfail(LBM_ERR_OOM, "the batch's pools exceed LBM_ALLOC_CAP_BYTES");
+    lbm_batch_destroy(b);
+    return nullptr;
+  }
   if (err == cudaSuccess) err = cudaMalloc(&b->pool_f, b->pool_f_bytes);
   if (err == cudaSuccess) err = cudaMalloc(&b->pool_psi, b->pool_psi_bytes);
   // d_flag[0] the numeric flag, [2] the stochastic-rounding salt, [4] the

@@ -180,6 +180,10 @@ cudaError_t batch_tma_persist_launch(int precision, const void* d_table, int cou
                                      int cur, int nsteps, unsigned* bar, unsigned* tickets, int* flag,
                                      unsigned long long stall_ns, cudaStream_t s);
 
+// True if LBM_ALLOC_CAP_BYTES is set and a device allocation of `bytes`
+// exceeds it (out-of-memory handling without exhausting a GPU).
+bool alloc_over_cap(size_t bytes);
+
 }  // namespace lbm
 
 // ---- the handle -------------------------------------------------------------

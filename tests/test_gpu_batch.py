@@ -239,3 +239,29 @@ def test_padded_tma_batch_equals_per_element_batch(L, precision, sr):
         assert m == res[0][1]
         for k in range(len(insts)):
             np.testing.assert_array_equal(r[k], res[0][0][k])
+
+
+# Out-of-memory handling without exhausting the GPU: the allocation cap
+# (LBM_ALLOC_CAP_BYTES) applies to the batch's pools at creation and to the
+# padded pool of form 2 at its first step; the batch stays usable in form 1.
+def test_batch_alloc_cap_gives_oom(L, monkeypatch):
+    insts = [dict(nx=3, ny=12, nz=10, tau=0.9, G=-5.5, R0=2.0, lam=3.0, eps=0.1, phase=0.0, rho_l=2.5,
+                  rho_v=0.15, width=2.0)]
+    monkeypatch.setenv("LBM_ALLOC_CAP_BYTES", "1024")
+    with pytest.raises(L.LbmError) as ei:
+        L.Batch(insts)
+    assert "LBM_ALLOC_CAP_BYTES" in str(ei.value)   # creation returns no handle, only the message
+    # FP32, nx = 3: the padded rows (4 elements) make the padded pool 4/3 of
+    # the A-B pool, above a cap 1.2 times the pools' size
+    n = 3 * 12 * 10
+    monkeypatch.setenv("LBM_ALLOC_CAP_BYTES", str(int(1.2 * (2 * 19 * n * 4 + n * 4))))
+    with L.Batch(insts) as b:
+        b.init()
+        with pytest.raises(L.LbmError) as ei:
+            b.step(2)
+        assert ei.value.status == L.LBM_ERR_OOM
+        b.set_option("fused", 1)
+        b.step(2)
+        b.sync()
+        assert b.diagnostics(0)["numeric_ok"] == 1
+    monkeypatch.delenv("LBM_ALLOC_CAP_BYTES")
