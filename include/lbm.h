@@ -325,7 +325,8 @@ int lbm_batch_set_stream(lbm_batch b, void *stream);
  * short at its edges, march through a run of z planes and compute psi of
  * the tile and its one-node ring in shared memory, so the populations are
  * read once per step (Eqs. 2-6 as in lbm_step).  2: the TMA-staged step of
- * lbm_step on 64 x 4 (FP32) or 64 x 8 (2-byte) tiles, for which the batch
+ * lbm_step on 64 x 4 (FP32) or 32 x 16 (2-byte) tiles (option "tile_width"),
+ * for which the batch
  * keeps a second pool with every row padded to a 16-byte multiple and moves
  * the state there and back by 2-D copies when the step form changes (a
  * read of one instance - diagnostics, populations - copies that instance
@@ -344,7 +345,10 @@ int lbm_batch_set_stream(lbm_batch b, void *stream);
  * barrier and the others give up after this long), "fused_fz" (z planes
  * per block of the single-pass step, default 16), "fused_group" (form 2:
  * z runs per block-order group, as lbm_set_option's; 0, the default: all
- * runs of a tile one after another), "graph" (0/1),
+ * runs of a tile one after another), "tile_width" (form 2: 64 - tiles of
+ * 64 x 4 (FP32) or 64 x 8 (2-byte) nodes -, 32 - tiles of 32 x 8 or 32 x
+ * 16 -, or 0, the default: 64 for FP32, 32 for 2-byte storage; the same
+ * results), "graph" (0/1),
  * "stochastic_rounding" (0/1, as lbm_set_option), and for the two-kernel
  * step "occupancy" (2, 3, 4; default 2), "vector" (0/1, default 1:
  * instances with even nx update two nodes per thread), "block_x",

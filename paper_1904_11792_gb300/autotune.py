@@ -163,12 +163,12 @@ def apply(lat: "L.Lattice", choice: dict) -> None:
 
 
 def tune_batch(batch: "L.Batch", blocks=((256, 1, 1), (128, 1, 1), (64, 1, 1)), occupancies=(2, 3, 4),
-               steps=20, verbose=False, fused_runs=(8, 16, 32), fused_forms=(2, 1)) -> dict:
+               steps=20, verbose=False, fused_runs=(8, 16, 32), fused_forms=(2, 1), tile_widths=(64, 32)) -> dict:
     """Times the batched step - the single-pass forms (2: TMA on padded
-    rows, with z runs in groups of one or all of a tile's runs; 1:
-    per-element copies) for each z run length, and the two-kernel
-    form for each block size / occupancy - and leaves the batch configured
-    with the fastest; returns the choice."""
+    rows, on tiles of each width in tile_widths, with z runs in groups of
+    one or all of a tile's runs; 1: per-element copies) for each z run
+    length, and the two-kernel form for each block size / occupancy - and
+    leaves the batch configured with the fastest; returns the choice."""
     import torch
     best = None
 
@@ -182,8 +182,9 @@ def tune_batch(batch: "L.Batch", blocks=((256, 1, 1), (128, 1, 1), (64, 1, 1)), 
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / steps
 
-    cands = [dict(fused=form, fused_fz=fz, fused_group=grp, block=[0, 0, 0], occupancy=0) for form in fused_forms
-             for fz in fused_runs for grp in ((0, 1) if form == 2 else (0,))]
+    cands = [dict(fused=form, fused_fz=fz, fused_group=grp, tile_width=tw, block=[0, 0, 0], occupancy=0)
+             for form in fused_forms for fz in fused_runs for grp in ((0, 1) if form == 2 else (0,))
+             for tw in (tile_widths if form == 2 else (0,))]
     cands += [dict(fused=0, fused_fz=0, block=list(b), occupancy=occ) for occ in occupancies for b in blocks]
     for c in cands:
         apply_batch(batch, c)
@@ -203,6 +204,7 @@ def apply_batch(batch: "L.Batch", choice: dict) -> None:
     if choice.get("fused"):
         batch.set_option("fused_fz", int(choice["fused_fz"]))
         batch.set_option("fused_group", int(choice.get("fused_group", 0)))
+        batch.set_option("tile_width", int(choice.get("tile_width", 0)))
         return
     for k, v in zip(("block_x", "block_y", "block_z"), (1, 1, 1)):
         batch.set_option(k, v)

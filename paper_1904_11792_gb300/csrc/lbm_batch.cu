@@ -249,6 +249,7 @@ struct lbm_batch_ctx {
   bool fused = true;               // option "fused": the single-pass step
   int gfz = 16;                    // its z run length (option "fused_fz")
   int ggrp = 0;                    // runs per block-order group of the padded form (option "fused_group")
+  int tma_w = 0;                   // tile width of the padded form, 32 or 64, 0: by storage (option "tile_width")
   bool tma = true;                 // option "fused" = 2 (the default): the single pass on padded rows (TMA)
   // its own pool, rows padded to 16 bytes, which holds the state while that
   // form steps (the state moves between the pools by 2-D copies)
@@ -256,7 +257,7 @@ struct lbm_batch_ctx {
   std::vector<long long> off_p;
   std::vector<int> px;
   void* d_ttable = nullptr;        // its tensor maps and block table
-  int tblocks = 0;
+  BatchTmaPlan tplan{};            // its launch
   bool ttable_ok = false;
   bool padded = false;             // the current state lives in pool_p
   std::vector<char> contig_ok;     // while padded: instance k's unpadded copy is current too
@@ -399,7 +400,15 @@ int ensure_contig(lbm_batch_ctx* b) {
   return LBM_OK;
 }
 
-// The padded pool, its tensor maps and block table, and the state in it.
+
+// Tile width of the padded form: 64 for FP32 storage, 32 for 2-byte
+// storage (on the 48-ligament sweep on GB300, 32-wide tiles leave fewer
+// lanes idle at the instances' x ends, 3 % faster for FP16, but their
+// narrower rows cost the bandwidth-bound FP32 step more DRAM traffic and
+// bandwidth: 16 % slower).
+int table_width(const lbm_batch_ctx* b) { return b->tma_w ? b->tma_w : (b->precision == LBM_F32 ? 64 : 32); }
+
+// The padded pool, its tensor maps and block tables, and the state in it.
 int ensure_padded(lbm_batch_ctx* b) {
   const size_t e = elem_size(b->precision);
   if (!b->pool_p) {
@@ -429,8 +438,8 @@ int ensure_padded(lbm_batch_ctx* b) {
       t[k].off_f = b->off_p[k];
       t[k].px = b->px[k];
     }
-    BCK(batch_tma_build(b->precision, t.data(), b->count, b->gfz, b->ggrp, b->pool_p, b->d_ttable, &b->tblocks,
-                        b->stream));
+    BCK(batch_tma_build(b->precision, table_width(b), t.data(), b->count, b->gfz, b->ggrp, b->pool_p,
+                        b->d_ttable, &b->tplan, b->stream));
     b->ttable_ok = true;
   }
   if (!b->padded) {
@@ -451,7 +460,7 @@ int enqueue_batch_step(lbm_batch_ctx* b, cudaStream_t s, int cur) {
   // offsets: instances of 113 M nodes or more take the two kernels
   const bool fused_fits = 19LL * b->max_nodes <= 0x7fffffffLL;
   if (tma_form(b))
-    BCK(batch_tma_launch(b->precision, b->d_ttable, b->count, b->tblocks, b->pool_p, cur, b->d_flag, s));
+    BCK(batch_tma_launch(b->precision, b->d_ttable, b->tplan, b->pool_p, cur, b->d_flag, s));
   // (the caller marks the unpadded copies stale: lbm_batch_step)
   else if (b->fused && fused_fits)
     BCK(batch_fused_launch(b->precision, b->d_ginst, b->count, b->gblocks, b->pool_f, cur, b->d_flag, s));
@@ -673,6 +682,11 @@ int lbm_batch_set_option(lbm_batch b, const char* key, double v) {
     b->persist_stall_ms = v;
     return LBM_OK;
   }
+  if (k == "tile_width") {
+    if (v != 0.0 && v != 32.0 && v != 64.0) return bfail(LBM_ERR_ARG, "tile_width must be 0, 32 or 64");
+    b->tma_w = (int)v;
+    return layout_tiles(b);
+  }
   if (k == "fused_group") {
     const long long n = (long long)v;
     if (n < 0 || n > 1 << 20 || (double)n != v) return bfail(LBM_ERR_ARG, "fused_group must be a non-negative integer");
@@ -752,7 +766,7 @@ int lbm_batch_step(lbm_batch b, int n) {
     }
     const unsigned long long stall_ns = (unsigned long long)(b->persist_stall_ms * 1e6);
     if (tma_form(b))
-      BCK(batch_tma_persist_launch(b->precision, b->d_ttable, b->count, b->tblocks, b->pool_p, b->cur, m,
+      BCK(batch_tma_persist_launch(b->precision, b->d_ttable, b->tplan, b->pool_p, b->cur, m,
                                    (unsigned*)(b->d_flag + 4), b->d_tickets, b->d_flag, stall_ns, b->stream));
     else
       BCK(batch_persist_launch(b->precision, b->d_ginst, b->count, b->gblocks, b->pool_f, b->cur, m,

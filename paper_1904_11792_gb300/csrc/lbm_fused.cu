@@ -134,9 +134,13 @@ cudaError_t fused_device_info(int* slots_per_sm, int* sms) {
   std::lock_guard<std::mutex> lock(mu);
   if (!slots_of[dev]) {
     for (const void* k : {(const void*)fused_kernel<P, false, COLL_SRT>, (const void*)fused_kernel<P, true, COLL_SRT>,
-                          (const void*)fused_kernel<P, false, COLL_MRT>, (const void*)fused_kernel<P, true, COLL_MRT>,
-                          (const void*)bfused_kernel<P>, (const void*)bpersist_kernel<P>})
+                          (const void*)fused_kernel<P, false, COLL_MRT>, (const void*)fused_kernel<P, true, COLL_MRT>})
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
+    for (const void* k : {(const void*)bfused_kernel<P, TX>, (const void*)bpersist_kernel<P, TX>})
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
+    for (const void* k : {(const void*)bfused_kernel<P, 32>, (const void*)bpersist_kernel<P, 32>})
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FusedShape<P, 32>::smem);
     int n_sm = 0, slots = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
@@ -257,10 +261,10 @@ cudaError_t launch_fused(int precision, const Geom& g, const Phys& ph, const voi
 
 namespace {
 
-template <int P>
+template <int P, int W>
 cudaError_t batch_tma_build_t(const BatchTmaInst* in, int count, int fz_req, int grp_req, const void* pool,
-                              void* d_table, int* blocks_out, cudaStream_t s) {
-  using S = FusedShape<P>;
+                              void* d_table, BatchTmaPlan* plan, cudaStream_t s) {
+  using S = FusedShape<P, W>;
   int slots_per_sm = 0, sms = 0;
   cudaError_t e = fused_device_info<P>(&slots_per_sm, &sms);   // the kernels' shared-memory limit
   if (e != cudaSuccess) return e;
@@ -283,7 +287,7 @@ cudaError_t batch_tma_build_t(const BatchTmaInst* in, int count, int fz_req, int
     t.px = b.px;
     t.dstride = (long long)b.px * b.g.ny * b.g.nz;
     t.maps = d_maps + 2 * k;
-    t.ntx = (b.g.nx + TX - 1) / TX;
+    t.ntx = (b.g.nx + W - 1) / W;
     const int nty = (b.g.ny + S::TY - 1) / S::TY;
     t.fz = std::min(fz_req > 0 ? fz_req : 16, b.g.nz);
     t.nchunks = (b.g.nz + t.fz - 1) / t.fz;
@@ -294,18 +298,83 @@ cudaError_t batch_tma_build_t(const BatchTmaInst* in, int count, int fz_req, int
     for (int arr = 0; arr < 2; ++arr) {
       const void* base = (const unsigned char*)pool + (size_t)(b.off_f + (long long)arr * Q * t.dstride) * es;
       Maps& m = tm[2 * k + arr];
-      e = make_map(&m.interior, P, b.g, base, TX, S::TY, b.px);
-      if (e == cudaSuccess) e = make_map(&m.row, P, b.g, base, TX, 1, b.px);
+      e = make_map(&m.interior, P, b.g, base, W, S::TY, b.px);
+      if (e == cudaSuccess) e = make_map(&m.row, P, b.g, base, W, 1, b.px);
       if (e == cudaSuccess) e = make_map(&m.col, P, b.g, base, cw, S::TY, b.px);
       if (e == cudaSuccess) e = make_map(&m.cor, P, b.g, base, cw, 1, b.px);
       if (e != cudaSuccess) return e;
     }
   }
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  *blocks_out = (int)blocks;
+  plan->width = W;
+  plan->count = count;
+  plan->blocks = (int)blocks;
   e = cudaMemcpyAsync(d_table, host.data(), host.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host table goes out of scope
   return e;
+}
+
+template <int P>
+cudaError_t batch_tma_build_w(int tile_w, const BatchTmaInst* insts, int count, int fz, int grp, const void* pool,
+                              void* d_table, BatchTmaPlan* plan, cudaStream_t s) {
+  if (tile_w == 32) return batch_tma_build_t<P, 32>(insts, count, fz, grp, pool, d_table, plan, s);
+  if (tile_w == TX) return batch_tma_build_t<P, TX>(insts, count, fz, grp, pool, d_table, plan, s);
+  return cudaErrorInvalidValue;
+}
+
+template <int P, int W>
+void batch_tma_launch_t(const void* d_table, const BatchTmaPlan& plan, void* pool, int cur, int* flag,
+                        cudaStream_t s) {
+  using S = FusedShape<P, W>;
+  bfused_kernel<P, W><<<plan.blocks, S::NT, S::smem, s>>>(reinterpret_cast<const BTInst*>(d_table), plan.count,
+                                                          (typename Prec<P>::T*)pool, cur, flag);
+}
+
+template <int P>
+cudaError_t batch_tma_launch_w(const void* d_table, const BatchTmaPlan& plan, void* pool, int cur, int* flag,
+                               cudaStream_t s) {
+  if (plan.width == 32)
+    batch_tma_launch_t<P, 32>(d_table, plan, pool, cur, flag, s);
+  else if (plan.width == TX)
+    batch_tma_launch_t<P, TX>(d_table, plan, pool, cur, flag, s);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+template <int P, int W>
+cudaError_t batch_tma_persist_t(const void* d_table, const BatchTmaPlan& plan, void* pool, int cur, int nsteps,
+                                unsigned* bar, unsigned* tickets, int* flag, unsigned long long stall_ns,
+                                cudaStream_t s) {
+  using S = FusedShape<P, W>;
+  using T = typename Prec<P>::T;
+  int slots_per_sm = 0, sms = 0, per_sm = 0;
+  cudaError_t e = fused_device_info<P>(&slots_per_sm, &sms);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bpersist_kernel<P, W>, S::NT, S::smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  int items = plan.blocks, count = plan.count;
+  const int grid = std::min(items, per_sm * sms);
+  e = cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tickets, 0, sizeof(unsigned) * (size_t)nsteps, s);
+  if (e != cudaSuccess) return e;
+  const BTInst* t = reinterpret_cast<const BTInst*>(d_table);
+  T* pf = (T*)pool;
+  void* args[] = {(void*)&t, (void*)&count, (void*)&pf, (void*)&cur, (void*)&nsteps,
+                  (void*)&items, (void*)&bar, (void*)&tickets, (void*)&flag, (void*)&stall_ns};
+  return cudaLaunchCooperativeKernel((const void*)bpersist_kernel<P, W>, dim3(grid), dim3(S::NT), args, S::smem, s);
+}
+
+template <int P>
+cudaError_t batch_tma_persist_w(const void* d_table, const BatchTmaPlan& plan, void* pool, int cur, int nsteps,
+                                unsigned* bar, unsigned* tickets, int* flag, unsigned long long stall_ns,
+                                cudaStream_t s) {
+  if (plan.width == 32)
+    return batch_tma_persist_t<P, 32>(d_table, plan, pool, cur, nsteps, bar, tickets, flag, stall_ns, s);
+  if (plan.width == TX)
+    return batch_tma_persist_t<P, TX>(d_table, plan, pool, cur, nsteps, bar, tickets, flag, stall_ns, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -316,77 +385,36 @@ size_t batch_tma_table_bytes(int count) {
 
 int batch_tma_row_align(int precision) { return 16 / (int)elem_size(precision); }
 
-cudaError_t batch_tma_build(int precision, const BatchTmaInst* insts, int count, int fz, int grp,
-                            const void* pool, void* d_table, int* blocks, cudaStream_t s) {
+cudaError_t batch_tma_build(int precision, int tile_w, const BatchTmaInst* insts, int count, int fz, int grp,
+                            const void* pool, void* d_table, BatchTmaPlan* plan, cudaStream_t s) {
   switch (precision) {
-    case LBM_F32: return batch_tma_build_t<LBM_F32>(insts, count, fz, grp, pool, d_table, blocks, s);
-    case LBM_F16DEV: return batch_tma_build_t<LBM_F16DEV>(insts, count, fz, grp, pool, d_table, blocks, s);
-    case LBM_BF16DEV: return batch_tma_build_t<LBM_BF16DEV>(insts, count, fz, grp, pool, d_table, blocks, s);
+    case LBM_F32: return batch_tma_build_w<LBM_F32>(tile_w, insts, count, fz, grp, pool, d_table, plan, s);
+    case LBM_F16DEV: return batch_tma_build_w<LBM_F16DEV>(tile_w, insts, count, fz, grp, pool, d_table, plan, s);
+    case LBM_BF16DEV: return batch_tma_build_w<LBM_BF16DEV>(tile_w, insts, count, fz, grp, pool, d_table, plan, s);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t batch_tma_launch(int precision, const void* d_table, int count, int blocks, void* pool, int cur,
+cudaError_t batch_tma_launch(int precision, const void* d_table, const BatchTmaPlan& plan, void* pool, int cur,
                              int* flag, cudaStream_t s) {
-  const BTInst* t = reinterpret_cast<const BTInst*>(d_table);
   switch (precision) {
-    case LBM_F32:
-      bfused_kernel<LBM_F32><<<blocks, FusedShape<LBM_F32>::NT, FusedShape<LBM_F32>::smem, s>>>(t, count,
-                                                                                             (float*)pool, cur, flag);
-      break;
-    case LBM_F16DEV:
-      bfused_kernel<LBM_F16DEV><<<blocks, FusedShape<LBM_F16DEV>::NT, FusedShape<LBM_F16DEV>::smem, s>>>(
-          t, count, (__half*)pool, cur, flag);
-      break;
-    case LBM_BF16DEV:
-      bfused_kernel<LBM_BF16DEV><<<blocks, FusedShape<LBM_BF16DEV>::NT, FusedShape<LBM_BF16DEV>::smem, s>>>(
-          t, count, (__nv_bfloat16*)pool, cur, flag);
-      break;
-    default:
-      return cudaErrorInvalidValue;
+    case LBM_F32: return batch_tma_launch_w<LBM_F32>(d_table, plan, pool, cur, flag, s);
+    case LBM_F16DEV: return batch_tma_launch_w<LBM_F16DEV>(d_table, plan, pool, cur, flag, s);
+    case LBM_BF16DEV: return batch_tma_launch_w<LBM_BF16DEV>(d_table, plan, pool, cur, flag, s);
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
-namespace {
-
-template <int P>
-cudaError_t batch_tma_persist_t(const void* d_table, int count, int items, void* pool, int cur, int nsteps,
-                                unsigned* bar, unsigned* tickets, int* flag, unsigned long long stall_ns,
-                                cudaStream_t s) {
-  using S = FusedShape<P>;
-  using T = typename Prec<P>::T;
-  int slots_per_sm = 0, sms = 0, per_sm = 0;
-  cudaError_t e = fused_device_info<P>(&slots_per_sm, &sms);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bpersist_kernel<P>, S::NT, S::smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-  const int grid = std::min(items, per_sm * sms);
-  e = cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(tickets, 0, sizeof(unsigned) * (size_t)nsteps, s);
-  if (e != cudaSuccess) return e;
-  const BTInst* t = reinterpret_cast<const BTInst*>(d_table);
-  T* pf = (T*)pool;
-  void* args[] = {(void*)&t, (void*)&count, (void*)&pf, (void*)&cur, (void*)&nsteps,
-                  (void*)&items, (void*)&bar, (void*)&tickets, (void*)&flag, (void*)&stall_ns};
-  return cudaLaunchCooperativeKernel((const void*)bpersist_kernel<P>, dim3(grid), dim3(S::NT), args, S::smem, s);
-}
-
-}  // namespace
-
-cudaError_t batch_tma_persist_launch(int precision, const void* d_table, int count, int items, void* pool,
+cudaError_t batch_tma_persist_launch(int precision, const void* d_table, const BatchTmaPlan& plan, void* pool,
                                      int cur, int nsteps, unsigned* bar, unsigned* tickets, int* flag,
                                      unsigned long long stall_ns, cudaStream_t s) {
   switch (precision) {
     case LBM_F32:
-      return batch_tma_persist_t<LBM_F32>(d_table, count, items, pool, cur, nsteps, bar, tickets, flag, stall_ns, s);
+      return batch_tma_persist_w<LBM_F32>(d_table, plan, pool, cur, nsteps, bar, tickets, flag, stall_ns, s);
     case LBM_F16DEV:
-      return batch_tma_persist_t<LBM_F16DEV>(d_table, count, items, pool, cur, nsteps, bar, tickets, flag, stall_ns,
-                                             s);
+      return batch_tma_persist_w<LBM_F16DEV>(d_table, plan, pool, cur, nsteps, bar, tickets, flag, stall_ns, s);
     case LBM_BF16DEV:
-      return batch_tma_persist_t<LBM_BF16DEV>(d_table, count, items, pool, cur, nsteps, bar, tickets, flag,
-                                              stall_ns, s);
+      return batch_tma_persist_w<LBM_BF16DEV>(d_table, plan, pool, cur, nsteps, bar, tickets, flag, stall_ns, s);
   }
   return cudaErrorInvalidValue;
 }

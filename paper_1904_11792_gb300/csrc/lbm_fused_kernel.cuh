@@ -50,7 +50,6 @@ namespace {
 constexpr int TX = 64;   // tile along x: 32 lanes x 2 nodes
 constexpr int NB = 2;    // plane buffers
 constexpr int NR = 4;    // psi ring slots
-constexpr int RW = TX + 4;   // ring row: position x - x0 + 2 (pairs start 8-byte aligned)
 constexpr unsigned long long kWaitNs = 2000000000ull;   // a wait on a plane gives up after 2 s
 
 __host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) & ~size_t(127); }
@@ -60,16 +59,22 @@ __host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) & ~si
 // per node: the ring of a 64 x 8 tile is 148 nodes for 512, of a 64 x 4 tile
 // 140 for 256; and the three warps of halo work are three of eight instead
 // of three of four, which the per-plane barrier waited for).
-template <int P> struct FusedShape {
+// W = 32 (the batched step's tiles, of lattices of any length, which waste
+// fewer lanes at their x ends): a warp takes two rows of 16 lanes x 2 nodes,
+// so the same threads cover a 32 x 8 (FP32) or 32 x 16 (2-byte) tile.
+template <int P, int W = TX> struct FusedShape {
   using T = typename Prec<P>::T;
   using C = typename Prec<P>::C;
-  static constexpr int TY = Prec<P>::dev ? 8 : 4;  // tile along y: one warp per row
-  static constexpr int NT = 32 * TY;
+  static_assert(W == 64 || W == 32, "tiles 64 or 32 nodes wide");
+  static constexpr int TXW = W;                     // tile along x
+  static constexpr int NT = 32 * (Prec<P>::dev ? 8 : 4);
+  static constexpr int TY = W == 64 ? NT / 32 : 2 * (NT / 32);   // tile along y: one (W 64) or two rows per warp
+  static constexpr int RWW = W + 4;                 // ring row: position x - x0 + 2 (pairs start 8-byte aligned)
   static constexpr int RH = TY + 2;                 // psi ring rows
   static constexpr int E = sizeof(T);
   static constexpr int CW = 16 / E;                               // one 16-byte TMA unit along x
-  static constexpr size_t int_bytes = (size_t)Q * TY * TX * E;    // box (64, TY, 1, 19)
-  static constexpr size_t row_bytes = (size_t)Q * TX * E;         // box (64, 1, 1, 19)
+  static constexpr size_t int_bytes = (size_t)Q * TY * W * E;     // box (W, TY, 1, 19)
+  static constexpr size_t row_bytes = (size_t)Q * W * E;          // box (W, 1, 1, 19)
   static constexpr size_t col_bytes = (size_t)Q * TY * CW * E;    // box (CW, TY, 1, 19)
   static constexpr size_t cor_bytes = (size_t)Q * CW * E;         // box (CW, 1, 1, 19)
   static constexpr size_t off_int = 0;
@@ -81,7 +86,7 @@ template <int P> struct FusedShape {
   static constexpr size_t cor_stride = align128(cor_bytes);
   static constexpr size_t plane = align128(off_cor + 4 * cor_stride);
   static constexpr size_t off_ring = NB * plane;
-  static constexpr size_t ring_bytes = align128((size_t)NR * RH * RW * sizeof(C));
+  static constexpr size_t ring_bytes = align128((size_t)NR * RH * RWW * sizeof(C));
   static constexpr size_t off_bar = off_ring + ring_bytes;
   static constexpr size_t smem = off_bar + (NB + 1) * sizeof(unsigned long long);   // + the test barrier
   static constexpr unsigned tx_bytes = (unsigned)(int_bytes + 2 * row_bytes + 2 * col_bytes + 4 * cor_bytes);
@@ -137,10 +142,10 @@ struct Maps {
 };
 
 // Issues the nine copies of plane zz into buffer b (one thread).
-template <int P>
+template <int P, int W = TX>
 __device__ __forceinline__ void issue_plane(unsigned char* smem, const Maps& m, int b, int x0, int y0, int xl,
                                             int xr, int ym, int yp, int zz, unsigned long long* bar) {
-  using S = FusedShape<P>;
+  using S = FusedShape<P, W>;
   unsigned char* base = smem + (size_t)b * S::plane;
   // order earlier generic-proxy reads of this buffer before the async writes
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -182,14 +187,16 @@ constexpr int fused_minb() {
   return Prec<P>::dev ? 2 : 3;
 }
 
-// The step of one block: work item u of a lattice (a tile and z run), tensor
-// maps `maps` of its source array, destination array dst with rows of px
-// elements and dstride elements per direction.  BATCH: the lattice is an
+// The step of one block: work item u of a lattice (a tile and z run) among
+// tiles of ntx columns, tensor maps `maps` of its source array, destination
+// array dst with rows of px elements and dstride elements per direction.
+// BATCH: the lattice is an
 // instance of the batched sweep of any size - tiles are cut at its x and y
 // edges (the tensor maps read zeros past them, and nodes there neither
 // store nor write psi), its rows are padded to a 16-byte multiple, and the
 // halo column at x = nx - 1 comes from the 16-byte box that contains it.
-template <int P, bool DIAG, int COLL, bool BATCH, bool SALT_GIVEN = false>
+// W: the tile width (32 only for BATCH).
+template <int P, bool DIAG, int COLL, bool BATCH, int W = TX, bool SALT_GIVEN = false>
 __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, const Phys& ph,
                                            typename Prec<P>::T* dst, int* flag, int ntx, int nchunks, int fz,
                                            int grp, const DiagOut& dg, int u, int px, long long dstride,
@@ -197,11 +204,12 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
   using T = typename Prec<P>::T;
   using C = typename Prec<P>::C;
   using V = typename Pair<P>::V;
-  using S = FusedShape<P>;
-  constexpr int TY = S::TY, RH = S::RH;
-  static_assert(2 * TY * TX * sizeof(double) + 10 * TY * sizeof(double) <= S::ring_bytes,
+  using S = FusedShape<P, W>;
+  constexpr int TY = S::TY, RH = S::RH, RW = S::RWW;
+  static_assert(!DIAG || 2 * TY * TX * sizeof(double) + 10 * TY * sizeof(double) <= S::ring_bytes,
                 "the diagnostics reduction reuses the psi ring");
   static_assert(!(BATCH && (DIAG || COLL != COLL_SRT)), "the batched step is the plain SRT step");
+  static_assert(W == TX || BATCH, "32-wide tiles for the batched step only");
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + S::off_bar);
   C* ring = reinterpret_cast<C*>(smem + S::off_ring);
@@ -216,11 +224,13 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
   const int zg = u / (grp * tiles), r = u - zg * grp * tiles;
   const int gs = min(grp, nchunks - zg * grp);   // runs in this group
   const int chunk = zg * grp + r % gs, xy = r / gs;
-  const int x0 = (xy % ntx) * TX, y0 = (xy / ntx) * TY;
+  const int x0 = (xy % ntx) * W, y0 = (xy / ntx) * TY;
   // tile extent (BATCH: cut at the lattice's edges)
-  const int w = BATCH ? min(TX, g.nx - x0) : TX, h = BATCH ? min(TY, g.ny - y0) : TY;
+  const int w = BATCH ? min(W, g.nx - x0) : W, h = BATCH ? min(TY, g.ny - y0) : TY;
   const int z0 = chunk * fz, z1 = min(z0 + fz, g.nz);
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+  // the thread's nodes: x0 + 2 xi, x0 + 2 xi + 1 of tile row tr
+  const int xi = W == TX ? lane : (lane & 15), tr = W == TX ? ty : 2 * ty + (lane >> 4);
   const int np = (z1 - z0) + 2;        // planes z0 - 1 .. z1, march index k in buffer k % NB
   // Even runs march up (z0 - 1 first), odd runs down (z1 first), so the plane
   // two neighbouring runs share is read by both near the same time (at the
@@ -232,7 +242,7 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
   // of the 16-byte box at xl; the right one, x0 + w, starts a box
   const int xl = x0 == 0 ? (BATCH ? (g.nx - 1) / S::CW * S::CW : g.nx - S::CW) : x0 - S::CW;
   const int lofs = BATCH && x0 == 0 ? g.nx - 1 - xl : S::CW - 1;
-  const int xr = x0 + w == g.nx ? 0 : x0 + TX;
+  const int xr = x0 + w == g.nx ? 0 : x0 + W;
   const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
           s2 = shift_of<P>(7, ph.rho_ref);
   auto zwrap = [&](int p) { return p < 0 ? p + g.nz : (p >= g.nz ? p - g.nz : p); };
@@ -245,17 +255,22 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
   // lanes.  (With scalar arithmetic the 8-row tile spread its halo rows one
   // node per lane over warps 0 - 3, with the scalar cells on warp 4; with
   // paired arithmetic the pair pass is cheaper: 0.9 % faster FP16 step.)
+  // 32-wide tiles: warp 0 takes both rows (16 lanes each), warps 1 (and 2)
+  // the scalar cells.
   // h_off: element offset in a plane buffer (-1: no cell), h_str: stride
   // between directions (one-node cells), h_ring: ring position.
   constexpr int SC = 4 + 2 * TY;                      // corner and column cells
-  constexpr int SW = 2;                               // the warp that takes them
-  static_assert((TY == 4 || TY == 8) && SC <= 32, "halo split for 4- or 8-row tiles");
+  constexpr int SW = W == TX ? 2 : 1;                 // the first warp that takes them
+  static_assert(W == TX ? (TY == 4 || TY == 8) && SC <= 32 : (TY == 8 || TY == 16) && SC <= 64,
+                "halo split for 64 x 4, 64 x 8, 32 x 8 and 32 x 16 tiles");
+  const bool hrow = W == TX ? ty < 2 : ty == 0;       // a thread of the halo rows
   int h_off = -1, h_str = 0, h_ring = 0;
-  if (ty < 2) {
-    h_off = (int)((ty ? S::off_bot : S::off_top) / S::E) + 2 * lane;
-    h_ring = (ty ? h + 1 : 0) * RW + 2 * lane + 2;
-  } else if (ty == SW && lane < SC) {
-    const int c = lane;
+  if (hrow) {
+    const int side = W == TX ? ty : lane >> 4;       // 0: row y0 - 1, 1: row y0 + h
+    h_off = (int)((side ? S::off_bot : S::off_top) / S::E) + 2 * xi;
+    h_ring = (side ? h + 1 : 0) * RW + 2 * xi + 2;
+  } else if (ty >= SW && (ty - SW) * 32 + lane < SC) {
+    const int c = (ty - SW) * 32 + lane;
     if (c < 4) {
       const int side = c >> 1, right = c & 1;   // corners in the copy order of issue_plane
       h_off = (int)((S::off_cor + c * S::cor_stride) / S::E) + (right ? 0 : lofs);
@@ -271,10 +286,10 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
   }
   // BATCH: this thread's nodes x0 + 2 lane (+1) of row y0 + ty lie in the
   // lattice (act: the first, act1: both)
-  const bool act = !BATCH || (ty < h && 2 * lane < w);
-  const bool act1 = !BATCH || (ty < h && 2 * lane + 1 < w);
-  // the halo row cells x0 + 2 lane (+1) of rows y0 - 1 and y0 + h
-  const bool hact = !BATCH || 2 * lane < w, hact1 = !BATCH || 2 * lane + 1 < w;
+  const bool act = !BATCH || (tr < h && 2 * xi < w);
+  const bool act1 = !BATCH || (tr < h && 2 * xi + 1 < w);
+  // the halo row cells x0 + 2 xi (+1) of rows y0 - 1 and y0 + h
+  const bool hact = !BATCH || 2 * xi < w, hact1 = !BATCH || 2 * xi + 1 < w;
 
   // dst + a N, the start of direction a in the destination array: with
   // 2-byte storage (bound by instruction issue) the stores address a
@@ -295,7 +310,7 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
   if (s_abort) return;
   if (tid == 0)
     for (int k = 0; k < NB && k < np; ++k)
-      issue_plane<P>(smem, maps, k, x0, y0, xl, xr, ym, yp, zplane(k), full + k);
+      issue_plane<P, W>(smem, maps, k, x0, y0, xl, xr, ym, yp, zplane(k), full + k);
 
   // the step's stochastic-rounding salt (SALT_GIVEN: by the caller, which
   // runs several steps in one launch)
@@ -327,7 +342,7 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
     float2 fp[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-      cur[a] = *reinterpret_cast<const V*>(buf + (a * TY + ty) * TX + 2 * lane);
+      cur[a] = *reinterpret_cast<const V*>(buf + (a * TY + tr) * W + 2 * xi);
       unpack_shifted<P>(cur[a], a == 0 ? s0 : (a <= 6 ? s1 : s2), fp[a].x, fp[a].y);
     }
     const float2 rr = rho_of<float2>(fp);
@@ -372,20 +387,20 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
     }
     if constexpr (BATCH) {
       if (act1)
-        *reinterpret_cast<float2*>(slot + (ty + 1) * RW + 2 * lane + 2) = make_float2(p0, p1);
+        *reinterpret_cast<float2*>(slot + (tr + 1) * RW + 2 * xi + 2) = make_float2(p0, p1);
       else if (act)
-        slot[(ty + 1) * RW + 2 * lane + 2] = p0;   // the right halo column follows
+        slot[(tr + 1) * RW + 2 * xi + 2] = p0;   // the right halo column follows
     } else if constexpr (sizeof(C) == 4) {
-      *reinterpret_cast<float2*>(slot + (ty + 1) * RW + 2 * lane + 2) = make_float2(p0, p1);
+      *reinterpret_cast<float2*>(slot + (tr + 1) * RW + 2 * xi + 2) = make_float2(p0, p1);
     } else {
-      *reinterpret_cast<double2*>(slot + (ty + 1) * RW + 2 * lane + 2) = make_double2(p0, p1);
+      *reinterpret_cast<double2*>(slot + (tr + 1) * RW + 2 * xi + 2) = make_double2(p0, p1);
     }
     // psi of this thread's halo cells
-    if (ty < 2) {
+    if (hrow) {
       float2 fh[Q];
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
-        unpack_shifted<P>(*reinterpret_cast<const V*>(buf + h_off + a * TX), a == 0 ? s0 : (a <= 6 ? s1 : s2),
+        unpack_shifted<P>(*reinterpret_cast<const V*>(buf + h_off + a * W), a == 0 ? s0 : (a <= 6 ? s1 : s2),
                           fh[a].x, fh[a].y);
       }
       const float2 rh = rho_of<float2>(fh);
@@ -407,13 +422,13 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
     // every psi of plane zplane(k) is in the ring and buffer b is read out
     if (__syncthreads_or(!ok)) break;
     if (tid == 0 && k + NB < np)
-      issue_plane<P>(smem, maps, b, x0, y0, xl, xr, ym, yp, zplane(k + NB), full + b);
+      issue_plane<P, W>(smem, maps, b, x0, y0, xl, xr, ym, yp, zplane(k + NB), full + b);
 
     if (k >= 2 && act) {
-      // collide + stream the two nodes (x0 + 2 lane, y0 + ty) of plane z =
+      // collide + stream the two nodes (x0 + 2 xi, y0 + tr) of plane z =
       // zplane(k - 1); plane z + dz has march index k - 1 + dir dz
       const int z = zplane(k - 1);
-      const int x = x0 + 2 * lane, y = y0 + ty;
+      const int x = x0 + 2 * xi, y = y0 + tr;
       const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x + 2 == g.nx ? 0 : x + 2;
       // right of node 0 (BATCH: x + 1 may be past the lattice's last column)
       const int xr0 = BATCH ? (x + 1 == g.nx ? 0 : x + 1) : x + 1;
@@ -425,7 +440,7 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
       for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
         for (int dz = -1; dz <= 1; ++dz) {
-          const C* row = ring + ((k - 1 + dir * dz) % NR) * RH * RW + (ty + 1 + dy) * RW + 2 * lane + 2;
+          const C* row = ring + ((k - 1 + dir * dz) % NR) * RH * RW + (tr + 1 + dy) * RW + 2 * xi + 2;
           if constexpr (sizeof(C) == 4) {
             const float2 v = *reinterpret_cast<const float2*>(row);
             q[dy + 1][dz + 1][1] = v.x;
@@ -625,54 +640,69 @@ struct BTInst {
   long long dstride;   // elements per direction: px ny nz
   const Maps* maps;    // tensor maps of its arrays 0 and 1 (device memory, 64-byte aligned)
   int px;              // elements per row (nx padded to a 16-byte multiple)
-  int block0;          // first block of the instance
+  int block0;          // first work item of the instance
   int ntx, nchunks, fz, grp;
 };
 
-// The single-pass step of a batch of lattices of any size, their rows
-// padded to 16-byte multiples: one launch, each block finds its instance
-// (the largest block0 <= blockIdx.x) and runs fused_body on it with that
-// instance's tensor maps, which live in global memory (ordered before their
-// use by the tensor-map proxy fence).
-template <int P>
-__global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, false, COLL_SRT>())
-    bfused_kernel(const BTInst* __restrict__ inst, int count, typename Prec<P>::T* pool, int cur, int* flag) {
+// The instance of work item w: the largest block0 <= w.
+__device__ __forceinline__ const BTInst& find_inst(const BTInst* __restrict__ inst, int count, int w) {
   int lo = 0, hi = count - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (inst[mid].block0 <= (int)blockIdx.x) lo = mid;
+    if (inst[mid].block0 <= w) lo = mid;
     else hi = mid - 1;
   }
-  const BTInst& I = inst[lo];
-  const Maps& m = I.maps[cur];
-  if (threadIdx.x == 0) {
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.interior) : "memory");
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.row) : "memory");
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.col) : "memory");
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.cor) : "memory");
-  }
+  return inst[lo];
+}
+
+__device__ __forceinline__ void acquire_maps(const Maps& m) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.interior) : "memory");
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.row) : "memory");
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.col) : "memory");
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.cor) : "memory");
+}
+
+// Work item u of instance I, arrays cur -> cur ^ 1.
+template <int P, int W, bool SALT_GIVEN>
+__device__ __forceinline__ void batch_item(const BTInst& I, int u, typename Prec<P>::T* pool, int cur, int* flag,
+                                           unsigned salt) {
   typename Prec<P>::T* dst = pool + I.off_f + (long long)(cur ^ 1) * Q * I.dstride;
   const DiagOut none{0.0, 0.0, nullptr, nullptr, 0ull};
-  fused_body<P, false, COLL_SRT, true>(m, I.g, I.ph, dst, flag, I.ntx, I.nchunks, I.fz, I.grp, none,
-                                       (int)blockIdx.x - I.block0, I.px, I.dstride);
+  const Maps& m = I.maps[cur];
+  if (threadIdx.x == 0) acquire_maps(m);
+  fused_body<P, false, COLL_SRT, true, W, SALT_GIVEN>(m, I.g, I.ph, dst, flag, I.ntx, I.nchunks, I.fz, I.grp, none,
+                                                      u, I.px, I.dstride, salt);
+}
+
+// The single-pass step of a batch of lattices of any size, their rows
+// padded to 16-byte multiples: one launch, each block finds its instance
+// and runs fused_body on its work item with that instance's tensor maps,
+// which live in global memory (ordered before their use by the tensor-map
+// proxy fence).  W: the tile width the table was built for.
+template <int P, int W>
+__global__ void __launch_bounds__(FusedShape<P, W>::NT, fused_minb<P, false, COLL_SRT>())
+    bfused_kernel(const BTInst* __restrict__ inst, int count, typename Prec<P>::T* pool, int cur, int* flag) {
+  const BTInst& I = find_inst(inst, count, (int)blockIdx.x);
+  batch_item<P, W, false>(I, (int)blockIdx.x - I.block0, pool, cur, flag, 0u);
 }
 
 // nsteps steps of the batched TMA step in one cooperative launch of
 // persistent blocks: in each step a block takes the next work item (from
 // tickets[s], zero before the launch) until none is left and runs fused_body
 // on it (its mbarriers invalidated after each item, the next item
-// initialises them again); grid barriers on *bar separate the steps (bounded:
-// a barrier that waits too long raises the timeout bit and the block
-// returns).  Step s runs arrays cur0 ^ (s & 1) -> the other with salt
-// salt0 + s, salt0 the salt word at the launch (the host advances the word
-// by nsteps after it): the results of nsteps launches of bfused_kernel.
-// stall_test_ns > 0 (a test hook of the failure path): block 0 skips the
-// first barrier, the others give up on it after stall_test_ns.
-template <int P>
-__global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, false, COLL_SRT>())
+// initialises them again); grid barriers on *bar
+// separate the steps (bounded: a barrier that waits too long raises the
+// timeout bit and the block returns).  Step s runs arrays cur0 ^ (s & 1) ->
+// the other with salt salt0 + s, salt0 the salt word at the launch (the host
+// advances the word by nsteps after it): the results of nsteps launches of
+// bfused_kernel.  stall_test_ns > 0 (a test hook of the failure path):
+// block 0 skips the first barrier, the others give up on it after
+// stall_test_ns.
+template <int P, int W>
+__global__ void __launch_bounds__(FusedShape<P, W>::NT, fused_minb<P, false, COLL_SRT>())
     bpersist_kernel(const BTInst* __restrict__ inst, int count, typename Prec<P>::T* pool, int cur0, int nsteps,
                     int items, unsigned* bar, unsigned* tickets, int* flag, unsigned long long stall_test_ns) {
-  using S = FusedShape<P>;
+  using S = FusedShape<P, W>;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + S::off_bar);
   __shared__ int s_item;
@@ -680,7 +710,6 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, false, COLL_S
   unsigned salt0 = 0u;
   if (Prec<P>::dev && ph0.sr) salt0 = *(const volatile unsigned*)ph0.salt;
   const unsigned long long limit = stall_test_ns ? stall_test_ns : kGridWaitNs;
-  const DiagOut none{0.0, 0.0, nullptr, nullptr, 0ull};
   for (int s = 0; s < nsteps; ++s) {
     // one read of the flag for the whole block: every thread returns or none
     if (__syncthreads_or(threadIdx.x == 0 && (*(volatile int*)flag & 2) != 0)) return;
@@ -690,23 +719,8 @@ __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, false, COLL_S
       __syncthreads();
       const int w = s_item;
       if (w >= items) break;
-      int lo = 0, hi = count - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (inst[mid].block0 <= w) lo = mid;
-        else hi = mid - 1;
-      }
-      const BTInst& I = inst[lo];
-      const Maps& m = I.maps[cur];
-      if (threadIdx.x == 0) {
-        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.interior) : "memory");
-        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.row) : "memory");
-        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.col) : "memory");
-        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m.cor) : "memory");
-      }
-      typename Prec<P>::T* dst = pool + I.off_f + (long long)(cur ^ 1) * Q * I.dstride;
-      fused_body<P, false, COLL_SRT, true, true>(m, I.g, I.ph, dst, flag, I.ntx, I.nchunks, I.fz, I.grp, none,
-                                                 w - I.block0, I.px, I.dstride, salt0 + (unsigned)s);
+      const BTInst& I = find_inst(inst, count, w);
+      batch_item<P, W, true>(I, w - I.block0, pool, cur, flag, salt0 + (unsigned)s);
       __syncthreads();   // the item's shared memory, barriers and s_item are done with
       if (threadIdx.x == 0)
         for (int b = 0; b < NB + 1; ++b)

@@ -162,21 +162,25 @@ struct BatchTmaInst {
   int px;
 };
 int batch_tma_row_align(int precision);
+// The launch of one step: tile width (32 or 64), instance records, blocks.
+struct BatchTmaPlan {
+  int width, count, blocks;
+};
 // Bytes of the device table (instance records and their tensor maps).
 size_t batch_tma_table_bytes(int count);
-// Encodes the tensor maps, builds the block table for z runs of fz planes
-// in groups of grp runs (0: all runs of a tile one after another) and
-// copies it to d_table (device, batch_tma_table_bytes); *blocks = blocks
-// of one launch.  FP32, FP16-dev, BF16-dev.  Synchronises s.
-cudaError_t batch_tma_build(int precision, const BatchTmaInst* insts, int count, int fz, int grp,
-                            const void* pool, void* d_table, int* blocks, cudaStream_t s);
+// Encodes the tensor maps, builds the block table for tiles tile_w (32 or
+// 64) nodes wide and z runs of fz planes in groups of grp runs (0: all runs
+// of a tile one after another), and copies it to d_table (device,
+// batch_tma_table_bytes).  FP32, FP16-dev, BF16-dev.  Synchronises s.
+cudaError_t batch_tma_build(int precision, int tile_w, const BatchTmaInst* insts, int count, int fz, int grp,
+                            const void* pool, void* d_table, BatchTmaPlan* plan, cudaStream_t s);
 // One step of every instance: padded pool arrays cur -> cur ^ 1.
-cudaError_t batch_tma_launch(int precision, const void* d_table, int count, int blocks, void* pool, int cur,
+cudaError_t batch_tma_launch(int precision, const void* d_table, const BatchTmaPlan& plan, void* pool, int cur,
                              int* flag, cudaStream_t s);
 // nsteps such steps in one cooperative launch of persistent blocks: grid
 // barriers on *bar (zeroed here), per-step work tickets tickets[nsteps]
 // (zeroed here); stall_ns > 0 is the barrier-timeout test hook.
-cudaError_t batch_tma_persist_launch(int precision, const void* d_table, int count, int items, void* pool,
+cudaError_t batch_tma_persist_launch(int precision, const void* d_table, const BatchTmaPlan& plan, void* pool,
                                      int cur, int nsteps, unsigned* bar, unsigned* tickets, int* flag,
                                      unsigned long long stall_ns, cudaStream_t s);
 

@@ -149,9 +149,10 @@ def test_fused_batch_equals_two_kernel_batch(L, precision):
 # the same), the instance shapes above, odd step counts and calls that
 # continue one another, and fewer persistent blocks than work items (each
 # block takes several tiles and z runs per step).
-@pytest.mark.parametrize("precision,form", [("f64", 1), ("f32", 1), ("f16dev", 1), ("bf16dev", 1),
-                                            ("f32", 2), ("f16dev", 2), ("bf16dev", 2)])
-def test_persistent_batch_equals_per_step_launches(L, precision, form):
+@pytest.mark.parametrize("precision,form,width", [("f64", 1, 0), ("f32", 1, 0), ("f16dev", 1, 0),
+                                                  ("bf16dev", 1, 0), ("f32", 2, 0), ("f16dev", 2, 0),
+                                                  ("bf16dev", 2, 0), ("f32", 2, 64), ("f16dev", 2, 32)])
+def test_persistent_batch_equals_per_step_launches(L, precision, form, width):
     insts = []
     for k, (nx, ny, nz) in enumerate(SHAPES + ((130, 64, 96),)):
         R0 = max(1.0, min(ny, nz) / 4.0)
@@ -161,6 +162,7 @@ def test_persistent_batch_equals_per_step_launches(L, precision, form):
     for persistent in (0, 1):
         with L.Batch(insts, precision=precision) as b:
             b.set_option("fused", form)
+            b.set_option("tile_width", width)
             b.set_option("persistent", persistent)
             b.set_option("fused_fz", 4)
             b.init()
@@ -204,17 +206,21 @@ def test_persistent_batch_barrier_timeout(L, form):
 
 
 # The single pass on padded rows (option fused = 2: per-instance tensor maps,
-# tiles of 64 x 4 (64 x 8 for 2-byte storage) cut at the instance's edges)
-# against the per-element single pass (fused = 1), bitwise: the shapes above
-# plus x extents around the 64-node tile (63, 64, 65, 130) and y extents that
-# leave a partial tile row; an odd number of steps over two calls, a run
-# that switches form in the middle (the state moves between the pools) and
-# diagnostics read in the middle.
-TMA_SHAPES = SHAPES + ((63, 9, 7), (64, 8, 5), (65, 13, 6), (130, 20, 37))
+# tiles cut at the instance's edges: tile_width 64, tiles of 64 x 4 (64 x 8
+# for 2-byte storage); 32, tiles of 32 x 8 (32 x 16); 0, 64 for FP32 and 32
+# for 2-byte storage) against the per-element single pass (fused = 1),
+# bitwise: the shapes above plus x extents around the 32- and 64-node tiles
+# (31, 33, 63, 64, 65, 96, 130) and y extents that leave a partial tile row
+# (9, 13, 17, 33); an odd number of steps over two calls, a run that switches
+# form in the middle (the state moves between the pools) and diagnostics
+# read in the middle.
+TMA_SHAPES = SHAPES + ((63, 9, 7), (64, 8, 5), (65, 13, 6), (130, 20, 37), (31, 17, 5), (96, 33, 4))
 
 
-@pytest.mark.parametrize("precision,sr", [("f32", 1), ("f16dev", 1), ("bf16dev", 1), ("f16dev", 0), ("bf16dev", 0)])
-def test_padded_tma_batch_equals_per_element_batch(L, precision, sr):
+@pytest.mark.parametrize("precision,sr,width", [("f32", 1, 0), ("f16dev", 1, 0), ("bf16dev", 1, 0),
+                                                ("f16dev", 0, 0), ("bf16dev", 0, 0), ("f32", 1, 32),
+                                                ("f16dev", 1, 32), ("f32", 1, 64), ("bf16dev", 0, 64)])
+def test_padded_tma_batch_equals_per_element_batch(L, precision, sr, width):
     insts = []
     for k, (nx, ny, nz) in enumerate(TMA_SHAPES):
         R0 = max(1.0, min(ny, nz) / 4.0)
@@ -224,6 +230,7 @@ def test_padded_tma_batch_equals_per_element_batch(L, precision, sr):
     for forms in ((1, 1), (2, 2), (2, 1), (1, 2)):
         with L.Batch(insts, precision=precision) as b:
             b.set_option("fused_fz", 4)
+            b.set_option("tile_width", width)
             b.set_option("stochastic_rounding", sr)
             b.init()
             b.set_option("fused", forms[0])
