@@ -405,6 +405,30 @@ __device__ __forceinline__ void psi_pair(const Geom& g, const Phys& ph, const ty
   }
 }
 
+// The four populations of slot `a` at x0 .. x0 + 3 of a row (x0 % 4 == 0,
+// 16-byte (FP32) or 8-byte (2-byte) aligned), unpacked and shifted.
+template <int P>
+__device__ __forceinline__ void load_quad(const typename Prec<P>::T* p, float sh, float v[4]) {
+  if constexpr (P == LBM_F32) {
+    const float4 w = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = w.x;
+    v[1] = w.y;
+    v[2] = w.z;
+    v[3] = w.w;
+  } else {
+    const uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
+    typename Pair<P>::V lo, hi;
+    memcpy(&lo, &raw.x, 4);
+    memcpy(&hi, &raw.y, 4);
+    Pair<P>::unpack(lo, v[0], v[1]);
+    Pair<P>::unpack(hi, v[2], v[3]);
+    v[0] += sh;
+    v[1] += sh;
+    v[2] += sh;
+    v[3] += sh;
+  }
+}
+
 // Four nodes i .. i + 3 (i % 4 == 0, nx % 4 == 0, LAYOUT_LOCAL): one 16-byte
 // (FP32) or 8-byte (FP16/BF16) load per population, one 16-byte psi store.
 template <int P>
@@ -417,26 +441,10 @@ __device__ __forceinline__ void psi_quad(const Geom& g, const Phys& ph, const ty
   float fv[4][Q];
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
-    const float sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
-    const typename Prec<P>::T* p = f + (long long)a * g.N + i;
-    if constexpr (P == LBM_F32) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-      fv[0][a] = v.x;
-      fv[1][a] = v.y;
-      fv[2][a] = v.z;
-      fv[3][a] = v.w;
-    } else {
-      const uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
-      typename Pair<P>::V lo, hi;
-      memcpy(&lo, &raw.x, 4);
-      memcpy(&hi, &raw.y, 4);
-      Pair<P>::unpack(lo, fv[0][a], fv[1][a]);
-      Pair<P>::unpack(hi, fv[2][a], fv[3][a]);
-      fv[0][a] += sh;
-      fv[1][a] += sh;
-      fv[2][a] += sh;
-      fv[3][a] += sh;
-    }
+    float v[4];
+    load_quad<P>(f + (long long)a * g.N + i, a == 0 ? s0 : (a <= 6 ? s1 : s2), v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) fv[k][a] = v[k];
   }
   // nodes (0, 1) and (2, 3) as float2 lanes (paired FP32 instructions, the
   // bits of the scalar form)
@@ -444,6 +452,66 @@ __device__ __forceinline__ void psi_quad(const Geom& g, const Phys& ph, const ty
 #pragma unroll
   for (int a = 0; a < Q; ++a) pa[a] = make_float2(fv[0][a], fv[1][a]), pb[a] = make_float2(fv[2][a], fv[3][a]);
   const float2 ra = rho_of<float2>(pa), rb = rho_of<float2>(pb);
+  raise_flag(bad_rho(ra.x) | bad_rho(ra.y) | bad_rho(rb.x) | bad_rho(rb.y), flag);
+  const float2 qa = psi_of2(ra, ph), qb = psi_of2(rb, ph);
+  *reinterpret_cast<float4*>(psi + i) = make_float4(qa.x, qa.y, qb.x, qb.y);
+}
+
+// Four nodes i .. i + 3 in the gather layout (AA before an odd step: slot
+// opp(a) at x - c_a; i % 4 == 0, nx % 4 == 0), for every lane of a warp
+// (live: i < N; the others compute on a valid quad and store nothing).  Per
+// direction one aligned vector load of the quad at x0 in the source row;
+// for c_x = +1 the node x0 - 1 comes from the lane below (its quad's last
+// node), for c_x = -1 the node x0 + 4 from the lane above (its first),
+// except where that lane holds another row or none (lanes 0 and 31, row
+// ends), which load it.  The same values, and psi, as psi_pair.
+template <int P>
+__device__ __forceinline__ void psi_quad_gather(const Geom& g, const Phys& ph, const typename Prec<P>::T* f,
+                                                typename Prec<P>::C* __restrict__ psi, int* __restrict__ flag,
+                                                long long i, bool live) {
+  static_assert(P != LBM_F64, "four-node psi pass is for 4- and 2-byte storage");
+  const float s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
+              s2 = shift_of<P>(7, ph.rho_ref);
+  const int lane = threadIdx.x & 31;
+  const int x0 = (int)(i % g.nx);
+  const long long r = i / g.nx;
+  const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+  const int yv[3] = {y == 0 ? g.ny - 1 : y - 1, y, y == g.ny - 1 ? 0 : y + 1};
+  const int zv[3] = {z == 0 ? g.nz - 1 : z - 1, z, z == g.nz - 1 ? 0 : z + 1};
+  const bool own_lo = lane == 0 || x0 == 0;            // loads x0 - 1 itself
+  const bool own_hi = lane == 31 || x0 + 4 == g.nx;    // loads x0 + 4 itself
+  const int xlo = x0 == 0 ? g.nx - 1 : x0 - 1, xhi = x0 + 4 == g.nx ? 0 : x0 + 4;
+  float fv[4][Q];
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const float sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
+    const typename Prec<P>::T* base = f + (long long)opp(a) * g.N + (long long)g.nx * (yv[1 - cy(a)] + g.ny * zv[1 - cz(a)]);
+    float v[4];
+    load_quad<P>(base + x0, sh, v);
+    if (cx(a) == 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) fv[k][a] = v[k];
+    } else if (cx(a) > 0) {   // x0 - 1 .. x0 + 2
+      float e = __shfl_up_sync(0xffffffffu, v[3], 1);
+      if (own_lo) e = load_shifted<P>(base + xlo, sh);
+      fv[0][a] = e;
+      fv[1][a] = v[0];
+      fv[2][a] = v[1];
+      fv[3][a] = v[2];
+    } else {                  // x0 + 1 .. x0 + 4
+      float e = __shfl_down_sync(0xffffffffu, v[0], 1);
+      if (own_hi) e = load_shifted<P>(base + xhi, sh);
+      fv[0][a] = v[1];
+      fv[1][a] = v[2];
+      fv[2][a] = v[3];
+      fv[3][a] = e;
+    }
+  }
+  float2 pa[Q], pb[Q];
+#pragma unroll
+  for (int a = 0; a < Q; ++a) pa[a] = make_float2(fv[0][a], fv[1][a]), pb[a] = make_float2(fv[2][a], fv[3][a]);
+  const float2 ra = rho_of<float2>(pa), rb = rho_of<float2>(pb);
+  if (!live) return;
   raise_flag(bad_rho(ra.x) | bad_rho(ra.y) | bad_rho(rb.x) | bad_rho(rb.y), flag);
   const float2 qa = psi_of2(ra, ph), qb = psi_of2(rb, ph);
   *reinterpret_cast<float4*>(psi + i) = make_float4(qa.x, qa.y, qb.x, qb.y);

@@ -143,10 +143,15 @@ def test_block_shapes_agree_bitwise(L, block):
 # layout equivalences: AA == A-B, graph == eager, checkpoint resume
 # ---------------------------------------------------------------------------
 
+# Shapes: nx odd (one node per thread), nx % 4 == 0 with rows that start
+# inside a warp (36: nine four-node groups per row; 132: 33, so a warp's
+# lanes 0 and 31 sit inside rows), as the four-node gather psi pass before
+# the AA odd step handles them.
 @pytest.mark.parametrize("precision", ["f64", "f32", "f16dev", "bf16dev"])
-@pytest.mark.parametrize("nsteps", [1, 2, 7, 20])
-def test_aa_equals_ab_bitwise(L, precision, nsteps):
-    shape = (33, 10, 9)
+@pytest.mark.parametrize("nsteps,shape", [(1, (33, 10, 9)), (2, (33, 10, 9)), (7, (33, 10, 9)), (20, (33, 10, 9)),
+                                          (2, (36, 10, 9)), (7, (36, 10, 9)), (3, (132, 6, 5)),
+                                          (8, (132, 6, 5))])
+def test_aa_equals_ab_bitwise(L, precision, nsteps, shape):
     f0 = lbm_inputs.random_populations(*shape, seed=13)
     out = []
     for pattern in ("ab", "aa"):
