@@ -237,7 +237,7 @@ def measure_lattice(torch, L, autotune, w, precision, patterns, args, rho_l, rho
                                        blocks=((128, 2, 1), (64, 4, 1)) if patterns == ("aa",) else
                                        ((128, 2, 1),),
                                        occupancies=(2, 3), tau=w.tau, G=w.G, steps=10, use_cache=False,
-                                       fused_runs=(8, 12, 16), fused_groups=(1, 4), reps=2)
+                                       fused_runs=(8, 12, 16, 32), fused_groups=(1, 4), reps=2)
     pattern = choice["pattern"]
     lat = L.Lattice(w.nx, w.ny, w.nz, w.tau, w.G, precision=precision, pattern=pattern,
                     rho_ref=rho_v if dev else 0.0)

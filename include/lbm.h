@@ -335,10 +335,12 @@ int lbm_batch_set_stream(lbm_batch b, void *stream);
  * the populations element by element (instances up to 113 M nodes, larger
  * ones take the two kernels).  0: a psi pass and a collide-stream kernel per
  * step), "persistent" (0/1, default 0: with a single-pass form (1 or 2),
- * every lbm_batch_step call runs its n steps as one
+ * every lbm_batch_step call runs its n steps (up to 1024 per launch) as one
  * cooperative launch of persistent blocks - as many as the GPU holds at once,
  * each taking several tiles and z runs per step - separated by grid-wide
- * barriers; the same results as one launch per step, no graph; a barrier
+ * barriers, replayed from a CUDA graph captured on the first call with that
+ * step count (option "graph" 0: launched directly); the same results as one
+ * launch per step; a barrier
  * that waits more than 2 s gives up, the launch returns and lbm_batch_sync
  * reports LBM_ERR_TIMEOUT with the state void), "persistent_stall_test" (a
  * test hook of that failure path, in ms, 0..10: one block skips the first

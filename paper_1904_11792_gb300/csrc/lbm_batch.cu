@@ -286,6 +286,13 @@ struct lbm_batch_ctx {
   bool initialized = false;
   bool use_graph = true;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // the persistent form's graphs: one cooperative launch of m steps from
+  // array `cur`, with its counter resets and the salt advance
+  struct PersistGraph {
+    int cur, m;
+    cudaGraphExec_t exec;
+  };
+  std::vector<PersistGraph> pgraphs;
   cudaStream_t stream = nullptr, own_stream = nullptr;
 };
 
@@ -308,6 +315,8 @@ void drop_graphs(lbm_batch_ctx* b) {
       cudaGraphExecDestroy(g);
       g = nullptr;
     }
+  for (auto& pg : b->pgraphs) cudaGraphExecDestroy(pg.exec);
+  b->pgraphs.clear();
 }
 
 // Recomputes the block table for the current block size and uploads it.
@@ -528,6 +537,53 @@ int bcuda(cudaError_t e, const char* where) {
   return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
 }
 
+// Steps of one persistent launch, and the graph of them.
+constexpr int kPersistSteps = 1024;
+
+// The counter resets, the cooperative launch of m steps from array cur and
+// the salt advance, on stream s.
+int enqueue_persist(lbm_batch_ctx* b, cudaStream_t s, int cur, int m) {
+  const unsigned long long stall_ns = (unsigned long long)(b->persist_stall_ms * 1e6);
+  if (tma_form(b))
+    BCK(batch_tma_persist_launch(b->precision, b->d_ttable, b->tplan, b->pool_p, cur, m,
+                                 (unsigned*)(b->d_flag + 4), b->d_tickets, b->d_flag, stall_ns, s));
+  else
+    BCK(batch_persist_launch(b->precision, b->d_ginst, b->count, b->gblocks, b->pool_f, cur, m,
+                             (unsigned*)(b->d_flag + 4), b->d_tickets, b->d_flag, stall_ns, s));
+  if (batch_sr(b)) BCK(launch_salt_add((unsigned*)(b->d_flag + 2), (unsigned)m, s));
+  return LBM_OK;
+}
+
+int capture_persist(lbm_batch_ctx* b, int cur, int m, cudaGraphExec_t* out) {
+  cudaStream_t cs;
+  BCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  int rc = LBM_OK;
+  if (e == cudaSuccess) {
+    rc = enqueue_persist(b, cs, cur, m);
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (rc == LBM_OK) e = e2;
+  }
+  cudaStreamDestroy(cs);
+  if (rc != LBM_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    (void)cudaGetLastError();
+    return rc != LBM_OK ? rc : bcuda(e, "persistent batch graph capture (option graph 0 launches it directly)");
+  }
+  cudaGraphExec_t ge = nullptr;
+  e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return bcuda(e, "cudaGraphInstantiate (persistent batch)");
+  if (b->pgraphs.size() >= 8) {   // calls of many step counts: keep the newest graphs
+    cudaGraphExecDestroy(b->pgraphs.front().exec);
+    b->pgraphs.erase(b->pgraphs.begin());
+  }
+  b->pgraphs.push_back({cur, m, ge});
+  *out = ge;
+  return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -680,6 +736,7 @@ int lbm_batch_set_option(lbm_batch b, const char* key, double v) {
   if (k == "persistent_stall_test") {
     if (!(v >= 0.0 && v <= 10.0)) return bfail(LBM_ERR_ARG, "persistent_stall_test must be in 0..10 ms");
     b->persist_stall_ms = v;
+    drop_graphs(b);   // the hook is an argument of the captured launches
     return LBM_OK;
   }
   if (k == "tile_width") {
@@ -757,21 +814,24 @@ int lbm_batch_step(lbm_batch b, int n) {
     if (b->padded) b->contig_ok.assign(b->count, 0);   // the steps below change the padded state
   }
   while (n > 0 && b->persistent && b->fused && (tma_form(b) || 19LL * b->max_nodes <= 0x7fffffffLL)) {
-    // up to kPersistSteps steps in one cooperative launch of persistent blocks
-    constexpr int kPersistSteps = 1024;
+    // up to kPersistSteps steps in one cooperative launch of persistent
+    // blocks, replayed from a graph (option graph, default on)
     const int m = std::min(n, kPersistSteps);
     if (!b->d_tickets) {
       BCK(cudaMalloc(&b->d_tickets, sizeof(unsigned) * kPersistSteps));
       b->tickets_n = kPersistSteps;
     }
-    const unsigned long long stall_ns = (unsigned long long)(b->persist_stall_ms * 1e6);
-    if (tma_form(b))
-      BCK(batch_tma_persist_launch(b->precision, b->d_ttable, b->tplan, b->pool_p, b->cur, m,
-                                   (unsigned*)(b->d_flag + 4), b->d_tickets, b->d_flag, stall_ns, b->stream));
-    else
-      BCK(batch_persist_launch(b->precision, b->d_ginst, b->count, b->gblocks, b->pool_f, b->cur, m,
-                               (unsigned*)(b->d_flag + 4), b->d_tickets, b->d_flag, stall_ns, b->stream));
-    if (batch_sr(b)) BCK(launch_salt_add((unsigned*)(b->d_flag + 2), (unsigned)m, b->stream));
+    if (b->use_graph) {
+      cudaGraphExec_t ge = nullptr;
+      for (const auto& pg : b->pgraphs)
+        if (pg.cur == b->cur && pg.m == m) ge = pg.exec;
+      if (!ge) {
+        if (int rc = capture_persist(b, b->cur, m, &ge)) return rc;
+      }
+      BCK(cudaGraphLaunch(ge, b->stream));
+    } else {
+      if (int rc = enqueue_persist(b, b->stream, b->cur, m)) return rc;
+    }
     b->cur ^= m & 1;
     b->step += m;
     n -= m;

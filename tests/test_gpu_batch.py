@@ -145,7 +145,8 @@ def test_fused_batch_equals_two_kernel_batch(L, precision):
 
 # The persistent form (option persistent, with either single-pass form: all
 # n steps of a call in one cooperative launch, grid barriers between the
-# steps) against one launch per step, bitwise: every precision (the stochastic-rounding salt advances
+# steps, replayed from a graph or launched directly) against one launch per
+# step, bitwise: every precision (the stochastic-rounding salt advances
 # the same), the instance shapes above, odd step counts and calls that
 # continue one another, and fewer persistent blocks than work items (each
 # block takes several tiles and z runs per step).
@@ -159,11 +160,12 @@ def test_persistent_batch_equals_per_step_launches(L, precision, form, width):
         insts.append(dict(nx=nx, ny=ny, nz=nz, tau=0.8 + 0.05 * k, G=-5.5, R0=R0, lam=float(nx), eps=0.1,
                           phase=0.3 * k, rho_l=2.5, rho_v=0.15, width=2.0))
     res = []
-    for persistent in (0, 1):
+    for persistent, graph in ((0, 1), (1, 1), (1, 0)):   # the persistent launch from a graph, and direct
         with L.Batch(insts, precision=precision) as b:
             b.set_option("fused", form)
             b.set_option("tile_width", width)
             b.set_option("persistent", persistent)
+            b.set_option("graph", graph)
             b.set_option("fused_fz", 4)
             b.init()
             b.step(1)
@@ -171,8 +173,9 @@ def test_persistent_batch_equals_per_step_launches(L, precision, form, width):
             b.step(6)
             b.sync()
             res.append([b.populations(k) for k in range(len(insts))])
-    for k in range(len(insts)):
-        np.testing.assert_array_equal(res[1][k], res[0][k])
+    for r in res[1:]:
+        for k in range(len(insts)):
+            np.testing.assert_array_equal(r[k], res[0][k])
 
 
 # The failure path of the persistent form's grid barrier, without a fault: a
