@@ -445,6 +445,86 @@ def test_grid1024_sampled_one_step(L, coex):
     assert rel(got, want) <= 1e-5
 
 
+def _patches_gather(t, N, nx, ny, nodes, c, opp, halo=2):
+    """As _patches, for a state in the AA gather layout (after an AA even
+    step): population a of node p sits in slot opp(a) at p - c_a."""
+    import torch
+    nz = N // (nx * ny)
+    i = torch.as_tensor(nodes, dtype=torch.int64, device=t.device)
+    x, y, z = i % nx, (i // nx) % ny, i // (nx * ny)
+    d = torch.arange(-halo, halo + 1, device=t.device)
+    w = 2 * halo + 1
+    out = []
+    for a in range(19):
+        zz = (z[:, None, None, None] + d[None, :, None, None] - int(c[a, 2])) % nz
+        yy = (y[:, None, None, None] + d[None, None, :, None] - int(c[a, 1])) % ny
+        xx = (x[:, None, None, None] + d[None, None, None, :] - int(c[a, 0])) % nx
+        out.append(t[int(opp[a]) * N + (xx + nx * (yy + ny * zz)).reshape(len(nodes), -1)])
+    return torch.stack(out, dim=1).double().cpu().numpy().reshape(len(nodes), 19, w, w, w)
+
+
+# The in-place AA pair at the large configuration's size (1024x512x512, the
+# FP16-deviation and FP32 AA steps the benchmark reports, default launch
+# shapes): the even step (in place, slots swapped) and the odd step (gather
+# and scatter, after the four-node gather psi pass for 2-byte storage) each
+# checked on sampled nodes against the oracle stepping the node's 5x5x5
+# neighbourhood of the decoded state.  After the even step the post-collision
+# population a of node x sits in slot opp(a) at x, so the oracle's streamed
+# population a of node y is the GPU's slot opp(a) at y - c_a; the odd step's
+# input is gathered from that layout and its output is in the natural one.
+# Tolerances as the one-step cases: 1e-5 relative for FP32, one storage ulp
+# of the stored deviation plus the FP32 arithmetic for FP16.
+@pytest.mark.parametrize("precision,eps", [("f32", None), ("f16dev", 2.0 ** -10)])
+def test_grid1024_aa_sampled_even_and_odd_steps(L, coex, precision, eps):
+    import torch
+    rl, rv = coex
+    w = lbm_inputs.GRID_1024
+    N = w.nx * w.ny * w.nz
+    c, wts, opp = oracle.lattice()
+    dev = precision.endswith("dev")
+    if dev:
+        shift = (wts * rv).astype(np.float32).astype(np.float16).astype(np.float64)
+        tdt = torch.float16
+    else:
+        shift = np.zeros(19)
+        tdt = torch.float32
+
+    def check(got, want):
+        if dev:
+            tol = 1.01 * (eps * np.abs(want - shift[None, :]) + 2.0 ** -24) + 4e-7 * np.abs(want)
+            err = np.abs(got - want)
+            assert (err <= tol).all(), float((err / tol).max())
+        else:
+            assert rel(got, want) <= 1e-5
+
+    with make(L, (w.nx, w.ny, w.nz), w.tau, w.G, precision, "aa", **(dict(rho_ref=rv) if dev else {})) as lat:
+        lat.init_ligament(w.R0, w.lam, w.eps, w.phase, rl, rv, w.width)
+        lat.step(20)                      # even count: the natural layout
+        lat.sync()
+        state = lat._buffers[0].view(tdt)[:19 * N]
+        u = lbm_inputs.uniform(4246, 200)
+        cz = (w.ny // 2) * w.nx + (w.nz // 2) * w.nx * w.ny
+        nodes = np.unique(np.concatenate([
+            (u * N).astype(np.int64), [0, N - 1, w.nx - 1, w.nx * w.ny - 1, cz + 17],
+            [x + w.nx * (w.ny // 2 + int(w.R0)) + w.nx * w.ny * (w.nz // 2) for x in (0, 3, 511, 1020, 1023)]]))
+        ti = torch.as_tensor(nodes, device="cuda")
+        xs, ys, zs = ti % w.nx, (ti // w.nx) % w.ny, ti // (w.nx * w.ny)
+        # even step
+        before = _patches(state, N, w.nx, w.ny, nodes) + shift[None, :, None, None, None]
+        lat.step(1)
+        lat.sync()
+        idx = torch.stack([int(opp[a]) * N + ((xs - int(c[a, 0])) % w.nx + w.nx * (((ys - int(c[a, 1])) % w.ny)
+                           + w.ny * ((zs - int(c[a, 2])) % w.nz))) for a in range(19)], dim=1)
+        got = state[idx].double().cpu().numpy() + shift[None, :]
+        check(got, np.stack([oracle.step(p, w.tau, w.G, 1)[:, 2, 2, 2] for p in before]))
+        # odd step
+        before = _patches_gather(state, N, w.nx, w.ny, nodes, c, opp) + shift[None, :, None, None, None]
+        lat.step(1)
+        lat.sync()
+        got = state[torch.arange(19, device="cuda")[None, :] * N + ti[:, None]].double().cpu().numpy() + shift[None, :]
+        check(got, np.stack([oracle.step(p, w.tau, w.G, 1)[:, 2, 2, 2] for p in before]))
+
+
 # The benchmark's FP16 / BF16 variants at their full size (1024x512x512,
 # fused step, its launch shape): one step on sampled nodes against the
 # oracle stepping each node's 5x5x5 neighbourhood of the decoded stored state
