@@ -32,7 +32,8 @@
 // step bitwise.  A-B streaming, 4- and 2-byte storage, lattices with
 // nx % 64 == 0 and ny % 4 == 0 (8 for 2-byte storage); bfused_kernel runs
 // the same body over the instances of a batch, of any size, whose rows the
-// batch pads to 16-byte multiples.
+// batch pads to 16-byte multiples, on 64-wide tiles or on 32-wide ones (two
+// rows of 16 lanes x two nodes per warp, twice as many rows per tile).
 //
 // This header holds the kernel and its device helpers; lbm_fused.cu holds
 // the host side (tensor maps, launch shape, launches).  Include it from one
