@@ -99,16 +99,23 @@ cudaError_t maps_for(int precision, const Geom& g, const void* base, Maps* out) 
 // more tiles than resident blocks runs stop at 8 planes (cap); small grids (256x128x128:
 // 1.96 waves of 19-plane runs, 0.114 ms, against 0.126 ms for 16-plane runs
 // in 2.25 waves) keep the wave count low instead.  2-byte storage, bound by
-// instruction issue and with half the bytes per plane in L2, has no cap
-// (1024x512x512 FP16: 32-plane runs 6.20 ms, 12-plane runs in fours 6.57).
+// instruction issue and with half the bytes per plane in L2, has no cap, and
+// on lattices with more tiles than resident blocks long runs cost it little
+// (1 + fz/2048: 1024x512x512 FP16, 1 run per group, 27-, 32-, 48-, 64-,
+// 86-, 128-, 256- and 512-plane runs take 4.598, 4.567, 4.524, 4.485, 4.506,
+// 4.491, 4.614 and 4.700 ms; BF16 is best at 64 too, 4.519 ms); on smaller
+// lattices 1 + fz/256 keeps the best shape (512x256x256: 20-plane runs
+// 0.5975 ms, 32 0.604, 64 0.604; 256x128x128: 15-plane runs 0.0894 ms, 32
+// 0.0933).
 int choose_fz(const Geom& g, long long tiles, long long slots, bool cap) {
   int best = g.nz;
   double best_cost = -1.0;
+  const double k = (!cap && tiles > slots) ? 2048.0 : 256.0;   // the long-run factor 1 + fz / k
   for (int fz = 4; fz <= g.nz; ++fz) {
     const long long chunks = (g.nz + fz - 1) / fz;
     const long long waves = (tiles * chunks + slots - 1) / slots;
     if (cap && fz > 8 && tiles > slots) continue;
-    const double cost = (double)waves * (fz + 2) * (1.0 + fz / 256.0);
+    const double cost = (double)waves * (fz + 2) * (1.0 + fz / k);
     if (best_cost < 0.0 || cost < best_cost) {
       best_cost = cost;
       best = fz;
