@@ -171,25 +171,35 @@ __device__ __forceinline__ C rho_of(const C f[Q]) {
 // reduction without the per-node rounding of rho, which in a uniform
 // region is the same at every node and does not average out.  FP64
 // storage: lo = 0.
-__device__ __forceinline__ float two_sum(float a, float b, float& e) {
-  const float s = __fadd_rn(a, b);
-  const float bp = __fsub_rn(s, a);
-  const float ap = __fsub_rn(s, bp);
-  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+// C = float, or float2 for two nodes at once (paired instructions, each lane
+// the bits of the scalar form: the paired difference is a - b rounded once).
+// The scalar adds are the round-to-nearest intrinsics, which the compiler
+// neither contracts nor reassociates.
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float2 radd(float2 a, float2 b) { return vadd(a, b); }
+__device__ __forceinline__ float2 rsub(float2 a, float2 b) { return vsub(a, b); }
+template <typename C>
+__device__ __forceinline__ C two_sum(C a, C b, C& e) {
+  const C s = radd(a, b);
+  const C bp = rsub(s, a);
+  const C ap = rsub(s, bp);
+  e = radd(rsub(a, ap), rsub(b, bp));
   return s;
 }
-__device__ __forceinline__ float rho_of_x(const float f[Q], float& lo) {
-  float e[18];
-  const float s1 = two_sum(f[1], f[2], e[0]), s3 = two_sum(f[3], f[4], e[1]), s5 = two_sum(f[5], f[6], e[2]),
-              s7 = two_sum(f[7], f[8], e[3]), s9 = two_sum(f[9], f[10], e[4]), s11 = two_sum(f[11], f[12], e[5]),
-              s13 = two_sum(f[13], f[14], e[6]), s15 = two_sum(f[15], f[16], e[7]),
-              s17 = two_sum(f[17], f[18], e[8]);
-  const float a = two_sum(two_sum(f[0], s1, e[9]), two_sum(s3, s5, e[10]), e[11]);
-  const float b = two_sum(two_sum(s7, s9, e[12]), two_sum(s11, s13, e[13]), e[14]);
-  const float c = two_sum(b, two_sum(s15, s17, e[15]), e[16]);
-  const float hi = two_sum(a, c, e[17]);
-  lo = (((e[0] + e[1]) + (e[2] + e[3])) + ((e[4] + e[5]) + (e[6] + e[7]))) +
-       (((e[8] + e[9]) + (e[10] + e[11])) + ((e[12] + e[13]) + (e[14] + e[15])) + (e[16] + e[17]));
+template <typename C>
+__device__ __forceinline__ C rho_of_x(const C f[Q], C& lo) {
+  C e[18];
+  const C s1 = two_sum(f[1], f[2], e[0]), s3 = two_sum(f[3], f[4], e[1]), s5 = two_sum(f[5], f[6], e[2]),
+          s7 = two_sum(f[7], f[8], e[3]), s9 = two_sum(f[9], f[10], e[4]), s11 = two_sum(f[11], f[12], e[5]),
+          s13 = two_sum(f[13], f[14], e[6]), s15 = two_sum(f[15], f[16], e[7]), s17 = two_sum(f[17], f[18], e[8]);
+  const C a = two_sum(two_sum(f[0], s1, e[9]), two_sum(s3, s5, e[10]), e[11]);
+  const C b = two_sum(two_sum(s7, s9, e[12]), two_sum(s11, s13, e[13]), e[14]);
+  const C c = two_sum(b, two_sum(s15, s17, e[15]), e[16]);
+  const C hi = two_sum(a, c, e[17]);
+  lo = radd(radd(radd(radd(e[0], e[1]), radd(e[2], e[3])), radd(radd(e[4], e[5]), radd(e[6], e[7]))),
+            radd(radd(radd(radd(e[8], e[9]), radd(e[10], e[11])), radd(radd(e[12], e[13]), radd(e[14], e[15]))),
+                 radd(e[16], e[17])));
   return hi;
 }
 __device__ __forceinline__ double rho_of_x(const double f[Q], double& lo) {

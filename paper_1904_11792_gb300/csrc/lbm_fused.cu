@@ -199,14 +199,16 @@ cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, i
   if (e != cudaSuccess) return e;
   const int ntx = g.nx / TX;
   using T = typename Prec<P>::T;
+  DirBases<T> db;
+  for (int a = 0; a < Q; ++a) db.p[a] = (T*)dst + (long long)a * g.N;
   if (!diag) {
     const DiagOut none{0.0, 0.0, nullptr, nullptr, stall_ns};
     if (ph.coll == COLL_MRT)
       fused_kernel<P, false, COLL_MRT><<<(unsigned)blocks, S::NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
-                                                                             fz, grp, none);
+                                                                             fz, grp, none, db);
     else
       fused_kernel<P, false, COLL_SRT><<<(unsigned)blocks, S::NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
-                                                                             fz, grp, none);
+                                                                             fz, grp, none, db);
     return cudaGetLastError();
   }
   const long long row_blocks = (long long)(g.ny / S::TY) * nchunks;
@@ -218,10 +220,10 @@ cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, i
   const DiagOut dg{diag->rho_l, diag->rho_v, slices, bl, stall_ns};
   if (ph.coll == COLL_MRT)
     fused_kernel<P, true, COLL_MRT><<<(unsigned)blocks, S::NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
-                                                                          fz, grp, dg);
+                                                                          fz, grp, dg, db);
   else
     fused_kernel<P, true, COLL_SRT><<<(unsigned)blocks, S::NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
-                                                                          fz, grp, dg);
+                                                                          fz, grp, dg, db);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_diag_reduce(g, (int)row_blocks, (int)blocks, slices, bl, slice_tot, diag->out, diag->ring_count,

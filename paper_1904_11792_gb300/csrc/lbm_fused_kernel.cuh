@@ -142,6 +142,15 @@ struct Maps {
   CUtensorMap interior, row, col, cor;
 };
 
+// Start of each direction's slab in the destination array (dst + a N) of
+// the single-lattice step, set by the host: a kernel parameter, so the
+// store address arithmetic takes each base from the constant bank (the
+// batched step, whose destination depends on the block's instance, keeps
+// them in shared memory).
+template <typename T> struct DirBases {
+  T* p[Q];
+};
+
 // Issues the nine copies of plane zz into buffer b (one thread).
 template <int P, int W = TX>
 __device__ __forceinline__ void issue_plane(unsigned char* smem, const Maps& m, int b, int x0, int y0, int xl,
@@ -201,7 +210,7 @@ template <int P, bool DIAG, int COLL, bool BATCH, int W = TX, bool SALT_GIVEN = 
 __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, const Phys& ph,
                                            typename Prec<P>::T* dst, int* flag, int ntx, int nchunks, int fz,
                                            int grp, const DiagOut& dg, int u, int px, long long dstride,
-                                           unsigned salt_given = 0u) {
+                                           const DirBases<typename Prec<P>::T>* db, unsigned salt_given = 0u) {
   using T = typename Prec<P>::T;
   using C = typename Prec<P>::C;
   using V = typename Pair<P>::V;
@@ -292,13 +301,14 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
   // the halo row cells x0 + 2 xi (+1) of rows y0 - 1 and y0 + h
   const bool hact = !BATCH || 2 * xi < w, hact1 = !BATCH || 2 * xi + 1 < w;
 
-  // dst + a N, the start of direction a in the destination array: with
-  // 2-byte storage (bound by instruction issue) the stores address a
-  // direction by this base and a 32-bit offset in it (N < 2^31), which saves
-  // the 64-bit arithmetic per direction and plane (measured: 1.4 % faster;
-  // the latency-bound FP32 step was 3 % slower this way)
+  // dst + a N, the start of direction a in the destination array: the
+  // stores address a direction by this base and a 32-bit offset in it (N <
+  // 2^31).  Single lattice: the bases are kernel parameters (db).  Batched
+  // step with 2-byte storage (bound by instruction issue): in shared memory,
+  // which saves the 64-bit arithmetic per direction and plane (measured: 1.4 %
+  // faster; a latency-bound FP32 step was 3 % slower this way).
   __shared__ T* s_dir[Q];
-  if (Prec<P>::dev && tid < Q) s_dir[tid] = dst + (long long)tid * N;
+  if (BATCH && Prec<P>::dev && tid < Q) s_dir[tid] = dst + (long long)tid * N;
   __shared__ int s_abort;
   if (tid == 0) {
     // bit 2 of the flag: a block (of this launch or an earlier one) gave up
@@ -359,12 +369,22 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
       jv[0][0] = jx2.x, jv[0][1] = jy2.x, jv[0][2] = jz2.x;
       jv[1][0] = jx2.y, jv[1][1] = jy2.y, jv[1][2] = jz2.y;
       if (k >= 1 && k <= np - 2) {
-        // the rounding error of each density (rho_of_x's high part is r0, r1)
-        C f0[Q], f1[Q];
+        // the rounding error of each density (rho_of_x's high part is r0,
+        // r1): both nodes in paired instructions for 4-byte storage; one
+        // node at a time for 2-byte storage, whose 128-register budget the
+        // paired form's error terms exceed (spills)
+        if constexpr (Prec<P>::dev) {
+          C f0[Q], f1[Q];
 #pragma unroll
-        for (int a = 0; a < Q; ++a) f0[a] = fp[a].x, f1[a] = fp[a].y;
-        rho_of_x(f0, lo[0]);
-        rho_of_x(f1, lo[1]);
+          for (int a = 0; a < Q; ++a) f0[a] = fp[a].x, f1[a] = fp[a].y;
+          rho_of_x(f0, lo[0]);
+          rho_of_x(f1, lo[1]);
+        } else {
+          float2 lo2;
+          rho_of_x<float2>(fp, lo2);
+          lo[0] = lo2.x;
+          lo[1] = lo2.y;
+        }
 #pragma unroll
         for (int n = 0; n < 2; ++n) {
           const C rho = n ? r1 : r0;
@@ -491,7 +511,7 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
         const C sh = a == 0 ? s0 : (a <= 6 ? s1 : s2);
         const int row = rowp * (yv[1 + cy(a)] + g.ny * zv[1 + cz(a)]);
         if constexpr (Prec<P>::dev) {
-          T* const base = s_dir[a];
+          T* const base = BATCH ? s_dir[a] : db->p[a];
           // the shift comes off both nodes in one paired difference
           const float2 sh2 = splat<float2>(sh);
           if (cx(a) == 0) {
@@ -512,7 +532,7 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
             // one conversion per node rounds both with the bits sr_bits gives
             // them (the high half a, the low half a + 1), so the stored values
             // equal those of the one-value conversions of the two-kernel step
-            T* const base_b = s_dir[a + 1];
+            T* const base_b = BATCH ? s_dir[a + 1] : db->p[a + 1];
             const int row_b = rowp * (yv[1 + cy(a + 1)] + g.ny * zv[1 + cz(a + 1)]);
             const unsigned j = (unsigned)(a + 1) >> 1;
             const float2 da = vsub(make_float2(fs0[a], fs1[a]), sh2);
@@ -528,7 +548,7 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
           }
           // even a with c_x != 0 under stochastic rounding: stored with a - 1
         } else {
-          T* base = dst + (long long)a * N + row;
+          T* base = (BATCH ? dst + (long long)a * N : db->p[a]) + row;
           if (cx(a) == 0) {
             if (act1)
               store_pair<P>(base + x, fs0[a], fs1[a], sh);
@@ -629,8 +649,8 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
 template <int P, bool DIAG, int COLL>
 __global__ void __launch_bounds__(FusedShape<P>::NT, fused_minb<P, DIAG, COLL>())
     fused_kernel(const __grid_constant__ Maps maps, Geom g, Phys ph, typename Prec<P>::T* dst, int* flag, int ntx,
-                 int nchunks, int fz, int grp, DiagOut dg) {
-  fused_body<P, DIAG, COLL, false>(maps, g, ph, dst, flag, ntx, nchunks, fz, grp, dg, blockIdx.x, g.nx, g.N);
+                 int nchunks, int fz, int grp, DiagOut dg, const __grid_constant__ DirBases<typename Prec<P>::T> db) {
+  fused_body<P, DIAG, COLL, false>(maps, g, ph, dst, flag, ntx, nchunks, fz, grp, dg, blockIdx.x, g.nx, g.N, &db);
 }
 
 // One instance of the batched TMA step (device table built by the host).
@@ -672,7 +692,7 @@ __device__ __forceinline__ void batch_item(const BTInst& I, int u, typename Prec
   const Maps& m = I.maps[cur];
   if (threadIdx.x == 0) acquire_maps(m);
   fused_body<P, false, COLL_SRT, true, W, SALT_GIVEN>(m, I.g, I.ph, dst, flag, I.ntx, I.nchunks, I.fz, I.grp, none,
-                                                      u, I.px, I.dstride, salt);
+                                                      u, I.px, I.dstride, nullptr, salt);
 }
 
 // The single-pass step of a batch of lattices of any size, their rows
