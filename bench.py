@@ -36,6 +36,7 @@ from __future__ import annotations
 
 import argparse
 import ctypes
+import dataclasses
 import hashlib
 import json
 import os
@@ -307,6 +308,8 @@ def run_ours(args):
     build.build()
     L.load()
     w = WORKLOADS[args.workload]
+    if args.nz > 0:
+        w = dataclasses.replace(w, nz=args.nz)
     N = w.nodes
     if args.rho_l and args.rho_v:
         rho_l, rho_v = args.rho_l, args.rho_v
@@ -347,7 +350,8 @@ def run_ours(args):
         step_model = STEP_BYTES_PER_LU[args.precision]
         launches_per_step = 2 * (LBM_PER_STEP - 1) + 4
     achieved = bpl * N / (avg * 1e-3) / 1e9
-    traffic = ncu_traffic(args.workload, args.precision, m["pattern"], fused, m["fz_used"], m["grp_used"])
+    traffic = None if args.nz > 0 else ncu_traffic(args.workload, args.precision, m["pattern"], fused,
+                                                   m["fz_used"], m["grp_used"])
     d = m["hist"][-1] if m["hist"] else {}
     e2e = None
     if lat is not None:
@@ -425,7 +429,8 @@ def run_variants(args, torch, L, autotune, w, rho_l, rho_v, fp32_glups, peak, wo
              "fused_launch": [m["fz_used"], m["grp_used"]] if m["fused"] else None,
              "numeric_ok": all(h["numeric_ok"] == 1 for h in m["hist"])}
         if m["fused"]:
-            e["traffic"] = ncu_traffic(args.workload, prec, pattern, True, m["fz_used"], m["grp_used"])
+            e["traffic"] = None if args.nz > 0 else ncu_traffic(args.workload, prec, pattern, True,
+                                                                m["fz_used"], m["grp_used"])
         out[name] = e
     try:
         out["batched_sweep48"] = batch_sweep(args, torch, L, autotune, rho_l, rho_v)
@@ -740,6 +745,10 @@ def main():
                          "1: per-element single pass, 0: two kernels)")
     ap.add_argument("--batch-size", type=int, default=48,
                     help="batch48: the first K instances of the sweep (profiling runs on a smaller batch)")
+    ap.add_argument("--nz", type=int, default=0,
+                    help="grid workloads: the same lattice with this many z planes (counter captures on a few "
+                         "GB whose traffic scales to the full lattice by the plane count); no traffic record "
+                         "is reported for it")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
