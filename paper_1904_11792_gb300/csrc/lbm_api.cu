@@ -466,6 +466,7 @@ lbm_handle lbm_create_ex(const lbm_config* cfg) {
   h->ph = Phys{cfg->tau, cfg->G, cfg->rho0, cfg->rho_ref, cfg->psi_form,
                cfg->precision >= LBM_F16DEV ? 1 : 0, COLL_SRT, 1.19, 1.4, 1.2, 1.4, 1.98};
   h->ph.inv_rho0 = 1.0 / cfg->rho0;
+  phys_finalize(h->ph, cfg->precision);
   h->block = (cfg->block_x && cfg->block_y && cfg->block_z)
                  ? dim3(cfg->block_x, cfg->block_y, cfg->block_z)
                  : default_block(h->g);
@@ -563,9 +564,11 @@ int lbm_set_option(lbm_handle h, const char* key, double v) {
   if (k == "tau") {
     if (!(v > 0.5)) return fail(LBM_ERR_ARG, "tau must be > 1/2");
     h->ph.tau = h->cfg.tau = v;
+    phys_finalize(h->ph, h->cfg.precision);
     drop_graphs(h);
   } else if (k == "G") {
     h->ph.G = h->cfg.G = v;
+    phys_finalize(h->ph, h->cfg.precision);
     drop_graphs(h);
   } else if (k == "rho_l") {
     h->rho_l = v;

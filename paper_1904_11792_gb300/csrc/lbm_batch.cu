@@ -645,6 +645,7 @@ lbm_batch lbm_batch_create(const lbm_instance* inst, int count, int precision, i
     I.ph = Phys{s.tau, s.G, rho0, precision >= LBM_F16DEV ? s.rho_v : 0.0, psi_form,
                 precision >= LBM_F16DEV ? 1 : 0};
     I.ph.inv_rho0 = 1.0 / rho0;
+    phys_finalize(I.ph, precision);
     I.off_f = off_f;
     I.off_psi = off_psi;
     // every instance's arrays start on a multiple of 8 elements (64 bytes in

@@ -375,8 +375,34 @@ struct Phys {
   // where the collision kernel of a step writes the next step's salt (the
   // other word of a pair; nullptr: a separate one-thread kernel advances it)
   unsigned* salt_next;
+  // FP32 forms of the constants above for kernels that compute in FP32, set
+  // by phys_finalize on the host whenever a Phys is built or changed: as
+  // kernel parameters they sit in the constant bank and enter FP32
+  // instructions as operands.  Converting the doubles in device code puts
+  // each conversion on the FP64 pipe (1/64 of the FP32 rate on GB300), and
+  // register-bound kernels repeat them in the step loop.  The values are
+  // the device's conversions bit for bit (IEEE round to nearest on both
+  // sides).
+  float G_f, tau_f, omega_f;   // G, tau, 1 / tau (FP32 division)
+  float rho0_f, ninv_rho0_f;   // rho0, -(1 / rho0)
+  float shift_f[3];            // storage shifts of the rest, axis and diagonal classes (deviation forms)
 };
 enum Collision { COLL_SRT = 0, COLL_MRT = 1 };
+// Sets the FP32 fields of ph from its doubles, for storage `precision`.
+__host__ inline void phys_finalize(Phys& ph, int precision) {
+  ph.G_f = (float)ph.G;
+  ph.tau_f = (float)ph.tau;
+  ph.omega_f = 1.0f / ph.tau_f;
+  ph.rho0_f = (float)ph.rho0;
+  ph.ninv_rho0_f = -(float)ph.inv_rho0;
+  const int lead[3] = {0, 1, 7};
+  for (int c = 0; c < 3; ++c) {
+    const float v = (float)(wgt(lead[c]) * ph.rho_ref);
+    ph.shift_f[c] = precision == LBM_F16DEV    ? __half2float(__float2half_rn(v))
+                    : precision == LBM_BF16DEV ? __bfloat162float(__float2bfloat16_rn(v))
+                                               : 0.0f;
+  }
+}
 __device__ __forceinline__ unsigned salt_of(const Phys& ph) { return ph.salt ? __ldg(ph.salt) : 0u; }
 // One thread of a step's collision kernel writes salt + 1 for the next step
 // into the other word of the pair, which nothing of this step reads.
@@ -433,16 +459,16 @@ __device__ __forceinline__ C psi_of(C rho, const Phys& ph) {
   } else {
     // products and the difference through the non-contracted forms: the
     // bits of psi_of2 below (a product fused into 1 - e would differ)
-    return __fmul_rn((float)ph.rho0, __fsub_rn(1.0f, expf(__fmul_rn(rho, -(float)ph.inv_rho0))));
+    return __fmul_rn(ph.rho0_f, __fsub_rn(1.0f, expf(__fmul_rn(rho, ph.ninv_rho0_f))));
   }
 }
 // psi of two FP32 lanes: per lane the bits of psi_of<float> ((-rho) c is rho
 // (-c), 1 - e is fma(e, -1, 1) rounded once)
 __device__ __forceinline__ float2 psi_of2(float2 rho, const Phys& ph) {
   if (ph.psi_form == LBM_PSI_RHO) return rho;
-  const float2 t = xmul(rho, splat<float2>(-(float)ph.inv_rho0));
+  const float2 t = xmul(rho, splat<float2>(ph.ninv_rho0_f));
   const float2 e = make_float2(expf(t.x), expf(t.y));
-  return xmul(splat<float2>((float)ph.rho0), vsub(splat<float2>(1.0f), e));
+  return xmul(splat<float2>(ph.rho0_f), vsub(splat<float2>(1.0f), e));
 }
 
 }  // namespace lbm

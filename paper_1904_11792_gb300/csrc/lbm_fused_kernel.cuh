@@ -253,8 +253,6 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
   const int xl = x0 == 0 ? (BATCH ? (g.nx - 1) / S::CW * S::CW : g.nx - S::CW) : x0 - S::CW;
   const int lofs = BATCH && x0 == 0 ? g.nx - 1 - xl : S::CW - 1;
   const int xr = x0 + w == g.nx ? 0 : x0 + W;
-  const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
-          s2 = shift_of<P>(7, ph.rho_ref);
   auto zwrap = [&](int p) { return p < 0 ? p + g.nz : (p >= g.nz ? p - g.nz : p); };
   auto zplane = [&](int k) { return zwrap(dir > 0 ? z0 - 1 + k : z1 - k); };   // plane of march index k
 
@@ -310,6 +308,12 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
   __shared__ T* s_dir[Q];
   if (BATCH && Prec<P>::dev && tid < Q) s_dir[tid] = dst + (long long)tid * N;
   __shared__ int s_abort;
+  // the deviation shifts, staged through shared memory so that they live in
+  // registers: the widening adds of the 2-byte loads take no constant-bank
+  // operand (read from the kernel parameters directly, the FP16 step was 4 %
+  // slower)
+  __shared__ float s_shift[3];
+  if (Prec<P>::dev && tid < 3) s_shift[tid] = ph.shift_f[tid];
   if (tid == 0) {
     // bit 2 of the flag: a block (of this launch or an earlier one) gave up
     // on a wait, the result is void; skip the work
@@ -319,6 +323,8 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
   }
   __syncthreads();
   if (s_abort) return;
+  const C s0 = Prec<P>::dev ? (C)s_shift[0] : (C)0, s1 = Prec<P>::dev ? (C)s_shift[1] : (C)0,
+          s2 = Prec<P>::dev ? (C)s_shift[2] : (C)0;
   if (tid == 0)
     for (int k = 0; k < NB && k < np; ++k)
       issue_plane<P, W>(smem, maps, k, x0, y0, xl, xr, ym, yp, zplane(k), full + k);

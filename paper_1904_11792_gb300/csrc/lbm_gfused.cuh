@@ -150,7 +150,7 @@ __device__ __forceinline__ void gfused_item(const GInst* __restrict__ inst, int 
   const int xs[3] = {xm, x, xp};
   const int yrow[3] = {g.nx * yv[0], g.nx * yv[1], g.nx * yv[2]};   // row offsets of y - 1, y, y + 1
 
-  const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref), s2 = shift_of<P>(7, ph.rho_ref);
+  const C s0 = shift_of<P>(0, ph), s1 = shift_of<P>(1, ph), s2 = shift_of<P>(7, ph);
   auto shift = [&](int a) { return a == 0 ? s0 : (a <= 6 ? s1 : s2); };
   const int plane_n = g.nx * g.ny;
 

@@ -76,6 +76,7 @@ int lbm_diagnostics_noalloc(const void* f, int nx, int ny, int nz, int precision
   // in the scratch has to start at zero.
   Phys ph{1.0, 0.0, 1.0, rho_ref, LBM_PSI_EXP, 0};
   ph.inv_rho0 = 1.0;
+  phys_finalize(ph, precision);
   e = launch_diagnostics(precision, LAYOUT_LOCAL, g, ph, f, rho_l, rho_v, scratch, out, nullptr,
                          nullptr, nullptr, 0, (cudaStream_t)stream);
   if (e != cudaSuccess) {

@@ -22,11 +22,13 @@
 
 namespace lbm {
 
+// The deviation shift of population a in storage P (the FP32 form the host
+// set in ph: storage_shift of ph.rho_ref).
 template <int P>
-__device__ __forceinline__ typename Prec<P>::C shift_of(int a, double rho_ref) {
+__device__ __forceinline__ typename Prec<P>::C shift_of(int a, const Phys& ph) {
   using C = typename Prec<P>::C;
   if constexpr (Prec<P>::dev) {
-    return (C)storage_shift<P>(a, rho_ref);
+    return (C)ph.shift_f[a == 0 ? 0 : (a <= 6 ? 1 : 2)];
   } else {
     return (C)0;
   }
@@ -214,12 +216,19 @@ __device__ __forceinline__ void collide_math_ls(const Phys& ph, const C f[Q], C 
   // only where written), so every kernel that inlines this function computes
   // the same bits whatever the compiler's contraction choices around it.
   const C w1 = splat<C>((S)(1.0 / 18.0)), w2 = splat<C>((S)(1.0 / 36.0));
-  const C gp = xmul(splat<C>(-(S)ph.G), pc);
+  // the constants in the arithmetic's precision (FP32: the host's
+  // conversions, read from the kernel parameters)
+  S G_s, tau_s, omega_s;
+  if constexpr (sizeof(S) == 4) {
+    G_s = ph.G_f, tau_s = ph.tau_f, omega_s = ph.omega_f;
+  } else {
+    G_s = (S)ph.G, tau_s = (S)ph.tau, omega_s = (S)1 / tau_s;
+  }
+  const C gp = xmul(splat<C>(-G_s), pc);
   const C Fx = xmul(gp, xfma(w1, ax, xmul(w2, dx)));
   const C Fy = xmul(gp, xfma(w1, ay, xmul(w2, dy)));
   const C Fz = xmul(gp, xfma(w1, az, xmul(w2, dz)));
   // Eq. 6
-  const S tau_s = (S)ph.tau;
   const C tau = splat<C>(tau_s);
   const C inv_rho = rcp_rn(rho);
   const C ux = xmul(xfma(tau, Fx, jx), inv_rho);
@@ -238,7 +247,6 @@ __device__ __forceinline__ void collide_math_ls(const Phys& ph, const C f[Q], C 
   // (with weights rounded to the arithmetic's precision the direct form of
   // Eq. 2 creates mass of relative order 1e-8 per FP32 collision in one
   // direction).
-  const S omega_s = (S)1 / tau_s;
   const C om1 = splat<C>((S)1 - omega_s);
   const C orho = xmul(splat<C>(omega_s), rho);
   const C q1 = xmul(orho, w1);
@@ -327,8 +335,8 @@ __device__ __forceinline__ void psi_node(const Geom& g, const Phys& ph,
                                          typename Prec<P>::C* __restrict__ psi,
                                          int* __restrict__ flag, long long i) {
   using C = typename Prec<P>::C;
-  const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
-          s2 = shift_of<P>(7, ph.rho_ref);
+  const C s0 = shift_of<P>(0, ph), s1 = shift_of<P>(1, ph),
+          s2 = shift_of<P>(7, ph);
   C fv[Q];
   if constexpr (LAYOUT == LAYOUT_LOCAL) {
 #pragma unroll
@@ -356,8 +364,8 @@ __device__ __forceinline__ void psi_pair(const Geom& g, const Phys& ph, const ty
                                          typename Prec<P>::C* __restrict__ psi,
                                          int* __restrict__ flag, long long i) {
   using C = typename Prec<P>::C;
-  const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
-          s2 = shift_of<P>(7, ph.rho_ref);
+  const C s0 = shift_of<P>(0, ph), s1 = shift_of<P>(1, ph),
+          s2 = shift_of<P>(7, ph);
   C f0[Q], f1[Q];
   if constexpr (LAYOUT == LAYOUT_LOCAL) {
 #pragma unroll
@@ -436,8 +444,8 @@ __device__ __forceinline__ void psi_quad(const Geom& g, const Phys& ph, const ty
                                          typename Prec<P>::C* __restrict__ psi,
                                          int* __restrict__ flag, long long i) {
   static_assert(P != LBM_F64, "four-node psi pass is for 4- and 2-byte storage");
-  const float s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
-              s2 = shift_of<P>(7, ph.rho_ref);
+  const float s0 = shift_of<P>(0, ph), s1 = shift_of<P>(1, ph),
+              s2 = shift_of<P>(7, ph);
   float fv[4][Q];
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
@@ -470,8 +478,8 @@ __device__ __forceinline__ void psi_quad_gather(const Geom& g, const Phys& ph, c
                                                 typename Prec<P>::C* __restrict__ psi, int* __restrict__ flag,
                                                 long long i, bool live) {
   static_assert(P != LBM_F64, "four-node psi pass is for 4- and 2-byte storage");
-  const float s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
-              s2 = shift_of<P>(7, ph.rho_ref);
+  const float s0 = shift_of<P>(0, ph), s1 = shift_of<P>(1, ph),
+              s2 = shift_of<P>(7, ph);
   const int lane = threadIdx.x & 31;
   const int x0 = (int)(i % g.nx);
   const long long r = i / g.nx;
@@ -533,8 +541,8 @@ __device__ __forceinline__ void collide_node(const Geom& g, const Phys& ph,
   nb.make(g, x, y, z);
   const int i = nb.idx(0, 0, 0);
   const long long N = g.N;
-  const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
-          s2 = shift_of<P>(7, ph.rho_ref);
+  const C s0 = shift_of<P>(0, ph), s1 = shift_of<P>(1, ph),
+          s2 = shift_of<P>(7, ph);
   C f[Q];
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
@@ -594,8 +602,8 @@ __device__ __forceinline__ void collide_pair(const Geom& g, const Phys& ph,
   };
   const int i0 = x0 + rows[1][1];
   const long long N = g.N;
-  const C s0 = shift_of<P>(0, ph.rho_ref), s1 = shift_of<P>(1, ph.rho_ref),
-          s2 = shift_of<P>(7, ph.rho_ref);
+  const C s0 = shift_of<P>(0, ph), s1 = shift_of<P>(1, ph),
+          s2 = shift_of<P>(7, ph);
 
   C f0[Q], f1[Q];
 #pragma unroll
