@@ -202,7 +202,7 @@ cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, i
   DirBases<T> db;
   for (int a = 0; a < Q; ++a) db.p[a] = (T*)dst + (long long)a * g.N;
   if (!diag) {
-    const DiagOut none{0.0, 0.0, nullptr, nullptr, stall_ns};
+    const DiagOut none = diag_out(0.0, 0.0, nullptr, nullptr, stall_ns);
     if (ph.coll == COLL_MRT)
       fused_kernel<P, false, COLL_MRT><<<(unsigned)blocks, S::NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
                                                                              fz, grp, none, db);
@@ -217,7 +217,7 @@ cudaError_t fused_t(const Geom& g, const Phys& ph, const void* src, void* dst, i
   double* slices = diag->scratch;
   double* bl = slices + (size_t)row_blocks * g.nx * 2;
   double* slice_tot = bl + (size_t)blocks * DIAG_NG;
-  const DiagOut dg{diag->rho_l, diag->rho_v, slices, bl, stall_ns};
+  const DiagOut dg = diag_out(diag->rho_l, diag->rho_v, slices, bl, stall_ns);
   if (ph.coll == COLL_MRT)
     fused_kernel<P, true, COLL_MRT><<<(unsigned)blocks, S::NT, S::smem, s>>>(m, g, ph, (T*)dst, flag, ntx, nchunks,
                                                                           fz, grp, dg, db);

@@ -186,7 +186,19 @@ struct DiagOut {
   // test hook (the timeout path of the bounded waits): > 0 makes every block
   // also wait, for at most this many ns, on a barrier nothing completes
   unsigned long long stall_test_ns;
+  // the liquid threshold (rho_l + rho_v) / 2, 1 / (rho_l - rho_v) and rho_v in
+  // FP32, computed on the host (diag_out): derived in device code they cost
+  // FP64-pipe operations (a division among them), which the register-bound
+  // diagnostic step repeated in its plane loop
+  float thr_f, inv_f, rv_f;
 };
+// DiagOut with its FP32 thresholds (host).
+__host__ inline DiagOut diag_out(double rho_l, double rho_v, double* slices, double* blocks,
+                                 unsigned long long stall_test_ns) {
+  // the device's own FP64 expressions, bit for bit (IEEE on both sides)
+  return DiagOut{rho_l, rho_v, slices, blocks, stall_test_ns, (float)(0.5 * (rho_l + rho_v)),
+                 (float)(1.0 / (rho_l - rho_v)), (float)rho_v};
+}
 
 // Blocks per SM the register budget must allow: 3 of 128 threads for 4-byte
 // storage (its 73 KB of shared memory allow no more), 2 of 256 threads for
@@ -343,8 +355,7 @@ __device__ __forceinline__ void fused_body(const Maps& maps, const Geom& g, cons
   C d_umax = 0, d_rmin = (C)3.0e38, d_rmax = (C)-3.0e38;
   C col_n[2] = {0, 0};
   bool d_bad = false;
-  const C d_thr = (C)(0.5 * (dg.rho_l + dg.rho_v)), d_inv = (C)(1.0 / (dg.rho_l - dg.rho_v)),
-          d_rv = (C)dg.rho_v;
+  const C d_thr = (C)dg.thr_f, d_inv = (C)dg.inv_f, d_rv = (C)dg.rv_f;
   int k = 0;
   for (; k < np; ++k) {
     const int b = k % NB;
@@ -694,7 +705,7 @@ template <int P, int W, bool SALT_GIVEN>
 __device__ __forceinline__ void batch_item(const BTInst& I, int u, typename Prec<P>::T* pool, int cur, int* flag,
                                            unsigned salt) {
   typename Prec<P>::T* dst = pool + I.off_f + (long long)(cur ^ 1) * Q * I.dstride;
-  const DiagOut none{0.0, 0.0, nullptr, nullptr, 0ull};
+  const DiagOut none{0.0, 0.0, nullptr, nullptr, 0ull, 0.0f, 0.0f, 0.0f};
   const Maps& m = I.maps[cur];
   if (threadIdx.x == 0) acquire_maps(m);
   fused_body<P, false, COLL_SRT, true, W, SALT_GIVEN>(m, I.g, I.ph, dst, flag, I.ntx, I.nchunks, I.fz, I.grp, none,
